@@ -1,0 +1,370 @@
+"""Benchmark of the walk-Laplacian hot path on GB300.
+
+Workload (one step): the nonbacktracking resolvent walk Laplacian of a
+Chung-Lu power-law graph (n = 1e6, degree exponent 2.5, mean degree 12,
+minimum degree 1), alpha = 0.5 / rho(Z_1), and the diffusion
+exp(-tau L) U0 for 16 point sources at tau in {0.1, 1, 10}: graph build
+(validation + spectral radius), walk degrees, then the Lanczos/CG diffusion,
+in the refined form (FP32 inner CG, FP64 residual, FP64 Lanczos). Inputs are
+resident on the GPU when the timed region starts.
+
+Metric: nnz * RHS * iterations per second over all operator SpMM
+applications of the step, plus time-to-1e-8 relative error of
+exp(-tau L) U0 for the refined and the plain FP64 form.
+
+Multi-GPU: replicas only - each rank runs its own 16 sources on its own
+copy of the graph (weak scaling, no collective on the data path).
+
+`--impl reference` times the CPU FP64 oracle's Krylov restatement
+(oracle/krylov.py) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_NODES = 1_000_000
+SEED_GRAPH = 20260100
+SEED_SRC = 20260101
+TAUS = [0.1, 1.0, 10.0]
+K_SRC = 16
+METRIC = "nnz*RHS*iters/s (exp(-tau L)u0, NBT resolvent, refined form)"
+UNIT = "nnz*RHS*iters/s"
+TIME_TO_RULE = {"tol": 1e-10, "outer_tol": 1e-9}  # stopping rule shared by both forms (time-to-1e-8)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    for f in ("wl_cg.cuh", "wl_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2601_11338_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_tag):
+    """Per-launch DRAM bytes of the dominant kernel from a committed ncu summary,
+    if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", f"{kernel_tag}.traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_src_sha") != kernel_src_hash():
+        return None
+    return d.get("dram_bytes_per_iteration")
+
+
+def make_workload(rank):
+    import wlgen
+    g = wlgen.chung_lu(N_NODES, seed=SEED_GRAPH)
+    nodes = wlgen.point_sources(g, K_SRC, SEED_SRC + rank)
+    return g, nodes
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import wlgen
+    from paper_2601_11338_gb300 import wl
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    g, nodes = make_workload(rank)
+    rp = torch.as_tensor(g.row_ptr.astype(np.int32), device=dev)
+    ci = torch.as_tensor(g.col_idx, device=dev)
+    U0 = torch.as_tensor(wlgen.unit_block(g.n, nodes), device=dev)
+    Df = torch.empty(g.n, dtype=torch.float64, device=dev)
+    U = torch.empty((len(TAUS), g.n, K_SRC), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    taus = np.array(TAUS)
+
+    def params(prec, tol, outer_tol):
+        return wl.make_params(f=wl.WL_F_RESOLVENT, alpha_rel=0.5, prec=prec, tol=tol, outer_tol=outer_tol,
+                              stream=stream.cuda_stream)
+
+    def step(prec=wl.WL_REFINED, tol=TIME_TO_RULE["tol"], outer_tol=TIME_TO_RULE["outer_tol"], out=U):
+        sb, sd, se = wl.wl_stats(), wl.wl_stats(), wl.wl_stats()
+        h = wl.wl_build(rp, ci, g.n, g.nnz, wl.WL_NBT, params(prec, tol, outer_tol), sb)
+        wl.wl_degrees(h, Df, sd)
+        wl.wl_expmv(h, U0, K_SRC, K_SRC, taus, out, K_SRC, se)
+        h.destroy()
+        return sb, sd, se
+
+    log(f"[rank {rank}] graph n={g.n} nnz={g.nnz}; warmup {args.warmup}")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    units = 0.0
+    launches = 0
+    kcg_ms = kcg_bytes = kres_ms = klan_ms = 0.0
+    kcg_launches = kcg_iters = 0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        sb, sd, se = step()
+        units += sd.nnz_rhs_iters + se.nnz_rhs_iters
+        launches += sb.launches + sd.launches + se.launches
+        for s in (sd, se):
+            kcg_ms += s.k_cg_ms
+            kcg_bytes += s.k_cg_bytes
+            kcg_launches += s.k_cg_launches
+            kcg_iters += s.k_cg_iters
+            kres_ms += s.k_res_ms
+            klan_ms += s.k_lan_ms
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms, units], dtype=torch.float64, device=dev)
+    if ws > 1:
+        tm = t.clone()
+        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
+        t = tm
+    ms_max, units_all = float(t[0]), float(t[1])
+    value = units_all / (ms_max / 1000.0)
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    # ---- time to 1e-8: reference u* (FP64, tight), then both forms under one rule
+    Ustar = torch.empty_like(U)
+    step(prec=wl.WL_FP64, tol=1e-13, outer_tol=1e-12, out=Ustar)
+    tt = {}
+    for name, prec in (("refined", wl.WL_REFINED), ("fp64", wl.WL_FP64)):
+        Ux = torch.empty_like(U)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, sd, se = step(prec=prec, out=Ux)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        err = max(float((torch.linalg.norm(Ux[t] - Ustar[t], dim=0) / torch.linalg.norm(Ustar[t], dim=0)).max())
+                  for t in range(len(TAUS)))
+        tt[name] = {"ms": e0.elapsed_time(e1), "max_rel_err": err, "cg_iters": sd.k_cg_iters + se.k_cg_iters,
+                    "lanczos_steps": se.outer_iters}
+    tt["speedup_refined_vs_fp64"] = tt["fp64"]["ms"] / tt["refined"]["ms"]
+    tt["rule"] = dict(TIME_TO_RULE)
+    # ---- end to end through the C ABI with host buffers
+    rp_h = g.row_ptr.astype(np.int32)
+    ci_h = np.ascontiguousarray(g.col_idx)
+    U0_h = wlgen.unit_block(g.n, nodes)
+    Df_h = np.empty(g.n)
+    U_h = np.empty((len(TAUS), g.n, K_SRC))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sb, sd, se = wl.wl_stats(), wl.wl_stats(), wl.wl_stats()
+    h = wl.wl_build(rp_h, ci_h, g.n, g.nnz, wl.WL_NBT, params(wl.WL_REFINED, TIME_TO_RULE["tol"],
+                                                             TIME_TO_RULE["outer_tol"]), sb)
+    wl.wl_degrees(h, Df_h, sd)
+    wl.wl_expmv(h, U0_h, K_SRC, K_SRC, taus, U_h, K_SRC, se)
+    h.destroy()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": (sd.nnz_rhs_iters + se.nnz_rhs_iters) / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(rp_h.nbytes + ci_h.nbytes + U0_h.nbytes),
+           "d2h_bytes_per_step": int(Df_h.nbytes + U_h.nbytes), "ms": e2e_s * 1000.0}
+    # ---- roofline of the dominant kernel (persistent CG, FP32, 16 columns)
+    peak, peak_kind = peaks()
+    fams = {"cg": kcg_ms, "residual64": kres_ms, "lanczos_step": klan_ms}
+    achieved = (kcg_bytes / (kcg_ms / 1000.0)) / 1e9 if kcg_ms > 0 else 0.0
+    traffic = recorded_traffic("cg_persistent_f32_k16")
+    roof = {"bound": "hbm", "kernel": "cg_persistent<float,16>", "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": (traffic * kcg_iters / max(kcg_launches, 1)) if traffic else None,
+            "bytes_alg_per_launch": kcg_bytes / max(kcg_launches, 1),
+            "avg_launch_ms": kcg_ms / max(kcg_launches, 1), "launches": kcg_launches,
+            "iters_per_launch": kcg_iters / max(kcg_launches, 1), "family_ms": fams,
+            "family_share": {k: v / max(sum(fams.values()), 1e-9) for k, v in fams.items()}}
+    # ---- CPU baseline: the oracle's Krylov restatement on a bounded sample
+    cpu = cpu_baseline(g, nodes) if not args.no_cpu else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "chung_lu_1e6_nbt_expmv_16src_3tau", "graph": "Chung-Lu power law",
+                   "n": g.n, "nnz": g.nnz, "gamma": 2.5, "mean_degree": 12, "min_degree": 1,
+                   "variant": "nbt", "f": "resolvent", "alpha": "0.5/rho(Z_1)", "rhs": K_SRC, "taus": TAUS,
+                   "form": "refined (FP32 CG + FP64 residual/update, FP64 Lanczos)",
+                   "stopping_rule": dict(TIME_TO_RULE), "parallelism": f"replicas{ws}",
+                   "l2": "flushed between steps (256 MB write inside the timed region); per-step working set > 10 GB",
+                   "seeds": {"graph": SEED_GRAPH, "sources": SEED_SRC}},
+        "time_to_1e-8": tt, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(g, nodes, budget_cols=1, max_steps=12):
+    """Time the oracle's CPU FP64 Krylov restatement on a sample of the workload:
+    the same graph and operator, `budget_cols` of the point sources, all taus,
+    the Lanczos process capped at `max_steps` steps (units are counted exactly,
+    so the throughput stays comparable)."""
+    from oracle import krylov
+
+    A = krylov.adjacency(g.row_ptr, g.col_idx, g.n)
+    n = g.n
+    t0 = time.perf_counter()
+    alpha = 0.5 / krylov.rho_companion_sparse(A, 1.0)
+    op = krylov.ResolventLaplacian(A, 1.0, alpha, tol=TIME_TO_RULE["tol"])
+    apps_cols = 0
+    steps = 0
+    for j in nodes[:budget_cols]:
+        u0 = np.zeros(n); u0[j] = 1.0
+        before = op.applications
+        _, m = krylov.lanczos_expmv(op.apply, u0, TAUS, tol=TIME_TO_RULE["outer_tol"], m_max=max_steps)
+        steps += m
+        apps_cols += op.applications - before
+    df_apps = op.applications - apps_cols
+    el = time.perf_counter() - t0
+    units = float(g.nnz) * (df_apps + apps_cols)
+    return {"value": units / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle/krylov.py (scipy CSR SpMV, FP64 CG + Lanczos) on the full Chung-Lu graph, "
+                      f"{budget_cols} of {K_SRC} sources, taus {TAUS}, Lanczos capped at {max_steps} steps; rho(Z_1) by ARPACK on Z; "
+                      f"{el:.1f} s, "
+                      f"{steps} Lanczos steps, {df_apps + apps_cols} CG iterations",
+            "seconds": el}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    g, nodes = make_workload(0)
+    for _ in range(args.warmup if args.warmup < 1 else 0):
+        pass
+    vals = []
+    for _ in range(max(1, args.steps)):
+        c = cpu_baseline(g, nodes)
+        vals.append(c)
+    value = statistics.median([v["value"] for v in vals])
+    secs = sum(v["seconds"] for v in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / len(vals),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "chung_lu_1e6_nbt_expmv_16src_3tau", "n": g.n, "nnz": g.nnz,
+                       "sample": vals[0]["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

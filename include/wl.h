@@ -1,0 +1,194 @@
+/*
+ * wl.h - C ABI of the GB300 walk-based Laplacian library (libwl.so).
+ *
+ * Computes, for a simple undirected graph with 0/1 adjacency A and degree
+ * matrix D (Sec. 2 of Arrigo and Durastante, "Walk based Laplacians for
+ * Modeling Diffusion on Complex Networks"):
+ *
+ *   phi    = phi(A, c) = sum_k c_k q_k(A)          (Def. BDTW-Laplacian)
+ *   D_f    = diag(phi 1)                            (walk degrees, Sec. 3.1)
+ *   L V    = D_f V - phi V                          (Eq. weighted_laplacian)
+ *   U(tau) = exp(-tau L) U0                         (Eq. diffusion_on_G_with_downweighted_walk)
+ *   tr(phi) estimated by XNysTrace                  (Alg. 1, last step)
+ *
+ * with q_k the backtrack-downweighted walk counts of Eq. qrec (mu = 0: all
+ * walks, Def. transformedlaplacian; mu = 1: nonbacktracking walks, Eq. Br).
+ * For the resolvent c = (1, alpha, alpha^2, ...), phi = (1 - mu^2 alpha^2) *
+ * M^{-1} with the sparse symmetric matrix
+ *
+ *   M = M_mu(alpha) = (1 - mu^2 alpha^2) I - alpha A + alpha^2 mu D,
+ *
+ * which is Eq. deformed for mu = 1 and its general-mu extension (remark after
+ * Prop. CGworks); M is positive definite for 0 <= alpha < 1 / rho(Z_mu)
+ * (Prop. CGworks, Eq. Zdef), so every phi V is one conjugate-gradient solve
+ * (Sec. 4.2).
+ *
+ * Conventions shared by every entry point
+ *  - Status: 0 (WL_OK) or a negative WL_ERR_* code; wl_status_string()
+ *    describes it. On error no output is guaranteed unless stated.
+ *  - Pointers: every array argument may be a device pointer or a host
+ *    pointer (pageable or pinned); the library detects which with
+ *    cudaPointerGetAttributes and stages host data through its own device
+ *    workspace. Every call returns after its device work has completed
+ *    (the solvers read per-column scalars back to decide convergence).
+ *  - Blocks of vectors are row-major n x k with a leading dimension
+ *    (elements between consecutive rows) ld >= k: element (i, j) is at
+ *    ptr[i * ld + j].
+ *  - Ownership: the caller owns every buffer it passes; the handle owns its
+ *    copy of the graph and all workspace, released by wl_destroy().
+ *  - A handle must not be used from two host threads at once.
+ */
+#ifndef WL_H
+#define WL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define WL_OK                  0
+#define WL_ERR_INVALID_ARG    -1  /* null pointer, negative size, bad enum, ld < k ... */
+#define WL_ERR_NOT_SYMMETRIC  -2  /* CSR pattern is not symmetric */
+#define WL_ERR_SELF_LOOP      -3  /* a diagonal entry is stored */
+#define WL_ERR_UNSORTED       -4  /* row_ptr not monotone, columns unsorted/duplicated/out of range */
+#define WL_ERR_ALPHA_RANGE    -5  /* alpha * rho(Z_mu) >= 1 or alpha < 0: phi undefined (Prop. whe-we-converge) */
+#define WL_ERR_NOT_SPD        -6  /* CG breakdown p^T M p <= 0: M not positive definite */
+#define WL_ERR_NONFINITE      -7  /* NaN / Inf met in inputs or iterates */
+#define WL_ERR_NO_CONVERGENCE -8  /* iteration cap reached; outputs hold the last iterate */
+#define WL_ERR_TIMEOUT        -9  /* a bounded device-side wait expired; kernel returned early */
+#define WL_ERR_OOM           -10  /* device allocation failed */
+#define WL_ERR_CUDA          -11  /* other CUDA runtime error (message via wl_last_error) */
+#define WL_ERR_UNSUPPORTED   -12  /* combination not provided (e.g. exp with mu > 0) */
+
+/* ------------------------------------------------------------ enums */
+typedef enum {
+  WL_ALLWALK = 0, /* mu = 0: q_k = A^k (Def. transformedlaplacian) */
+  WL_NBT     = 1, /* mu = 1: nonbacktracking counts p_k (Eq. Br) */
+  WL_BTDW    = 2  /* mu from wl_params.mu, backtrack weight theta = 1 - mu (Eq. qrec) */
+} wl_variant;
+
+typedef enum {
+  WL_F_RESOLVENT = 0, /* c_k = alpha^k, f(x) = (1 - alpha x)^{-1}  (Sec. 3.2.1) */
+  WL_F_EXP       = 1, /* c_k = beta^k / k!, f(x) = exp(beta x); all-walk (mu = 0) only */
+  WL_F_IDENTITY  = 2  /* c = (0, 1, 0, ...): phi = A, L = D - A (Sec. 3.1) */
+} wl_func;
+
+typedef enum {
+  WL_FP64    = 0, /* every vector operation in FP64 ("plain FP64 Krylov") */
+  WL_REFINED = 1  /* inner CG in FP32, FP64 residual and update (iterative refinement) */
+} wl_precision;
+
+/* ------------------------------------------------------------ structs */
+/* Simple undirected graph: symmetric 0/1 pattern, no self-loops, strictly
+ * increasing column indices within each row, row_ptr[0] = 0,
+ * row_ptr[n] = nnz < 2^31. Values are implicit (all ones). */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int32_t* row_ptr; /* n + 1 entries, host or device */
+  const int32_t* col_idx; /* nnz entries, host or device */
+} wl_csr;
+
+typedef struct {
+  wl_func f;
+  double alpha;      /* resolvent scale, used when alpha_rel <= 0 */
+  double alpha_rel;  /* > 0: alpha = alpha_rel / rho(Z_mu), rho computed by wl_build */
+  double beta;       /* exp scale; <= 0: beta = 1 / lambda_max(A) (Sec. 4.1.2) */
+  double mu;         /* WL_BTDW only: mu in [0, 1]; theta = 1 - mu */
+  wl_precision prec;
+  double tol;        /* relative residual target of each solve (<= 0: 1e-12) */
+  int max_iter;      /* CG iteration cap per solve (<= 0: 2000) */
+  int max_outer;     /* Lanczos step cap of wl_expmv (<= 0: 400) */
+  double outer_tol;  /* wl_expmv relative accuracy target (<= 0: 1e-10) */
+  void* stream;      /* cudaStream_t the handle works on; NULL: legacy default stream */
+} wl_params;
+
+typedef struct {
+  int status;         /* status of the call */
+  int iters;          /* operator SpMM applications (lockstep blocks) in the call */
+  int outer_iters;    /* Lanczos steps (wl_expmv) */
+  int refinements;    /* FP64 residual evaluations (WL_REFINED) */
+  double rel_res;     /* largest final relative residual over the call's solves */
+  double time_ms;     /* device time of the call (CUDA events on the handle's stream) */
+  double nnz_rhs_iters; /* sum over SpMM applications of nnz * columns */
+  double bytes_alg;   /* algorithmic bytes of the CG iterations (4 nnz + 4 (n+1) + 6 n k s each) */
+  double alpha, beta, mu, rho, lambda_max; /* parameters in force */
+  int launches;       /* CUDA kernels launched by the call */
+  /* device time of the call's kernels by family, from CUDA events recorded
+   * on the handle's stream around each launch */
+  int k_cg_launches;  /* persistent CG kernels (FP32 in WL_REFINED, FP64 otherwise) */
+  int k_cg_iters;     /* CG iterations executed by those launches */
+  double k_cg_ms;
+  double k_cg_bytes;  /* algorithmic bytes of those iterations */
+  int k_res_launches; /* FP64 residual kernels */
+  double k_res_ms;
+  int k_lan_launches; /* Lanczos step kernels */
+  double k_lan_ms;
+} wl_stats;
+
+typedef struct wl_handle wl_handle;
+
+/* ------------------------------------------------------------ core calls */
+
+/* Copies and validates the graph (sorted rows, indices in range, no
+ * self-loops, symmetric pattern), estimates lambda_max(A) and rho(Z_mu)
+ * by Lanczos (Prop. whe-we-converge, Alg. 1 "approximate the spectral
+ * radius"), fixes alpha (and beta), and checks alpha * rho(Z_mu) < 1.
+ * `A` and its arrays may be freed after the call. *out receives the handle
+ * (NULL on error). `st` may be NULL. */
+int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out, wl_stats* st);
+
+/* Updates the per-call settings of a handle: prec, tol, max_iter,
+ * max_outer, outer_tol and stream (the operator parameters stay fixed). */
+int wl_set_params(wl_handle* h, const wl_params* p);
+
+/* Walk degrees D_f = phi 1 (total communicability, Sec. 3.1), n FP64
+ * values. The result is also cached in the handle for wl_apply/wl_expmv.
+ * Resolvent: one CG solve M x = (1 - mu^2 alpha^2) 1 (Sec. 4.2). */
+int wl_degrees(wl_handle* h, double* Df, wl_stats* st);
+
+/* W = L V = D_f (.) V - phi V for k columns (Eq. weighted_laplacian); V
+ * and W are n x k FP64 blocks with leading dimensions ldv, ldw (>= k).
+ * Computes D_f first if it is not cached. k = 0 is a no-op. */
+int wl_apply(wl_handle* h, const double* V, int64_t ldv, int k, double* W, int64_t ldw, wl_stats* st);
+
+/* U(tau_t) = exp(-tau_t L) U0 for t = 0..ntau-1 (diffusion equation in
+ * column form; L = L^T), by Lanczos on L with one apply per step
+ * (Sec. 4.1, Krylov evaluation of f(A)v). U0 is n x k (ld ldu); U holds
+ * ntau blocks, block t at U + t * n * ldo, each n x k with leading dimension
+ * ldo. taus is a host array of ntau values >= 0. */
+int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* taus, int ntau,
+             double* U, int64_t ldo, wl_stats* st);
+
+/* XNysTrace estimate of tr(phi) with M Gaussian test vectors (Alg. 1,
+ * "XNysTrace(Y, Omega)"). Omega (n x M) is drawn on the device by
+ * Philox4x32-10 from `seed` (element e = i M + j uses block e / 4, see the
+ * library documentation), rounded to bfloat16; Y = phi Omega is solved in
+ * FP32 CG; the Gram matrices [Omega Y]^T Y are accumulated in FP32 from
+ * exact bf16 products; the leave-one-out core runs in FP64. Writes the
+ * estimate and the error estimate std(t_i)/sqrt(M) to the host scalars.
+ * omega_out (optional, n x M uint16 bf16 bits, host or device) receives
+ * Omega. 2 <= M <= 64. */
+int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, uint16_t* omega_out,
+             wl_stats* st);
+
+/* Optional starting guess x0 (n FP64 values, host or device) for the D_f
+ * solve of wl_degrees; NULL clears it (start from 0). Copied. */
+int wl_set_warm_start(wl_handle* h, const double* x0);
+
+/* Parameters in force: alpha, beta, mu, rho(Z_mu), lambda_max(A) (host). */
+int wl_get_info(const wl_handle* h, wl_stats* info);
+
+void wl_destroy(wl_handle* h);
+
+const char* wl_status_string(int status);
+
+/* Text of the last CUDA error seen by the calling thread (or ""). */
+const char* wl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WL_H */

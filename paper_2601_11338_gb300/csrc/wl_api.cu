@@ -1,0 +1,1051 @@
+// C ABI of libwl.so (declared in include/wl.h): handle management, graph
+// validation, spectral scale, and the orchestration of the CUDA kernels for
+// walk degrees, Laplacian action and diffusion. All arithmetic on vectors
+// runs in the kernels; host code only sequences launches, reads back per-
+// column scalars and decides convergence.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "wl.h"
+#include "wl_host.h"
+
+using namespace wl;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+int set_cuda_error(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  (void)cudaGetLastError();
+  return (e == cudaErrorMemoryAllocation) ? WL_ERR_OOM : WL_ERR_CUDA;
+}
+
+#define WL_CU(call)                                  \
+  do {                                               \
+    cudaError_t e__ = (call);                        \
+    if (e__ != cudaSuccess) return set_cuda_error(e__, #call); \
+  } while (0)
+
+#define WL_TRY(call)          \
+  do {                        \
+    int s__ = (call);         \
+    if (s__ != WL_OK) return s__; \
+  } while (0)
+
+int ensure(Buf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return WL_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return set_cuda_error(e, "cudaMalloc");
+  }
+  b.bytes = bytes;
+  return WL_OK;
+}
+
+void release(Buf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Column blocks used for k columns: powers of two up to 64, largest first.
+std::vector<int> column_blocks(int k) {
+  std::vector<int> out;
+  while (k > 0) {
+    int b = 64;
+    while (b > k) b >>= 1;
+    out.push_back(b);
+    k -= b;
+  }
+  return out;
+}
+
+struct SolveInfo {
+  int iters = 0;
+  int cg_iters = 0;
+  int refinements = 0;
+  double max_rel = 0.0;
+  int status = WL_OK;
+  double nnz_rhs = 0.0;
+  double bytes = 0.0;
+};
+
+}  // namespace
+
+struct wl_handle {
+  int64_t n = 0, nnz = 0;
+  Graph g{};
+  wl_variant variant = WL_ALLWALK;
+  wl_params prm{};
+  double mu = 0, alpha = 0, beta = 0, rho = 0, lmax = 0;
+  double ca = 1, cA = 0, cD = 0;  // M = ca I + cA A + cD D
+  double a_scale = 1;             // phi = a_scale * M^{-1}
+  cudaStream_t stream = nullptr;
+  GridBar* bar = nullptr;
+  std::map<std::tuple<int, int, int>, PartDev> parts;
+  Buf csr_rp, csr_col;
+  Buf x, r, p, q;         // CG vectors (FP64 or FP32), n * 64 doubles each at most
+  Buf x64, b64, r64;      // refinement
+  Buf d32, r32;
+  Buf part;               // partial sums
+  Buf small;              // per-column scalars
+  Buf Df;
+  bool have_Df = false;
+  Buf warm;
+  bool have_warm = false;
+  Buf basis;
+  size_t basis_blocks = 0;
+  Buf Tab, ybuf, yprev, errb;
+  Buf stage_a, stage_b;   // host <-> device staging
+  Buf packV, packX;
+  Buf lan;                // Lanczos extreme vectors
+  double* h_pin = nullptr;  // pinned host scratch (4096 doubles)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // per-call kernel timing: event pairs recorded on the stream around launches
+  struct Rec {
+    int a, b, cat;
+  };
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<Rec> recs;
+  int launches = 0;
+};
+
+namespace {
+
+cudaStream_t S(wl_handle* h) { return h->stream; }
+
+enum { kCatCG = 0, kCatRes = 1, kCatLan = 2 };
+
+int ev_get(wl_handle* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    h->ev_pool.push_back(e);
+  }
+  return (int)h->ev_used++;
+}
+
+// record the start event of a timed launch; returns the record index
+int prof_begin(wl_handle* h, int cat) {
+  h->launches++;
+  const int a = ev_get(h), b = ev_get(h);
+  if (a < 0 || b < 0) return -1;
+  cudaEventRecord(h->ev_pool[a], h->stream);
+  h->recs.push_back({a, b, cat});
+  return (int)h->recs.size() - 1;
+}
+
+void prof_end(wl_handle* h, int i) {
+  if (i >= 0) cudaEventRecord(h->ev_pool[h->recs[i].b], h->stream);
+}
+
+void prof_reset(wl_handle* h) {
+  h->recs.clear();
+  h->ev_used = 0;
+  h->launches = 0;
+}
+
+// count an untimed launch
+inline void counted(wl_handle* h, int n = 1) { h->launches += n; }
+
+int get_part(wl_handle* h, int G, int Tw, int Tc, PartDev** out) {
+  auto key = std::make_tuple(G, Tw, Tc);
+  auto it = h->parts.find(key);
+  if (it != h->parts.end()) {
+    *out = &it->second;
+    return WL_OK;
+  }
+  PartDev p;
+  p.G = G;
+  p.Tw = Tw;
+  p.Tc = Tc;
+  WL_CU(cudaMalloc(&p.rb, sizeof(int32_t) * (G + 1)));
+  WL_CU(cudaMalloc(&p.seg, sizeof(int32_t) * 4 * G));
+  WL_CU(cudaMalloc(&p.order, sizeof(int32_t) * std::max<int64_t>(h->n, 1)));
+  WL_CU(launch_partition(h->g, p, S(h)));
+  h->parts[key] = p;
+  *out = &h->parts[key];
+  return WL_OK;
+}
+
+int reset_bar(wl_handle* h) {
+  WL_CU(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), S(h)));
+  return WL_OK;
+}
+
+int check_bar(wl_handle* h) {
+  int err = 0;
+  WL_CU(cudaMemcpyAsync(&err, &h->bar->err, sizeof(int), cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaStreamSynchronize(S(h)));
+  return err;
+}
+
+// scalars area layout (doubles): [0,64) bnorm2/rr, [64,128) bb, [128,192) gamma,
+// [192,256) ints status (as int32 region), [256,320) skip ints, [320] iters
+struct Smalls {
+  double* rr;
+  double* bb;
+  double* gamma;
+  int* status;
+  int* skip;
+  int* iters;
+  double* misc;  // 64 doubles
+  int* flags;
+};
+
+Smalls smalls(wl_handle* h) {
+  double* base = (double*)h->small.p;
+  Smalls s;
+  s.rr = base;
+  s.bb = base + 64;
+  s.gamma = base + 128;
+  s.status = (int*)(base + 192);
+  s.skip = (int*)(base + 256);
+  s.iters = (int*)(base + 320);
+  s.misc = base + 384;
+  s.flags = (int*)(base + 448);
+  return s;
+}
+
+double alg_bytes_per_iter(wl_handle* h, int K, int s) {
+  return 4.0 * (double)h->nnz + 4.0 * (double)(h->n + 1) + 6.0 * (double)h->n * K * s;
+}
+
+// FP64 lockstep CG on M x = b for K columns (b, x contiguous n x K doubles).
+// x holds the starting guess on entry (zero unless a warm start is given).
+int solve_fp64(wl_handle* h, const double* b, double* x, int K, double tol, bool x_is_zero, SolveInfo& info) {
+  const int G = cg_grid_f64(K);
+  int Tw, Tc;
+  thresholds_f64(K, &Tw, &Tc);
+  PartDev* pd;
+  WL_TRY(get_part(h, G, Tw, Tc, &pd));
+  const size_t nk = (size_t)h->n * K;
+  WL_TRY(ensure(h->r, nk * 8));
+  WL_TRY(ensure(h->p, nk * 8));
+  WL_TRY(ensure(h->q, nk * 8));
+  WL_TRY(ensure(h->part, (size_t)G * 64 * 2 * 8 + 1024));
+  Smalls sm = smalls(h);
+  const double* bn2 = nullptr;
+  if (x_is_zero) {
+    WL_CU(cudaMemcpyAsync(h->r.p, b, nk * 8, cudaMemcpyDeviceToDevice, S(h)));
+  } else {
+    const int Gr = res_grid(K);
+    PartDev* pr;
+    int Twr, Tcr;
+    thresholds_f64(K, &Twr, &Tcr);
+    WL_TRY(get_part(h, Gr, Twr, Tcr, &pr));
+    ResArgs ra{h->g, pr->view(), x, nullptr, b, (double*)h->r.p, nullptr, h->ca, h->cA, h->cD,
+               (double*)h->part.p, sm.rr, sm.bb, h->bar, 0};
+    WL_TRY(reset_bar(h));
+    const int pi = prof_begin(h, kCatRes);
+    WL_CU(launch_residual64(K, ra, Gr, S(h)));
+    prof_end(h, pi);
+    bn2 = sm.bb;
+    info.nnz_rhs += (double)h->nnz * K;
+  }
+  CgArgs<double> a{h->g, pd->view(), x, (double*)h->r.p, (double*)h->p.p, (double*)h->q.p,
+                   h->ca, h->cA, h->cD, bn2, nullptr, (double*)h->part.p, sm.gamma, sm.status,
+                   h->bar, h->prm.max_iter, tol * tol, sm.iters};
+  WL_TRY(reset_bar(h));
+  const int pc = prof_begin(h, kCatCG);
+  WL_CU(launch_cg_f64(K, a, G, S(h)));
+  prof_end(h, pc);
+  // read back per-column results
+  double* hp = h->h_pin;
+  WL_CU(cudaMemcpyAsync(hp, sm.gamma, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaMemcpyAsync(hp + 64, sm.status, 64 * 4, cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaMemcpyAsync(hp + 128, sm.iters, 4, cudaMemcpyDeviceToHost, S(h)));
+  if (bn2) WL_CU(cudaMemcpyAsync(hp + 192, bn2, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
+  const int berr = check_bar(h);
+  if (berr) return berr;
+  const int* st = (const int*)(hp + 64);
+  const int it = *(const int*)(hp + 128);
+  info.iters += it;
+  info.cg_iters += it;
+  info.nnz_rhs += (double)it * h->nnz * K;
+  info.bytes += (double)it * alg_bytes_per_iter(h, K, 8);
+  for (int c = 0; c < K; ++c) {
+    if (st[c] != 0 && info.status == WL_OK) info.status = st[c];
+  }
+  // relative residual of the recurrence (reference |b| from the first residual)
+  if (!bn2) {
+    // |b|^2 is gamma_0; not returned separately: report the recurrence norm ratio via a colnorm of b
+    counted(h);
+    WL_CU(launch_colnorms(b, h->n, K, sm.misc, S(h)));
+    WL_CU(cudaMemcpyAsync(hp + 192, sm.misc, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaStreamSynchronize(S(h)));
+    for (int c = 0; c < K; ++c) hp[192 + c] = hp[192 + c] * hp[192 + c];
+  }
+  for (int c = 0; c < K; ++c) {
+    const double b2 = hp[192 + c];
+    if (b2 > 0) info.max_rel = std::max(info.max_rel, std::sqrt(hp[c] / b2));
+  }
+  return WL_OK;
+}
+
+// Refined solve: FP64 iterate and residual, FP32 inner CG corrections.
+int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, bool x_is_zero, SolveInfo& info) {
+  const int G = cg_grid_f32(K);
+  int Tw, Tc;
+  thresholds_f32(K, &Tw, &Tc);
+  PartDev* pd;
+  WL_TRY(get_part(h, G, Tw, Tc, &pd));
+  const int Gr = res_grid(K);
+  int Twr, Tcr;
+  thresholds_f64(K, &Twr, &Tcr);
+  PartDev* pr;
+  WL_TRY(get_part(h, Gr, Twr, Tcr, &pr));
+  const size_t nk = (size_t)h->n * K;
+  WL_TRY(ensure(h->r, nk * 4));
+  WL_TRY(ensure(h->p, nk * 4));
+  WL_TRY(ensure(h->q, nk * 4));
+  WL_TRY(ensure(h->d32, nk * 4));
+  WL_TRY(ensure(h->r32, nk * 4));
+  WL_TRY(ensure(h->r64, nk * 8));
+  WL_TRY(ensure(h->part, (size_t)std::max(G, Gr) * 64 * 2 * 8 + 1024));
+  Smalls sm = smalls(h);
+  if (x_is_zero) WL_CU(cudaMemsetAsync(x, 0, nk * 8, S(h)));
+  WL_CU(cudaMemsetAsync(h->d32.p, 0, nk * 4, S(h)));
+  double* hp = h->h_pin;
+  const double inner_tol = 2e-5;  // relative reduction per FP32 correction
+  const int max_ref = 12;
+  for (int ref = 0;; ++ref) {
+    ResArgs ra{h->g, pr->view(), x, (float*)h->d32.p, b, (double*)h->r64.p, (float*)h->r32.p,
+               h->ca, h->cA, h->cD, (double*)h->part.p, sm.rr, sm.bb, h->bar, ref > 0 ? 1 : 0};
+    WL_TRY(reset_bar(h));
+    const int pi = prof_begin(h, kCatRes);
+    WL_CU(launch_residual64(K, ra, Gr, S(h)));
+    prof_end(h, pi);
+    info.refinements++;
+    info.nnz_rhs += (double)h->nnz * K;
+    WL_CU(cudaMemcpyAsync(hp, sm.rr, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaMemcpyAsync(hp + 64, sm.bb, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
+    const int berr = check_bar(h);
+    if (berr) return berr;
+    bool all = true;
+    double mx = 0.0;
+    int skip[64];
+    for (int c = 0; c < K; ++c) {
+      const double rr = hp[c], bb = hp[64 + c];
+      if (!std::isfinite(rr)) {
+        info.status = WL_ERR_NONFINITE;
+        return WL_OK;
+      }
+      const double rel = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+      mx = std::max(mx, rel);
+      skip[c] = (rel <= tol) ? 1 : 0;
+      if (!skip[c]) all = false;
+    }
+    info.max_rel = mx;
+    if (all) break;
+    if (ref >= max_ref) {
+      if (info.status == WL_OK) info.status = WL_ERR_NO_CONVERGENCE;
+      break;
+    }
+    WL_CU(cudaMemcpyAsync(sm.skip, skip, K * sizeof(int), cudaMemcpyHostToDevice, S(h)));
+    CgArgs<float> a{h->g, pd->view(), (float*)h->d32.p, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
+                    h->ca, h->cA, h->cD, nullptr, sm.skip, (double*)h->part.p, sm.gamma, sm.status,
+                    h->bar, h->prm.max_iter, inner_tol * inner_tol, sm.iters};
+    WL_TRY(reset_bar(h));
+    const int pc = prof_begin(h, kCatCG);
+    WL_CU(launch_cg_f32(K, a, G, S(h)));
+    prof_end(h, pc);
+    WL_CU(cudaMemcpyAsync(hp + 128, sm.iters, 4, cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaMemcpyAsync(hp + 130, sm.status, 64 * 4, cudaMemcpyDeviceToHost, S(h)));
+    const int berr2 = check_bar(h);
+    if (berr2) return berr2;
+    const int it = *(const int*)(hp + 128);
+    const int* st = (const int*)(hp + 130);
+    for (int c = 0; c < K; ++c)
+      if (!skip[c] && (st[c] == WL_ERR_NOT_SPD || st[c] == WL_ERR_NONFINITE)) {
+        info.status = st[c];
+        return WL_OK;
+      }
+    info.iters += it;
+    info.cg_iters += it;
+    info.nnz_rhs += (double)it * h->nnz * K;
+    info.bytes += (double)it * alg_bytes_per_iter(h, K, 4);
+  }
+  return WL_OK;
+}
+
+int solve(wl_handle* h, const double* b, double* x, int K, bool x_is_zero, SolveInfo& info) {
+  const double tol = h->prm.tol;
+  if (h->prm.prec == WL_REFINED) return solve_refined(h, b, x, K, tol, x_is_zero, info);
+  if (x_is_zero) WL_CU(cudaMemsetAsync(x, 0, (size_t)h->n * K * 8, S(h)));
+  return solve_fp64(h, b, x, K, tol, x_is_zero, info);
+}
+
+// phi X for a packed block V (n x K, device): X = M^{-1} (a V) for the
+// resolvent; the result goes to X (n x K).
+int phi_apply(wl_handle* h, const double* Vp, double* X, int K, SolveInfo& info) {
+  const size_t nk = (size_t)h->n * K;
+  WL_TRY(ensure(h->b64, nk * 8));
+  // b = a V
+  counted(h);
+  WL_CU(launch_pack(Vp, K, 0, K, h->n, h->a_scale, h->b64.p, false, S(h)));
+  return solve(h, (const double*)h->b64.p, X, K, true, info);
+}
+
+int compute_Df(wl_handle* h, SolveInfo& info) {
+  WL_TRY(ensure(h->Df, (size_t)std::max<int64_t>(h->n, 1) * 8));
+  double* Df = (double*)h->Df.p;
+  if (h->prm.f == WL_F_IDENTITY) {
+    counted(h);
+    WL_CU(launch_degree_vector(h->g, Df, S(h)));
+  } else if (h->prm.f == WL_F_RESOLVENT) {
+    WL_TRY(ensure(h->b64, (size_t)h->n * 8));
+    counted(h);
+    WL_CU(launch_fill((double*)h->b64.p, h->a_scale, h->n, S(h)));
+    bool zero = true;
+    if (h->have_warm) {
+      WL_CU(cudaMemcpyAsync(Df, h->warm.p, (size_t)h->n * 8, cudaMemcpyDeviceToDevice, S(h)));
+      zero = false;
+    }
+    WL_TRY(solve(h, (const double*)h->b64.p, Df, 1, zero, info));
+  } else {
+    return WL_ERR_UNSUPPORTED;
+  }
+  h->have_Df = true;
+  return WL_OK;
+}
+
+// ------------------------------------------------------------------ spectral scale
+// Extreme eigenvalues of Op = c0 I + cA A + cD D by Lanczos (k = 1).
+int lanczos_ext(wl_handle* h, double c0, double cA, double cD, int m, double* th_max, double* th_min,
+                double* conv) {
+  const int G = lanczos_ext_grid();
+  int Tw, Tc;
+  thresholds_f64(1, &Tw, &Tc);
+  PartDev* pd;
+  WL_TRY(get_part(h, G, Tw, Tc, &pd));
+  WL_TRY(ensure(h->lan, (size_t)h->n * 3 * 8 + 2 * 512 * 8));
+  WL_TRY(ensure(h->part, (size_t)G * 64 * 2 * 8 + 1024));
+  Smalls sm = smalls(h);
+  double* v = (double*)h->lan.p;
+  double* ab = v + (size_t)h->n * 3;
+  m = std::min<int64_t>(m, std::max<int64_t>(h->n, 1));
+  m = std::min(m, 512);
+  LanczosExtArgs a{h->g, pd->view(), c0, cA, cD, v, ab, ab + 512, (double*)h->part.p, sm.misc, h->bar, m,
+                   std::max(1, m / 8), 0x5EEDull};
+  WL_TRY(reset_bar(h));
+  counted(h);
+  WL_CU(launch_lanczos_extreme(a, G, S(h)));
+  WL_CU(cudaMemcpyAsync(h->h_pin, sm.misc, 5 * 8, cudaMemcpyDeviceToHost, S(h)));
+  const int berr = check_bar(h);
+  if (berr) return berr;
+  const double* o = h->h_pin;
+  *th_max = o[0];
+  *th_min = o[2];
+  if (conv) *conv = std::max(std::fabs(o[0] - o[1]) / (std::fabs(o[0]) + 1e-300),
+                             std::fabs(o[2] - o[3]) / (std::fabs(o[2]) + std::fabs(o[0]) + 1e-300));
+  return WL_OK;
+}
+
+int lambda_max_adaptive(wl_handle* h, double c0, double cA, double cD, double* lmax) {
+  double mx = 0, mn = 0, cv = 1;
+  int m = 96;
+  for (;;) {
+    WL_TRY(lanczos_ext(h, c0, cA, cD, m, &mx, &mn, &cv));
+    if (cv < 1e-10 || m >= 480 || m >= h->n) break;
+    m *= 2;
+  }
+  *lmax = mx;
+  return WL_OK;
+}
+
+// rho(Z_mu): largest lambda with lambda_max(A - (mu/lambda)(D - mu I)) = lambda
+// (the quadratic eigenproblem of Eq. Zdef), by a bracketed Illinois iteration.
+int rho_companion(wl_handle* h, double mu, double lmaxA, double* rho) {
+  if (mu == 0.0 || lmaxA <= 0.0) {
+    *rho = lmaxA;
+    return WL_OK;
+  }
+  auto hfun = [&](double lam, double* val) -> int {
+    double lm;
+    WL_TRY(lambda_max_adaptive(h, mu * mu / lam, 1.0, -mu / lam, &lm));
+    *val = lm - lam;
+    return WL_OK;
+  };
+  double hi = lmaxA, fhi;
+  WL_TRY(hfun(hi, &fhi));
+  if (fhi > 0) {  // can only happen through rounding; widen
+    hi *= 1.01;
+    WL_TRY(hfun(hi, &fhi));
+  }
+  double lo = 0.5 * hi, flo;
+  WL_TRY(hfun(lo, &flo));
+  int guard = 0;
+  while (flo <= 0 && guard++ < 40) {
+    hi = lo;
+    fhi = flo;
+    lo *= 0.5;
+    WL_TRY(hfun(lo, &flo));
+  }
+  if (flo <= 0) {
+    *rho = 0.0;
+    return WL_OK;
+  }
+  int side = 0;
+  for (int it = 0; it < 60 && (hi - lo) > 1e-12 * hi; ++it) {
+    double x = (lo * fhi - hi * flo) / (fhi - flo);
+    if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
+    double fx;
+    WL_TRY(hfun(x, &fx));
+    if (fx > 0) {
+      lo = x;
+      flo = fx;
+      if (side == 1) fhi *= 0.5;
+      side = 1;
+    } else {
+      hi = x;
+      fhi = fx;
+      if (side == -1) flo *= 0.5;
+      side = -1;
+    }
+    if (std::fabs(fx) < 1e-13 * x) {
+      lo = hi = x;
+      break;
+    }
+  }
+  *rho = 0.5 * (lo + hi);
+  return WL_OK;
+}
+
+// stage a caller array into device memory (copy if host)
+int stage_in(wl_handle* h, Buf& st, const void* src, size_t bytes, const void** dev) {
+  if (is_device_ptr(src)) {
+    *dev = src;
+    return WL_OK;
+  }
+  WL_TRY(ensure(st, bytes));
+  WL_CU(cudaMemcpyAsync(st.p, src, bytes, cudaMemcpyHostToDevice, S(h)));
+  *dev = st.p;
+  return WL_OK;
+}
+
+void begin_timer(wl_handle* h) {
+  prof_reset(h);
+  cudaEventRecord(h->ev0, S(h));
+}
+
+double end_timer(wl_handle* h) {
+  cudaEventRecord(h->ev1, S(h));
+  cudaEventSynchronize(h->ev1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  return ms;
+}
+
+void fill_stats(wl_handle* h, wl_stats* st, const SolveInfo& in, int status, double ms, int outer) {
+  if (!st) {
+    prof_reset(h);
+    return;
+  }
+  memset(st, 0, sizeof(*st));
+  st->launches = h->launches;
+  for (const auto& r : h->recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, h->ev_pool[r.a], h->ev_pool[r.b]) != cudaSuccess) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    if (r.cat == kCatCG) { st->k_cg_launches++; st->k_cg_ms += t; }
+    else if (r.cat == kCatRes) { st->k_res_launches++; st->k_res_ms += t; }
+    else { st->k_lan_launches++; st->k_lan_ms += t; }
+  }
+  st->k_cg_iters = in.cg_iters;
+  st->k_cg_bytes = in.bytes;
+  prof_reset(h);
+  st->status = status;
+  st->iters = in.iters;
+  st->outer_iters = outer;
+  st->refinements = in.refinements;
+  st->rel_res = in.max_rel;
+  st->time_ms = ms;
+  st->nnz_rhs_iters = in.nnz_rhs;
+  st->bytes_alg = in.bytes;
+  st->alpha = h->alpha;
+  st->beta = h->beta;
+  st->mu = h->mu;
+  st->rho = h->rho;
+  st->lambda_max = h->lmax;
+}
+
+void free_handle(wl_handle* h) {
+  if (!h) return;
+  for (auto& kv : h->parts) {
+    cudaFree(kv.second.rb);
+    cudaFree(kv.second.seg);
+    cudaFree(kv.second.order);
+  }
+  Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
+                 &h->r32, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
+                 &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->lan};
+  for (Buf* b : bufs) release(*b);
+  if (h->bar) cudaFree(h->bar);
+  if (h->h_pin) cudaFreeHost(h->h_pin);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+}
+
+void default_params(wl_params* p) {
+  if (p->tol <= 0) p->tol = 1e-12;
+  if (p->max_iter <= 0) p->max_iter = 2000;
+  if (p->max_outer <= 0) p->max_outer = 400;
+  if (p->max_outer > 500) p->max_outer = 500;
+  if (p->outer_tol <= 0) p->outer_tol = 1e-10;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* wl_status_string(int s) {
+  switch (s) {
+    case WL_OK: return "ok";
+    case WL_ERR_INVALID_ARG: return "invalid argument";
+    case WL_ERR_NOT_SYMMETRIC: return "adjacency pattern is not symmetric";
+    case WL_ERR_SELF_LOOP: return "self-loop stored in the adjacency";
+    case WL_ERR_UNSORTED: return "CSR malformed: row_ptr not monotone, or columns unsorted, duplicated or out of range";
+    case WL_ERR_ALPHA_RANGE: return "alpha * rho(Z_mu) >= 1: the walk series diverges";
+    case WL_ERR_NOT_SPD: return "CG breakdown: operator not positive definite";
+    case WL_ERR_NONFINITE: return "non-finite value in inputs or iterates";
+    case WL_ERR_NO_CONVERGENCE: return "iteration cap reached before the tolerance";
+    case WL_ERR_TIMEOUT: return "bounded device wait expired";
+    case WL_ERR_OOM: return "device memory allocation failed";
+    case WL_ERR_CUDA: return "CUDA runtime error";
+    case WL_ERR_UNSUPPORTED: return "combination not supported";
+  }
+  return "unknown status";
+}
+
+const char* wl_last_error(void) { return g_last_error.c_str(); }
+
+int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out, wl_stats* st) {
+  if (!out) return WL_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!A || !p || A->n < 0 || A->nnz < 0 || A->nnz >= (int64_t)INT32_MAX || A->n >= (int64_t)INT32_MAX)
+    return WL_ERR_INVALID_ARG;
+  if ((A->n > 0 && !A->row_ptr) || (A->nnz > 0 && !A->col_idx)) return WL_ERR_INVALID_ARG;
+  if (v != WL_ALLWALK && v != WL_NBT && v != WL_BTDW) return WL_ERR_INVALID_ARG;
+  if (p->f != WL_F_RESOLVENT && p->f != WL_F_EXP && p->f != WL_F_IDENTITY) return WL_ERR_INVALID_ARG;
+  if (p->prec != WL_FP64 && p->prec != WL_REFINED) return WL_ERR_INVALID_ARG;
+  double mu = (v == WL_ALLWALK) ? 0.0 : (v == WL_NBT ? 1.0 : p->mu);
+  if (!(mu >= 0.0 && mu <= 1.0)) return WL_ERR_INVALID_ARG;
+  if (p->f == WL_F_EXP && mu != 0.0) return WL_ERR_UNSUPPORTED;
+  if (p->f == WL_F_EXP) return WL_ERR_UNSUPPORTED;  // exponential variant: not provided by this build
+
+  wl_handle* h = new wl_handle();
+  h->n = A->n;
+  h->nnz = A->nnz;
+  h->variant = v;
+  h->prm = *p;
+  default_params(&h->prm);
+  h->mu = mu;
+  h->stream = (cudaStream_t)p->stream;
+  int rc = WL_OK;
+  auto fail = [&](int code) {
+    free_handle(h);
+    if (st) {
+      memset(st, 0, sizeof(*st));
+      st->status = code;
+    }
+    return code;
+  };
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess)
+    return fail(set_cuda_error(cudaGetLastError(), "cudaEventCreate"));
+  if (cudaMallocHost(&h->h_pin, 4096 * sizeof(double)) != cudaSuccess)
+    return fail(set_cuda_error(cudaGetLastError(), "cudaMallocHost"));
+  if (cudaMalloc(&h->bar, sizeof(GridBar)) != cudaSuccess) return fail(set_cuda_error(cudaGetLastError(), "cudaMalloc"));
+  if ((rc = ensure(h->small, 8192)) != WL_OK) return fail(rc);
+  if ((rc = ensure(h->csr_rp, sizeof(int32_t) * (A->n + 1))) != WL_OK) return fail(rc);
+  if ((rc = ensure(h->csr_col, sizeof(int32_t) * std::max<int64_t>(A->nnz, 1))) != WL_OK) return fail(rc);
+  begin_timer(h);
+  {
+    cudaError_t e1 = cudaMemcpyAsync(h->csr_rp.p, A->row_ptr, sizeof(int32_t) * (A->n + 1), cudaMemcpyDefault, S(h));
+    cudaError_t e2 = A->nnz > 0 ? cudaMemcpyAsync(h->csr_col.p, A->col_idx, sizeof(int32_t) * A->nnz,
+                                                  cudaMemcpyDefault, S(h))
+                                : cudaSuccess;
+    if (e1 != cudaSuccess || e2 != cudaSuccess)
+      return fail(set_cuda_error(e1 != cudaSuccess ? e1 : e2, "copy CSR"));
+  }
+  h->g = Graph{(const int32_t*)h->csr_rp.p, (const int32_t*)h->csr_col.p, h->n, h->nnz};
+  // validation
+  Smalls sm = smalls(h);
+  if (cudaMemsetAsync(sm.flags, 0, sizeof(int), S(h)) != cudaSuccess) return fail(WL_ERR_CUDA);
+  if (cudaError_t e = launch_validate(h->g, sm.flags, S(h)); e != cudaSuccess) return fail(set_cuda_error(e, "validate"));
+  int flags = 0;
+  if (cudaMemcpyAsync(&flags, sm.flags, sizeof(int), cudaMemcpyDeviceToHost, S(h)) != cudaSuccess ||
+      cudaStreamSynchronize(S(h)) != cudaSuccess)
+    return fail(set_cuda_error(cudaGetLastError(), "validate readback"));
+  if (flags & 3) return fail(WL_ERR_UNSORTED);
+  if (flags & 4) return fail(WL_ERR_SELF_LOOP);
+  if (flags & 8) return fail(WL_ERR_NOT_SYMMETRIC);
+
+  // spectral scale and parameters
+  h->lmax = 0.0;
+  h->rho = 0.0;
+  if (h->n > 0 && h->nnz > 0) {
+    if ((rc = lambda_max_adaptive(h, 0.0, 1.0, 0.0, &h->lmax)) != WL_OK) return fail(rc);
+    if (p->f == WL_F_RESOLVENT) {
+      if ((rc = rho_companion(h, mu, h->lmax, &h->rho)) != WL_OK) return fail(rc);
+    } else {
+      h->rho = h->lmax;
+    }
+  }
+  if (p->f == WL_F_RESOLVENT) {
+    double alpha = p->alpha;
+    if (p->alpha_rel > 0) {
+      if (!(h->rho > 0)) return fail(WL_ERR_ALPHA_RANGE);
+      alpha = p->alpha_rel / h->rho;
+    }
+    if (!(alpha >= 0.0) || !std::isfinite(alpha) || alpha * h->rho >= 1.0) return fail(WL_ERR_ALPHA_RANGE);
+    h->alpha = alpha;
+    h->a_scale = 1.0 - mu * mu * alpha * alpha;
+    h->ca = h->a_scale;
+    h->cA = -alpha;
+    h->cD = alpha * alpha * mu;
+  } else {
+    h->alpha = 0.0;
+    h->a_scale = 1.0;
+    h->ca = 0.0;
+    h->cA = -1.0;
+    h->cD = 1.0;
+  }
+  h->beta = 0.0;
+  const double ms = end_timer(h);
+  if (st) {
+    SolveInfo none;
+    fill_stats(h, st, none, WL_OK, ms, 0);
+  }
+  *out = h;
+  return WL_OK;
+}
+
+int wl_set_params(wl_handle* h, const wl_params* p) {
+  if (!h || !p) return WL_ERR_INVALID_ARG;
+  if (p->prec != WL_FP64 && p->prec != WL_REFINED) return WL_ERR_INVALID_ARG;
+  h->prm.prec = p->prec;
+  h->prm.tol = p->tol;
+  h->prm.max_iter = p->max_iter;
+  h->prm.max_outer = p->max_outer;
+  h->prm.outer_tol = p->outer_tol;
+  h->prm.stream = p->stream;
+  h->stream = (cudaStream_t)p->stream;
+  default_params(&h->prm);
+  return WL_OK;
+}
+
+int wl_get_info(const wl_handle* h, wl_stats* info) {
+  if (!h || !info) return WL_ERR_INVALID_ARG;
+  memset(info, 0, sizeof(*info));
+  info->alpha = h->alpha;
+  info->beta = h->beta;
+  info->mu = h->mu;
+  info->rho = h->rho;
+  info->lambda_max = h->lmax;
+  return WL_OK;
+}
+
+int wl_set_warm_start(wl_handle* h, const double* x0) {
+  if (!h) return WL_ERR_INVALID_ARG;
+  if (!x0) {
+    h->have_warm = false;
+    return WL_OK;
+  }
+  int rc = ensure(h->warm, (size_t)std::max<int64_t>(h->n, 1) * 8);
+  if (rc) return rc;
+  WL_CU(cudaMemcpyAsync(h->warm.p, x0, (size_t)h->n * 8, cudaMemcpyDefault, S(h)));
+  h->have_warm = true;
+  h->have_Df = false;
+  return WL_OK;
+}
+
+int wl_degrees(wl_handle* h, double* Df, wl_stats* st) {
+  if (!h || (!Df && h->n > 0)) return WL_ERR_INVALID_ARG;
+  SolveInfo info;
+  begin_timer(h);
+  int rc = WL_OK;
+  if (h->n > 0) {
+    h->have_Df = false;
+    rc = compute_Df(h, info);
+    if (rc == WL_OK) {
+      cudaError_t e = cudaMemcpyAsync(Df, h->Df.p, (size_t)h->n * 8, cudaMemcpyDefault, S(h));
+      if (e != cudaSuccess) rc = set_cuda_error(e, "copy Df");
+    }
+  }
+  const double ms = end_timer(h);
+  if (rc == WL_OK) rc = info.status;
+  fill_stats(h, st, info, rc, ms, 0);
+  return rc;
+}
+
+int wl_apply(wl_handle* h, const double* V, int64_t ldv, int k, double* W, int64_t ldw, wl_stats* st) {
+  if (!h || k < 0 || (k > 0 && h->n > 0 && (!V || !W || ldv < k || ldw < k))) return WL_ERR_INVALID_ARG;
+  SolveInfo info;
+  begin_timer(h);
+  int rc = WL_OK;
+  if (k == 0 || h->n == 0) {
+    fill_stats(h, st, info, WL_OK, end_timer(h), 0);
+    return WL_OK;
+  }
+  const int64_t n = h->n;
+  const bool w_dev = is_device_ptr(W);
+  const double* Vd = nullptr;
+  double* Wd = W;
+  do {
+    if (!h->have_Df && (rc = compute_Df(h, info)) != WL_OK) break;
+    if ((rc = stage_in(h, h->stage_a, V, (size_t)n * ldv * 8, (const void**)&Vd)) != WL_OK) break;
+    if (!w_dev) {
+      if ((rc = ensure(h->stage_b, (size_t)n * ldw * 8)) != WL_OK) break;
+      Wd = (double*)h->stage_b.p;
+      if (ldw != k) cudaMemcpyAsync(Wd, W, (size_t)n * ldw * 8, cudaMemcpyHostToDevice, S(h));
+    }
+    int c0 = 0;
+    for (int K : column_blocks(k)) {
+      if ((rc = ensure(h->packV, (size_t)n * K * 8)) != WL_OK) break;
+      if ((rc = ensure(h->packX, (size_t)n * K * 8)) != WL_OK) break;
+      counted(h);
+      cudaError_t e = launch_pack(Vd, ldv, c0, K, n, 1.0, h->packV.p, false, S(h));
+      if (e != cudaSuccess) { rc = set_cuda_error(e, "pack"); break; }
+      if (h->prm.f == WL_F_IDENTITY) {
+        PartDev* pd;
+        int Tw, Tc;
+        thresholds_f64(K, &Tw, &Tc);
+        if ((rc = get_part(h, cg_grid_f64(K), Tw, Tc, &pd)) != WL_OK) break;
+        counted(h);
+        e = launch_laplacian_apply(h->g, *pd, (const double*)h->packV.p, K, c0, Wd, ldw, S(h));
+        info.nnz_rhs += (double)h->nnz * K;
+        info.iters += 1;
+      } else {
+        if ((rc = phi_apply(h, (const double*)h->packV.p, (double*)h->packX.p, K, info)) != WL_OK) break;
+        counted(h);
+        e = launch_apply_out(Vd, ldv, (const double*)h->packX.p, (const double*)h->Df.p, n, K, c0, Wd, ldw, S(h));
+      }
+      if (e != cudaSuccess) { rc = set_cuda_error(e, "apply"); break; }
+      c0 += K;
+    }
+    if (rc != WL_OK) break;
+    if (!w_dev) {
+      cudaError_t e = cudaMemcpyAsync(W, Wd, (size_t)n * ldw * 8, cudaMemcpyDeviceToHost, S(h));
+      if (e != cudaSuccess) { rc = set_cuda_error(e, "copy W"); break; }
+    }
+  } while (0);
+  const double ms = end_timer(h);
+  if (rc == WL_OK) rc = info.status;
+  fill_stats(h, st, info, rc, ms, 0);
+  return rc;
+}
+
+int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* taus, int ntau, double* U,
+             int64_t ldo, wl_stats* st) {
+  if (!h || k < 0 || ntau < 0 || ntau > kMaxTau) return WL_ERR_INVALID_ARG;
+  if (k > 0 && h->n > 0 && (!U0 || !U || !taus || ldu < k || ldo < k)) return WL_ERR_INVALID_ARG;
+  for (int t = 0; t < ntau; ++t)
+    if (!(taus[t] >= 0.0) || !std::isfinite(taus[t])) return WL_ERR_INVALID_ARG;
+  SolveInfo info;
+  begin_timer(h);
+  if (k == 0 || ntau == 0 || h->n == 0) {
+    fill_stats(h, st, info, WL_OK, end_timer(h), 0);
+    return WL_OK;
+  }
+  const int64_t n = h->n;
+  int rc = WL_OK;
+  int outer_total = 0;
+  const bool u_dev = is_device_ptr(U);
+  const double* U0d = nullptr;
+  double* Ud = U;
+  const int ldT = 512;
+  const int maxm = std::min(h->prm.max_outer, ldT - 1);
+  const int check = 4;
+  do {
+    if (h->prm.f != WL_F_IDENTITY && !h->have_Df && (rc = compute_Df(h, info)) != WL_OK) break;
+    if ((rc = stage_in(h, h->stage_a, U0, (size_t)n * ldu * 8, (const void**)&U0d)) != WL_OK) break;
+    if (!u_dev) {
+      if ((rc = ensure(h->stage_b, (size_t)ntau * n * ldo * 8)) != WL_OK) break;
+      Ud = (double*)h->stage_b.p;
+      if (ldo != k) cudaMemcpyAsync(Ud, U, (size_t)ntau * n * ldo * 8, cudaMemcpyHostToDevice, S(h));
+    }
+    double* dtaus = (double*)h->small.p + 512;
+    if (cudaMemcpyAsync(dtaus, taus, ntau * 8, cudaMemcpyHostToDevice, S(h)) != cudaSuccess) { rc = WL_ERR_CUDA; break; }
+    int c0 = 0;
+    for (int K : column_blocks(k)) {
+      const size_t blk = (size_t)n * K;
+      size_t want_blocks = (size_t)std::min(maxm + 1, 160);
+      if (h->basis_blocks < want_blocks || h->basis.bytes < want_blocks * blk * 8) {
+        if ((rc = ensure(h->basis, want_blocks * blk * 8)) != WL_OK) break;
+        h->basis_blocks = want_blocks;
+      }
+      size_t cap_blocks = h->basis.bytes / (blk * 8);
+      if ((rc = ensure(h->Tab, (size_t)2 * K * ldT * 8 + 64 * 8 * 4)) != WL_OK) break;
+      if ((rc = ensure(h->ybuf, (size_t)K * ntau * ldT * 8)) != WL_OK) break;
+      if ((rc = ensure(h->yprev, (size_t)K * ntau * ldT * 8)) != WL_OK) break;
+      if ((rc = ensure(h->errb, (size_t)K * ntau * 8 * 2 + 64 * 4 * 3)) != WL_OK) break;
+      if ((rc = ensure(h->packX, blk * 8)) != WL_OK) break;
+      double* basis = (double*)h->basis.p;
+      double* Ta = (double*)h->Tab.p;
+      double* Tb = Ta + (size_t)K * ldT;
+      double* nrm = Tb + (size_t)K * ldT;
+      int* done = (int*)((double*)h->errb.p + (size_t)K * ntau * 2);
+      int* mcol = done + 64;
+      int* mprev = done + 128;
+      double* errd = (double*)h->errb.p;
+      // V_0 = U0 block / |U0 block| (per column)
+      counted(h, 3);
+      cudaError_t e = launch_pack(U0d, ldu, c0, K, n, 1.0, h->packX.p, false, S(h));
+      if (e == cudaSuccess) e = launch_colnorms((const double*)h->packX.p, n, K, nrm, S(h));
+      if (e == cudaSuccess) e = launch_scale_cols((const double*)h->packX.p, n, K, nrm, basis, S(h));
+      if (e != cudaSuccess) { rc = set_cuda_error(e, "expmv init"); break; }
+      // done flags: zero columns
+      WL_CU(cudaMemcpyAsync(h->h_pin, nrm, K * 8, cudaMemcpyDeviceToHost, S(h)));
+      WL_CU(cudaStreamSynchronize(S(h)));
+      std::vector<int> hdone(K), hzero(K, 0);
+      for (int c = 0; c < K; ++c) hdone[c] = (h->h_pin[c] > 0.0) ? 0 : 1;
+      WL_CU(cudaMemcpyAsync(done, hdone.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
+      WL_CU(cudaMemcpyAsync(mprev, hzero.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
+      const int Gs = lanczos_step_grid(K);
+      int Tw, Tc;
+      thresholds_f64(K, &Tw, &Tc);
+      PartDev* pd;
+      if ((rc = get_part(h, Gs, Tw, Tc, &pd)) != WL_OK) break;
+      if ((rc = ensure(h->part, (size_t)std::max(Gs, 1) * 64 * 2 * 8 + 1024)) != WL_OK) break;
+      int m = 0;
+      bool converged = false;
+      for (int j = 0; j < maxm; ++j) {
+        if ((size_t)(j + 2) > cap_blocks) {
+          // grow the basis (double), keeping the blocks computed so far
+          Buf nb;
+          size_t nbk = std::min<size_t>((size_t)maxm + 1, cap_blocks * 2);
+          if ((rc = ensure(nb, nbk * blk * 8)) != WL_OK) break;
+          WL_CU(cudaMemcpyAsync(nb.p, h->basis.p, cap_blocks * blk * 8, cudaMemcpyDeviceToDevice, S(h)));
+          WL_CU(cudaStreamSynchronize(S(h)));
+          release(h->basis);
+          h->basis = nb;
+          h->basis_blocks = nbk;
+          cap_blocks = nbk;
+          basis = (double*)h->basis.p;
+        }
+        double* vj = basis + (size_t)j * blk;
+        double* vjm1 = j > 0 ? basis + (size_t)(j - 1) * blk : nullptr;
+        double* vjp1 = basis + (size_t)(j + 1) * blk;
+        LanczosStepArgs la{h->g, pd->view(), vj, vjm1, nullptr, (const double*)h->Df.p, 0, 0, 0, vjp1,
+                           Ta, Tb, done, (double*)h->part.p, h->bar, j, ldT, 0};
+        if (h->prm.f == WL_F_IDENTITY) {
+          la.mode = 1;
+          la.c0 = 0.0;
+          la.cA = -1.0;
+          la.cD = 1.0;
+          info.nnz_rhs += (double)h->nnz * K;
+          info.iters += 1;
+        } else {
+          if ((rc = phi_apply(h, vj, (double*)h->packX.p, K, info)) != WL_OK) break;
+          if (info.status != WL_OK) break;
+          la.X = (const double*)h->packX.p;
+        }
+        if ((rc = reset_bar(h)) != WL_OK) break;
+        const int pl = prof_begin(h, kCatLan);
+        e = launch_lanczos_step(K, la, Gs, S(h));
+        prof_end(h, pl);
+        if (e != cudaSuccess) { rc = set_cuda_error(e, "lanczos_step"); break; }
+        m = j + 1;
+        ++outer_total;
+        if (m % check == 0 || m == maxm) {
+          std::vector<int> hm(K, m);
+          WL_CU(cudaMemcpyAsync(mcol, hm.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
+          TridiagArgs ta{Ta, Tb, mcol, dtaus, (double*)h->ybuf.p, (double*)h->yprev.p, mprev, errd, ldT, ntau, 1,
+                         kChebMax};
+          counted(h);
+          e = launch_tridiag_exp(ta, K, S(h));
+          if (e != cudaSuccess) { rc = set_cuda_error(e, "tridiag_exp"); break; }
+          WL_CU(cudaMemcpyAsync(mprev, mcol, K * 4, cudaMemcpyDeviceToDevice, S(h)));
+          WL_CU(cudaMemcpyAsync(h->h_pin, errd, (size_t)K * ntau * 8, cudaMemcpyDeviceToHost, S(h)));
+          const int berr = check_bar(h);
+          if (berr) { rc = berr; break; }
+          bool all = true;
+          for (int c = 0; c < K && all; ++c)
+            for (int t = 0; t < ntau; ++t)
+              if (!(h->h_pin[c * ntau + t] <= h->prm.outer_tol)) { all = false; break; }
+          if (all) { converged = true; break; }
+        }
+      }
+      if (rc != WL_OK || info.status != WL_OK) break;
+      if (!converged) info.status = WL_ERR_NO_CONVERGENCE;
+      // final y for all columns at m (recompute if the last step was not a check)
+      if (m % check != 0 && m != maxm) {
+        std::vector<int> hm(K, m);
+        WL_CU(cudaMemcpyAsync(mcol, hm.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
+        TridiagArgs ta{Ta, Tb, mcol, dtaus, (double*)h->ybuf.p, (double*)h->yprev.p, mprev, errd, ldT, ntau, 1,
+                       kChebMax};
+        counted(h);
+        e = launch_tridiag_exp(ta, K, S(h));
+        if (e != cudaSuccess) { rc = set_cuda_error(e, "tridiag_exp"); break; }
+      }
+      {
+        std::vector<int> hm(K, m);
+        WL_CU(cudaMemcpyAsync(mcol, hm.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
+      }
+      CombineArgs ca{basis, (const double*)h->ybuf.p, mcol, nrm, Ud, n, ldo, n * ldo, c0, ldT, ntau};
+      counted(h);
+      e = launch_combine(K, ca, S(h));
+      if (e != cudaSuccess) { rc = set_cuda_error(e, "combine"); break; }
+      c0 += K;
+    }
+    if (rc != WL_OK) break;
+    if (!u_dev) {
+      cudaError_t e = cudaMemcpyAsync(U, Ud, (size_t)ntau * n * ldo * 8, cudaMemcpyDeviceToHost, S(h));
+      if (e != cudaSuccess) { rc = set_cuda_error(e, "copy U"); break; }
+    }
+  } while (0);
+  const double ms = end_timer(h);
+  if (rc == WL_OK) rc = info.status;
+  fill_stats(h, st, info, rc, ms, outer_total);
+  return rc;
+}
+
+int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, uint16_t* omega_out, wl_stats* st) {
+  (void)h; (void)M; (void)seed; (void)est; (void)err_est; (void)omega_out; (void)st;
+  return WL_ERR_UNSUPPORTED;
+}
+
+void wl_destroy(wl_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_handle(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,307 @@
+// Lockstep conjugate gradients on M = ca I + cA A + cD D for K columns at once,
+// as one persistent cooperative kernel (Sec. 4.2: each application of the
+// resolvent walk Laplacian is one CG solve with the deformed Laplacian, which
+// is positive definite for alpha < 1 / rho(Z), Prop. CGworks).
+//
+// Per iteration two phases, each ending in a bounded grid barrier:
+//   U: r -= alpha q ; gamma' = (r, r)                      (own rows, coalesced)
+//   S: s = M r (gather) ; x += alpha_prev p ; p = r + beta p ;
+//      q = s + beta q ; delta = (p, q)                      (own rows, by class)
+// so that q = M p is carried by the recurrence q_new = M r + beta q_old and
+// the SpMM reads only r. The x update is deferred by one phase so it rides
+// on the S pass that reads p anyway. Scalars are FP64 in shared memory and
+// every CTA reduces the per-CTA partials in the same order, so all CTAs take
+// identical decisions and reruns are bit-identical.
+//
+// Vector traffic per iteration: U reads r, q, writes r; S gathers r, reads
+// x, p, q, writes x, p, q: 10 n K s bytes plus 4 nnz + 4 (n + 1) of graph.
+#pragma once
+#include "wl_common.cuh"
+
+namespace wl {
+
+enum ColStatus : int { kColActive = 0, kColDone = 1 };
+
+template <typename T>
+struct CgArgs {
+  Graph g;
+  Part pt;
+  T* x;
+  T* r;
+  T* p;
+  T* q;
+  double ca, cA, cD;      // operator coefficients
+  const double* bnorm2;   // K: ||b_c||^2 (convergence reference); NULL: use ||r_0||^2
+  const int* skip;        // K or NULL: columns marked nonzero are left untouched
+  double* part;           // 2 * G * K partials (ping-pong)
+  double* gamma_out;      // K: final ||r_c||^2 (recurrence)
+  int* status;            // K: 0 ok, WL_ERR_* per column
+  GridBar* bar;
+  int max_iter;
+  double tol2;            // relative tolerance squared
+  int* iters_out;         // S phases executed
+};
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kBlock) cg_persistent(CgArgs<T> a) {
+  using C = Cfg<T, K>;
+  constexpr int VW = C::VW;
+  constexpr int NW = kBlock / 32;
+  __shared__ double s_tmp[kBlock];
+  __shared__ double s_w[NW * K];
+  __shared__ double s_red[K];
+  __shared__ double s_alpha[K], s_beta[K], s_gamma[K], s_b2[K];
+  __shared__ int s_done[K], s_stat[K], s_all;
+  __shared__ __align__(16) T s_gath[kBlock * VW];
+
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int r0 = a.pt.rb[cta], r1 = a.pt.rb[cta + 1];
+  const size_t v0 = (size_t)r0 * K / VW, v1 = (size_t)r1 * K / VW;  // vector range
+  const int mycol = (tid % C::G) * VW;                                 // first column of this thread
+  const T ca = (T)a.ca, cA = (T)a.cA, cD = (T)a.cD;
+  int buf = 0;
+  int iters = 0;
+
+  // ---- U0: gamma = (r, r)
+  {
+    T acc[VW];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) acc[v] = T(0);
+#pragma unroll 4
+    for (size_t e = v0 + tid; e < v1; e += kBlock) {
+      const Pack<T, VW> rr = ldp<T, VW>(a.r + e * VW);
+#pragma unroll
+      for (int v = 0; v < VW; ++v) acc[v] += rr.v[v] * rr.v[v];
+    }
+    cta_column_sums<T, K>(acc, s_w, a.part + (size_t)buf * G * K + (size_t)cta * K);
+  }
+  if (!grid_sync(a.bar, G)) return;
+  reduce_partials<K>(a.part + (size_t)buf * G * K, G, s_tmp, s_red);
+  buf ^= 1;
+  if (tid < K) {
+    const double g0 = s_red[tid], b2 = a.bnorm2 ? a.bnorm2[tid] : g0;
+    s_gamma[tid] = g0;
+    s_b2[tid] = b2;
+    s_alpha[tid] = 0.0;
+    s_beta[tid] = 0.0;
+    s_stat[tid] = 0;
+    int done = (b2 <= 0.0) || (g0 <= a.tol2 * b2) || (a.skip && a.skip[tid]);
+    if (!isfinite(g0)) { done = 1; s_stat[tid] = WL_ERR_NONFINITE; }
+    s_done[tid] = done;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int all = 1;
+    for (int c = 0; c < K; ++c) all &= s_done[c];
+    s_all = all;
+  }
+  __syncthreads();
+
+  bool first = true;
+  while (!s_all) {
+    // ---- S: s = M r; x += alpha p; p = r + beta p; q = s + beta q; delta = (p, q)
+    {
+      T al[VW], be[VW], dacc[VW];
+#pragma unroll
+      for (int v = 0; v < VW; ++v) {
+        al[v] = (T)s_alpha[mycol + v];
+        be[v] = (T)s_beta[mycol + v];
+        dacc[v] = T(0);
+      }
+      auto op = [&](int row, int deg, int lane_off, const T (&nb)[VW]) {
+        const size_t o = (size_t)row * K + lane_off;
+        const Pack<T, VW> rr = ldp<T, VW>(a.r + o);
+        Pack<T, VW> pp, qq;
+        const T dg = (T)deg;
+        if (first) {
+#pragma unroll
+          for (int v = 0; v < VW; ++v) {
+            const T s = ca * rr.v[v] + cA * nb[v] + cD * dg * rr.v[v];
+            pp.v[v] = rr.v[v];
+            qq.v[v] = s;
+            dacc[v] += pp.v[v] * qq.v[v];
+          }
+        } else {
+          Pack<T, VW> xx = ldp<T, VW>(a.x + o);
+          pp = ldp<T, VW>(a.p + o);
+          qq = ldp<T, VW>(a.q + o);
+#pragma unroll
+          for (int v = 0; v < VW; ++v) {
+            const T s = ca * rr.v[v] + cA * nb[v] + cD * dg * rr.v[v];
+            xx.v[v] += al[v] * pp.v[v];
+            pp.v[v] = rr.v[v] + be[v] * pp.v[v];
+            qq.v[v] = s + be[v] * qq.v[v];
+            dacc[v] += pp.v[v] * qq.v[v];
+          }
+          stp<T, VW>(a.x + o, xx);
+        }
+        stp<T, VW>(a.p + o, pp);
+        stp<T, VW>(a.q + o, qq);
+      };
+      for_rows_gather<T, K>(a.g, a.pt, a.r, s_gath, op);
+      cta_column_sums<T, K>(dacc, s_w, a.part + (size_t)buf * G * K + (size_t)cta * K);
+    }
+    ++iters;
+    first = false;
+    if (!grid_sync(a.bar, G)) return;
+    reduce_partials<K>(a.part + (size_t)buf * G * K, G, s_tmp, s_red);
+    buf ^= 1;
+    if (tid < K) {
+      const double delta = s_red[tid];
+      if (!s_done[tid]) {
+        if (!isfinite(delta)) {
+          s_stat[tid] = WL_ERR_NONFINITE; s_done[tid] = 1; s_alpha[tid] = 0.0;
+        } else if (delta <= 0.0) {
+          s_stat[tid] = WL_ERR_NOT_SPD; s_done[tid] = 1; s_alpha[tid] = 0.0;
+        } else {
+          s_alpha[tid] = s_gamma[tid] / delta;
+        }
+      } else {
+        s_alpha[tid] = 0.0;
+      }
+    }
+    __syncthreads();
+
+    // ---- U: r -= alpha q; gamma' = (r, r)
+    {
+      T al[VW], acc[VW];
+#pragma unroll
+      for (int v = 0; v < VW; ++v) {
+        al[v] = (T)s_alpha[mycol + v];
+        acc[v] = T(0);
+      }
+#pragma unroll 4
+      for (size_t e = v0 + tid; e < v1; e += kBlock) {
+        Pack<T, VW> rr = ldp<T, VW>(a.r + e * VW);
+        const Pack<T, VW> qq = ldp<T, VW>(a.q + e * VW);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          rr.v[v] -= al[v] * qq.v[v];
+          acc[v] += rr.v[v] * rr.v[v];
+        }
+        stp<T, VW>(a.r + e * VW, rr);
+      }
+      cta_column_sums<T, K>(acc, s_w, a.part + (size_t)buf * G * K + (size_t)cta * K);
+    }
+    if (!grid_sync(a.bar, G)) return;
+    reduce_partials<K>(a.part + (size_t)buf * G * K, G, s_tmp, s_red);
+    buf ^= 1;
+    if (tid < K) {
+      const double gnew = s_red[tid];
+      if (!s_done[tid]) {
+        if (!isfinite(gnew)) {
+          s_stat[tid] = WL_ERR_NONFINITE; s_done[tid] = 1; s_beta[tid] = 0.0;
+        } else {
+          s_beta[tid] = gnew / s_gamma[tid];
+          s_gamma[tid] = gnew;
+          if (gnew <= a.tol2 * s_b2[tid]) { s_done[tid] = 1; s_beta[tid] = 0.0; }
+        }
+      } else {
+        s_beta[tid] = 0.0;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int all = 1;
+      for (int c = 0; c < K; ++c) all &= s_done[c];
+      if (iters >= a.max_iter) all = 1;
+      s_all = all;
+    }
+    __syncthreads();
+  }
+
+  // ---- F: x += alpha p (the deferred update of the last U phase)
+  if (!first) {
+    T al[VW];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) al[v] = (T)s_alpha[mycol + v];
+#pragma unroll 4
+    for (size_t e = v0 + tid; e < v1; e += kBlock) {
+      Pack<T, VW> xx = ldp<T, VW>(a.x + e * VW);
+      const Pack<T, VW> pp = ldp<T, VW>(a.p + e * VW);
+#pragma unroll
+      for (int v = 0; v < VW; ++v) xx.v[v] += al[v] * pp.v[v];
+      stp<T, VW>(a.x + e * VW, xx);
+    }
+  }
+  if (cta == 0 && tid < K) {
+    a.gamma_out[tid] = s_gamma[tid];
+    int st = s_stat[tid];
+    if (st == 0 && !s_done[tid]) st = WL_ERR_NO_CONVERGENCE;
+    a.status[tid] = st;
+    if (tid == 0) *a.iters_out = iters;
+  }
+}
+
+// ------------------------------------------------------------------ FP64 residual for refinement
+// x64 += d32 (skipped when `accumulate` is 0), grid barrier, then
+// r64 = b64 - M x64 (gather of x64), r32 = (float) r64, d32 = 0, and the
+// column norms ||r64||^2 written to rr_out (by CTA 0 after a second barrier).
+struct ResArgs {
+  Graph g;
+  Part pt;
+  double* x;        // FP64 iterate
+  float* d;         // FP32 correction from the last inner solve (zeroed here)
+  const double* b;  // FP64 right-hand side
+  double* r;        // FP64 residual out
+  float* r32;       // FP32 right-hand side of the next inner solve
+  double ca, cA, cD;
+  double* part;     // G * 2K
+  double* rr_out;   // K: ||r64||^2
+  double* bb_out;   // K: ||b||^2
+  GridBar* bar;
+  int accumulate;
+};
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) residual64(ResArgs a) {
+  using C = Cfg<double, K>;
+  using CF = Cfg<float, K>;
+  constexpr int VW = C::VW;
+  constexpr int NW = kBlock / 32;
+  __shared__ double s_tmp[kBlock];
+  __shared__ double s_w[NW * K];
+  __shared__ double s_red[K];
+  __shared__ __align__(16) double s_gath[kBlock * VW];
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int r0 = a.pt.rb[cta], r1 = a.pt.rb[cta + 1];
+  const size_t e0 = (size_t)r0 * K, e1 = (size_t)r1 * K;
+  double* part_r = a.part;
+  double* part_b = a.part + (size_t)G * K;
+  if (a.accumulate && a.d) {
+    for (size_t e = e0 + tid; e < e1; e += kBlock) a.x[e] += (double)__ldcg(a.d + e);
+    if (!grid_sync(a.bar, G)) return;
+  }
+  double acc[VW], bacc[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) acc[v] = bacc[v] = 0.0;
+  const double ca = a.ca, cA = a.cA, cD = a.cD;
+  auto op = [&](int row, int deg, int lane_off, const double (&nb)[VW]) {
+    const size_t o = (size_t)row * K + lane_off;
+    const Pack<double, VW> xx = ldp<double, VW>(a.x + o);
+    const Pack<double, VW> bb = ldp<double, VW>(a.b + o);
+    Pack<double, VW> rr;
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      rr.v[v] = bb.v[v] - (ca * xx.v[v] + cA * nb[v] + cD * (double)deg * xx.v[v]);
+      acc[v] += rr.v[v] * rr.v[v];
+      bacc[v] += bb.v[v] * bb.v[v];
+      if (a.r32) a.r32[o + v] = (float)rr.v[v];
+      if (a.d) a.d[o + v] = 0.0f;
+    }
+    stp<double, VW>(a.r + o, rr);
+  };
+  for_rows_gather<double, K>(a.g, a.pt, a.x, s_gath, op);
+  cta_column_sums<double, K>(acc, s_w, part_r + (size_t)cta * K);
+  cta_column_sums<double, K>(bacc, s_w, part_b + (size_t)cta * K);
+  if (!grid_sync(a.bar, G)) return;
+  if (cta == 0) {
+    reduce_partials<K>(part_r, G, s_tmp, s_red);
+    if (tid < K) a.rr_out[tid] = s_red[tid];
+    reduce_partials<K>(part_b, G, s_tmp, s_red);
+    if (tid < K) a.bb_out[tid] = s_red[tid];
+  }
+  (void)CF::VW;
+}
+
+}  // namespace wl

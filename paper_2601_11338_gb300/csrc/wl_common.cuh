@@ -1,0 +1,299 @@
+// Device-side building blocks shared by the walk-Laplacian kernels.
+//
+// Data layout: the graph is CSR with int32 row_ptr / col_idx and implicit
+// unit values; vector blocks are row-major n x K with the K values of a
+// node contiguous, so one gathered neighbour row is K * sizeof(T) contiguous
+// bytes (64 B for K = 16 FP32) read with 16-byte vector loads.
+//
+// Work split: a persistent grid of G CTAs; CTA g owns the contiguous rows
+// [rb[g], rb[g+1]) chosen so that deg + kRowCost per row is balanced. Inside
+// its range the rows are listed by class (order[], built once per
+// partition):
+//   class C  deg > Tc          : the whole CTA gathers the row, reduced in smem
+//   class W  Tw < deg <= Tc    : one warp per row, reduced by shuffles
+//   class S  deg <= Tw         : one subgroup of G lanes per row, rows sorted
+//                                by decreasing degree so a warp's rows are
+//                                equally long
+// Elementwise phases walk the contiguous range, fully coalesced.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wl.h"
+
+namespace wl {
+
+constexpr int kBlock = 256;        // threads per CTA of the persistent kernels
+constexpr int kRowCost = 2;        // partition cost of a row beyond its entries
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // every device-side wait gives up after 2 s
+
+// ------------------------------------------------------------------ grid barrier
+// Sense counter + generation word in global memory. Used only by kernels
+// launched cooperatively (all CTAs co-resident). Every wait is bounded:
+// after kWaitLimitNs it records WL_ERR_TIMEOUT in `err` and returns false,
+// and every caller then leaves the kernel.
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+  int err;
+  int pad;
+};
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = ld_acquire(&b->gen);
+    __threadfence();
+    const unsigned prev = atomicAdd(&b->count, 1u);
+    if (prev == nblocks - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      st_release(&b->gen, g + 1u);
+    } else {
+      const uint64_t t0 = globaltimer_ns();
+      while (ld_acquire(&b->gen) == g) {
+        if (*(volatile int*)&b->err != 0) {  // another CTA gave up: leave too
+          ok = 0;
+          break;
+        }
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          atomicExch(&b->err, WL_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (ok && *(volatile int*)&b->err != 0) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------------------ vector config
+template <typename T, int K>
+struct Cfg {
+  static constexpr int VEC = 16 / (int)sizeof(T);  // elements in 16 bytes
+  static constexpr int VW = K < VEC ? K : VEC;     // elements per lane
+  static constexpr int G = K / VW;                 // lanes per row (subgroup)
+  static constexpr int SUB = 32 / G;               // subgroups per warp
+  static constexpr int NSUB = kBlock / G;          // subgroups per CTA
+  static constexpr int Tw = 2 * SUB;               // class S if deg <= Tw
+  static constexpr int Tc = 8 * NSUB > Tw ? 8 * NSUB : Tw;  // class C if deg > Tc
+  static_assert(G >= 1 && G <= 32, "subgroup size");
+  static_assert(K % VW == 0, "K must be a multiple of the lane width");
+};
+
+template <typename T, int VW>
+struct alignas(sizeof(T) * VW) Pack {
+  T v[VW];
+};
+
+template <typename T, int VW>
+struct VecOf;
+template <>
+struct VecOf<float, 4> { using type = float4; };
+template <>
+struct VecOf<float, 2> { using type = float2; };
+template <>
+struct VecOf<float, 1> { using type = float; };
+template <>
+struct VecOf<double, 2> { using type = double2; };
+template <>
+struct VecOf<double, 1> { using type = double; };
+
+// Loads of vectors that the same kernel rewrites between grid barriers go
+// through L2 (ld.global.cg): L1 is not coherent across SMs, and a load
+// through a const __restrict__ pointer may otherwise become ld.global.nc.
+template <typename T, int VW>
+__device__ __forceinline__ Pack<T, VW> ldp(const T* p) {
+  using V = typename VecOf<T, VW>::type;
+  union {
+    V v;
+    Pack<T, VW> pk;
+  } u;
+  u.v = __ldcg(reinterpret_cast<const V*>(p));
+  return u.pk;
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ void stp(T* p, const Pack<T, VW>& x) {
+  *reinterpret_cast<Pack<T, VW>*>(p) = x;
+}
+
+// ------------------------------------------------------------------ partition view
+struct Part {
+  const int32_t* rb;     // G + 1 row boundaries
+  const int32_t* seg;    // 4 G: [C start, W start, S start, end) offsets into order
+  const int32_t* order;  // n row ids grouped per CTA by class
+};
+
+struct Graph {
+  const int32_t* row_ptr;
+  const int32_t* col;
+  int64_t n;
+  int64_t nnz;
+};
+
+// Sum of X over the neighbours of a row for this lane's VW columns, visiting
+// entries beg + t*step for t = 0, 1, ...; 4 independent gathers in flight.
+template <typename T, int K, int VW>
+__device__ __forceinline__ void gather_row(const int32_t* __restrict__ col, int beg, int end, int step,
+                                           const T* X, int lane_off, T (&acc)[VW]) {
+  int e = beg;
+  for (; e + 3 * step < end; e += 4 * step) {
+    const int32_t j0 = __ldg(col + e);
+    const int32_t j1 = __ldg(col + e + step);
+    const int32_t j2 = __ldg(col + e + 2 * step);
+    const int32_t j3 = __ldg(col + e + 3 * step);
+    const Pack<T, VW> a0 = ldp<T, VW>(X + (size_t)j0 * K + lane_off);
+    const Pack<T, VW> a1 = ldp<T, VW>(X + (size_t)j1 * K + lane_off);
+    const Pack<T, VW> a2 = ldp<T, VW>(X + (size_t)j2 * K + lane_off);
+    const Pack<T, VW> a3 = ldp<T, VW>(X + (size_t)j3 * K + lane_off);
+#pragma unroll
+    for (int v = 0; v < VW; ++v) acc[v] += (a0.v[v] + a1.v[v]) + (a2.v[v] + a3.v[v]);
+  }
+  for (; e < end; e += step) {
+    const int32_t j0 = __ldg(col + e);
+    const Pack<T, VW> a0 = ldp<T, VW>(X + (size_t)j0 * K + lane_off);
+#pragma unroll
+    for (int v = 0; v < VW; ++v) acc[v] += a0.v[v];
+  }
+}
+
+// Visit every row of this CTA's partition. For each row, exactly one
+// subgroup (lanes sl = 0..G-1 of it) calls op(row, deg, lane_off, nbr_sum)
+// where nbr_sum[v] = sum over neighbours j of X[j, lane_off + v]. `red`
+// must hold kBlock * VW values of T in shared memory.
+template <typename T, int K, class Op>
+__device__ __forceinline__ void for_rows_gather(const Graph& g, const Part& pt, const T* X,
+                                                T* red, Op& op) {
+  using C = Cfg<T, K>;
+  constexpr int VW = C::VW;
+  const int cta = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int sub = tid / C::G;        // subgroup id in CTA
+  const int sl = tid % C::G;         // lane in subgroup
+  const int lane_off = sl * VW;
+  const int c0 = pt.seg[4 * cta + 0], c1 = pt.seg[4 * cta + 1];
+  const int c2 = pt.seg[4 * cta + 2], c3 = pt.seg[4 * cta + 3];
+
+  // class C: whole CTA per row
+  for (int o = c0; o < c1; ++o) {
+    const int row = pt.order[o];
+    const int beg = g.row_ptr[row], end = g.row_ptr[row + 1];
+    T acc[VW];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) acc[v] = T(0);
+    gather_row<T, K, VW>(g.col, beg + sub, end, C::NSUB, X, lane_off, acc);
+#pragma unroll
+    for (int v = 0; v < VW; ++v) red[tid * VW + v] = acc[v];
+    __syncthreads();
+    if (sub == 0) {
+      for (int s = 1; s < C::NSUB; ++s)
+#pragma unroll
+        for (int v = 0; v < VW; ++v) acc[v] += red[(s * C::G + sl) * VW + v];
+      op(row, end - beg, lane_off, acc);
+    }
+    __syncthreads();
+  }
+  // class W: one warp per row
+  constexpr int NW = kBlock / 32;
+  for (int o = c1 + warp; o < c2; o += NW) {
+    const int row = pt.order[o];
+    const int beg = g.row_ptr[row], end = g.row_ptr[row + 1];
+    T acc[VW];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) acc[v] = T(0);
+    gather_row<T, K, VW>(g.col, beg + lane / C::G, end, C::SUB, X, lane_off, acc);
+#pragma unroll
+    for (int off = C::G; off < 32; off <<= 1)
+#pragma unroll
+      for (int v = 0; v < VW; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+    if (lane < C::G) op(row, end - beg, lane_off, acc);
+  }
+  // class S: one subgroup per row
+  for (int o = c2 + sub; o < c3; o += C::NSUB) {
+    const int row = pt.order[o];
+    const int beg = g.row_ptr[row], end = g.row_ptr[row + 1];
+    T acc[VW];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) acc[v] = T(0);
+    gather_row<T, K, VW>(g.col, beg, end, 1, X, lane_off, acc);
+    op(row, end - beg, lane_off, acc);
+  }
+}
+
+// Deterministic reduction of per-CTA partials part[g * K + c] (g < G) to
+// out[c] (shared memory, double). Every CTA obtains bit-identical results.
+template <int K>
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int G, double* s_tmp,
+                                                double* out) {
+  constexpr int J = kBlock / K;  // chunks per column
+  const int tid = threadIdx.x;
+  const int c = tid % K, j = tid / K;
+  double s = 0.0;
+  for (int g = j; g < G; g += J) s += __ldcg(part + (size_t)g * K + c);
+  s_tmp[tid] = s;
+  __syncthreads();
+  if (tid < K) {
+    double t = 0.0;
+    for (int jj = 0; jj < J; ++jj) t += s_tmp[jj * K + tid];
+    out[tid] = t;
+  }
+  __syncthreads();
+}
+
+// Per-thread column partials -> per-CTA column sums. Thread t owns columns
+// (t % G) * VW + v, v < VW, in both the gather layout (subgroup lane sl =
+// t % G) and the elementwise layout (vector index t + i * kBlock, since
+// kBlock * VW is a multiple of K). Sums lanes of equal t % G by a fixed
+// shuffle tree, then warps in order: deterministic. s_w holds
+// (kBlock / 32) * K doubles; dst (K values, shared or global) is written by
+// threads c < K.
+template <typename T, int K>
+__device__ __forceinline__ void cta_column_sums(const T (&val)[Cfg<T, K>::VW], double* s_w, double* dst) {
+  using C = Cfg<T, K>;
+  constexpr int VW = C::VW, G = C::G, NW = kBlock / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double a[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) a[v] = (double)val[v];
+#pragma unroll
+  for (int off = G; off < 32; off <<= 1)
+#pragma unroll
+    for (int v = 0; v < VW; ++v) a[v] += __shfl_xor_sync(0xffffffffu, a[v], off);
+  if (lane < G)
+#pragma unroll
+    for (int v = 0; v < VW; ++v) s_w[warp * K + lane * VW + v] = a[v];
+  __syncthreads();
+  if (tid < K) {
+    double t = 0.0;
+    for (int w = 0; w < NW; ++w) t += s_w[w * K + tid];
+    dst[tid] = t;
+  }
+  __syncthreads();
+}
+
+}  // namespace wl

@@ -1,0 +1,83 @@
+// Host-side launchers shared by the translation units of libwl.so.
+// Every kernel is launched from the translation unit that defines it; the
+// API code in wl_api.cu reaches them through these declarations.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wl_cg.cuh"
+#include "wl_common.cuh"
+#include "wl_lanczos.cuh"
+
+namespace wl {
+
+struct PartDev {
+  int G = 0;
+  int Tw = 0, Tc = 0;
+  int32_t* rb = nullptr;
+  int32_t* seg = nullptr;
+  int32_t* order = nullptr;
+  Part view() const { return Part{rb, seg, order}; }
+};
+
+// ---- wl_k_misc.cu
+// rb/seg/order for G CTAs with class thresholds Tw, Tc (arrays allocated by caller)
+cudaError_t launch_partition(const Graph& g, PartDev& p, cudaStream_t s);
+// flags[0] bit0: row_ptr not monotone / bounds; bit1: column out of range or
+// unsorted/duplicate; bit2: self loop; bit3: asymmetric
+cudaError_t launch_validate(const Graph& g, int* flags, cudaStream_t s);
+// dst (n x kb, contiguous, double or float) = scale * src[:, c0:c0+kb] (leading dim ld)
+cudaError_t launch_pack(const double* src, int64_t ld, int c0, int kb, int64_t n, double scale, void* dst,
+                        bool to_f32, cudaStream_t s);
+// W[:, c0:c0+K] = Df (.) V[:, c0:c0+K] - X  (X contiguous n x K)
+cudaError_t launch_apply_out(const double* V, int64_t ldv, const double* X, const double* Df, int64_t n, int K,
+                             int c0, double* W, int64_t ldw, cudaStream_t s);
+// W[:, c0:c0+K] = Df (.) V[:, c0:c0+K] - V[:, c0:c0+K] * 0 - X where Df = d (identity case uses gather)
+cudaError_t launch_fill(double* dst, double v, int64_t count, cudaStream_t s);
+cudaError_t launch_degree_vector(const Graph& g, double* out, cudaStream_t s);
+// out[c] = |X[:, c]|_2 (X contiguous n x K), deterministic
+cudaError_t launch_colnorms(const double* X, int64_t n, int K, double* out, cudaStream_t s);
+// Y[:, c] = X[:, c] * inv[c]
+cudaError_t launch_scale_cols(const double* X, int64_t n, int K, const double* inv, double* Y, cudaStream_t s);
+cudaError_t launch_f2d_acc(const float* src, double* dst, int64_t count, cudaStream_t s);
+// identity-function apply: W[:, c0:c0+K] = d (.) V - A V for V packed n x K
+cudaError_t launch_laplacian_apply(const Graph& g, const PartDev& p, const double* Vp, int K, int c0, double* W,
+                                   int64_t ldw, cudaStream_t s);
+
+// ---- wl_k_cg64.cu / wl_k_cg32.cu
+int cg_grid_f64(int K);  // cooperative grid size of the CG kernel (FP64, K columns)
+int cg_grid_f32(int K);
+void thresholds_f64(int K, int* Tw, int* Tc);  // class thresholds of Cfg<T, K>
+void thresholds_f32(int K, int* Tw, int* Tc);
+cudaError_t launch_cg_f64(int K, const CgArgs<double>& a, int G, cudaStream_t s);
+cudaError_t launch_cg_f32(int K, const CgArgs<float>& a, int G, cudaStream_t s);
+int res_grid(int K);
+cudaError_t launch_residual64(int K, const ResArgs& a, int G, cudaStream_t s);
+
+// ---- wl_k_lanczos.cu
+int lanczos_ext_grid();
+int lanczos_step_grid(int K);
+cudaError_t launch_lanczos_extreme(const LanczosExtArgs& a, int G, cudaStream_t s);
+cudaError_t launch_lanczos_step(int K, const LanczosStepArgs& a, int G, cudaStream_t s);
+cudaError_t launch_tridiag_exp(const TridiagArgs& a, int K, cudaStream_t s);
+cudaError_t launch_combine(int K, const CombineArgs& a, cudaStream_t s);
+
+// cooperative launch helper (all CTAs co-resident; required by grid_sync)
+template <typename Args>
+inline cudaError_t coop_launch(const void* fn, int G, const Args& a, cudaStream_t s) {
+  void* params[] = {const_cast<Args*>(&a)};
+  return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kBlock), params, 0, s);
+}
+
+// grid size: CTAs per SM from the occupancy calculator (capped) times SMs
+inline int coop_grid(const void* fn, int cap_per_sm) {
+  int dev = 0, sms = 0, nb = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kBlock, 0);
+  if (nb > cap_per_sm) nb = cap_per_sm;
+  if (nb < 1) nb = 1;
+  return nb * sms;
+}
+
+}  // namespace wl

@@ -1,0 +1,505 @@
+// Lanczos kernels (Sec. 4.1: f(A) v ~ |v| Q_k f(H_k) e_1 with the Lanczos
+// process for symmetric operators), all FP64.
+//
+//  lanczos_extreme : m Lanczos steps on Op = c0 I + cA A + cD D (k = 1) in one
+//                    persistent kernel, then the extreme eigenvalues of T_m by
+//                    Sturm-count bisection. Used for lambda_max(A) and for the
+//                    spectral-radius search of Z_mu (Prop. whe-we-converge).
+//  lanczos_step    : one step of K lockstep Lanczos recurrences on the walk
+//                    Laplacian, w = D_f (.) v - X (X = phi v from a CG solve) or
+//                    w = Op v; alpha, beta, and the next basis block.
+//  tridiag_exp     : y = exp(-tau T_m) e_1 for one (column, tau) per CTA by the
+//                    Chebyshev expansion of the exponential, whose coefficients
+//                    are scaled modified Bessel functions e^{-z} I_k(z)
+//                    (computed by Miller's backward recurrence).
+//  combine         : U(tau) = |u0| V_m y(tau), one read of the basis for all tau.
+#pragma once
+#include "wl_common.cuh"
+
+namespace wl {
+
+// ------------------------------------------------------------------ Sturm bisection
+// Number of eigenvalues of the symmetric tridiagonal (a[0..m), b[0..m-1)) that
+// are < x (LDL^T inertia).
+__device__ inline int sturm_count(const double* a, const double* b, int m, double x) {
+  int cnt = 0;
+  double q = a[0] - x;
+  if (q < 0.0) ++cnt;
+  for (int i = 1; i < m; ++i) {
+    const double qq = (q == 0.0) ? 1e-300 : q;
+    q = a[i] - x - b[i - 1] * b[i - 1] / qq;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// idx-th smallest eigenvalue (0-based) by bisection on [lo, hi].
+__device__ inline double tridiag_eig(const double* a, const double* b, int m, int idx) {
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < m ? fabs(b[i]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+  }
+  for (int it = 0; it < 100 && hi - lo > 1e-15 * fmax(fabs(lo), fabs(hi)) + 1e-300; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(a, b, m, mid) > idx) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// ------------------------------------------------------------------ extreme Lanczos
+struct LanczosExtArgs {
+  Graph g;
+  Part pt;
+  double c0, cA, cD;
+  double* v;       // 3 * n doubles: three rotating basis vectors
+  double* alpha;   // m
+  double* beta;    // m
+  double* part;    // 2 * G
+  double* out;     // [0] theta_max(T_m), [1] theta_max(T_{m-check}), [2] theta_min(T_m), [3] theta_min(T_{m-check}), [4] m_eff
+  GridBar* bar;
+  int m;
+  int check;
+  uint64_t seed;
+};
+
+__device__ inline double start_component(int64_t i, uint64_t seed) {
+  uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + seed;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return 1.0 + 0.25 * ((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+}
+
+#ifdef WL_LANCZOS_KERNELS
+__global__ void __launch_bounds__(kBlock) lanczos_extreme(LanczosExtArgs a) {
+  constexpr int K = 1;
+  constexpr int VW = 1;
+  constexpr int NW = kBlock / 32;
+  __shared__ double s_tmp[kBlock];
+  __shared__ double s_w[NW * K];
+  __shared__ double s_red[K];
+  __shared__ __align__(16) double s_gath[kBlock];
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int r0 = a.pt.rb[cta], r1 = a.pt.rb[cta + 1];
+  const int64_t n = a.g.n;
+  double* vp = a.v;          // v_{j-1}
+  double* vc = a.v + n;      // v_j
+  double* w = a.v + 2 * n;   // w
+  int buf = 0;
+
+  // start vector: positive, mildly perturbed, normalised
+  {
+    double acc[1] = {0.0};
+    for (int i = r0 + tid; i < r1; i += kBlock) {
+      const double x = start_component(i, a.seed);
+      w[i] = x;
+      vp[i] = 0.0;
+      acc[0] += x * x;
+    }
+    cta_column_sums<double, K>(acc, s_w, a.part + (size_t)buf * G + cta);
+  }
+  if (!grid_sync(a.bar, G)) return;
+  reduce_partials<K>(a.part + (size_t)buf * G, G, s_tmp, s_red);
+  buf ^= 1;
+  {
+    const double inv = 1.0 / sqrt(s_red[0]);
+    for (int i = r0 + tid; i < r1; i += kBlock) vc[i] = __ldcg(w + i) * inv;
+  }
+  if (!grid_sync(a.bar, G)) return;
+  double beta_prev = 0.0;
+  int m_eff = a.m;
+  for (int j = 0; j < a.m; ++j) {
+    // w = Op v_j ; alpha = (v_j, w)
+    double acc[1] = {0.0};
+    auto op = [&](int row, int deg, int lane_off, const double (&nb)[VW]) {
+      const double vi = __ldcg(vc + row);
+      const double wi = a.c0 * vi + a.cA * nb[0] + a.cD * (double)deg * vi;
+      w[row] = wi;
+      acc[0] += vi * wi;
+      (void)lane_off;
+    };
+    for_rows_gather<double, K>(a.g, a.pt, vc, s_gath, op);
+    cta_column_sums<double, K>(acc, s_w, a.part + (size_t)buf * G + cta);
+    if (!grid_sync(a.bar, G)) return;
+    reduce_partials<K>(a.part + (size_t)buf * G, G, s_tmp, s_red);
+    buf ^= 1;
+    const double alpha = s_red[0];
+    // w -= alpha v_j + beta_{j-1} v_{j-1}; beta = |w|
+    double acc2[1] = {0.0};
+    for (int i = r0 + tid; i < r1; i += kBlock) {
+      const double wi = __ldcg(w + i) - alpha * __ldcg(vc + i) - beta_prev * __ldcg(vp + i);
+      w[i] = wi;
+      acc2[0] += wi * wi;
+    }
+    cta_column_sums<double, K>(acc2, s_w, a.part + (size_t)buf * G + cta);
+    if (!grid_sync(a.bar, G)) return;
+    reduce_partials<K>(a.part + (size_t)buf * G, G, s_tmp, s_red);
+    buf ^= 1;
+    const double beta = sqrt(s_red[0]);
+    if (cta == 0 && tid == 0) {
+      a.alpha[j] = alpha;
+      a.beta[j] = beta;
+    }
+    if (!(beta > 1e-13 * (fabs(alpha) + beta_prev + 1e-300)) || j + 1 == a.m) {
+      m_eff = j + 1;
+      break;
+    }
+    // v_{j+1} = w / beta into the v_{j-1} slot, then rotate
+    const double inv = 1.0 / beta;
+    for (int i = r0 + tid; i < r1; i += kBlock) vp[i] = __ldcg(w + i) * inv;
+    double* t = vp; vp = vc; vc = t;
+    beta_prev = beta;
+    if (!grid_sync(a.bar, G)) return;
+  }
+  if (cta == 0) {
+    __syncthreads();
+    if (tid < 4) {
+      const int mm = (tid & 1) ? (m_eff > a.check ? m_eff - a.check : m_eff) : m_eff;
+      double* al = a.alpha;
+      double* be = a.beta;
+      const double th = (tid < 2) ? tridiag_eig(al, be, mm, mm - 1) : tridiag_eig(al, be, mm, 0);
+      a.out[tid] = th;
+    }
+    if (tid == 0) a.out[4] = (double)m_eff;
+  }
+}
+
+#endif  // WL_LANCZOS_KERNELS
+
+// ------------------------------------------------------------------ one Lanczos step on L
+struct LanczosStepArgs {
+  Graph g;
+  Part pt;
+  const double* vj;     // n x K
+  const double* vjm1;   // n x K (ignored when first)
+  const double* X;      // n x K: phi v_j from the inner solve (mode 0)
+  const double* Df;     // n walk degrees (mode 0)
+  double c0, cA, cD;    // mode 1: w = Op v_j
+  double* vjp1;         // n x K out
+  double* Ta;           // K x ldT alphas
+  double* Tb;           // K x ldT betas
+  int* done;            // K flags (in/out)
+  double* part;         // 2 * G * K
+  GridBar* bar;
+  int j;                // step index (0-based); T entries written at [c * ldT + j]
+  int ldT;
+  int mode;             // 0: w = Df v - X ; 1: w = Op v (gather)
+};
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) lanczos_step(LanczosStepArgs a) {
+  using C = Cfg<double, K>;
+  constexpr int VW = C::VW;
+  constexpr int NW = kBlock / 32;
+  __shared__ double s_tmp[kBlock];
+  __shared__ double s_w[NW * K];
+  __shared__ double s_red[K];
+  __shared__ double s_alpha[K], s_bprev[K];
+  __shared__ __align__(16) double s_gath[kBlock * VW];
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int r0 = a.pt.rb[cta], r1 = a.pt.rb[cta + 1];
+  const size_t v0 = (size_t)r0 * K / VW, v1 = (size_t)r1 * K / VW;
+  const int mycol = (tid % C::G) * VW;
+  const bool first = (a.j == 0);
+  double acc[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) acc[v] = 0.0;
+  if (a.mode == 0) {
+#pragma unroll 2
+    for (size_t e = v0 + tid; e < v1; e += kBlock) {
+      const size_t row = e * VW / K;
+      const double d = __ldg(a.Df + row);
+      const Pack<double, VW> vv = ldp<double, VW>(a.vj + e * VW);
+      const Pack<double, VW> xx = ldp<double, VW>(a.X + e * VW);
+      Pack<double, VW> ww;
+#pragma unroll
+      for (int v = 0; v < VW; ++v) {
+        ww.v[v] = d * vv.v[v] - xx.v[v];
+        acc[v] += vv.v[v] * ww.v[v];
+      }
+      stp<double, VW>(a.vjp1 + e * VW, ww);
+    }
+  } else {
+    auto op = [&](int row, int deg, int lane_off, const double (&nb)[VW]) {
+      const size_t o = (size_t)row * K + lane_off;
+      const Pack<double, VW> vv = ldp<double, VW>(a.vj + o);
+      Pack<double, VW> ww;
+#pragma unroll
+      for (int v = 0; v < VW; ++v) {
+        ww.v[v] = a.c0 * vv.v[v] + a.cA * nb[v] + a.cD * (double)deg * vv.v[v];
+        acc[v] += vv.v[v] * ww.v[v];
+      }
+      stp<double, VW>(a.vjp1 + o, ww);
+    };
+    for_rows_gather<double, K>(a.g, a.pt, a.vj, s_gath, op);
+  }
+  cta_column_sums<double, K>(acc, s_w, a.part + (size_t)cta * K);
+  if (!grid_sync(a.bar, G)) return;
+  reduce_partials<K>(a.part, G, s_tmp, s_red);
+  if (tid < K) {
+    const int dn = a.done[tid];
+    s_alpha[tid] = dn ? 0.0 : s_red[tid];
+    s_bprev[tid] = (first || dn) ? 0.0 : a.Tb[tid * a.ldT + a.j - 1];
+  }
+  __syncthreads();
+  double al[VW], bp[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) {
+    al[v] = s_alpha[mycol + v];
+    bp[v] = s_bprev[mycol + v];
+    acc[v] = 0.0;
+  }
+#pragma unroll 2
+  for (size_t e = v0 + tid; e < v1; e += kBlock) {
+    Pack<double, VW> ww = ldp<double, VW>(a.vjp1 + e * VW);
+    const Pack<double, VW> vv = ldp<double, VW>(a.vj + e * VW);
+    Pack<double, VW> vm;
+    if (!first) vm = ldp<double, VW>(a.vjm1 + e * VW);
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      ww.v[v] -= al[v] * vv.v[v];
+      if (!first) ww.v[v] -= bp[v] * vm.v[v];
+      acc[v] += ww.v[v] * ww.v[v];
+    }
+    stp<double, VW>(a.vjp1 + e * VW, ww);
+  }
+  cta_column_sums<double, K>(acc, s_w, a.part + (size_t)G * K + (size_t)cta * K);
+  if (!grid_sync(a.bar, G)) return;
+  reduce_partials<K>(a.part + (size_t)G * K, G, s_tmp, s_red);
+  __shared__ double s_inv[K];
+  if (tid < K) {
+    const double b = sqrt(s_red[tid]);
+    const int dn = a.done[tid];
+    // invariant subspace reached (lucky breakdown): the column is exact
+    const bool brk = dn || !(b > 1e-13 * (fabs(s_alpha[tid]) + s_bprev[tid] + 1e-300));
+    s_inv[tid] = brk ? 0.0 : 1.0 / b;
+    if (cta == 0) {
+      a.Ta[tid * a.ldT + a.j] = s_alpha[tid];
+      a.Tb[tid * a.ldT + a.j] = brk ? 0.0 : b;
+      if (brk && !dn) a.done[tid] = 2;  // 2: converged by breakdown at this step
+    }
+  }
+  __syncthreads();
+  double iv[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) iv[v] = s_inv[mycol + v];
+  for (size_t e = v0 + tid; e < v1; e += kBlock) {
+    Pack<double, VW> ww = ldp<double, VW>(a.vjp1 + e * VW);
+#pragma unroll
+    for (int v = 0; v < VW; ++v) ww.v[v] *= iv[v];
+    stp<double, VW>(a.vjp1 + e * VW, ww);
+  }
+}
+
+// ------------------------------------------------------------------ exp of the tridiagonal
+struct TridiagArgs {
+  const double* Ta;   // K x ldT
+  const double* Tb;   // K x ldT
+  const int* mcol;    // K: steps available per column
+  const double* taus; // ntau
+  double* y;          // K x ntau x ldT (out)
+  double* yprev;      // K x ntau x ldT (previous result, updated in place after err)
+  const int* mprev;   // K: length of yprev (0: none)
+  double* err;        // K x ntau: |y - [yprev; 0]|_2
+  int ldT;
+  int ntau;
+  int psd;            // 1: operator is PSD, use 0 as lower spectral bound
+  int max_terms;      // cap of the expansion length
+};
+
+constexpr int kTridiagMax = 512;    // max Lanczos steps handled per column
+constexpr int kChebMax = 2048;      // max Chebyshev terms (|tau| (hi - lo) / 2 up to ~4e4)
+
+#ifdef WL_LANCZOS_KERNELS
+__global__ void __launch_bounds__(kBlock) tridiag_exp(TridiagArgs a) {
+  __shared__ double s_a[kTridiagMax], s_b[kTridiagMax];
+  __shared__ double s_v[3][kTridiagMax];
+  __shared__ double s_c[kChebMax];
+  __shared__ double s_lohi[2];
+  __shared__ int s_N;
+  const int c = blockIdx.x, t = blockIdx.y, tid = threadIdx.x;
+  const int m = a.mcol[c];
+  const double tau = a.taus[t];
+  for (int i = tid; i < m; i += kBlock) {
+    s_a[i] = a.Ta[c * a.ldT + i];
+    s_b[i] = (i + 1 < m) ? a.Tb[c * a.ldT + i] : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < m; ++i) {
+      const double r = (i > 0 ? fabs(s_b[i - 1]) : 0.0) + fabs(s_b[i]);
+      lo = fmin(lo, s_a[i] - r);
+      hi = fmax(hi, s_a[i] + r);
+    }
+    if (a.psd) lo = fmax(lo, 0.0);
+    if (hi < lo) hi = lo;
+    s_lohi[0] = lo;
+    s_lohi[1] = hi;
+    // coefficients of exp(-tau x) on [lo, hi] in Chebyshev polynomials of
+    // t = (x - mid) / half: exp(-tau x) = exp(-tau mid) exp(-z t), z = tau half,
+    // exp(-z t) = I_0(|z|) + 2 sum_k s^k I_k(|z|) T_k(t), s = -sign(z).
+    const double half = 0.5 * (hi - lo);
+    const double zz = fabs(tau) * half;
+    int N = (int)ceil(sqrt(90.0 * zz) + 30.0);
+    if (N > a.max_terms - 1) N = a.max_terms - 1;
+    if (N > kChebMax - 1) N = kChebMax - 1;
+    if (zz < 1e-30) {  // exp(-z t) = 1 + O(1e-30) on [-1, 1]
+      s_c[0] = 1.0;
+      N = 0;
+    } else {
+      // Miller: backward recurrence I_{k-1} = (2k / z) I_k + I_{k+1}, normalised
+      // by I_0 + 2 sum I_k = e^z (so the stored values are e^{-z} I_k).
+      const int M0 = 2 * N + 60;
+      double ikp1 = 0.0, ik = 1e-280;
+      for (int k = M0; k >= 1; --k) {
+        const double ikm1 = (2.0 * k / zz) * ik + ikp1;
+        ikp1 = ik;
+        ik = ikm1;
+        if (k - 1 <= N) s_c[k - 1] = ik;
+        if (fabs(ik) > 1e250) {
+          ik *= 1e-250;
+          ikp1 *= 1e-250;
+          for (int q = k - 1; q <= N; ++q) s_c[q] *= 1e-250;
+        }
+      }
+      // ik now holds I_0 (scaled); complete the normalisation sum with the
+      // tail k > N from the stored values only (the tail beyond N is < 1e-18).
+      double S = s_c[0];
+      for (int k = 1; k <= N; ++k) S += 2.0 * s_c[k];
+      const double sgn = (tau >= 0.0) ? -1.0 : 1.0;
+      double sk = 1.0;
+      for (int k = 0; k <= N; ++k) {
+        s_c[k] = (k == 0 ? 1.0 : 2.0) * sk * (s_c[k] / S);
+        sk *= sgn;
+      }
+    }
+    s_N = N;
+  }
+  __syncthreads();
+  const double lo = s_lohi[0], hi = s_lohi[1];
+  const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+  const double zz = fabs(tau) * half;
+  const double pref = exp(-tau * mid + zz);
+  const int N = s_N;
+  const double ih = (half > 0.0) ? 1.0 / half : 0.0;
+  // Chebyshev three-term recurrence on vectors: v0 = e1, v1 = T~ e1,
+  // v_{k+1} = 2 T~ v_k - v_{k-1}, T~ = (T - mid I) / half
+  constexpr int RPT = kTridiagMax / kBlock;  // rows per thread
+  double yacc[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int i = tid + q * kBlock;
+    yacc[q] = 0.0;
+    if (i < m) {
+      s_v[0][i] = (i == 0) ? 1.0 : 0.0;
+      yacc[q] = s_c[0] * s_v[0][i];
+    }
+  }
+  __syncthreads();
+  int pv = 0, cv = 0, nv = 1;
+  if (N >= 1) {
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int i = tid + q * kBlock;
+      if (i < m) {
+        double s = (s_a[i] - mid) * s_v[0][i];
+        if (i > 0) s += s_b[i - 1] * s_v[0][i - 1];
+        if (i + 1 < m) s += s_b[i] * s_v[0][i + 1];
+        s_v[1][i] = s * ih;
+        yacc[q] += s_c[1] * s_v[1][i];
+      }
+    }
+    __syncthreads();
+    pv = 0; cv = 1; nv = 2;
+    for (int k = 2; k <= N; ++k) {
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int i = tid + q * kBlock;
+        if (i < m) {
+          double s = (s_a[i] - mid) * s_v[cv][i];
+          if (i > 0) s += s_b[i - 1] * s_v[cv][i - 1];
+          if (i + 1 < m) s += s_b[i] * s_v[cv][i + 1];
+          const double nxt = 2.0 * s * ih - s_v[pv][i];
+          s_v[nv][i] = nxt;
+          yacc[q] += s_c[k] * nxt;
+        }
+      }
+      __syncthreads();
+      const int tmp = pv; pv = cv; cv = nv; nv = tmp;
+    }
+  }
+  // write y and the change against the previous result
+  double* yo = a.y + ((size_t)c * a.ntau + t) * a.ldT;
+  double* yp = a.yprev + ((size_t)c * a.ntau + t) * a.ldT;
+  const int mp = a.mprev[c];
+  double e2 = 0.0;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int i = tid + q * kBlock;
+    if (i < m) {
+      const double yi = pref * yacc[q];
+      yo[i] = yi;
+      const double d = yi - (i < mp ? yp[i] : 0.0);
+      e2 += d * d;
+    }
+  }
+  s_v[0][tid] = e2;  // reuse (m may be < kBlock, slots are free after the loop)
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int i = 0; i < kBlock; ++i) s += s_v[0][i];
+    a.err[c * a.ntau + t] = sqrt(s);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int i = tid + q * kBlock;
+    if (i < m) yp[i] = yo[i];
+  }
+}
+
+#endif  // WL_LANCZOS_KERNELS
+
+// ------------------------------------------------------------------ U = |u0| V y
+struct CombineArgs {
+  const double* basis;  // m blocks of n x K (block j at basis + j n K)
+  const double* y;      // K x ntau x ldT
+  const int* mcol;      // K: steps per column
+  const double* nrm;    // K: |u0_c|
+  double* out;          // ntau blocks, element (t, i, c) at out[t * tstride + i * ld + c0 + c]
+  int64_t n;
+  int64_t ld;
+  int64_t tstride;
+  int c0;
+  int ldT;
+  int ntau;
+};
+
+constexpr int kMaxTau = 8;
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) combine(CombineArgs a) {
+  const size_t total = (size_t)a.n * K;
+  for (size_t e = (size_t)blockIdx.x * kBlock + threadIdx.x; e < total; e += (size_t)gridDim.x * kBlock) {
+    const int c = (int)(e % K);
+    const size_t i = e / K;
+    const int m = a.mcol[c];
+    double acc[kMaxTau];
+#pragma unroll
+    for (int t = 0; t < kMaxTau; ++t) acc[t] = 0.0;
+    const double* yc = a.y + (size_t)c * a.ntau * a.ldT;
+    for (int j = 0; j < m; ++j) {
+      const double vij = __ldcs(a.basis + (size_t)j * total + e);
+#pragma unroll
+      for (int t = 0; t < kMaxTau; ++t)
+        if (t < a.ntau) acc[t] += vij * __ldg(yc + (size_t)t * a.ldT + j);
+    }
+    const double s = a.nrm[c];
+    for (int t = 0; t < a.ntau; ++t) a.out[(size_t)t * a.tstride + i * a.ld + a.c0 + c] = s * acc[t];
+  }
+}
+
+}  // namespace wl

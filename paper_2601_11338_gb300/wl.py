@@ -1,0 +1,196 @@
+"""Thin ctypes binding of libwl.so (include/wl.h), same names as the C ABI.
+
+Argument marshalling only: every computation runs in the CUDA library. Array
+arguments may be numpy arrays (host) or torch tensors (host or CUDA); they
+are passed as raw pointers. The library must be built (see `build.py`); if
+it is missing or fails to load, every call raises - there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+WL_OK = 0
+WL_ERR_INVALID_ARG = -1
+WL_ERR_NOT_SYMMETRIC = -2
+WL_ERR_SELF_LOOP = -3
+WL_ERR_UNSORTED = -4
+WL_ERR_ALPHA_RANGE = -5
+WL_ERR_NOT_SPD = -6
+WL_ERR_NONFINITE = -7
+WL_ERR_NO_CONVERGENCE = -8
+WL_ERR_TIMEOUT = -9
+WL_ERR_OOM = -10
+WL_ERR_CUDA = -11
+WL_ERR_UNSUPPORTED = -12
+
+WL_ALLWALK, WL_NBT, WL_BTDW = 0, 1, 2
+WL_F_RESOLVENT, WL_F_EXP, WL_F_IDENTITY = 0, 1, 2
+WL_FP64, WL_REFINED = 0, 1
+
+
+class wl_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p)]
+
+
+class wl_params(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_int), ("alpha", ctypes.c_double), ("alpha_rel", ctypes.c_double),
+                ("beta", ctypes.c_double), ("mu", ctypes.c_double), ("prec", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
+                ("outer_tol", ctypes.c_double), ("stream", ctypes.c_void_p)]
+
+
+class wl_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("refinements", ctypes.c_int), ("rel_res", ctypes.c_double), ("time_ms", ctypes.c_double),
+                ("nnz_rhs_iters", ctypes.c_double), ("bytes_alg", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("mu", ctypes.c_double),
+                ("rho", ctypes.c_double), ("lambda_max", ctypes.c_double), ("launches", ctypes.c_int),
+                ("k_cg_launches", ctypes.c_int), ("k_cg_iters", ctypes.c_int), ("k_cg_ms", ctypes.c_double),
+                ("k_cg_bytes", ctypes.c_double), ("k_res_launches", ctypes.c_int), ("k_res_ms", ctypes.c_double),
+                ("k_lan_launches", ctypes.c_int), ("k_lan_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class WLError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status}) {last_error()}")
+
+
+_lib = None
+LIB_PATH = _build.LIB
+
+
+def lib():
+    """Load libwl.so (building it first if its sources are newer)."""
+    global _lib
+    if _lib is None:
+        if _build.needs_build():
+            _build.build()
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        L.wl_build.argtypes = [ctypes.POINTER(wl_csr), c_int, ctypes.POINTER(wl_params),
+                               ctypes.POINTER(vp), ctypes.POINTER(wl_stats)]
+        L.wl_set_params.argtypes = [vp, ctypes.POINTER(wl_params)]
+        L.wl_degrees.argtypes = [vp, vp, ctypes.POINTER(wl_stats)]
+        L.wl_apply.argtypes = [vp, vp, i64, c_int, vp, i64, ctypes.POINTER(wl_stats)]
+        L.wl_expmv.argtypes = [vp, vp, i64, c_int, vp, c_int, vp, i64, ctypes.POINTER(wl_stats)]
+        L.wl_trace.argtypes = [vp, c_int, ctypes.c_uint64, vp, vp, vp, ctypes.POINTER(wl_stats)]
+        L.wl_set_warm_start.argtypes = [vp, vp]
+        L.wl_get_info.argtypes = [vp, ctypes.POINTER(wl_stats)]
+        L.wl_destroy.argtypes = [vp]
+        L.wl_destroy.restype = None
+        L.wl_status_string.argtypes = [c_int]
+        L.wl_status_string.restype = ctypes.c_char_p
+        L.wl_last_error.restype = ctypes.c_char_p
+        for name in ("wl_build", "wl_set_params", "wl_degrees", "wl_apply", "wl_expmv", "wl_trace",
+                     "wl_set_warm_start", "wl_get_info"):
+            getattr(L, name).restype = c_int
+        _lib = L
+    return _lib
+
+
+def status_string(s):
+    return lib().wl_status_string(int(s)).decode()
+
+
+def last_error():
+    return lib().wl_last_error().decode()
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (no copy)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def make_params(f=WL_F_RESOLVENT, alpha=0.0, alpha_rel=0.0, beta=0.0, mu=0.0, prec=WL_FP64, tol=0.0,
+                max_iter=0, max_outer=0, outer_tol=0.0, stream=None):
+    return wl_params(f, alpha, alpha_rel, beta, mu, prec, tol, max_iter, max_outer, outer_tol, stream)
+
+
+class Handle:
+    """Owns a wl_handle*; keeps references to nothing else (the library copies the graph)."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        if getattr(self, "ptr", None):
+            lib().wl_destroy(self.ptr)
+            self.ptr = None
+
+
+def _check(rc, where, allow=()):
+    if rc != WL_OK and rc not in allow:
+        raise WLError(rc, where)
+    return rc
+
+
+def wl_build(row_ptr, col_idx, n, nnz, variant, params, stats=None):
+    A = wl_csr(n, nnz, _ptr(row_ptr), _ptr(col_idx))
+    h = ctypes.c_void_p()
+    st = stats if stats is not None else wl_stats()
+    _check(lib().wl_build(ctypes.byref(A), variant, ctypes.byref(params), ctypes.byref(h), ctypes.byref(st)),
+           "wl_build")
+    return Handle(h)
+
+
+def wl_set_params(h, params):
+    _check(lib().wl_set_params(h.ptr, ctypes.byref(params)), "wl_set_params")
+
+
+def wl_degrees(h, Df, stats=None, allow=()):
+    st = stats if stats is not None else wl_stats()
+    return _check(lib().wl_degrees(h.ptr, _ptr(Df), ctypes.byref(st)), "wl_degrees", allow)
+
+
+def wl_apply(h, V, ldv, k, W, ldw, stats=None, allow=()):
+    st = stats if stats is not None else wl_stats()
+    return _check(lib().wl_apply(h.ptr, _ptr(V), ldv, k, _ptr(W), ldw, ctypes.byref(st)), "wl_apply", allow)
+
+
+def wl_expmv(h, U0, ldu, k, taus, U, ldo, stats=None, allow=()):
+    st = stats if stats is not None else wl_stats()
+    taus = np.ascontiguousarray(taus, dtype=np.float64)
+    return _check(lib().wl_expmv(h.ptr, _ptr(U0), ldu, k, taus.ctypes.data, len(taus), _ptr(U), ldo,
+                                 ctypes.byref(st)), "wl_expmv", allow)
+
+
+def wl_trace(h, M, seed, omega_out=None, stats=None):
+    st = stats if stats is not None else wl_stats()
+    est = ctypes.c_double()
+    err = ctypes.c_double()
+    _check(lib().wl_trace(h.ptr, M, seed, ctypes.byref(est), ctypes.byref(err), _ptr(omega_out),
+                          ctypes.byref(st)), "wl_trace")
+    return est.value, err.value
+
+
+def wl_set_warm_start(h, x0):
+    _check(lib().wl_set_warm_start(h.ptr, _ptr(x0)), "wl_set_warm_start")
+
+
+def wl_get_info(h):
+    st = wl_stats()
+    _check(lib().wl_get_info(h.ptr, ctypes.byref(st)), "wl_get_info")
+    return st

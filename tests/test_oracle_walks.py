@@ -240,3 +240,35 @@ def test_first_singular_t_is_inverse_rho(mu):
     assert abs(t * rho - 1) < 1e-9
     if mu == 0.0:
         assert abs(rho - spectral.lambda_max(A)) < 1e-10
+
+
+# ---------------------------------------------------------------- CPU Krylov restatement (Sec. 4)
+@pytest.mark.parametrize("mu", [0.0, 1.0])
+def test_cpu_krylov_matches_dense_definitions(mu):
+    """CG on M (Sec. 4.2) and Lanczos exp(-tau T_m) (Sec. 4.1) reproduce the
+    dense definitions: D_f = phi 1, L V, exp(-tau L) u0."""
+    from oracle import krylov
+    g = wlgen.erdos_renyi(300, 6, 21)
+    A = dense(g)
+    alpha = 0.5 / spectral.rho_companion(A, mu)
+    phi = walks.phi_resolvent_closed(A, mu, alpha)
+    L = walks.walk_laplacian(phi)
+    op = krylov.ResolventLaplacian(krylov.adjacency(g.row_ptr, g.col_idx, g.n), mu, alpha, tol=1e-14)
+    np.testing.assert_allclose(op.Df, walks.walk_degrees(phi), rtol=1e-12)
+    V = np.random.default_rng(0).standard_normal((g.n, 3))
+    np.testing.assert_allclose(op.apply(V), L @ V, rtol=0, atol=1e-11 * np.abs(L @ V).max())
+    u0 = np.zeros(g.n); u0[4] = 1.0
+    U, m = krylov.lanczos_expmv(op.apply, u0, [0.1, 1.0, 10.0], tol=1e-12)
+    want = walks.diffusion(L, u0[:, None], [0.1, 1.0, 10.0])
+    for u, w in zip(U, want):
+        assert np.linalg.norm(u - w[:, 0]) <= 1e-10 * np.linalg.norm(w)
+    assert 0 < m <= 300
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.5, 1.0])
+def test_sparse_companion_radius_matches_dense(mu):
+    from oracle import krylov
+    g = wlgen.erdos_renyi(200, 6, 22)
+    A = dense(g)
+    got = krylov.rho_companion_sparse(krylov.adjacency(g.row_ptr, g.col_idx, g.n), mu)
+    assert abs(got - spectral.rho_companion(A, mu)) <= 1e-8 * got
