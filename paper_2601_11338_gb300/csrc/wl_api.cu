@@ -17,6 +17,7 @@
 
 #include "wl.h"
 #include "wl_host.h"
+#include "wl_trace.cuh"
 
 using namespace wl;
 
@@ -129,6 +130,7 @@ struct wl_handle {
   Buf stage_a, stage_b;   // host <-> device staging
   Buf packV, packX;
   Buf lan;                // Lanczos extreme vectors
+  Buf omega, gram;        // sketch and Gram workspace
   double* h_pin = nullptr;  // pinned host scratch (4096 doubles)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // per-call kernel timing: event pairs recorded on the stream around launches
@@ -612,7 +614,7 @@ void free_handle(wl_handle* h) {
   }
   Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
                  &h->r32, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
-                 &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->lan};
+                 &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->lan, &h->omega, &h->gram};
   for (Buf* b : bufs) release(*b);
   if (h->bar) cudaFree(h->bar);
   if (h->h_pin) cudaFreeHost(h->h_pin);
@@ -1038,8 +1040,86 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
 }
 
 int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, uint16_t* omega_out, wl_stats* st) {
-  (void)h; (void)M; (void)seed; (void)est; (void)err_est; (void)omega_out; (void)st;
-  return WL_ERR_UNSUPPORTED;
+  if (!h || !est || !err_est || M < 2 || M > kMaxSketch) return WL_ERR_INVALID_ARG;
+  if (h->prm.f != WL_F_RESOLVENT) return WL_ERR_UNSUPPORTED;
+  SolveInfo info;
+  begin_timer(h);
+  *est = 0.0;
+  *err_est = 0.0;
+  if (h->n == 0) {
+    fill_stats(h, st, info, WL_OK, end_timer(h), 0);
+    return WL_OK;
+  }
+  const int64_t n = h->n;
+  int K = 1;
+  while (K < M) K <<= 1;
+  int rc = WL_OK;
+  do {
+    const size_t nk = (size_t)n * K;
+    if ((rc = ensure(h->omega, (size_t)n * M * sizeof(uint16_t))) != WL_OK) break;
+    if ((rc = ensure(h->x, nk * 4)) != WL_OK) break;      // Y (FP32)
+    if ((rc = ensure(h->r32, nk * 4)) != WL_OK) break;    // right-hand side / residual
+    if ((rc = ensure(h->p, nk * 4)) != WL_OK) break;
+    if ((rc = ensure(h->q, nk * 4)) != WL_OK) break;
+    const int Gg = gram_grid(n);
+    if ((rc = ensure(h->gram, (size_t)Gg * 2 * kMaxSketch * kMaxSketch * 4 + 2 * kMaxSketch * kMaxSketch * 8 +
+                                 128 * 8)) != WL_OK) break;
+    uint16_t* omega = (uint16_t*)h->omega.p;
+    float* partial = (float*)h->gram.p;
+    double* gout = (double*)((char*)h->gram.p + (size_t)Gg * 2 * kMaxSketch * kMaxSketch * 4);
+    double* core = gout + 2 * kMaxSketch * kMaxSketch;
+    counted(h, 2);
+    cudaError_t e = launch_philox_sketch(omega, n, M, seed, S(h));
+    if (e == cudaSuccess) e = launch_sketch_rhs(omega, n, M, K, h->a_scale, (float*)h->r32.p, S(h));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->x.p, 0, nk * 4, S(h));
+    if (e != cudaSuccess) { rc = set_cuda_error(e, "sketch"); break; }
+    // Y = M^{-1} (a Omega) in FP32 lockstep CG
+    const int G = cg_grid_f32(K);
+    int Tw, Tc;
+    thresholds_f32(K, &Tw, &Tc);
+    PartDev* pd;
+    if ((rc = get_part(h, G, Tw, Tc, &pd)) != WL_OK) break;
+    if ((rc = ensure(h->part, (size_t)G * 64 * 2 * 8 + 1024)) != WL_OK) break;
+    Smalls sm = smalls(h);
+    const double tol = std::max(h->prm.tol, 1e-7);
+    CgArgs<float> a{h->g, pd->view(), (float*)h->x.p, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
+                    h->ca, h->cA, h->cD, nullptr, nullptr, (double*)h->part.p, sm.gamma, sm.status,
+                    h->bar, h->prm.max_iter, tol * tol, sm.iters};
+    if ((rc = reset_bar(h)) != WL_OK) break;
+    const int pc = prof_begin(h, kCatCG);
+    e = launch_cg_f32(K, a, G, S(h));
+    prof_end(h, pc);
+    if (e != cudaSuccess) { rc = set_cuda_error(e, "cg_f32"); break; }
+    counted(h, 3);
+    e = launch_gram(omega, (const float*)h->x.p, n, M, K, partial, Gg, gout, S(h));
+    if (e == cudaSuccess) e = launch_nys_core(gout, M, core, S(h));
+    if (e != cudaSuccess) { rc = set_cuda_error(e, "gram/core"); break; }
+    double* hp = h->h_pin;
+    WL_CU(cudaMemcpyAsync(hp, core, 8 * 8, cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaMemcpyAsync(hp + 16, sm.iters, 4, cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaMemcpyAsync(hp + 17, sm.status, 64 * 4, cudaMemcpyDeviceToHost, S(h)));
+    const int berr = check_bar(h);
+    if (berr) { rc = berr; break; }
+    const int it = *(const int*)(hp + 16);
+    const int* cst = (const int*)(hp + 17);
+    info.iters += it;
+    info.cg_iters += it;
+    info.nnz_rhs += (double)it * h->nnz * K;
+    info.bytes += (double)it * alg_bytes_per_iter(h, K, 4);
+    for (int c = 0; c < M; ++c)
+      if (cst[c] != 0 && info.status == WL_OK) info.status = cst[c];
+    if (hp[2] != 0.0) { rc = WL_ERR_NOT_SPD; break; }
+    *est = hp[0];
+    *err_est = hp[1];
+    if (omega_out) {
+      e = cudaMemcpyAsync(omega_out, omega, (size_t)n * M * sizeof(uint16_t), cudaMemcpyDefault, S(h));
+      if (e != cudaSuccess) { rc = set_cuda_error(e, "copy omega"); break; }
+    }
+  } while (0);
+  const double ms = end_timer(h);
+  if (rc == WL_OK) rc = info.status;
+  fill_stats(h, st, info, rc, ms, 0);
+  return rc;
 }
 
 void wl_destroy(wl_handle* h) {

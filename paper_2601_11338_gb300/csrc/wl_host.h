@@ -62,6 +62,16 @@ cudaError_t launch_lanczos_step(int K, const LanczosStepArgs& a, int G, cudaStre
 cudaError_t launch_tridiag_exp(const TridiagArgs& a, int K, cudaStream_t s);
 cudaError_t launch_combine(int K, const CombineArgs& a, cudaStream_t s);
 
+// ---- wl_k_trace.cu
+cudaError_t launch_philox_sketch(uint16_t* omega, int64_t n, int M, uint64_t seed, cudaStream_t s);
+cudaError_t launch_sketch_rhs(const uint16_t* omega, int64_t n, int M, int K, double a, float* B, cudaStream_t s);
+int gram_grid(int64_t n);
+// H = Omega^T Y and G = Y^T Y into out (128 x 64 doubles); partial holds G x 128 x 64 floats
+cudaError_t launch_gram(const uint16_t* omega, const float* Y, int64_t n, int M, int K, float* partial, int G,
+                        double* out, cudaStream_t s);
+// out[0] estimate, out[1] error estimate, out[2] status, out[8 + i] = t_i
+cudaError_t launch_nys_core(const double* gram, int M, double* out, cudaStream_t s);
+
 // cooperative launch helper (all CTAs co-resident; required by grid_sync)
 template <typename Args>
 inline cudaError_t coop_launch(const void* fn, int G, const Args& a, cudaStream_t s) {

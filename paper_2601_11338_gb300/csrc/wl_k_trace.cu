@@ -1,0 +1,54 @@
+// XNysTrace kernels: Philox sketch, right-hand side, Gram, leave-one-out core.
+#define WL_TRACE_KERNELS
+#include "wl_host.h"
+#include "wl_trace.cuh"
+
+namespace wl {
+
+static unsigned grid_cap(int64_t work, int64_t per, int cap) {
+  int64_t b = (work + per - 1) / per;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+cudaError_t launch_philox_sketch(uint16_t* omega, int64_t n, int M, uint64_t seed, cudaStream_t s) {
+  const int64_t total = n * M;
+  philox_sketch<<<grid_cap((total + 3) / 4, 256, 152 * 32), 256, 0, s>>>(omega, total, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_rhs(const uint16_t* omega, int64_t n, int M, int K, double a, float* B, cudaStream_t s) {
+  sketch_rhs<<<grid_cap(n * K, 256, 152 * 32), 256, 0, s>>>(omega, n, M, K, (float)a, B);
+  return cudaGetLastError();
+}
+
+int gram_grid(int64_t n) {
+  // about 4096 rows per chunk, at most 8 CTAs per SM worth of chunks
+  int64_t g = (n + 4095) / 4096;
+  if (g > 152 * 8) g = 152 * 8;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_gram(const uint16_t* omega, const float* Y, int64_t n, int M, int K, float* partial, int G,
+                        double* out, cudaStream_t s) {
+  const int64_t chunk = (n + G - 1) / G;
+  gram_cc<<<G, 256, 0, s>>>(omega, Y, n, M, K, chunk, partial);
+  gram_reduce<<<(2 * kMaxSketch * kMaxSketch + 255) / 256, 256, 0, s>>>(partial, G, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nys_core(const double* gram, int M, double* out, cudaStream_t s) {
+  const int smem = 4 * kMaxSketch * kMaxSketch * (int)sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(nys_core, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  nys_core<<<1, 256, smem, s>>>(gram, M, out);
+  return cudaGetLastError();
+}
+
+}  // namespace wl

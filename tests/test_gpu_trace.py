@@ -1,0 +1,66 @@
+"""XNysTrace through the C ABI against the oracle (Alg. 1, last step).
+
+The sketch Omega is bit-exact (integer Philox words, FP64 Box-Muller on
+both sides, bfloat16 rounding). The estimate uses FP32 CG for Y = phi Omega
+and FP32 Gram sums, so it is compared with the oracle's literal
+leave-one-out estimate on exact phi within 1e-5 relative (error estimate
+within 1e-2 relative: it is a spread of nearly equal t_i)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import wlgen
+from oracle import graph, philox, spectral, walks, xnys
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "rmat14_trace.json")
+
+
+def WL(g, **kw):
+    from paper_2601_11338_gb300.api import WalkLaplacian
+    return WalkLaplacian(g.row_ptr.astype(np.int32), g.col_idx, g.n, **kw)
+
+
+@pytest.mark.parametrize("M", [64, 7, 2])
+def test_sketch_is_bit_exact(M):
+    g = wlgen.erdos_renyi(1000, 8, 3)
+    w = WL(g, alpha_rel=0.5)
+    om = torch.empty((g.n, M), dtype=torch.int16, device="cuda")
+    w.trace(M, 12345 + M, om)
+    got = om.cpu().numpy().view(np.uint16)
+    _, want = philox.gaussian_sketch(g.n, M, 12345 + M)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("variant,mu,M", [("allwalk", 0.0, 64), ("nbt", 1.0, 16), ("btdw", 0.5, 7)])
+def test_estimate_matches_literal_leave_one_out(variant, mu, M):
+    g = wlgen.erdos_renyi(700, 8, 4)
+    A = graph.dense_adjacency(g.row_ptr, g.col_idx, g.n)
+    w = WL(g, variant=variant, mu=mu, alpha_rel=0.5, tol=1e-7)
+    alpha = w.info["alpha"]
+    phi = walks.phi_resolvent_closed(A, mu, alpha)
+    seed = 777 + M
+    est, err = w.trace(M, seed)
+    Om, _ = philox.gaussian_sketch(g.n, M, seed)
+    e_o, r_o, _ = xnys.xnystrace(phi, Om)
+    assert abs(est - e_o) <= 1e-5 * abs(e_o), (est, e_o)
+    assert abs(err - r_o) <= 1e-2 * r_o, (err, r_o)
+
+
+def test_rmat14_estimate_against_exact_trace():
+    """R-MAT scale 14, all-walk resolvent at alpha = 0.5 / lambda_max(A): the
+    estimate lies within a few error estimates of the exact trace computed by
+    the oracle's dense eigendecomposition (tests/golden/rmat14_trace.json)."""
+    gold = json.load(open(GOLDEN))
+    g = wlgen.rmat(gold["scale"], gold["edge_factor"], gold["a"], gold["b"], gold["c"], seed=gold["seed"])
+    assert g.n == gold["n"] and g.nnz == gold["nnz"]
+    w = WL(g, alpha=gold["alpha"], tol=1e-7)
+    ests = [w.trace(64, s) for s in (1, 2, 3)]
+    tr = gold["trace_allwalk_resolvent"]
+    for est, err in ests:
+        assert abs(est - tr) <= 6 * err + 1e-6 * tr, (est, err, tr)
+        assert err < 1e-3 * tr
