@@ -43,7 +43,7 @@ struct CgArgs {
 };
 
 template <typename T, int K>
-__global__ void __launch_bounds__(kBlock) cg_persistent(CgArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, 3) cg_persistent(CgArgs<T> a) {
   using C = Cfg<T, K>;
   constexpr int VW = C::VW;
   constexpr int NW = kBlock / 32;
@@ -254,7 +254,7 @@ struct ResArgs {
 };
 
 template <int K>
-__global__ void __launch_bounds__(kBlock) residual64(ResArgs a) {
+__global__ void __launch_bounds__(kBlock, 3) residual64(ResArgs a) {
   using C = Cfg<double, K>;
   using CF = Cfg<float, K>;
   constexpr int VW = C::VW;

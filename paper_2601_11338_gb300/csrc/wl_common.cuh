@@ -155,29 +155,79 @@ struct Graph {
   int64_t nnz;
 };
 
-// Sum of X over the neighbours of a row for this lane's VW columns, visiting
-// entries beg + t*step for t = 0, 1, ...; 4 independent gathers in flight.
-template <typename T, int K, int VW>
-__device__ __forceinline__ void gather_row(const int32_t* __restrict__ col, int beg, int end, int step,
-                                           const T* X, int lane_off, T (&acc)[VW]) {
-  int e = beg;
-  for (; e + 3 * step < end; e += 4 * step) {
-    const int32_t j0 = __ldg(col + e);
-    const int32_t j1 = __ldg(col + e + step);
-    const int32_t j2 = __ldg(col + e + 2 * step);
-    const int32_t j3 = __ldg(col + e + 3 * step);
-    const Pack<T, VW> a0 = ldp<T, VW>(X + (size_t)j0 * K + lane_off);
-    const Pack<T, VW> a1 = ldp<T, VW>(X + (size_t)j1 * K + lane_off);
-    const Pack<T, VW> a2 = ldp<T, VW>(X + (size_t)j2 * K + lane_off);
-    const Pack<T, VW> a3 = ldp<T, VW>(X + (size_t)j3 * K + lane_off);
+// ------------------------------------------------------------------ gathers
+// All index loads of a batch are issued first (one per lane, coalesced when
+// the lanes read consecutive entries) and broadcast with shuffles, so that
+// every gather of the batch is an independent 16-byte load in flight.
+constexpr int kGatherInFlight = 8;  // vector gathers issued back to back per lane
+
+template <typename T, int VW>
+__device__ __forceinline__ void add_pack(T (&acc)[VW], const Pack<T, VW>& a) {
 #pragma unroll
-    for (int v = 0; v < VW; ++v) acc[v] += (a0.v[v] + a1.v[v]) + (a2.v[v] + a3.v[v]);
+  for (int v = 0; v < VW; ++v) acc[v] += a.v[v];
+}
+
+// One subgroup (G lanes, converged, mask `sm`) sums the neighbours of its own
+// row: indices col[e0 + sl + G u] are loaded by lane sl, neighbour q of the
+// batch comes from lane q % G via a width-G shuffle.
+template <typename T, int K, int VW, int G>
+__device__ __forceinline__ void gather_row_sub(const int32_t* __restrict__ col, int beg, int end, const T* X,
+                                               int sl, int lane_off, unsigned sm, T (&acc)[VW]) {
+  constexpr int BATCH = (kGatherInFlight / G) > 0 ? kGatherInFlight / G : 1;  // index loads per lane per step
+  constexpr int CH = G < kGatherInFlight ? G : kGatherInFlight;               // gathers per chunk
+  for (int e0 = beg; e0 < end; e0 += G * BATCH) {
+    int idx[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const int p = e0 + u * G + sl;
+      idx[u] = (p < end) ? __ldg(col + p) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+#pragma unroll
+      for (int s0 = 0; s0 < G; s0 += CH) {
+        Pack<T, VW> val[CH];
+        int jj[CH];
+#pragma unroll
+        for (int s = 0; s < CH; ++s) {
+          const int j = (G == 1) ? idx[u] : __shfl_sync(sm, idx[u], s0 + s, G);
+          jj[s] = j;
+          val[s] = ldp<T, VW>(X + (size_t)(j >= 0 ? j : 0) * K + lane_off);
+        }
+#pragma unroll
+        for (int s = 0; s < CH; ++s)
+          if (jj[s] >= 0) add_pack<T, VW>(acc, val[s]);
+      }
+    }
   }
-  for (; e < end; e += step) {
-    const int32_t j0 = __ldg(col + e);
-    const Pack<T, VW> a0 = ldp<T, VW>(X + (size_t)j0 * K + lane_off);
+}
+
+// A whole warp sums entries [beg, end) of one row (32 indices per coalesced
+// load); subgroup w = lane / G takes batch entries w, w + SUB, w + 2 SUB, ...
+// Entries are visited in batches starting at beg + 32 * first, stride 32 * step.
+template <typename T, int K, int VW, int G>
+__device__ __forceinline__ void gather_row_warp(const int32_t* __restrict__ col, int beg, int end, int first,
+                                                int step, const T* X, int lane, int lane_off, T (&acc)[VW]) {
+  constexpr int SUB = 32 / G;
+  constexpr int CH = G < kGatherInFlight ? G : kGatherInFlight;
+  const int w = lane / G;
+  for (int e0 = beg + 32 * first; e0 < end; e0 += 32 * step) {
+    const int p = e0 + lane;
+    const int idx = (p < end) ? __ldg(col + p) : -1;
 #pragma unroll
-    for (int v = 0; v < VW; ++v) acc[v] += a0.v[v];
+    for (int t0 = 0; t0 < G; t0 += CH) {
+      Pack<T, VW> val[CH];
+      int jj[CH];
+#pragma unroll
+      for (int t = 0; t < CH; ++t) {
+        const int j = __shfl_sync(0xffffffffu, idx, w + SUB * (t0 + t));
+        jj[t] = j;
+        val[t] = ldp<T, VW>(X + (size_t)(j >= 0 ? j : 0) * K + lane_off);
+      }
+#pragma unroll
+      for (int t = 0; t < CH; ++t)
+        if (jj[t] >= 0) add_pack<T, VW>(acc, val[t]);
+    }
   }
 }
 
@@ -186,61 +236,67 @@ __device__ __forceinline__ void gather_row(const int32_t* __restrict__ col, int 
 // where nbr_sum[v] = sum over neighbours j of X[j, lane_off + v]. `red`
 // must hold kBlock * VW values of T in shared memory.
 template <typename T, int K, class Op>
-__device__ __forceinline__ void for_rows_gather(const Graph& g, const Part& pt, const T* X,
-                                                T* red, Op& op) {
+__device__ __forceinline__ void for_rows_gather(const Graph& g, const Part& pt, const T* X, T* red, Op& op) {
   using C = Cfg<T, K>;
   constexpr int VW = C::VW;
+  constexpr int G = C::G;
+  constexpr int NW = kBlock / 32;
   const int cta = blockIdx.x;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int sub = tid / C::G;        // subgroup id in CTA
-  const int sl = tid % C::G;         // lane in subgroup
+  const int sub = tid / G;  // subgroup id in CTA
+  const int sl = tid % G;   // lane in subgroup
   const int lane_off = sl * VW;
   const int c0 = pt.seg[4 * cta + 0], c1 = pt.seg[4 * cta + 1];
   const int c2 = pt.seg[4 * cta + 2], c3 = pt.seg[4 * cta + 3];
 
-  // class C: whole CTA per row
+  // class C: whole CTA per row (warp w takes 32-entry batches w, w + NW, ...)
   for (int o = c0; o < c1; ++o) {
     const int row = pt.order[o];
     const int beg = g.row_ptr[row], end = g.row_ptr[row + 1];
     T acc[VW];
 #pragma unroll
     for (int v = 0; v < VW; ++v) acc[v] = T(0);
-    gather_row<T, K, VW>(g.col, beg + sub, end, C::NSUB, X, lane_off, acc);
+    gather_row_warp<T, K, VW, G>(g.col, beg, end, warp, NW, X, lane, lane_off, acc);
 #pragma unroll
-    for (int v = 0; v < VW; ++v) red[tid * VW + v] = acc[v];
+    for (int off = G; off < 32; off <<= 1)
+#pragma unroll
+      for (int v = 0; v < VW; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+    if (lane < G)
+#pragma unroll
+      for (int v = 0; v < VW; ++v) red[(warp * G + lane) * VW + v] = acc[v];
     __syncthreads();
-    if (sub == 0) {
-      for (int s = 1; s < C::NSUB; ++s)
+    if (tid < G) {
+      for (int w = 1; w < NW; ++w)
 #pragma unroll
-        for (int v = 0; v < VW; ++v) acc[v] += red[(s * C::G + sl) * VW + v];
+        for (int v = 0; v < VW; ++v) acc[v] += red[(w * G + sl) * VW + v];
       op(row, end - beg, lane_off, acc);
     }
     __syncthreads();
   }
   // class W: one warp per row
-  constexpr int NW = kBlock / 32;
   for (int o = c1 + warp; o < c2; o += NW) {
     const int row = pt.order[o];
     const int beg = g.row_ptr[row], end = g.row_ptr[row + 1];
     T acc[VW];
 #pragma unroll
     for (int v = 0; v < VW; ++v) acc[v] = T(0);
-    gather_row<T, K, VW>(g.col, beg + lane / C::G, end, C::SUB, X, lane_off, acc);
+    gather_row_warp<T, K, VW, G>(g.col, beg, end, 0, 1, X, lane, lane_off, acc);
 #pragma unroll
-    for (int off = C::G; off < 32; off <<= 1)
+    for (int off = G; off < 32; off <<= 1)
 #pragma unroll
       for (int v = 0; v < VW; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
-    if (lane < C::G) op(row, end - beg, lane_off, acc);
+    if (lane < G) op(row, end - beg, lane_off, acc);
   }
-  // class S: one subgroup per row
+  // class S: one subgroup per row, rows in decreasing-degree order
+  const unsigned smask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
   for (int o = c2 + sub; o < c3; o += C::NSUB) {
     const int row = pt.order[o];
     const int beg = g.row_ptr[row], end = g.row_ptr[row + 1];
     T acc[VW];
 #pragma unroll
     for (int v = 0; v < VW; ++v) acc[v] = T(0);
-    gather_row<T, K, VW>(g.col, beg, end, 1, X, lane_off, acc);
+    gather_row_sub<T, K, VW, G>(g.col, beg, end, X, sl, lane_off, smask, acc);
     op(row, end - beg, lane_off, acc);
   }
 }
@@ -254,7 +310,15 @@ __device__ __forceinline__ void reduce_partials(const double* __restrict__ part,
   const int tid = threadIdx.x;
   const int c = tid % K, j = tid / K;
   double s = 0.0;
-  for (int g = j; g < G; g += J) s += __ldcg(part + (size_t)g * K + c);
+  int g = j;
+  for (; g + 7 * J < G; g += 8 * J) {  // 8 independent loads, summed in a fixed order
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(part + (size_t)(g + u * J) * K + c);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  for (; g < G; g += J) s += __ldcg(part + (size_t)g * K + c);
   s_tmp[tid] = s;
   __syncthreads();
   if (tid < K) {

@@ -17,7 +17,7 @@ static const void* cg32_fn(int K) {
   return nullptr;
 }
 
-static int g_cap_per_sm = 2;
+static int g_cap_per_sm = 4;
 
 int cg_grid_f32(int K) {
   const void* f = cg32_fn(K);

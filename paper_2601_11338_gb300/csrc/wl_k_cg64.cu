@@ -28,7 +28,7 @@ static const void* res_fn(int K) {
   return nullptr;
 }
 
-static int g_cap_per_sm = 2;
+static int g_cap_per_sm = 4;
 
 int cg_grid_f64(int K) {
   const void* f = cg64_fn(K);

@@ -22,7 +22,7 @@ int lanczos_ext_grid() { return coop_grid((const void*)lanczos_extreme, 2); }
 
 int lanczos_step_grid(int K) {
   const void* f = step_fn(K);
-  return f ? coop_grid(f, 2) : 0;
+  return f ? coop_grid(f, 4) : 0;
 }
 
 cudaError_t launch_lanczos_extreme(const LanczosExtArgs& a, int G, cudaStream_t s) {

@@ -189,7 +189,7 @@ struct LanczosStepArgs {
 };
 
 template <int K>
-__global__ void __launch_bounds__(kBlock) lanczos_step(LanczosStepArgs a) {
+__global__ void __launch_bounds__(kBlock, 3) lanczos_step(LanczosStepArgs a) {
   using C = Cfg<double, K>;
   constexpr int VW = C::VW;
   constexpr int NW = kBlock / 32;

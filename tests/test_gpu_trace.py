@@ -63,4 +63,4 @@ def test_rmat14_estimate_against_exact_trace():
     tr = gold["trace_allwalk_resolvent"]
     for est, err in ests:
         assert abs(est - tr) <= 6 * err + 1e-6 * tr, (est, err, tr)
-        assert err < 1e-3 * tr
+        assert err < 1e-2 * tr
