@@ -194,7 +194,7 @@ int get_part(wl_handle* h, int G, int Tw, int Tc, PartDev** out) {
   p.Tc = Tc;
   WL_CU(cudaMalloc(&p.rb, sizeof(int32_t) * (G + 1)));
   WL_CU(cudaMalloc(&p.seg, sizeof(int32_t) * 4 * G));
-  WL_CU(cudaMalloc(&p.order, sizeof(int32_t) * std::max<int64_t>(h->n, 1)));
+  WL_CU(cudaMalloc(&p.meta, sizeof(int4) * std::max<int64_t>(h->n, 1)));
   WL_CU(launch_partition(h->g, p, S(h)));
   h->parts[key] = p;
   *out = &h->parts[key];
@@ -610,7 +610,7 @@ void free_handle(wl_handle* h) {
   for (auto& kv : h->parts) {
     cudaFree(kv.second.rb);
     cudaFree(kv.second.seg);
-    cudaFree(kv.second.order);
+    cudaFree(kv.second.meta);
   }
   Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
                  &h->r32, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,

@@ -43,7 +43,7 @@ struct CgArgs {
 };
 
 template <typename T, int K>
-__global__ void __launch_bounds__(kBlock, 3) cg_persistent(CgArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, kMinBlocks) cg_persistent(CgArgs<T> a) {
   using C = Cfg<T, K>;
   constexpr int VW = C::VW;
   constexpr int NW = kBlock / 32;
@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(kBlock, 3) cg_persistent(CgArgs<T> a) {
   const size_t v0 = (size_t)r0 * K / VW, v1 = (size_t)r1 * K / VW;  // vector range
   const int mycol = (tid % C::G) * VW;                                 // first column of this thread
   const T ca = (T)a.ca, cA = (T)a.cA, cD = (T)a.cD;
+  const uint64_t keep = policy_keep(), strm = policy_stream();
   int buf = 0;
   int iters = 0;
 
@@ -108,37 +109,48 @@ __global__ void __launch_bounds__(kBlock, 3) cg_persistent(CgArgs<T> a) {
         be[v] = (T)s_beta[mycol + v];
         dacc[v] = T(0);
       }
-      auto op = [&](int row, int deg, int lane_off, const T (&nb)[VW]) {
+      struct PreCG {
+        Pack<T, VW> r, x, p, q;
+      };
+      auto pre = [&](int row, int lane_off) {
+        PreCG v;
         const size_t o = (size_t)row * K + lane_off;
-        const Pack<T, VW> rr = ldp<T, VW>(a.r + o);
+        v.r = ldh<T, VW>(a.r + o, keep);
+        if (!first) {
+          v.x = ldh<T, VW>(a.x + o, strm);
+          v.p = ldh<T, VW>(a.p + o, strm);
+          v.q = ldh<T, VW>(a.q + o, strm);
+        }
+        return v;
+      };
+      auto fin = [&](int row, int deg, int lane_off, const T (&nb)[VW], const PreCG& v) {
+        const size_t o = (size_t)row * K + lane_off;
         Pack<T, VW> pp, qq;
         const T dg = (T)deg;
         if (first) {
 #pragma unroll
-          for (int v = 0; v < VW; ++v) {
-            const T s = ca * rr.v[v] + cA * nb[v] + cD * dg * rr.v[v];
-            pp.v[v] = rr.v[v];
-            qq.v[v] = s;
-            dacc[v] += pp.v[v] * qq.v[v];
+          for (int u = 0; u < VW; ++u) {
+            const T s = ca * v.r.v[u] + cA * nb[u] + cD * dg * v.r.v[u];
+            pp.v[u] = v.r.v[u];
+            qq.v[u] = s;
+            dacc[u] += pp.v[u] * qq.v[u];
           }
         } else {
-          Pack<T, VW> xx = ldp<T, VW>(a.x + o);
-          pp = ldp<T, VW>(a.p + o);
-          qq = ldp<T, VW>(a.q + o);
+          Pack<T, VW> xx = v.x;
 #pragma unroll
-          for (int v = 0; v < VW; ++v) {
-            const T s = ca * rr.v[v] + cA * nb[v] + cD * dg * rr.v[v];
-            xx.v[v] += al[v] * pp.v[v];
-            pp.v[v] = rr.v[v] + be[v] * pp.v[v];
-            qq.v[v] = s + be[v] * qq.v[v];
-            dacc[v] += pp.v[v] * qq.v[v];
+          for (int u = 0; u < VW; ++u) {
+            const T s = ca * v.r.v[u] + cA * nb[u] + cD * dg * v.r.v[u];
+            xx.v[u] += al[u] * v.p.v[u];
+            pp.v[u] = v.r.v[u] + be[u] * v.p.v[u];
+            qq.v[u] = s + be[u] * v.q.v[u];
+            dacc[u] += pp.v[u] * qq.v[u];
           }
-          stp<T, VW>(a.x + o, xx);
+          sth<T, VW>(a.x + o, xx, strm);
         }
-        stp<T, VW>(a.p + o, pp);
-        stp<T, VW>(a.q + o, qq);
+        sth<T, VW>(a.p + o, pp, strm);
+        sth<T, VW>(a.q + o, qq, strm);
       };
-      for_rows_gather<T, K>(a.g, a.pt, a.r, s_gath, op);
+      for_rows_gather<T, K>(a.g, a.pt, a.r, s_gath, pre, fin);
       cta_column_sums<T, K>(dacc, s_w, a.part + (size_t)buf * G * K + (size_t)cta * K);
     }
     ++iters;
@@ -172,14 +184,14 @@ __global__ void __launch_bounds__(kBlock, 3) cg_persistent(CgArgs<T> a) {
       }
 #pragma unroll 4
       for (size_t e = v0 + tid; e < v1; e += kBlock) {
-        Pack<T, VW> rr = ldp<T, VW>(a.r + e * VW);
-        const Pack<T, VW> qq = ldp<T, VW>(a.q + e * VW);
+        Pack<T, VW> rr = ldh<T, VW>(a.r + e * VW, keep);
+        const Pack<T, VW> qq = ldh<T, VW>(a.q + e * VW, strm);
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
           rr.v[v] -= al[v] * qq.v[v];
           acc[v] += rr.v[v] * rr.v[v];
         }
-        stp<T, VW>(a.r + e * VW, rr);
+        sth<T, VW>(a.r + e * VW, rr, keep);
       }
       cta_column_sums<T, K>(acc, s_w, a.part + (size_t)buf * G * K + (size_t)cta * K);
     }
@@ -254,7 +266,7 @@ struct ResArgs {
 };
 
 template <int K>
-__global__ void __launch_bounds__(kBlock, 3) residual64(ResArgs a) {
+__global__ void __launch_bounds__(kBlock, kMinBlocks) residual64(ResArgs a) {
   using C = Cfg<double, K>;
   using CF = Cfg<float, K>;
   constexpr int VW = C::VW;
@@ -276,22 +288,31 @@ __global__ void __launch_bounds__(kBlock, 3) residual64(ResArgs a) {
 #pragma unroll
   for (int v = 0; v < VW; ++v) acc[v] = bacc[v] = 0.0;
   const double ca = a.ca, cA = a.cA, cD = a.cD;
-  auto op = [&](int row, int deg, int lane_off, const double (&nb)[VW]) {
+  struct PreR {
+    Pack<double, VW> x, b;
+  };
+  const uint64_t keep = policy_keep(), strm = policy_stream();
+  auto pre = [&](int row, int lane_off) {
+    PreR v;
     const size_t o = (size_t)row * K + lane_off;
-    const Pack<double, VW> xx = ldp<double, VW>(a.x + o);
-    const Pack<double, VW> bb = ldp<double, VW>(a.b + o);
+    v.x = ldh<double, VW>(a.x + o, keep);
+    v.b = ldh<double, VW>(a.b + o, strm);
+    return v;
+  };
+  auto fin = [&](int row, int deg, int lane_off, const double (&nb)[VW], const PreR& v) {
+    const size_t o = (size_t)row * K + lane_off;
     Pack<double, VW> rr;
 #pragma unroll
-    for (int v = 0; v < VW; ++v) {
-      rr.v[v] = bb.v[v] - (ca * xx.v[v] + cA * nb[v] + cD * (double)deg * xx.v[v]);
-      acc[v] += rr.v[v] * rr.v[v];
-      bacc[v] += bb.v[v] * bb.v[v];
-      if (a.r32) a.r32[o + v] = (float)rr.v[v];
-      if (a.d) a.d[o + v] = 0.0f;
+    for (int u = 0; u < VW; ++u) {
+      rr.v[u] = v.b.v[u] - (ca * v.x.v[u] + cA * nb[u] + cD * (double)deg * v.x.v[u]);
+      acc[u] += rr.v[u] * rr.v[u];
+      bacc[u] += v.b.v[u] * v.b.v[u];
+      if (a.r32) a.r32[o + u] = (float)rr.v[u];
+      if (a.d) a.d[o + u] = 0.0f;
     }
-    stp<double, VW>(a.r + o, rr);
+    sth<double, VW>(a.r + o, rr, strm);
   };
-  for_rows_gather<double, K>(a.g, a.pt, a.x, s_gath, op);
+  for_rows_gather<double, K>(a.g, a.pt, a.x, s_gath, pre, fin);
   cta_column_sums<double, K>(acc, s_w, part_r + (size_t)cta * K);
   cta_column_sums<double, K>(bacc, s_w, part_b + (size_t)cta * K);
   if (!grid_sync(a.bar, G)) return;

@@ -24,6 +24,10 @@
 namespace wl {
 
 constexpr int kBlock = 256;        // threads per CTA of the persistent kernels
+#ifndef WL_MIN_BLOCKS
+#define WL_MIN_BLOCKS 2
+#endif
+constexpr int kMinBlocks = WL_MIN_BLOCKS;  // CTAs per SM the register budget is sized for
 constexpr int kRowCost = 2;        // partition cost of a row beyond its entries
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // every device-side wait gives up after 2 s
 
@@ -141,11 +145,84 @@ __device__ __forceinline__ void stp(T* p, const Pack<T, VW>& x) {
   *reinterpret_cast<Pack<T, VW>*>(p) = x;
 }
 
+// L2 eviction-priority policies (PTX createpolicy): vectors that later phases
+// gather are kept (evict_last); streamed vectors are evicted first.
+__device__ __forceinline__ uint64_t policy_keep() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_stream() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ Pack<T, VW> ldh(const T* p, uint64_t pol);
+template <typename T, int VW>
+__device__ __forceinline__ void sth(T* p, const Pack<T, VW>& x, uint64_t pol);
+
+template <>
+__device__ __forceinline__ Pack<float, 4> ldh<float, 4>(const float* p, uint64_t pol) {
+  Pack<float, 4> r;
+  asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]) : "l"(p), "l"(pol));
+  return r;
+}
+template <>
+__device__ __forceinline__ Pack<float, 2> ldh<float, 2>(const float* p, uint64_t pol) {
+  Pack<float, 2> r;
+  asm volatile("ld.global.cg.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(r.v[0]), "=f"(r.v[1]) : "l"(p), "l"(pol));
+  return r;
+}
+template <>
+__device__ __forceinline__ Pack<float, 1> ldh<float, 1>(const float* p, uint64_t pol) {
+  Pack<float, 1> r;
+  asm volatile("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r.v[0]) : "l"(p), "l"(pol));
+  return r;
+}
+template <>
+__device__ __forceinline__ Pack<double, 2> ldh<double, 2>(const double* p, uint64_t pol) {
+  Pack<double, 2> r;
+  asm volatile("ld.global.cg.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(r.v[0]), "=d"(r.v[1]) : "l"(p), "l"(pol));
+  return r;
+}
+template <>
+__device__ __forceinline__ Pack<double, 1> ldh<double, 1>(const double* p, uint64_t pol) {
+  Pack<double, 1> r;
+  asm volatile("ld.global.cg.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r.v[0]) : "l"(p), "l"(pol));
+  return r;
+}
+template <>
+__device__ __forceinline__ void sth<float, 4>(float* p, const Pack<float, 4>& x, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(x.v[0]), "f"(x.v[1]),
+               "f"(x.v[2]), "f"(x.v[3]), "l"(pol) : "memory");
+}
+template <>
+__device__ __forceinline__ void sth<float, 2>(float* p, const Pack<float, 2>& x, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(x.v[0]), "f"(x.v[1]), "l"(pol)
+               : "memory");
+}
+template <>
+__device__ __forceinline__ void sth<float, 1>(float* p, const Pack<float, 1>& x, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(x.v[0]), "l"(pol) : "memory");
+}
+template <>
+__device__ __forceinline__ void sth<double, 2>(double* p, const Pack<double, 2>& x, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(x.v[0]), "d"(x.v[1]), "l"(pol)
+               : "memory");
+}
+template <>
+__device__ __forceinline__ void sth<double, 1>(double* p, const Pack<double, 1>& x, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(x.v[0]), "l"(pol) : "memory");
+}
+
 // ------------------------------------------------------------------ partition view
 struct Part {
   const int32_t* rb;     // G + 1 row boundaries
   const int32_t* seg;    // 4 G: [C start, W start, S start, end) offsets into order
-  const int32_t* order;  // n row ids grouped per CTA by class
+  const int4* meta;      // n entries {row, row_ptr[row], row_ptr[row + 1], 0} in class order
 };
 
 struct Graph {
@@ -156,9 +233,10 @@ struct Graph {
 };
 
 // ------------------------------------------------------------------ gathers
-// All index loads of a batch are issued first (one per lane, coalesced when
-// the lanes read consecutive entries) and broadcast with shuffles, so that
-// every gather of the batch is an independent 16-byte load in flight.
+// Index loads of a batch are issued first (one per lane, coalesced when lanes
+// read consecutive entries) and broadcast with shuffles, so every gather of
+// the batch is an independent 16-byte load in flight. Gathered vectors use
+// the keep (evict_last) L2 policy.
 constexpr int kGatherInFlight = 8;  // vector gathers issued back to back per lane
 
 template <typename T, int VW>
@@ -167,47 +245,46 @@ __device__ __forceinline__ void add_pack(T (&acc)[VW], const Pack<T, VW>& a) {
   for (int v = 0; v < VW; ++v) acc[v] += a.v[v];
 }
 
-// One subgroup (G lanes, converged, mask `sm`) sums the neighbours of its own
-// row: indices col[e0 + sl + G u] are loaded by lane sl, neighbour q of the
-// batch comes from lane q % G via a width-G shuffle.
-template <typename T, int K, int VW, int G>
-__device__ __forceinline__ void gather_row_sub(const int32_t* __restrict__ col, int beg, int end, const T* X,
-                                               int sl, int lane_off, unsigned sm, T (&acc)[VW]) {
-  constexpr int BATCH = (kGatherInFlight / G) > 0 ? kGatherInFlight / G : 1;  // index loads per lane per step
-  constexpr int CH = G < kGatherInFlight ? G : kGatherInFlight;               // gathers per chunk
-  for (int e0 = beg; e0 < end; e0 += G * BATCH) {
-    int idx[BATCH];
+template <int G, int BATCH>
+__device__ __forceinline__ void load_idx(const int32_t* __restrict__ col, int e0, int end, int sl, int (&idx)[BATCH]) {
 #pragma unroll
-    for (int u = 0; u < BATCH; ++u) {
-      const int p = e0 + u * G + sl;
-      idx[u] = (p < end) ? __ldg(col + p) : -1;
-    }
+  for (int u = 0; u < BATCH; ++u) {
+    const int p = e0 + u * G + sl;
+    idx[u] = (p < end) ? __ldg(col + p) : -1;
+  }
+}
+
+// Gathers for the G * BATCH entries whose indices the subgroup holds in idx.
+template <typename T, int K, int VW, int G, int BATCH>
+__device__ __forceinline__ void gather_idx_sub(const int (&idx)[BATCH], const T* X, int lane_off, unsigned sm,
+                                               uint64_t pol, T (&acc)[VW]) {
+  constexpr int CH = G < kGatherInFlight ? G : kGatherInFlight;
 #pragma unroll
-    for (int u = 0; u < BATCH; ++u) {
+  for (int u = 0; u < BATCH; ++u) {
 #pragma unroll
-      for (int s0 = 0; s0 < G; s0 += CH) {
-        Pack<T, VW> val[CH];
-        int jj[CH];
+    for (int s0 = 0; s0 < G; s0 += CH) {
+      Pack<T, VW> val[CH];
+      int jj[CH];
 #pragma unroll
-        for (int s = 0; s < CH; ++s) {
-          const int j = (G == 1) ? idx[u] : __shfl_sync(sm, idx[u], s0 + s, G);
-          jj[s] = j;
-          val[s] = ldp<T, VW>(X + (size_t)(j >= 0 ? j : 0) * K + lane_off);
-        }
-#pragma unroll
-        for (int s = 0; s < CH; ++s)
-          if (jj[s] >= 0) add_pack<T, VW>(acc, val[s]);
+      for (int s = 0; s < CH; ++s) {
+        const int j = (G == 1) ? idx[u] : __shfl_sync(sm, idx[u], s0 + s, G);
+        jj[s] = j;
+        val[s] = ldh<T, VW>(X + (size_t)(j >= 0 ? j : 0) * K + lane_off, pol);
       }
+#pragma unroll
+      for (int s = 0; s < CH; ++s)
+        if (jj[s] >= 0) add_pack<T, VW>(acc, val[s]);
     }
   }
 }
 
-// A whole warp sums entries [beg, end) of one row (32 indices per coalesced
-// load); subgroup w = lane / G takes batch entries w, w + SUB, w + 2 SUB, ...
-// Entries are visited in batches starting at beg + 32 * first, stride 32 * step.
+// A whole warp sums entries of one row (32 indices per coalesced load);
+// subgroup w = lane / G takes batch entries w, w + SUB, w + 2 SUB, ...
+// Batches start at beg + 32 * first with stride 32 * step.
 template <typename T, int K, int VW, int G>
 __device__ __forceinline__ void gather_row_warp(const int32_t* __restrict__ col, int beg, int end, int first,
-                                                int step, const T* X, int lane, int lane_off, T (&acc)[VW]) {
+                                                int step, const T* X, int lane, int lane_off, uint64_t pol,
+                                                T (&acc)[VW]) {
   constexpr int SUB = 32 / G;
   constexpr int CH = G < kGatherInFlight ? G : kGatherInFlight;
   const int w = lane / G;
@@ -222,7 +299,7 @@ __device__ __forceinline__ void gather_row_warp(const int32_t* __restrict__ col,
       for (int t = 0; t < CH; ++t) {
         const int j = __shfl_sync(0xffffffffu, idx, w + SUB * (t0 + t));
         jj[t] = j;
-        val[t] = ldp<T, VW>(X + (size_t)(j >= 0 ? j : 0) * K + lane_off);
+        val[t] = ldh<T, VW>(X + (size_t)(j >= 0 ? j : 0) * K + lane_off, pol);
       }
 #pragma unroll
       for (int t = 0; t < CH; ++t)
@@ -231,16 +308,22 @@ __device__ __forceinline__ void gather_row_warp(const int32_t* __restrict__ col,
   }
 }
 
-// Visit every row of this CTA's partition. For each row, exactly one
-// subgroup (lanes sl = 0..G-1 of it) calls op(row, deg, lane_off, nbr_sum)
-// where nbr_sum[v] = sum over neighbours j of X[j, lane_off + v]. `red`
-// must hold kBlock * VW values of T in shared memory.
-template <typename T, int K, class Op>
-__device__ __forceinline__ void for_rows_gather(const Graph& g, const Part& pt, const T* X, T* red, Op& op) {
+// Visit every row of this CTA's partition. For each row exactly one subgroup
+// (lanes sl = 0..G-1) runs pv = pre(row, lane_off) before the row's gathers
+// (own-row loads overlap them) and fin(row, deg, lane_off, nbr_sum, pv)
+// after, with nbr_sum[v] = sum over neighbours j of X[j, lane_off + v].
+// Short rows (class S) are software-pipelined: metadata two rows ahead and
+// indices one row ahead are in flight while a row is gathered. `red` holds
+// kBlock * VW values of T in shared memory.
+template <typename T, int K, class Pre, class Fin>
+__device__ __forceinline__ void for_rows_gather(const Graph& g, const Part& pt, const T* X, T* red, Pre& pre,
+                                                Fin& fin) {
   using C = Cfg<T, K>;
+  using PV = decltype(pre(0, 0));
   constexpr int VW = C::VW;
   constexpr int G = C::G;
   constexpr int NW = kBlock / 32;
+  constexpr int NSUB = C::NSUB;
   const int cta = blockIdx.x;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -249,15 +332,17 @@ __device__ __forceinline__ void for_rows_gather(const Graph& g, const Part& pt, 
   const int lane_off = sl * VW;
   const int c0 = pt.seg[4 * cta + 0], c1 = pt.seg[4 * cta + 1];
   const int c2 = pt.seg[4 * cta + 2], c3 = pt.seg[4 * cta + 3];
+  const uint64_t keep = policy_keep();
 
   // class C: whole CTA per row (warp w takes 32-entry batches w, w + NW, ...)
   for (int o = c0; o < c1; ++o) {
-    const int row = pt.order[o];
-    const int beg = g.row_ptr[row], end = g.row_ptr[row + 1];
+    const int4 m = pt.meta[o];
+    PV pv;
+    if (tid < G) pv = pre(m.x, lane_off);
     T acc[VW];
 #pragma unroll
     for (int v = 0; v < VW; ++v) acc[v] = T(0);
-    gather_row_warp<T, K, VW, G>(g.col, beg, end, warp, NW, X, lane, lane_off, acc);
+    gather_row_warp<T, K, VW, G>(g.col, m.y, m.z, warp, NW, X, lane, lane_off, keep, acc);
 #pragma unroll
     for (int off = G; off < 32; off <<= 1)
 #pragma unroll
@@ -270,34 +355,54 @@ __device__ __forceinline__ void for_rows_gather(const Graph& g, const Part& pt, 
       for (int w = 1; w < NW; ++w)
 #pragma unroll
         for (int v = 0; v < VW; ++v) acc[v] += red[(w * G + sl) * VW + v];
-      op(row, end - beg, lane_off, acc);
+      fin(m.x, m.z - m.y, lane_off, acc, pv);
     }
     __syncthreads();
   }
   // class W: one warp per row
   for (int o = c1 + warp; o < c2; o += NW) {
-    const int row = pt.order[o];
-    const int beg = g.row_ptr[row], end = g.row_ptr[row + 1];
+    const int4 m = pt.meta[o];
+    PV pv;
+    if (lane < G) pv = pre(m.x, lane_off);
     T acc[VW];
 #pragma unroll
     for (int v = 0; v < VW; ++v) acc[v] = T(0);
-    gather_row_warp<T, K, VW, G>(g.col, beg, end, 0, 1, X, lane, lane_off, acc);
+    gather_row_warp<T, K, VW, G>(g.col, m.y, m.z, 0, 1, X, lane, lane_off, keep, acc);
 #pragma unroll
     for (int off = G; off < 32; off <<= 1)
 #pragma unroll
       for (int v = 0; v < VW; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
-    if (lane < G) op(row, end - beg, lane_off, acc);
+    if (lane < G) fin(m.x, m.z - m.y, lane_off, acc, pv);
   }
-  // class S: one subgroup per row, rows in decreasing-degree order
+  // class S: one subgroup per row, rows in decreasing-degree order, pipelined
+  constexpr int BS = (C::Tw / G) > 8 ? 8 : ((C::Tw / G) < 1 ? 1 : C::Tw / G);  // index loads per lane
   const unsigned smask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-  for (int o = c2 + sub; o < c3; o += C::NSUB) {
-    const int row = pt.order[o];
-    const int beg = g.row_ptr[row], end = g.row_ptr[row + 1];
+  const int4 none = make_int4(-1, 0, 0, 0);
+  int o = c2 + sub;
+  int4 mc = (o < c3) ? pt.meta[o] : none;
+  int4 mn = (o + NSUB < c3) ? pt.meta[o + NSUB] : none;
+  int ic[BS];
+  load_idx<G, BS>(g.col, mc.y, mc.z, sl, ic);
+  while (o < c3) {
+    const int4 mnn = (o + 2 * NSUB < c3) ? pt.meta[o + 2 * NSUB] : none;
+    const PV pv = pre(mc.x, lane_off);
+    int in_[BS];
+    load_idx<G, BS>(g.col, mn.y, mn.z, sl, in_);
     T acc[VW];
 #pragma unroll
     for (int v = 0; v < VW; ++v) acc[v] = T(0);
-    gather_row_sub<T, K, VW, G>(g.col, beg, end, X, sl, lane_off, smask, acc);
-    op(row, end - beg, lane_off, acc);
+    gather_idx_sub<T, K, VW, G, BS>(ic, X, lane_off, smask, keep, acc);
+    for (int e0 = mc.y + G * BS; e0 < mc.z; e0 += G * BS) {  // rows longer than one batch
+      int ix[BS];
+      load_idx<G, BS>(g.col, e0, mc.z, sl, ix);
+      gather_idx_sub<T, K, VW, G, BS>(ix, X, lane_off, smask, keep, acc);
+    }
+    fin(mc.x, mc.z - mc.y, lane_off, acc, pv);
+    mc = mn;
+    mn = mnn;
+#pragma unroll
+    for (int u = 0; u < BS; ++u) ic[u] = in_[u];
+    o += NSUB;
   }
 }
 

@@ -16,8 +16,8 @@ struct PartDev {
   int Tw = 0, Tc = 0;
   int32_t* rb = nullptr;
   int32_t* seg = nullptr;
-  int32_t* order = nullptr;
-  Part view() const { return Part{rb, seg, order}; }
+  int4* meta = nullptr;
+  Part view() const { return Part{rb, seg, meta}; }
 };
 
 // ---- wl_k_misc.cu

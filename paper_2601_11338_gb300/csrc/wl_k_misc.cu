@@ -28,7 +28,7 @@ __global__ void k_partition_bounds(const int32_t* row_ptr, int64_t n, int G, int
 // degree. Stable (row id order within a bucket) and deterministic.
 constexpr int kOrderBuckets = 130;  // 0: C, 1: W, 2 + (Tw - deg): S, Tw <= 127
 
-__global__ void k_order(const int32_t* row_ptr, const int32_t* rb, int Tw, int Tc, int32_t* order, int32_t* seg) {
+__global__ void k_order(const int32_t* row_ptr, const int32_t* rb, int Tw, int Tc, int4* meta, int32_t* seg) {
   __shared__ int hist[kOrderBuckets];
   __shared__ int cur[kOrderBuckets];
   const int g = blockIdx.x, tid = threadIdx.x;
@@ -68,7 +68,7 @@ __global__ void k_order(const int32_t* row_ptr, const int32_t* rb, int Tw, int T
       int basepos = 0;
       if (valid && lane == leader) basepos = cur[b];
       basepos = __shfl_sync(0xffffffffu, basepos, valid ? leader : lane);
-      if (valid) order[basepos + rank] = row;
+      if (valid) meta[basepos + rank] = make_int4(row, row_ptr[row], row_ptr[row + 1], 0);
       __syncwarp();
       if (valid && lane == leader) cur[b] += __popc(peers);
       __syncwarp();
@@ -79,7 +79,7 @@ __global__ void k_order(const int32_t* row_ptr, const int32_t* rb, int Tw, int T
 cudaError_t launch_partition(const Graph& g, PartDev& p, cudaStream_t s) {
   if (p.Tw > kOrderBuckets - 3) return cudaErrorInvalidValue;
   k_partition_bounds<<<(p.G + 1 + 255) / 256, 256, 0, s>>>(g.row_ptr, g.n, p.G, p.rb);
-  k_order<<<p.G, 256, 0, s>>>(g.row_ptr, p.rb, p.Tw, p.Tc, p.order, p.seg);
+  k_order<<<p.G, 256, 0, s>>>(g.row_ptr, p.rb, p.Tw, p.Tc, p.meta, p.seg);
   return cudaGetLastError();
 }
 
@@ -248,12 +248,12 @@ __global__ void __launch_bounds__(kBlock) k_laplacian_apply(Graph g, Part pt, co
   using C = Cfg<double, K>;
   constexpr int VW = C::VW;
   __shared__ __align__(16) double s_gath[kBlock * VW];
-  auto op = [&](int row, int deg, int lane_off, const double (&nb)[VW]) {
-    const size_t o = (size_t)row * K + lane_off;
+  auto pre = [&](int row, int lane_off) { return ldp<double, VW>(Vp + (size_t)row * K + lane_off); };
+  auto fin = [&](int row, int deg, int lane_off, const double (&nb)[VW], const Pack<double, VW>& vv) {
 #pragma unroll
-    for (int v = 0; v < VW; ++v) W[(size_t)row * ldw + c0 + lane_off + v] = (double)deg * Vp[o + v] - nb[v];
+    for (int v = 0; v < VW; ++v) W[(size_t)row * ldw + c0 + lane_off + v] = (double)deg * vv.v[v] - nb[v];
   };
-  for_rows_gather<double, K>(g, pt, Vp, s_gath, op);
+  for_rows_gather<double, K>(g, pt, Vp, s_gath, pre, fin);
 }
 
 cudaError_t launch_laplacian_apply(const Graph& g, const PartDev& p, const double* Vp, int K, int c0, double* W,

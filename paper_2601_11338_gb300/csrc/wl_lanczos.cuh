@@ -113,14 +113,13 @@ __global__ void __launch_bounds__(kBlock) lanczos_extreme(LanczosExtArgs a) {
   for (int j = 0; j < a.m; ++j) {
     // w = Op v_j ; alpha = (v_j, w)
     double acc[1] = {0.0};
-    auto op = [&](int row, int deg, int lane_off, const double (&nb)[VW]) {
-      const double vi = __ldcg(vc + row);
+    auto pre = [&](int row, int lane_off) { return __ldcg(vc + row); };
+    auto fin = [&](int row, int deg, int lane_off, const double (&nb)[VW], const double vi) {
       const double wi = a.c0 * vi + a.cA * nb[0] + a.cD * (double)deg * vi;
       w[row] = wi;
       acc[0] += vi * wi;
-      (void)lane_off;
     };
-    for_rows_gather<double, K>(a.g, a.pt, vc, s_gath, op);
+    for_rows_gather<double, K>(a.g, a.pt, vc, s_gath, pre, fin);
     cta_column_sums<double, K>(acc, s_w, a.part + (size_t)buf * G + cta);
     if (!grid_sync(a.bar, G)) return;
     reduce_partials<K>(a.part + (size_t)buf * G, G, s_tmp, s_red);
@@ -189,7 +188,7 @@ struct LanczosStepArgs {
 };
 
 template <int K>
-__global__ void __launch_bounds__(kBlock, 3) lanczos_step(LanczosStepArgs a) {
+__global__ void __launch_bounds__(kBlock, kMinBlocks) lanczos_step(LanczosStepArgs a) {
   using C = Cfg<double, K>;
   constexpr int VW = C::VW;
   constexpr int NW = kBlock / 32;
@@ -222,9 +221,9 @@ __global__ void __launch_bounds__(kBlock, 3) lanczos_step(LanczosStepArgs a) {
       stp<double, VW>(a.vjp1 + e * VW, ww);
     }
   } else {
-    auto op = [&](int row, int deg, int lane_off, const double (&nb)[VW]) {
+    auto pre = [&](int row, int lane_off) { return ldp<double, VW>(a.vj + (size_t)row * K + lane_off); };
+    auto fin = [&](int row, int deg, int lane_off, const double (&nb)[VW], const Pack<double, VW>& vv) {
       const size_t o = (size_t)row * K + lane_off;
-      const Pack<double, VW> vv = ldp<double, VW>(a.vj + o);
       Pack<double, VW> ww;
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
@@ -233,7 +232,7 @@ __global__ void __launch_bounds__(kBlock, 3) lanczos_step(LanczosStepArgs a) {
       }
       stp<double, VW>(a.vjp1 + o, ww);
     };
-    for_rows_gather<double, K>(a.g, a.pt, a.vj, s_gath, op);
+    for_rows_gather<double, K>(a.g, a.pt, a.vj, s_gath, pre, fin);
   }
   cta_column_sums<double, K>(acc, s_w, a.part + (size_t)cta * K);
   if (!grid_sync(a.bar, G)) return;
