@@ -22,6 +22,17 @@ namespace wl {
 
 enum ColStatus : int { kColActive = 0, kColDone = 1 };
 
+#ifdef WL_PHASE_TIMING
+// experiment builds only: per-CTA timestamps of the first iterations
+constexpr int kStampIters = 8, kStampEv = 4, kStampCtas = 1024;
+__device__ unsigned long long g_stamps[kStampCtas * kStampIters * kStampEv];
+#define WL_STAMP(it, ev)                                                                         \
+  if (threadIdx.x == 0 && blockIdx.x < kStampCtas && (it) < kStampIters)                          \
+    g_stamps[(blockIdx.x * kStampIters + (it)) * kStampEv + (ev)] = globaltimer_ns();
+#else
+#define WL_STAMP(it, ev)
+#endif
+
 template <typename T>
 struct CgArgs {
   Graph g;
@@ -100,6 +111,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) cg_persistent(CgArgs<T> a)
 
   bool first = true;
   while (!s_all) {
+    WL_STAMP(iters, 0);
     // ---- S: s = M r; x += alpha p; p = r + beta p; q = s + beta q; delta = (p, q)
     {
       T al[VW], be[VW], dacc[VW];
@@ -153,6 +165,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) cg_persistent(CgArgs<T> a)
       for_rows_gather<T, K>(a.g, a.pt, a.r, s_gath, pre, fin);
       cta_column_sums<T, K>(dacc, s_w, a.part + (size_t)buf * G * K + (size_t)cta * K);
     }
+    WL_STAMP(iters, 1);
     ++iters;
     first = false;
     if (!grid_sync(a.bar, G)) return;
@@ -174,6 +187,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) cg_persistent(CgArgs<T> a)
     }
     __syncthreads();
 
+    WL_STAMP(iters - 1, 2);
     // ---- U: r -= alpha q; gamma' = (r, r)
     {
       T al[VW], acc[VW];
@@ -195,6 +209,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) cg_persistent(CgArgs<T> a)
       }
       cta_column_sums<T, K>(acc, s_w, a.part + (size_t)buf * G * K + (size_t)cta * K);
     }
+    WL_STAMP(iters - 1, 3);
     if (!grid_sync(a.bar, G)) return;
     reduce_partials<K>(a.part + (size_t)buf * G * K, G, s_tmp, s_red);
     buf ^= 1;

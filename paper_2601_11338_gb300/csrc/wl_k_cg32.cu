@@ -44,3 +44,9 @@ void thresholds_f32(int K, int* Tw, int* Tc) {
 }
 
 }  // namespace wl
+
+#ifdef WL_PHASE_TIMING
+extern "C" int wl_debug_stamps(unsigned long long* out, int count) {
+  return (int)cudaMemcpyFromSymbol(out, wl::g_stamps, sizeof(unsigned long long) * count);
+}
+#endif
