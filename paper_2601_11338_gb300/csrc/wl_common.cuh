@@ -102,8 +102,14 @@ struct Cfg {
   static constexpr int G = K / VW;                 // lanes per row (subgroup)
   static constexpr int SUB = 32 / G;               // subgroups per warp
   static constexpr int NSUB = kBlock / G;          // subgroups per CTA
-  static constexpr int Tw = 2 * SUB;               // class S if deg <= Tw
-  static constexpr int Tc = 8 * NSUB > Tw ? 8 * NSUB : Tw;  // class C if deg > Tc
+  // index loads per lane per batch; a batch covers E = G * BS entries and
+  // every lane issues E independent gathers for it
+  static constexpr int BS = (16 / G) > 8 ? 8 : ((16 / G) < 1 ? 1 : 16 / G);
+  static constexpr int E = G * BS;
+  // rows with more than Tc entries are gathered by the whole CTA; all others
+  // by one subgroup (chains of at most 32 batches)
+  static constexpr int Tc = 32 * E;
+  static constexpr int Tw = Tc;  // no warp-per-row class
   static_assert(G >= 1 && G <= 32, "subgroup size");
   static_assert(K % VW == 0, "K must be a multiple of the lane width");
 };
@@ -288,9 +294,11 @@ __device__ __forceinline__ void gather_row_warp(const int32_t* __restrict__ col,
   constexpr int SUB = 32 / G;
   constexpr int CH = G < kGatherInFlight ? G : kGatherInFlight;
   const int w = lane / G;
-  for (int e0 = beg + 32 * first; e0 < end; e0 += 32 * step) {
-    const int p = e0 + lane;
-    const int idx = (p < end) ? __ldg(col + p) : -1;
+  int e0 = beg + 32 * first;
+  int idx = (e0 + lane < end) ? __ldg(col + e0 + lane) : -1;
+  for (; e0 < end; e0 += 32 * step) {
+    const int e1 = e0 + 32 * step;  // next batch's indices in flight during this batch's gathers
+    const int idx_next = (e1 + lane < end) ? __ldg(col + e1 + lane) : -1;
 #pragma unroll
     for (int t0 = 0; t0 < G; t0 += CH) {
       Pack<T, VW> val[CH];
@@ -305,6 +313,7 @@ __device__ __forceinline__ void gather_row_warp(const int32_t* __restrict__ col,
       for (int t = 0; t < CH; ++t)
         if (jj[t] >= 0) add_pack<T, VW>(acc, val[t]);
     }
+    idx = idx_next;
   }
 }
 
@@ -331,7 +340,7 @@ __device__ __forceinline__ void for_rows_gather(const Graph& g, const Part& pt, 
   const int sl = tid % G;   // lane in subgroup
   const int lane_off = sl * VW;
   const int c0 = pt.seg[4 * cta + 0], c1 = pt.seg[4 * cta + 1];
-  const int c2 = pt.seg[4 * cta + 2], c3 = pt.seg[4 * cta + 3];
+  const int c3 = pt.seg[4 * cta + 3];
   const uint64_t keep = policy_keep();
 
   // class C: whole CTA per row (warp w takes 32-entry batches w, w + NW, ...)
@@ -359,50 +368,49 @@ __device__ __forceinline__ void for_rows_gather(const Graph& g, const Part& pt, 
     }
     __syncthreads();
   }
-  // class W: one warp per row
-  for (int o = c1 + warp; o < c2; o += NW) {
-    const int4 m = pt.meta[o];
-    PV pv;
-    if (lane < G) pv = pre(m.x, lane_off);
-    T acc[VW];
-#pragma unroll
-    for (int v = 0; v < VW; ++v) acc[v] = T(0);
-    gather_row_warp<T, K, VW, G>(g.col, m.y, m.z, 0, 1, X, lane, lane_off, keep, acc);
-#pragma unroll
-    for (int off = G; off < 32; off <<= 1)
-#pragma unroll
-      for (int v = 0; v < VW; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
-    if (lane < G) fin(m.x, m.z - m.y, lane_off, acc, pv);
-  }
-  // class S: one subgroup per row, rows in decreasing-degree order, pipelined
-  constexpr int BS = (C::Tw / G) > 8 ? 8 : ((C::Tw / G) < 1 ? 1 : C::Tw / G);  // index loads per lane
+  // rows with at most Tc entries: one subgroup per row, rows in decreasing
+  // degree order, as one flat loop over index batches of E entries; the next
+  // batch's indices (same row or the next row's first) and the metadata of
+  // the row after next are in flight while a batch is gathered.
+  constexpr int BS = C::BS, E = C::E;
   const unsigned smask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
   const int4 none = make_int4(-1, 0, 0, 0);
-  int o = c2 + sub;
+  int o = c1 + sub;  // class W is empty: Tw == Tc
   int4 mc = (o < c3) ? pt.meta[o] : none;
   int4 mn = (o + NSUB < c3) ? pt.meta[o + NSUB] : none;
+  int e = mc.y;
   int ic[BS];
-  load_idx<G, BS>(g.col, mc.y, mc.z, sl, ic);
-  while (o < c3) {
-    const int4 mnn = (o + 2 * NSUB < c3) ? pt.meta[o + 2 * NSUB] : none;
-    const PV pv = pre(mc.x, lane_off);
-    int in_[BS];
-    load_idx<G, BS>(g.col, mn.y, mn.z, sl, in_);
-    T acc[VW];
+  load_idx<G, BS>(g.col, e, mc.z, sl, ic);
+  PV pv;
+  if (o < c3) pv = pre(mc.x, lane_off);
+  T acc[VW];
 #pragma unroll
-    for (int v = 0; v < VW; ++v) acc[v] = T(0);
+  for (int v = 0; v < VW; ++v) acc[v] = T(0);
+  while (o < c3) {
+    const int e_next = e + E;
+    const bool same = e_next < mc.z;
+    int4 mnn = none;
+    if (!same && o + 2 * NSUB < c3) mnn = pt.meta[o + 2 * NSUB];
+    int in_[BS];
+    if (same)
+      load_idx<G, BS>(g.col, e_next, mc.z, sl, in_);
+    else
+      load_idx<G, BS>(g.col, mn.y, mn.z, sl, in_);
     gather_idx_sub<T, K, VW, G, BS>(ic, X, lane_off, smask, keep, acc);
-    for (int e0 = mc.y + G * BS; e0 < mc.z; e0 += G * BS) {  // rows longer than one batch
-      int ix[BS];
-      load_idx<G, BS>(g.col, e0, mc.z, sl, ix);
-      gather_idx_sub<T, K, VW, G, BS>(ix, X, lane_off, smask, keep, acc);
+    if (!same) {
+      fin(mc.x, mc.z - mc.y, lane_off, acc, pv);
+#pragma unroll
+      for (int v = 0; v < VW; ++v) acc[v] = T(0);
+      o += NSUB;
+      mc = mn;
+      mn = mnn;
+      if (o < c3) pv = pre(mc.x, lane_off);
+      e = mc.y;
+    } else {
+      e = e_next;
     }
-    fin(mc.x, mc.z - mc.y, lane_off, acc, pv);
-    mc = mn;
-    mn = mnn;
 #pragma unroll
     for (int u = 0; u < BS; ++u) ic[u] = in_[u];
-    o += NSUB;
   }
 }
 

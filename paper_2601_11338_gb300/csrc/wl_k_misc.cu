@@ -26,7 +26,7 @@ __global__ void k_partition_bounds(const int32_t* row_ptr, int64_t n, int G, int
 // One CTA per partition; one warp scatters the partition's rows into
 // order[] by class C (deg > Tc), W (Tw < deg <= Tc), then S by decreasing
 // degree. Stable (row id order within a bucket) and deterministic.
-constexpr int kOrderBuckets = 130;  // 0: C, 1: W, 2 + (Tw - deg): S, Tw <= 127
+constexpr int kOrderBuckets = 1030;  // 0: C, 1: W, 2 + (Tw - deg): S, Tw <= 1027
 
 __global__ void k_order(const int32_t* row_ptr, const int32_t* rb, int Tw, int Tc, int4* meta, int32_t* seg) {
   __shared__ int hist[kOrderBuckets];
