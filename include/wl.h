@@ -103,6 +103,9 @@ typedef struct {
   int max_outer;     /* Lanczos step cap of wl_expmv (<= 0: 400) */
   double outer_tol;  /* wl_expmv relative accuracy target (<= 0: 1e-10) */
   void* stream;      /* cudaStream_t the handle works on; NULL: legacy default stream */
+  int reorder;       /* 0: keep the caller's node order internally; 1: relabel nodes by
+                        decreasing degree inside the handle (better gather locality).
+                        Results are always returned in the caller's node order. */
 } wl_params;
 
 typedef struct {

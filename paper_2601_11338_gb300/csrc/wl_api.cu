@@ -131,6 +131,11 @@ struct wl_handle {
   Buf packV, packX;
   Buf lan;                // Lanczos extreme vectors
   Buf omega, gram;        // sketch and Gram workspace
+  Buf omega_int;          // sketch rows in the internal node order
+  Buf ptmp;               // partition / relabel scratch (int64)
+  Buf perm_b, iperm_b;    // node relabelling: perm[new] = old, iperm[old] = new
+  int32_t* perm = nullptr;
+  int32_t* iperm = nullptr;
   double* h_pin = nullptr;  // pinned host scratch (4096 doubles)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // per-call kernel timing: event pairs recorded on the stream around launches
@@ -195,7 +200,9 @@ int get_part(wl_handle* h, int G, int Tw, int Tc, PartDev** out) {
   WL_CU(cudaMalloc(&p.rb, sizeof(int32_t) * (G + 1)));
   WL_CU(cudaMalloc(&p.seg, sizeof(int32_t) * 4 * G));
   WL_CU(cudaMalloc(&p.meta, sizeof(int4) * std::max<int64_t>(h->n, 1)));
-  WL_CU(launch_partition(h->g, p, S(h)));
+  WL_TRY(ensure(h->ptmp, sizeof(int64_t) * (2 * (size_t)(h->n + 1) + (size_t)h->n / 1024 + 8)));
+  counted(h, 4);
+  WL_CU(launch_partition_weighted(h->g, p, (int64_t*)h->ptmp.p, S(h)));
   h->parts[key] = p;
   *out = &h->parts[key];
   return WL_OK;
@@ -605,6 +612,25 @@ void fill_stats(wl_handle* h, wl_stats* st, const SolveInfo& in, int status, dou
   st->lambda_max = h->lmax;
 }
 
+// internal-order n-vector -> caller's array (host or device), undoing the relabelling
+int copy_out_vec(wl_handle* h, const double* src, double* dst) {
+  const size_t bytes = (size_t)h->n * 8;
+  if (!h->perm) {
+    WL_CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, S(h)));
+    return WL_OK;
+  }
+  double* d = dst;
+  const bool dev = is_device_ptr(dst);
+  if (!dev) {
+    WL_TRY(ensure(h->stage_b, bytes));
+    d = (double*)h->stage_b.p;
+  }
+  counted(h);
+  WL_CU(launch_permute_vec(src, h->n, h->perm, true, d, S(h)));
+  if (!dev) WL_CU(cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, S(h)));
+  return WL_OK;
+}
+
 void free_handle(wl_handle* h) {
   if (!h) return;
   for (auto& kv : h->parts) {
@@ -614,7 +640,8 @@ void free_handle(wl_handle* h) {
   }
   Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
                  &h->r32, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
-                 &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->lan, &h->omega, &h->gram};
+                 &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->lan, &h->omega, &h->gram,
+                 &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b};
   for (Buf* b : bufs) release(*b);
   if (h->bar) cudaFree(h->bar);
   if (h->h_pin) cudaFreeHost(h->h_pin);
@@ -719,6 +746,41 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
   if (flags & 4) return fail(WL_ERR_SELF_LOOP);
   if (flags & 8) return fail(WL_ERR_NOT_SYMMETRIC);
 
+  // optional relabelling by decreasing degree (internal only)
+  if (p->reorder == 1 && h->n > 1) {
+    Buf rp2, col2;
+    if ((rc = ensure(h->perm_b, sizeof(int32_t) * h->n)) != WL_OK) return fail(rc);
+    if ((rc = ensure(h->iperm_b, sizeof(int32_t) * h->n)) != WL_OK) return fail(rc);
+    if ((rc = ensure(rp2, sizeof(int32_t) * (h->n + 1))) != WL_OK) return fail(rc);
+    if ((rc = ensure(col2, sizeof(int32_t) * std::max<int64_t>(h->nnz, 1))) != WL_OK) {
+      release(rp2);
+      return fail(rc);
+    }
+    if ((rc = ensure(h->ptmp, sizeof(int64_t) * relabel_tmp_i64(h->n))) != WL_OK) {
+      release(rp2);
+      release(col2);
+      return fail(rc);
+    }
+    h->perm = (int32_t*)h->perm_b.p;
+    h->iperm = (int32_t*)h->iperm_b.p;
+    counted(h, 9);
+    cudaError_t e = launch_relabel(h->g, h->perm, h->iperm, (int32_t*)rp2.p, (int32_t*)col2.p,
+                                   (int64_t*)h->ptmp.p, S(h));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S(h));
+    if (e != cudaSuccess) {
+      release(rp2);
+      release(col2);
+      return fail(set_cuda_error(e, "relabel"));
+    }
+    release(h->csr_rp);
+    release(h->csr_col);
+    h->csr_rp = rp2;
+    h->csr_col = col2;
+    h->g = Graph{(const int32_t*)h->csr_rp.p, (const int32_t*)h->csr_col.p, h->n, h->nnz};
+  } else if (p->reorder != 0 && p->reorder != 1) {
+    return fail(WL_ERR_INVALID_ARG);
+  }
+
   // spectral scale and parameters
   h->lmax = 0.0;
   h->rho = 0.0;
@@ -792,7 +854,16 @@ int wl_set_warm_start(wl_handle* h, const double* x0) {
   }
   int rc = ensure(h->warm, (size_t)std::max<int64_t>(h->n, 1) * 8);
   if (rc) return rc;
-  WL_CU(cudaMemcpyAsync(h->warm.p, x0, (size_t)h->n * 8, cudaMemcpyDefault, S(h)));
+  if (h->perm) {
+    const void* src = nullptr;
+    rc = stage_in(h, h->stage_a, x0, (size_t)h->n * 8, &src);
+    if (rc) return rc;
+    counted(h);
+    WL_CU(launch_permute_vec((const double*)src, h->n, h->perm, false, (double*)h->warm.p, S(h)));
+  } else {
+    WL_CU(cudaMemcpyAsync(h->warm.p, x0, (size_t)h->n * 8, cudaMemcpyDefault, S(h)));
+  }
+  WL_CU(cudaStreamSynchronize(S(h)));
   h->have_warm = true;
   h->have_Df = false;
   return WL_OK;
@@ -806,10 +877,7 @@ int wl_degrees(wl_handle* h, double* Df, wl_stats* st) {
   if (h->n > 0) {
     h->have_Df = false;
     rc = compute_Df(h, info);
-    if (rc == WL_OK) {
-      cudaError_t e = cudaMemcpyAsync(Df, h->Df.p, (size_t)h->n * 8, cudaMemcpyDefault, S(h));
-      if (e != cudaSuccess) rc = set_cuda_error(e, "copy Df");
-    }
+    if (rc == WL_OK) rc = copy_out_vec(h, (const double*)h->Df.p, Df);
   }
   const double ms = end_timer(h);
   if (rc == WL_OK) rc = info.status;
@@ -843,7 +911,8 @@ int wl_apply(wl_handle* h, const double* V, int64_t ldv, int k, double* W, int64
       if ((rc = ensure(h->packV, (size_t)n * K * 8)) != WL_OK) break;
       if ((rc = ensure(h->packX, (size_t)n * K * 8)) != WL_OK) break;
       counted(h);
-      cudaError_t e = launch_pack(Vd, ldv, c0, K, n, 1.0, h->packV.p, false, S(h));
+      cudaError_t e = h->perm ? launch_pack_perm(Vd, ldv, c0, K, n, 1.0, h->perm, (double*)h->packV.p, S(h))
+                              : launch_pack(Vd, ldv, c0, K, n, 1.0, h->packV.p, false, S(h));
       if (e != cudaSuccess) { rc = set_cuda_error(e, "pack"); break; }
       if (h->prm.f == WL_F_IDENTITY) {
         PartDev* pd;
@@ -851,13 +920,16 @@ int wl_apply(wl_handle* h, const double* V, int64_t ldv, int k, double* W, int64
         thresholds_f64(K, &Tw, &Tc);
         if ((rc = get_part(h, cg_grid_f64(K), Tw, Tc, &pd)) != WL_OK) break;
         counted(h);
-        e = launch_laplacian_apply(h->g, *pd, (const double*)h->packV.p, K, c0, Wd, ldw, S(h));
+        e = launch_laplacian_apply(h->g, *pd, (const double*)h->packV.p, K, c0, h->perm, Wd, ldw, S(h));
         info.nnz_rhs += (double)h->nnz * K;
         info.iters += 1;
       } else {
         if ((rc = phi_apply(h, (const double*)h->packV.p, (double*)h->packX.p, K, info)) != WL_OK) break;
         counted(h);
-        e = launch_apply_out(Vd, ldv, (const double*)h->packX.p, (const double*)h->Df.p, n, K, c0, Wd, ldw, S(h));
+        e = h->perm ? launch_apply_out_perm((const double*)h->packV.p, (const double*)h->packX.p,
+                                            (const double*)h->Df.p, n, K, c0, h->perm, Wd, ldw, S(h))
+                    : launch_apply_out(Vd, ldv, (const double*)h->packX.p, (const double*)h->Df.p, n, K, c0, Wd,
+                                       ldw, S(h));
       }
       if (e != cudaSuccess) { rc = set_cuda_error(e, "apply"); break; }
       c0 += K;
@@ -929,7 +1001,8 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
       double* errd = (double*)h->errb.p;
       // V_0 = U0 block / |U0 block| (per column)
       counted(h, 3);
-      cudaError_t e = launch_pack(U0d, ldu, c0, K, n, 1.0, h->packX.p, false, S(h));
+      cudaError_t e = h->perm ? launch_pack_perm(U0d, ldu, c0, K, n, 1.0, h->perm, (double*)h->packX.p, S(h))
+                              : launch_pack(U0d, ldu, c0, K, n, 1.0, h->packX.p, false, S(h));
       if (e == cudaSuccess) e = launch_colnorms((const double*)h->packX.p, n, K, nrm, S(h));
       if (e == cudaSuccess) e = launch_scale_cols((const double*)h->packX.p, n, K, nrm, basis, S(h));
       if (e != cudaSuccess) { rc = set_cuda_error(e, "expmv init"); break; }
@@ -1021,7 +1094,7 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
         std::vector<int> hm(K, m);
         WL_CU(cudaMemcpyAsync(mcol, hm.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
       }
-      CombineArgs ca{basis, (const double*)h->ybuf.p, mcol, nrm, Ud, n, ldo, n * ldo, c0, ldT, ntau};
+      CombineArgs ca{basis, (const double*)h->ybuf.p, mcol, nrm, Ud, n, ldo, n * ldo, c0, ldT, ntau, h->perm};
       counted(h);
       e = launch_combine(K, ca, S(h));
       if (e != cudaSuccess) { rc = set_cuda_error(e, "combine"); break; }
@@ -1070,7 +1143,14 @@ int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, u
     double* core = gout + 2 * kMaxSketch * kMaxSketch;
     counted(h, 2);
     cudaError_t e = launch_philox_sketch(omega, n, M, seed, S(h));
-    if (e == cudaSuccess) e = launch_sketch_rhs(omega, n, M, K, h->a_scale, (float*)h->r32.p, S(h));
+    uint16_t* om_int = omega;  // sketch rows in the internal node order
+    if (e == cudaSuccess && h->perm) {
+      if ((rc = ensure(h->omega_int, (size_t)n * M * sizeof(uint16_t))) != WL_OK) break;
+      om_int = (uint16_t*)h->omega_int.p;
+      counted(h);
+      e = launch_permute_rows_u16(omega, n, M, h->perm, om_int, S(h));
+    }
+    if (e == cudaSuccess) e = launch_sketch_rhs(om_int, n, M, K, h->a_scale, (float*)h->r32.p, S(h));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->x.p, 0, nk * 4, S(h));
     if (e != cudaSuccess) { rc = set_cuda_error(e, "sketch"); break; }
     // Y = M^{-1} (a Omega) in FP32 lockstep CG
@@ -1091,7 +1171,7 @@ int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, u
     prof_end(h, pc);
     if (e != cudaSuccess) { rc = set_cuda_error(e, "cg_f32"); break; }
     counted(h, 3);
-    e = launch_gram(omega, (const float*)h->x.p, n, M, K, partial, Gg, gout, S(h));
+    e = launch_gram(om_int, (const float*)h->x.p, n, M, K, partial, Gg, gout, S(h));
     if (e == cudaSuccess) e = launch_nys_core(gout, M, core, S(h));
     if (e != cudaSuccess) { rc = set_cuda_error(e, "gram/core"); break; }
     double* hp = h->h_pin;

@@ -41,8 +41,23 @@ cudaError_t launch_colnorms(const double* X, int64_t n, int K, double* out, cuda
 cudaError_t launch_scale_cols(const double* X, int64_t n, int K, const double* inv, double* Y, cudaStream_t s);
 cudaError_t launch_f2d_acc(const float* src, double* dst, int64_t count, cudaStream_t s);
 // identity-function apply: W[:, c0:c0+K] = d (.) V - A V for V packed n x K
-cudaError_t launch_laplacian_apply(const Graph& g, const PartDev& p, const double* Vp, int K, int c0, double* W,
-                                   int64_t ldw, cudaStream_t s);
+cudaError_t launch_laplacian_apply(const Graph& g, const PartDev& p, const double* Vp, int K, int c0,
+                                   const int32_t* perm, double* W, int64_t ldw, cudaStream_t s);
+
+// node relabelling by decreasing degree: perm[new] = old, iperm[old] = new,
+// relabelled CSR in new_rp / new_col; tmp holds relabel_tmp_i64(n) int64
+cudaError_t launch_relabel(const Graph& g, int32_t* perm, int32_t* iperm, int32_t* new_rp, int32_t* new_col,
+                           int64_t* tmp, cudaStream_t s);
+size_t relabel_tmp_i64(int64_t n);
+cudaError_t launch_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* tmp, cudaStream_t s);
+// partition by prefix of cost(row) = deg + kRowCost (hub rows weighted x3); tmp: 2 (n + 1) + n / 1024 + 4 int64
+cudaError_t launch_partition_weighted(const Graph& g, PartDev& p, int64_t* tmp, cudaStream_t s);
+cudaError_t launch_pack_perm(const double* src, int64_t ld, int c0, int kb, int64_t n, double scale,
+                             const int32_t* perm, double* dst, cudaStream_t s);
+cudaError_t launch_apply_out_perm(const double* Vp, const double* X, const double* Df, int64_t n, int K, int c0,
+                                  const int32_t* perm, double* W, int64_t ldw, cudaStream_t s);
+cudaError_t launch_permute_vec(const double* in, int64_t n, const int32_t* perm, bool scatter, double* out,
+                               cudaStream_t s);
 
 // ---- wl_k_cg64.cu / wl_k_cg32.cu
 int cg_grid_f64(int K);  // cooperative grid size of the CG kernel (FP64, K columns)
@@ -64,6 +79,9 @@ cudaError_t launch_combine(int K, const CombineArgs& a, cudaStream_t s);
 
 // ---- wl_k_trace.cu
 cudaError_t launch_philox_sketch(uint16_t* omega, int64_t n, int M, uint64_t seed, cudaStream_t s);
+// dst[r * M + j] = src[perm[r] * M + j]
+cudaError_t launch_permute_rows_u16(const uint16_t* src, int64_t n, int M, const int32_t* perm, uint16_t* dst,
+                                    cudaStream_t s);
 cudaError_t launch_sketch_rhs(const uint16_t* omega, int64_t n, int M, int K, double a, float* B, cudaStream_t s);
 int gram_grid(int64_t n);
 // H = Omega^T Y and G = Y^T Y into out (128 x 64 doubles); partial holds G x 128 x 64 floats

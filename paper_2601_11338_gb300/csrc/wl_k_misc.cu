@@ -2,6 +2,8 @@
 // nnz-balanced row partition, per-CTA degree-class ordering, CSR validation
 // (Sec. 2: simple graph = symmetric, loop-free 0/1 pattern), block packing
 // and the apply epilogue W = D_f (.) V - phi V (Eq. weighted_laplacian).
+#include <algorithm>
+
 #include "wl_host.h"
 
 namespace wl {
@@ -243,32 +245,298 @@ cudaError_t launch_f2d_acc(const float* src, double* dst, int64_t count, cudaStr
 
 // W[:, c0:c0+K] = d (.) V - A V (identity function: L = D - A, Sec. 3.1)
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_laplacian_apply(Graph g, Part pt, const double* Vp, int c0, double* W,
-                                                            int64_t ldw) {
+__global__ void __launch_bounds__(kBlock) k_laplacian_apply(Graph g, Part pt, const double* Vp, int c0,
+                                                            const int32_t* perm, double* W, int64_t ldw) {
   using C = Cfg<double, K>;
   constexpr int VW = C::VW;
   __shared__ __align__(16) double s_gath[kBlock * VW];
   auto pre = [&](int row, int lane_off) { return ldp<double, VW>(Vp + (size_t)row * K + lane_off); };
   auto fin = [&](int row, int deg, int lane_off, const double (&nb)[VW], const Pack<double, VW>& vv) {
 #pragma unroll
-    for (int v = 0; v < VW; ++v) W[(size_t)row * ldw + c0 + lane_off + v] = (double)deg * vv.v[v] - nb[v];
+    for (int v = 0; v < VW; ++v)
+      W[(size_t)(perm ? perm[row] : row) * ldw + c0 + lane_off + v] = (double)deg * vv.v[v] - nb[v];
   };
   for_rows_gather<double, K>(g, pt, Vp, s_gath, pre, fin);
 }
 
-cudaError_t launch_laplacian_apply(const Graph& g, const PartDev& p, const double* Vp, int K, int c0, double* W,
-                                   int64_t ldw, cudaStream_t s) {
+cudaError_t launch_laplacian_apply(const Graph& g, const PartDev& p, const double* Vp, int K, int c0,
+                                   const int32_t* perm, double* W, int64_t ldw, cudaStream_t s) {
   const Part pt = p.view();
   switch (K) {
-    case 1: k_laplacian_apply<1><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, W, ldw); break;
-    case 2: k_laplacian_apply<2><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, W, ldw); break;
-    case 4: k_laplacian_apply<4><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, W, ldw); break;
-    case 8: k_laplacian_apply<8><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, W, ldw); break;
-    case 16: k_laplacian_apply<16><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, W, ldw); break;
-    case 32: k_laplacian_apply<32><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, W, ldw); break;
-    case 64: k_laplacian_apply<64><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, W, ldw); break;
+    case 1: k_laplacian_apply<1><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, perm, W, ldw); break;
+    case 2: k_laplacian_apply<2><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, perm, W, ldw); break;
+    case 4: k_laplacian_apply<4><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, perm, W, ldw); break;
+    case 8: k_laplacian_apply<8><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, perm, W, ldw); break;
+    case 16: k_laplacian_apply<16><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, perm, W, ldw); break;
+    case 32: k_laplacian_apply<32><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, perm, W, ldw); break;
+    case 64: k_laplacian_apply<64><<<p.G, kBlock, 0, s>>>(g, pt, Vp, c0, perm, W, ldw); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+}  // namespace wl
+
+// ======================================================================
+// Node relabelling by decreasing degree (optional at build): nodes of
+// similar degree become contiguous, so the most gathered rows (the hubs and
+// their peers) share cache lines and stay in L2. The relabelled CSR keeps
+// the pattern P A P^T; every vector crossing the C ABI is permuted on the
+// way in and out, so callers never see the internal order.
+// ======================================================================
+namespace wl {
+
+constexpr int kScanBlock = 1024;
+
+// exclusive scan of in[0..n) (int64) into out[0..n] (out[n] = total);
+// two levels: per-block sums, then a single-CTA scan of the block sums.
+__global__ void k_scan_blocks(const int64_t* in, int64_t n, int64_t* out, int64_t* bsum) {
+  __shared__ int64_t s[kScanBlock];
+  const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+  s[threadIdx.x] = (i < n) ? in[i] : 0;
+  __syncthreads();
+  for (int off = 1; off < kScanBlock; off <<= 1) {
+    const int64_t v = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+    __syncthreads();
+    s[threadIdx.x] += v;
+    __syncthreads();
+  }
+  if (i < n) out[i] = s[threadIdx.x] - ((i < n) ? in[i] : 0);
+  if (threadIdx.x == kScanBlock - 1) bsum[blockIdx.x] = s[threadIdx.x];
+}
+
+__global__ void k_scan_sums(int64_t* bsum, int64_t nb) {
+  // one CTA, sequential chunks of kScanBlock
+  __shared__ int64_t s[kScanBlock];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += kScanBlock) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t x = (i < nb) ? bsum[i] : 0;
+    s[threadIdx.x] = x;
+    __syncthreads();
+    for (int off = 1; off < kScanBlock; off <<= 1) {
+      const int64_t v = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+      __syncthreads();
+      s[threadIdx.x] += v;
+      __syncthreads();
+    }
+    if (i < nb) bsum[i] = carry + s[threadIdx.x] - x;  // exclusive
+    __syncthreads();
+    if (threadIdx.x == kScanBlock - 1) carry += s[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void k_scan_add(int64_t* out, int64_t n, const int64_t* bsum) {
+  const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+  if (i < n) out[i] += bsum[blockIdx.x];
+  if (i == 0) out[n] = bsum[gridDim.x];
+}
+
+cudaError_t launch_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* tmp, cudaStream_t s) {
+  const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+  if (n == 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+  k_scan_blocks<<<(unsigned)nb, kScanBlock, 0, s>>>(in, n, out, tmp);
+  k_scan_sums<<<1, kScanBlock, 0, s>>>(tmp, nb);
+  k_scan_add<<<(unsigned)nb, kScanBlock, 0, s>>>(out, n, tmp);
+  return cudaGetLastError();
+}
+
+// ---- stable counting sort of nodes by key = 31 - floor(log2(deg + 1)) (hubs first)
+constexpr int kSortChunk = 4096;
+constexpr int kKeys = 32;
+
+__device__ __forceinline__ int degree_key(const int32_t* row_ptr, int64_t i) {
+  const int d = row_ptr[i + 1] - row_ptr[i];
+  return 31 - (31 - __clz(d + 1));  // = __clz(d + 1): larger degree -> smaller key
+}
+
+// hist[key * nchunks + chunk]
+__global__ void k_key_hist(const int32_t* row_ptr, int64_t n, int64_t* hist, int nchunks) {
+  __shared__ int h[kKeys];
+  if (threadIdx.x < kKeys) h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t b = (int64_t)blockIdx.x * kSortChunk;
+  for (int64_t i = b + threadIdx.x; i < b + kSortChunk && i < n; i += blockDim.x)
+    atomicAdd(&h[degree_key(row_ptr, i)], 1);
+  __syncthreads();
+  if (threadIdx.x < kKeys) hist[(int64_t)threadIdx.x * nchunks + blockIdx.x] = h[threadIdx.x];
+}
+
+// one warp per chunk scatters in row order (stable): perm[new] = old
+__global__ void k_key_scatter(const int32_t* row_ptr, int64_t n, const int64_t* off, int nchunks, int32_t* perm) {
+  __shared__ int64_t cur[kKeys];
+  const int lane = threadIdx.x;
+  if (lane < kKeys) cur[lane] = off[(int64_t)lane * nchunks + blockIdx.x];
+  __syncwarp();
+  const int64_t b = (int64_t)blockIdx.x * kSortChunk;
+  for (int64_t base = b; base < b + kSortChunk && base < n; base += 32) {
+    const int64_t i = base + lane;
+    const bool valid = i < n && i < b + kSortChunk;
+    const int key = valid ? degree_key(row_ptr, i) : -1;
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
+    const unsigned peers = __match_any_sync(0xffffffffu, key) & act;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    const int leader = __ffs(peers) - 1;
+    int64_t pos = 0;
+    if (valid && lane == leader) pos = cur[key];
+    pos = __shfl_sync(0xffffffffu, pos, valid ? leader : lane);
+    if (valid) perm[pos + rank] = (int32_t)i;
+    __syncwarp();
+    if (valid && lane == leader) cur[key] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+__global__ void k_inverse_perm(const int32_t* perm, int64_t n, int32_t* iperm) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    iperm[perm[i]] = (int32_t)i;
+}
+
+__global__ void k_perm_degrees(const int32_t* row_ptr, const int32_t* perm, int64_t n, int64_t* deg) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t o = perm[i];
+    deg[i] = row_ptr[o + 1] - row_ptr[o];
+  }
+}
+
+__global__ void k_i64_to_i32(const int64_t* in, int64_t n, int32_t* out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)in[i];
+}
+
+// warp per new row: copy the old row's neighbours mapped to new labels
+__global__ void k_perm_cols(const int32_t* row_ptr, const int32_t* col, const int32_t* perm, const int32_t* iperm,
+                            const int32_t* new_rp, int64_t n, int32_t* new_col) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nw) {
+    const int32_t o = perm[r];
+    const int beg = row_ptr[o], end = row_ptr[o + 1], dst = new_rp[r];
+    for (int e = beg + lane; e < end; e += 32) new_col[dst + (e - beg)] = iperm[col[e]];
+  }
+}
+
+cudaError_t launch_relabel(const Graph& g, int32_t* perm, int32_t* iperm, int32_t* new_rp, int32_t* new_col,
+                           int64_t* tmp_i64 /* 2 (n + 1) + 2 * 32 * chunks + 2 */, cudaStream_t s) {
+  const int64_t n = g.n;
+  if (n == 0) return cudaMemsetAsync(new_rp, 0, sizeof(int32_t), s);
+  const int nch = (int)((n + kSortChunk - 1) / kSortChunk);
+  int64_t* hist = tmp_i64;                           // 32 * nch (+1)
+  int64_t* off = hist + (int64_t)kKeys * nch + 1;    // 32 * nch + 1
+  int64_t* sc = off + (int64_t)kKeys * nch + 1;      // scan scratch
+  k_key_hist<<<nch, 256, 0, s>>>(g.row_ptr, n, hist, nch);
+  cudaError_t e = launch_scan(hist, (int64_t)kKeys * nch, off, sc, s);
+  if (e != cudaSuccess) return e;
+  k_key_scatter<<<nch, 32, 0, s>>>(g.row_ptr, n, off, nch, perm);
+  const unsigned gb = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32);
+  k_inverse_perm<<<gb, 256, 0, s>>>(perm, n, iperm);
+  int64_t* deg = sc + (n / kScanBlock + 2);   // n
+  int64_t* rp64 = deg + n;                    // n + 1
+  int64_t* sc2 = rp64 + n + 1;
+  k_perm_degrees<<<gb, 256, 0, s>>>(g.row_ptr, perm, n, deg);
+  e = launch_scan(deg, n, rp64, sc2, s);
+  if (e != cudaSuccess) return e;
+  k_i64_to_i32<<<gb, 256, 0, s>>>(rp64, n, new_rp);
+  const int64_t warps = std::min<int64_t>(n, 152 * 64);
+  k_perm_cols<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(g.row_ptr, g.col, perm, iperm, new_rp, n, new_col);
+  return cudaGetLastError();
+}
+
+size_t relabel_tmp_i64(int64_t n) {
+  const int64_t nch = (n + kSortChunk - 1) / kSortChunk;
+  return (size_t)(2 * (kKeys * nch + 1) + (kKeys * nch) / kScanBlock + 2 + (n / kScanBlock + 2) + n + (n + 1) +
+                  n / kScanBlock + 4);
+}
+
+// ---- cost-weighted partition: cost(row) = deg + kRowCost, hub rows (deg > Tc) x3
+__global__ void k_row_cost(const int32_t* row_ptr, int64_t n, int Tc, int64_t* cost) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int d = row_ptr[i + 1] - row_ptr[i];
+    cost[i] = (int64_t)(d > Tc ? 3 * d : d) + kRowCost;
+  }
+}
+
+__global__ void k_partition_prefix(const int64_t* prefix, int64_t n, int G, int32_t* rb) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g > G) return;
+  if (g == 0) { rb[0] = 0; return; }
+  if (g == G) { rb[G] = (int32_t)n; return; }
+  const double target = (double)prefix[n] * (double)g / (double)G;
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((double)prefix[mid] < target) lo = mid + 1; else hi = mid;
+  }
+  rb[g] = (int32_t)lo;
+}
+
+cudaError_t launch_partition_weighted(const Graph& g, PartDev& p, int64_t* tmp /* 2 (n + 1) + n / 1024 + 4 */,
+                                      cudaStream_t s) {
+  const int64_t n = g.n;
+  if (p.Tw > kOrderBuckets - 3) return cudaErrorInvalidValue;
+  int64_t* cost = tmp;
+  int64_t* prefix = cost + n + 1;
+  int64_t* sc = prefix + n + 1;
+  const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
+  k_row_cost<<<gb, 256, 0, s>>>(g.row_ptr, n, p.Tc, cost);
+  cudaError_t e = launch_scan(cost, n, prefix, sc, s);
+  if (e != cudaSuccess) return e;
+  k_partition_prefix<<<(p.G + 1 + 255) / 256, 256, 0, s>>>(prefix, n, p.G, p.rb);
+  k_order<<<p.G, 256, 0, s>>>(g.row_ptr, p.rb, p.Tw, p.Tc, p.meta, p.seg);
+  return cudaGetLastError();
+}
+
+// ---- permuted copies across the API boundary
+// dst[new * K + c] = scale * src[perm[new] * ld + c0 + c]
+__global__ void k_pack_perm(const double* src, int64_t ld, int c0, int kb, int64_t n, double scale,
+                            const int32_t* perm, double* dst) {
+  const int64_t total = n * kb;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / kb;
+    const int c = (int)(e % kb);
+    dst[e] = scale * src[(int64_t)perm[i] * ld + c0 + c];
+  }
+}
+
+// W[perm[i] * ldw + c0 + c] = Df[i] * Vp[i * K + c] - X[i * K + c]
+__global__ void k_apply_out_perm(const double* Vp, const double* X, const double* Df, int64_t n, int K, int c0,
+                                 const int32_t* perm, double* W, int64_t ldw) {
+  const int64_t total = n * K;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / K;
+    const int c = (int)(e % K);
+    W[(int64_t)perm[i] * ldw + c0 + c] = Df[i] * Vp[e] - X[e];
+  }
+}
+
+// out[perm[i]] = in[i] (scatter to caller order) or out[i] = in[perm[i]] (gather)
+__global__ void k_permute_vec(const double* in, int64_t n, const int32_t* perm, int scatter, double* out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (scatter) out[perm[i]] = in[i]; else out[i] = in[perm[i]];
+  }
+}
+
+cudaError_t launch_pack_perm(const double* src, int64_t ld, int c0, int kb, int64_t n, double scale,
+                             const int32_t* perm, double* dst, cudaStream_t s) {
+  k_pack_perm<<<grid_for(n * kb), 256, 0, s>>>(src, ld, c0, kb, n, scale, perm, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_out_perm(const double* Vp, const double* X, const double* Df, int64_t n, int K, int c0,
+                                  const int32_t* perm, double* W, int64_t ldw, cudaStream_t s) {
+  k_apply_out_perm<<<grid_for(n * K), 256, 0, s>>>(Vp, X, Df, n, K, c0, perm, W, ldw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_vec(const double* in, int64_t n, const int32_t* perm, bool scatter, double* out,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_permute_vec<<<grid_for(n), 256, 0, s>>>(in, n, perm, scatter ? 1 : 0, out);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,20 @@ cudaError_t launch_philox_sketch(uint16_t* omega, int64_t n, int M, uint64_t see
   return cudaGetLastError();
 }
 
+__global__ void permute_rows_u16(const uint16_t* src, int64_t n, int M, const int32_t* perm, uint16_t* dst) {
+  const int64_t total = n * M;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / M;
+    dst[e] = src[(int64_t)perm[r] * M + (e % M)];
+  }
+}
+
+cudaError_t launch_permute_rows_u16(const uint16_t* src, int64_t n, int M, const int32_t* perm, uint16_t* dst,
+                                    cudaStream_t s) {
+  permute_rows_u16<<<grid_cap(n * M, 256, 152 * 32), 256, 0, s>>>(src, n, M, perm, dst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sketch_rhs(const uint16_t* omega, int64_t n, int M, int K, double a, float* B, cudaStream_t s) {
   sketch_rhs<<<grid_cap(n * K, 256, 152 * 32), 256, 0, s>>>(omega, n, M, K, (float)a, B);
   return cudaGetLastError();

@@ -475,6 +475,7 @@ struct CombineArgs {
   int c0;
   int ldT;
   int ntau;
+  const int32_t* perm;  // internal row i goes to caller row perm[i] (NULL: identity)
 };
 
 constexpr int kMaxTau = 8;
@@ -497,7 +498,8 @@ __global__ void __launch_bounds__(kBlock) combine(CombineArgs a) {
         if (t < a.ntau) acc[t] += vij * __ldg(yc + (size_t)t * a.ldT + j);
     }
     const double s = a.nrm[c];
-    for (int t = 0; t < a.ntau; ++t) a.out[(size_t)t * a.tstride + i * a.ld + a.c0 + c] = s * acc[t];
+    const size_t io = a.perm ? (size_t)a.perm[i] : i;
+    for (int t = 0; t < a.ntau; ++t) a.out[(size_t)t * a.tstride + io * a.ld + a.c0 + c] = s * acc[t];
   }
 }
 

@@ -42,7 +42,7 @@ class wl_params(ctypes.Structure):
     _fields_ = [("f", ctypes.c_int), ("alpha", ctypes.c_double), ("alpha_rel", ctypes.c_double),
                 ("beta", ctypes.c_double), ("mu", ctypes.c_double), ("prec", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
-                ("outer_tol", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("outer_tol", ctypes.c_double), ("stream", ctypes.c_void_p), ("reorder", ctypes.c_int)]
 
 
 class wl_stats(ctypes.Structure):
@@ -122,8 +122,8 @@ def _ptr(a):
 
 
 def make_params(f=WL_F_RESOLVENT, alpha=0.0, alpha_rel=0.0, beta=0.0, mu=0.0, prec=WL_FP64, tol=0.0,
-                max_iter=0, max_outer=0, outer_tol=0.0, stream=None):
-    return wl_params(f, alpha, alpha_rel, beta, mu, prec, tol, max_iter, max_outer, outer_tol, stream)
+                max_iter=0, max_outer=0, outer_tol=0.0, stream=None, reorder=1):
+    return wl_params(f, alpha, alpha_rel, beta, mu, prec, tol, max_iter, max_outer, outer_tol, stream, reorder)
 
 
 class Handle:

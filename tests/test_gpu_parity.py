@@ -43,14 +43,15 @@ def oracle_for(A, mu, alpha):
 
 
 # ------------------------------------------------------------ the small workload
+@pytest.mark.parametrize("reorder", [0, 1])
 @pytest.mark.parametrize("prec", ["fp64", "refined"])
-def test_erdos_renyi_allwalk_resolvent(prec):
+def test_erdos_renyi_allwalk_resolvent(prec, reorder):
     """ER n = 2000, mean degree 8, all-walk resolvent, alpha = 0.5 / lambda_max(A):
     D_f, L V for 4 Gaussian vectors, exp(-tau L) e_1 at tau = 1."""
     g = wlgen.erdos_renyi(2000, 8, 20260000)
     A = dense(g)
     w = WL(g, variant="allwalk", alpha_rel=0.5, prec=prec, tol=1e-13 if prec == "fp64" else 1e-12,
-           outer_tol=1e-13)
+           outer_tol=1e-13, reorder=reorder)
     info = w.info
     lmax = spectral.lambda_max(A)
     assert abs(info["lambda_max"] - lmax) <= 1e-9 * lmax
@@ -82,12 +83,14 @@ def hub_graph():
     return wlgen.csr_from_edges(n, s, d, "hub")
 
 
+@pytest.mark.parametrize("reorder", [0, 1])
 @pytest.mark.parametrize("variant,mu", [("nbt", 1.0), ("btdw", 0.5), ("btdw", 0.25), ("allwalk", 0.0)])
 @pytest.mark.parametrize("prec", ["fp64", "refined"])
-def test_variants_apply_and_degrees(variant, mu, prec):
+def test_variants_apply_and_degrees(variant, mu, prec, reorder):
     g = hub_graph()
     A = dense(g)
-    w = WL(g, variant=variant, mu=mu, alpha_rel=0.5, prec=prec, tol=1e-13 if prec == "fp64" else 1e-12)
+    w = WL(g, variant=variant, mu=mu, alpha_rel=0.5, prec=prec, tol=1e-13 if prec == "fp64" else 1e-12,
+           reorder=reorder)
     info = w.info
     rho = spectral.rho_companion(A, mu)
     assert abs(info["rho"] - rho) <= 1e-7 * rho
@@ -117,11 +120,12 @@ def test_nbt_diffusion_several_taus(prec):
         assert U[t].min() >= -1e-12
 
 
-def test_identity_function_is_combinatorial_laplacian():
+@pytest.mark.parametrize("reorder", [0, 1])
+def test_identity_function_is_combinatorial_laplacian(reorder):
     g = hub_graph()
     A = dense(g)
     L = graph.combinatorial_laplacian(A)
-    w = WL(g, f="identity")
+    w = WL(g, f="identity", reorder=reorder)
     np.testing.assert_array_equal(cpu(w.degrees()), A.sum(1))
     V = wlgen.gaussian_block(g.n, 8, 3)
     np.testing.assert_allclose(cpu(w.apply(torch.as_tensor(V, device="cuda"))), L @ V, rtol=0, atol=1e-12)
@@ -212,9 +216,10 @@ def test_iteration_cap_reports_no_convergence():
     assert rc == wl.WL_ERR_NO_CONVERGENCE and w.last.iters == 2
 
 
-def test_host_pointers_match_device_pointers():
+@pytest.mark.parametrize("reorder", [0, 1])
+def test_host_pointers_match_device_pointers(reorder):
     g = wlgen.erdos_renyi(800, 8, 9)
-    w = WL(g, alpha_rel=0.5, tol=1e-13)
+    w = WL(g, alpha_rel=0.5, tol=1e-13, reorder=reorder)
     from paper_2601_11338_gb300 import wl
     V = wlgen.gaussian_block(g.n, 4, 1)
     Wh = np.zeros_like(V)

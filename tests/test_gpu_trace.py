@@ -25,10 +25,11 @@ def WL(g, **kw):
     return WalkLaplacian(g.row_ptr.astype(np.int32), g.col_idx, g.n, **kw)
 
 
+@pytest.mark.parametrize("reorder", [0, 1])
 @pytest.mark.parametrize("M", [64, 7, 2])
-def test_sketch_is_bit_exact(M):
+def test_sketch_is_bit_exact(M, reorder):
     g = wlgen.erdos_renyi(1000, 8, 3)
-    w = WL(g, alpha_rel=0.5)
+    w = WL(g, alpha_rel=0.5, reorder=reorder)
     om = torch.empty((g.n, M), dtype=torch.int16, device="cuda")
     w.trace(M, 12345 + M, om)
     got = om.cpu().numpy().view(np.uint16)
@@ -36,11 +37,11 @@ def test_sketch_is_bit_exact(M):
     assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("variant,mu,M", [("allwalk", 0.0, 64), ("nbt", 1.0, 16), ("btdw", 0.5, 7)])
-def test_estimate_matches_literal_leave_one_out(variant, mu, M):
+@pytest.mark.parametrize("variant,mu,M,reorder", [("allwalk", 0.0, 64, 1), ("nbt", 1.0, 16, 0), ("btdw", 0.5, 7, 1)])
+def test_estimate_matches_literal_leave_one_out(variant, mu, M, reorder):
     g = wlgen.erdos_renyi(700, 8, 4)
     A = graph.dense_adjacency(g.row_ptr, g.col_idx, g.n)
-    w = WL(g, variant=variant, mu=mu, alpha_rel=0.5, tol=1e-7)
+    w = WL(g, variant=variant, mu=mu, alpha_rel=0.5, tol=1e-7, reorder=reorder)
     alpha = w.info["alpha"]
     phi = walks.phi_resolvent_closed(A, mu, alpha)
     seed = 777 + M
