@@ -113,7 +113,7 @@ struct wl_handle {
   double a_scale = 1;             // phi = a_scale * M^{-1}
   cudaStream_t stream = nullptr;
   GridBar* bar = nullptr;
-  std::map<std::tuple<int, int, int>, PartDev> parts;
+  std::map<std::tuple<int, int, int, int>, PartDev> parts;
   Buf csr_rp, csr_col;
   Buf x, r, p, q;         // CG vectors (FP64 or FP32), n * 64 doubles each at most
   Buf x64, b64, r64;      // refinement
@@ -186,8 +186,11 @@ void prof_reset(wl_handle* h) {
 // count an untimed launch
 inline void counted(wl_handle* h, int n = 1) { h->launches += n; }
 
-int get_part(wl_handle* h, int G, int Tw, int Tc, PartDev** out) {
-  auto key = std::make_tuple(G, Tw, Tc);
+// Partition for a persistent kernel of G CTAs working on K columns of
+// `vbytes`-byte values: a row moves about 10 K vbytes per CG iteration (the
+// vector streams), an entry 4 + K vbytes (index and gathered row).
+int get_part(wl_handle* h, int G, int Tw, int Tc, PartDev** out, int K = 16, int vbytes = 4) {
+  auto key = std::make_tuple(G, Tw, Tc, K * vbytes);
   auto it = h->parts.find(key);
   if (it != h->parts.end()) {
     *out = &it->second;
@@ -197,6 +200,8 @@ int get_part(wl_handle* h, int G, int Tw, int Tc, PartDev** out) {
   p.G = G;
   p.Tw = Tw;
   p.Tc = Tc;
+  p.row_bytes = 10 * K * vbytes;
+  p.entry_bytes = 4 + K * vbytes;
   WL_CU(cudaMalloc(&p.rb, sizeof(int32_t) * (G + 1)));
   WL_CU(cudaMalloc(&p.seg, sizeof(int32_t) * 4 * G));
   WL_CU(cudaMalloc(&p.meta, sizeof(int4) * std::max<int64_t>(h->n, 1)));
@@ -258,7 +263,7 @@ int solve_fp64(wl_handle* h, const double* b, double* x, int K, double tol, bool
   int Tw, Tc;
   thresholds_f64(K, &Tw, &Tc);
   PartDev* pd;
-  WL_TRY(get_part(h, G, Tw, Tc, &pd));
+  WL_TRY(get_part(h, G, Tw, Tc, &pd, K, 8));
   const size_t nk = (size_t)h->n * K;
   WL_TRY(ensure(h->r, nk * 8));
   WL_TRY(ensure(h->p, nk * 8));
@@ -273,7 +278,7 @@ int solve_fp64(wl_handle* h, const double* b, double* x, int K, double tol, bool
     PartDev* pr;
     int Twr, Tcr;
     thresholds_f64(K, &Twr, &Tcr);
-    WL_TRY(get_part(h, Gr, Twr, Tcr, &pr));
+    WL_TRY(get_part(h, Gr, Twr, Tcr, &pr, K, 8));
     ResArgs ra{h->g, pr->view(), x, nullptr, b, (double*)h->r.p, nullptr, h->ca, h->cA, h->cD,
                (double*)h->part.p, sm.rr, sm.bb, h->bar, 0};
     WL_TRY(reset_bar(h));
@@ -329,12 +334,12 @@ int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, b
   int Tw, Tc;
   thresholds_f32(K, &Tw, &Tc);
   PartDev* pd;
-  WL_TRY(get_part(h, G, Tw, Tc, &pd));
+  WL_TRY(get_part(h, G, Tw, Tc, &pd, K, 4));
   const int Gr = res_grid(K);
   int Twr, Tcr;
   thresholds_f64(K, &Twr, &Tcr);
   PartDev* pr;
-  WL_TRY(get_part(h, Gr, Twr, Tcr, &pr));
+  WL_TRY(get_part(h, Gr, Twr, Tcr, &pr, K, 8));
   const size_t nk = (size_t)h->n * K;
   WL_TRY(ensure(h->r, nk * 4));
   WL_TRY(ensure(h->p, nk * 4));
@@ -458,7 +463,7 @@ int lanczos_ext(wl_handle* h, double c0, double cA, double cD, int m, double* th
   int Tw, Tc;
   thresholds_f64(1, &Tw, &Tc);
   PartDev* pd;
-  WL_TRY(get_part(h, G, Tw, Tc, &pd));
+  WL_TRY(get_part(h, G, Tw, Tc, &pd, 1, 8));
   WL_TRY(ensure(h->lan, (size_t)h->n * 3 * 8 + 2 * 512 * 8));
   WL_TRY(ensure(h->part, (size_t)G * 64 * 2 * 8 + 1024));
   Smalls sm = smalls(h);
@@ -918,7 +923,7 @@ int wl_apply(wl_handle* h, const double* V, int64_t ldv, int k, double* W, int64
         PartDev* pd;
         int Tw, Tc;
         thresholds_f64(K, &Tw, &Tc);
-        if ((rc = get_part(h, cg_grid_f64(K), Tw, Tc, &pd)) != WL_OK) break;
+        if ((rc = get_part(h, cg_grid_f64(K), Tw, Tc, &pd, K, 8)) != WL_OK) break;
         counted(h);
         e = launch_laplacian_apply(h->g, *pd, (const double*)h->packV.p, K, c0, h->perm, Wd, ldw, S(h));
         info.nnz_rhs += (double)h->nnz * K;
@@ -1017,7 +1022,7 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
       int Tw, Tc;
       thresholds_f64(K, &Tw, &Tc);
       PartDev* pd;
-      if ((rc = get_part(h, Gs, Tw, Tc, &pd)) != WL_OK) break;
+      if ((rc = get_part(h, Gs, Tw, Tc, &pd, K, 8)) != WL_OK) break;
       if ((rc = ensure(h->part, (size_t)std::max(Gs, 1) * 64 * 2 * 8 + 1024)) != WL_OK) break;
       int m = 0;
       bool converged = false;
@@ -1158,7 +1163,7 @@ int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, u
     int Tw, Tc;
     thresholds_f32(K, &Tw, &Tc);
     PartDev* pd;
-    if ((rc = get_part(h, G, Tw, Tc, &pd)) != WL_OK) break;
+    if ((rc = get_part(h, G, Tw, Tc, &pd, K, 4)) != WL_OK) break;
     if ((rc = ensure(h->part, (size_t)G * 64 * 2 * 8 + 1024)) != WL_OK) break;
     Smalls sm = smalls(h);
     const double tol = std::max(h->prm.tol, 1e-7);

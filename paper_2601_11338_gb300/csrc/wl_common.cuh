@@ -275,7 +275,7 @@ __device__ __forceinline__ void gather_idx_sub(const int (&idx)[BATCH], const T*
       for (int s = 0; s < CH; ++s) {
         const int j = (G == 1) ? idx[u] : __shfl_sync(sm, idx[u], s0 + s, G);
         jj[s] = j;
-        val[s] = ldh<T, VW>(X + (size_t)(j >= 0 ? j : 0) * K + lane_off, pol);
+        if (j >= 0) val[s] = ldh<T, VW>(X + (size_t)j * K + lane_off, pol);  // predicated: no load past the row
       }
 #pragma unroll
       for (int s = 0; s < CH; ++s)
@@ -307,7 +307,7 @@ __device__ __forceinline__ void gather_row_warp(const int32_t* __restrict__ col,
       for (int t = 0; t < CH; ++t) {
         const int j = __shfl_sync(0xffffffffu, idx, w + SUB * (t0 + t));
         jj[t] = j;
-        val[t] = ldh<T, VW>(X + (size_t)(j >= 0 ? j : 0) * K + lane_off, pol);
+        if (j >= 0) val[t] = ldh<T, VW>(X + (size_t)j * K + lane_off, pol);
       }
 #pragma unroll
       for (int t = 0; t < CH; ++t)

@@ -14,6 +14,7 @@ namespace wl {
 struct PartDev {
   int G = 0;
   int Tw = 0, Tc = 0;
+  int row_bytes = 0, entry_bytes = 0;  // partition cost model (bytes per row / per entry)
   int32_t* rb = nullptr;
   int32_t* seg = nullptr;
   int4* meta = nullptr;

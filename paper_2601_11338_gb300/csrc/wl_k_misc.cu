@@ -453,11 +453,14 @@ size_t relabel_tmp_i64(int64_t n) {
                   n / kScanBlock + 4);
 }
 
-// ---- cost-weighted partition: cost(row) = deg + kRowCost, hub rows (deg > Tc) x3
-__global__ void k_row_cost(const int32_t* row_ptr, int64_t n, int Tc, int64_t* cost) {
+// ---- cost-weighted partition, in bytes moved per CG iteration:
+// cost(row) = row_bytes + deg * entry_bytes, with hub rows (deg > Tc,
+// gathered by the whole CTA in a latency-bound chain) counted three times.
+__global__ void k_row_cost(const int32_t* row_ptr, int64_t n, int Tc, int row_bytes, int entry_bytes,
+                           int64_t* cost) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int d = row_ptr[i + 1] - row_ptr[i];
-    cost[i] = (int64_t)(d > Tc ? 3 * d : d) + kRowCost;
+    const int64_t d = row_ptr[i + 1] - row_ptr[i];
+    cost[i] = (int64_t)row_bytes + (d > Tc ? 3 : 1) * d * (int64_t)entry_bytes;
   }
 }
 
@@ -483,7 +486,7 @@ cudaError_t launch_partition_weighted(const Graph& g, PartDev& p, int64_t* tmp /
   int64_t* prefix = cost + n + 1;
   int64_t* sc = prefix + n + 1;
   const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
-  k_row_cost<<<gb, 256, 0, s>>>(g.row_ptr, n, p.Tc, cost);
+  k_row_cost<<<gb, 256, 0, s>>>(g.row_ptr, n, p.Tc, p.row_bytes, p.entry_bytes, cost);
   cudaError_t e = launch_scan(cost, n, prefix, sc, s);
   if (e != cudaSuccess) return e;
   k_partition_prefix<<<(p.G + 1 + 255) / 256, 256, 0, s>>>(prefix, n, p.G, p.rb);
