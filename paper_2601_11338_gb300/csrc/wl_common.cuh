@@ -28,6 +28,9 @@ constexpr int kBlock = 256;        // threads per CTA of the persistent kernels
 #define WL_MIN_BLOCKS 2
 #endif
 constexpr int kMinBlocks = WL_MIN_BLOCKS;  // CTAs per SM the register budget is sized for
+#ifndef WL_BATCH_ENTRIES
+#define WL_BATCH_ENTRIES 16  // neighbour entries per subgroup batch (gathers in flight per lane)
+#endif
 constexpr int kRowCost = 2;        // partition cost of a row beyond its entries
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // every device-side wait gives up after 2 s
 
@@ -104,7 +107,7 @@ struct Cfg {
   static constexpr int NSUB = kBlock / G;          // subgroups per CTA
   // index loads per lane per batch; a batch covers E = G * BS entries and
   // every lane issues E independent gathers for it
-  static constexpr int BS = (16 / G) > 8 ? 8 : ((16 / G) < 1 ? 1 : 16 / G);
+  static constexpr int BS = (WL_BATCH_ENTRIES / G) > 8 ? 8 : ((WL_BATCH_ENTRIES / G) < 1 ? 1 : WL_BATCH_ENTRIES / G);
   static constexpr int E = G * BS;
   // rows with more than Tc entries are gathered by the whole CTA; all others
   // by one subgroup (chains of at most 32 batches)
@@ -164,64 +167,97 @@ __device__ __forceinline__ uint64_t policy_stream() {
   return p;
 }
 
+// Vector loads used inside the persistent kernels. WL_GATHER_LOAD selects the
+// form: 0 = ld.global.cg (L2 only), 1 = default ld.global (L1 allocating;
+// coherent across the grid barriers, whose gpu-scope acquire fence orders
+// them after the other CTAs' writes), 2 = ld.global.cg with an L2
+// eviction-priority policy.
+#ifndef WL_GATHER_LOAD
+#define WL_GATHER_LOAD 1
+#endif
+
 template <typename T, int VW>
-__device__ __forceinline__ Pack<T, VW> ldh(const T* p, uint64_t pol);
+__device__ __forceinline__ Pack<T, VW> ldh_asm(const T* p, uint64_t pol);
+
 template <typename T, int VW>
-__device__ __forceinline__ void sth(T* p, const Pack<T, VW>& x, uint64_t pol);
+__device__ __forceinline__ Pack<T, VW> ldh(const T* p, uint64_t pol) {
+#if WL_GATHER_LOAD == 2
+  return ldh_asm<T, VW>(p, pol);
+#elif WL_GATHER_LOAD == 1
+  (void)pol;
+  return *reinterpret_cast<const Pack<T, VW>*>(p);
+#else
+  (void)pol;
+  return ldp<T, VW>(p);
+#endif
+}
 
 template <>
-__device__ __forceinline__ Pack<float, 4> ldh<float, 4>(const float* p, uint64_t pol) {
+__device__ __forceinline__ Pack<float, 4> ldh_asm<float, 4>(const float* p, uint64_t pol) {
   Pack<float, 4> r;
   asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
                : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]) : "l"(p), "l"(pol));
   return r;
 }
 template <>
-__device__ __forceinline__ Pack<float, 2> ldh<float, 2>(const float* p, uint64_t pol) {
+__device__ __forceinline__ Pack<float, 2> ldh_asm<float, 2>(const float* p, uint64_t pol) {
   Pack<float, 2> r;
   asm volatile("ld.global.cg.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(r.v[0]), "=f"(r.v[1]) : "l"(p), "l"(pol));
   return r;
 }
 template <>
-__device__ __forceinline__ Pack<float, 1> ldh<float, 1>(const float* p, uint64_t pol) {
+__device__ __forceinline__ Pack<float, 1> ldh_asm<float, 1>(const float* p, uint64_t pol) {
   Pack<float, 1> r;
   asm volatile("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r.v[0]) : "l"(p), "l"(pol));
   return r;
 }
 template <>
-__device__ __forceinline__ Pack<double, 2> ldh<double, 2>(const double* p, uint64_t pol) {
+__device__ __forceinline__ Pack<double, 2> ldh_asm<double, 2>(const double* p, uint64_t pol) {
   Pack<double, 2> r;
   asm volatile("ld.global.cg.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(r.v[0]), "=d"(r.v[1]) : "l"(p), "l"(pol));
   return r;
 }
 template <>
-__device__ __forceinline__ Pack<double, 1> ldh<double, 1>(const double* p, uint64_t pol) {
+__device__ __forceinline__ Pack<double, 1> ldh_asm<double, 1>(const double* p, uint64_t pol) {
   Pack<double, 1> r;
   asm volatile("ld.global.cg.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r.v[0]) : "l"(p), "l"(pol));
   return r;
 }
+template <typename T, int VW>
+__device__ __forceinline__ void sth_asm(T* p, const Pack<T, VW>& x, uint64_t pol);
+
 template <>
-__device__ __forceinline__ void sth<float, 4>(float* p, const Pack<float, 4>& x, uint64_t pol) {
+__device__ __forceinline__ void sth_asm<float, 4>(float* p, const Pack<float, 4>& x, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(x.v[0]), "f"(x.v[1]),
                "f"(x.v[2]), "f"(x.v[3]), "l"(pol) : "memory");
 }
 template <>
-__device__ __forceinline__ void sth<float, 2>(float* p, const Pack<float, 2>& x, uint64_t pol) {
+__device__ __forceinline__ void sth_asm<float, 2>(float* p, const Pack<float, 2>& x, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(x.v[0]), "f"(x.v[1]), "l"(pol)
                : "memory");
 }
 template <>
-__device__ __forceinline__ void sth<float, 1>(float* p, const Pack<float, 1>& x, uint64_t pol) {
+__device__ __forceinline__ void sth_asm<float, 1>(float* p, const Pack<float, 1>& x, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(x.v[0]), "l"(pol) : "memory");
 }
 template <>
-__device__ __forceinline__ void sth<double, 2>(double* p, const Pack<double, 2>& x, uint64_t pol) {
+__device__ __forceinline__ void sth_asm<double, 2>(double* p, const Pack<double, 2>& x, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(x.v[0]), "d"(x.v[1]), "l"(pol)
                : "memory");
 }
 template <>
-__device__ __forceinline__ void sth<double, 1>(double* p, const Pack<double, 1>& x, uint64_t pol) {
+__device__ __forceinline__ void sth_asm<double, 1>(double* p, const Pack<double, 1>& x, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(x.v[0]), "l"(pol) : "memory");
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ void sth(T* p, const Pack<T, VW>& x, uint64_t pol) {
+#if WL_GATHER_LOAD == 2
+  sth_asm<T, VW>(p, x, pol);
+#else
+  (void)pol;
+  stp<T, VW>(p, x);
+#endif
 }
 
 // ------------------------------------------------------------------ partition view
