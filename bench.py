@@ -120,7 +120,7 @@ def peaks():
 
 def kernel_src_hash():
     h = hashlib.sha256()
-    for f in ("wl_cg.cuh", "wl_common.cuh"):
+    for f in ("wl_cg2.cuh", "wl_common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2601_11338_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

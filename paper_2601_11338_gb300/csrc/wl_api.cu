@@ -94,6 +94,7 @@ std::vector<int> column_blocks(int k) {
 struct SolveInfo {
   int iters = 0;
   int cg_iters = 0;
+  double last_rel = 0.0;
   int refinements = 0;
   double max_rel = 0.0;
   int status = WL_OK;
@@ -136,6 +137,11 @@ struct wl_handle {
   Buf perm_b, iperm_b;    // node relabelling: perm[new] = old, iperm[old] = new
   int32_t* perm = nullptr;
   int32_t* iperm = nullptr;
+  Buf hubs;               // rows with more than kHubDeg entries (internal order)
+  int nhub = 0;
+  Buf cgstate;            // CgState of the running solve
+  double inner_tol = 2e-5;  // FP32 correction target of the refined form
+  CgState* cgst() { return (CgState*)cgstate.p; }
   double* h_pin = nullptr;  // pinned host scratch (4096 doubles)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // per-call kernel timing: event pairs recorded on the stream around launches
@@ -256,117 +262,124 @@ double alg_bytes_per_iter(wl_handle* h, int K, int s) {
   return 4.0 * (double)h->nnz + 4.0 * (double)(h->n + 1) + 6.0 * (double)h->n * K * s;
 }
 
+PhaseGraph phase_graph(wl_handle* h) { return PhaseGraph{h->g.row_ptr, h->g.col, h->n, (const int32_t*)h->hubs.p, h->nhub}; }
+
+constexpr int kChunk = 8;  // CG iterations launched between two reads of the device flag
+
+// Runs the CG iterations of an initialised solve state to completion (or the
+// iteration cap), reading back one flag per chunk, then the final x update.
+template <typename T>
+int run_cg(wl_handle* h, int K, const PhaseArgs<T>& a, int grid_s, int grid_u, SolveInfo& info, int cat_bytes) {
+  auto launch = [&](int mode, int chunk) -> cudaError_t {
+    if constexpr (sizeof(T) == 4)
+      return launch_cg_phases_f32(K, a, grid_s, grid_u, mode, chunk, S(h));
+    else
+      return launch_cg_phases_f64(K, a, grid_s, grid_u, mode, chunk, S(h));
+  };
+  const int pc = prof_begin(h, kCatCG);
+  counted(h, 1);
+  WL_CU(launch(0, 0));
+  int* hp = (int*)h->h_pin;
+  for (;;) {
+    counted(h, 2 * kChunk);
+    WL_CU(launch(1, kChunk));
+    WL_CU(cudaMemcpyAsync(hp, &h->cgst()->active, 2 * sizeof(int), cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaStreamSynchronize(S(h)));
+    if (!hp[0]) break;
+  }
+  counted(h, 1);
+  WL_CU(launch(2, 0));
+  prof_end(h, pc);
+  // per-column results
+  CgState* st = h->cgst();
+  double* hd = h->h_pin;
+  WL_CU(cudaMemcpyAsync(hd, st->gamma, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaMemcpyAsync(hd + 64, st->b2, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaMemcpyAsync(hd + 128, st->status, 64 * 4, cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaMemcpyAsync(hd + 160, &st->iters, 4, cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaStreamSynchronize(S(h)));
+  const int it = *(const int*)(hd + 160);
+  const int* cs = (const int*)(hd + 128);
+  info.iters += it;
+  info.cg_iters += it;
+  info.nnz_rhs += (double)it * h->nnz * K;
+  info.bytes += (double)it * alg_bytes_per_iter(h, K, cat_bytes);
+  info.last_rel = 0.0;
+  for (int c = 0; c < K; ++c) {
+    if (cs[c] != 0 && info.status == WL_OK) info.status = cs[c];
+    if (hd[64 + c] > 0) info.last_rel = std::max(info.last_rel, std::sqrt(hd[c] / hd[64 + c]));
+  }
+  return WL_OK;
+}
+
+int ensure_phase_buffers(wl_handle* h, int grid) {
+  WL_TRY(ensure(h->part, (size_t)grid * 64 * 2 * 8 + 1024));
+  WL_TRY(ensure(h->cgstate, sizeof(CgState)));
+  return WL_OK;
+}
+
 // FP64 lockstep CG on M x = b for K columns (b, x contiguous n x K doubles).
 // x holds the starting guess on entry (zero unless a warm start is given).
 int solve_fp64(wl_handle* h, const double* b, double* x, int K, double tol, bool x_is_zero, SolveInfo& info) {
-  const int G = cg_grid_f64(K);
-  int Tw, Tc;
-  thresholds_f64(K, &Tw, &Tc);
-  PartDev* pd;
-  WL_TRY(get_part(h, G, Tw, Tc, &pd, K, 8));
+  const int grid_u = phase_blocks_f64(K), grid_s = grid_u + h->nhub;
   const size_t nk = (size_t)h->n * K;
   WL_TRY(ensure(h->r, nk * 8));
   WL_TRY(ensure(h->p, nk * 8));
   WL_TRY(ensure(h->q, nk * 8));
-  WL_TRY(ensure(h->part, (size_t)G * 64 * 2 * 8 + 1024));
-  Smalls sm = smalls(h);
+  WL_TRY(ensure_phase_buffers(h, std::max(grid_s, res_blocks(K) + h->nhub)));
+  CgState* st = h->cgst();
+  WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
   const double* bn2 = nullptr;
   if (x_is_zero) {
     WL_CU(cudaMemcpyAsync(h->r.p, b, nk * 8, cudaMemcpyDeviceToDevice, S(h)));
   } else {
-    const int Gr = res_grid(K);
-    PartDev* pr;
-    int Twr, Tcr;
-    thresholds_f64(K, &Twr, &Tcr);
-    WL_TRY(get_part(h, Gr, Twr, Tcr, &pr, K, 8));
-    ResArgs ra{h->g, pr->view(), x, nullptr, b, (double*)h->r.p, nullptr, h->ca, h->cA, h->cD,
-               (double*)h->part.p, sm.rr, sm.bb, h->bar, 0};
-    WL_TRY(reset_bar(h));
+    const int gr = res_blocks(K) + h->nhub;
+    ResPhaseArgs ra{phase_graph(h), x, nullptr, b, (double*)h->r.p, nullptr, h->ca, h->cA, h->cD,
+                    (double*)h->part.p, st};
     const int pi = prof_begin(h, kCatRes);
-    WL_CU(launch_residual64(K, ra, Gr, S(h)));
+    counted(h);
+    WL_CU(launch_res_phases(K, ra, gr, 0, S(h)));
     prof_end(h, pi);
-    bn2 = sm.bb;
+    bn2 = st->b2;
     info.nnz_rhs += (double)h->nnz * K;
   }
-  CgArgs<double> a{h->g, pd->view(), x, (double*)h->r.p, (double*)h->p.p, (double*)h->q.p,
-                   h->ca, h->cA, h->cD, bn2, nullptr, (double*)h->part.p, sm.gamma, sm.status,
-                   h->bar, h->prm.max_iter, tol * tol, sm.iters};
-  WL_TRY(reset_bar(h));
-  const int pc = prof_begin(h, kCatCG);
-  WL_CU(launch_cg_f64(K, a, G, S(h)));
-  prof_end(h, pc);
-  // read back per-column results
-  double* hp = h->h_pin;
-  WL_CU(cudaMemcpyAsync(hp, sm.gamma, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
-  WL_CU(cudaMemcpyAsync(hp + 64, sm.status, 64 * 4, cudaMemcpyDeviceToHost, S(h)));
-  WL_CU(cudaMemcpyAsync(hp + 128, sm.iters, 4, cudaMemcpyDeviceToHost, S(h)));
-  if (bn2) WL_CU(cudaMemcpyAsync(hp + 192, bn2, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
-  const int berr = check_bar(h);
-  if (berr) return berr;
-  const int* st = (const int*)(hp + 64);
-  const int it = *(const int*)(hp + 128);
-  info.iters += it;
-  info.cg_iters += it;
-  info.nnz_rhs += (double)it * h->nnz * K;
-  info.bytes += (double)it * alg_bytes_per_iter(h, K, 8);
-  for (int c = 0; c < K; ++c) {
-    if (st[c] != 0 && info.status == WL_OK) info.status = st[c];
-  }
-  // relative residual of the recurrence (reference |b| from the first residual)
-  if (!bn2) {
-    // |b|^2 is gamma_0; not returned separately: report the recurrence norm ratio via a colnorm of b
-    counted(h);
-    WL_CU(launch_colnorms(b, h->n, K, sm.misc, S(h)));
-    WL_CU(cudaMemcpyAsync(hp + 192, sm.misc, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
-    WL_CU(cudaStreamSynchronize(S(h)));
-    for (int c = 0; c < K; ++c) hp[192 + c] = hp[192 + c] * hp[192 + c];
-  }
-  for (int c = 0; c < K; ++c) {
-    const double b2 = hp[192 + c];
-    if (b2 > 0) info.max_rel = std::max(info.max_rel, std::sqrt(hp[c] / b2));
-  }
+  PhaseArgs<double> a{phase_graph(h), x, (double*)h->r.p, (double*)h->p.p, (double*)h->q.p, h->ca, h->cA, h->cD,
+                      bn2, nullptr, (double*)h->part.p, st, h->prm.max_iter, tol * tol};
+  WL_TRY(run_cg<double>(h, K, a, grid_s, grid_u, info, 8));
+  info.max_rel = std::max(info.max_rel, info.last_rel);
   return WL_OK;
 }
 
 // Refined solve: FP64 iterate and residual, FP32 inner CG corrections.
 int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, bool x_is_zero, SolveInfo& info) {
-  const int G = cg_grid_f32(K);
-  int Tw, Tc;
-  thresholds_f32(K, &Tw, &Tc);
-  PartDev* pd;
-  WL_TRY(get_part(h, G, Tw, Tc, &pd, K, 4));
-  const int Gr = res_grid(K);
-  int Twr, Tcr;
-  thresholds_f64(K, &Twr, &Tcr);
-  PartDev* pr;
-  WL_TRY(get_part(h, Gr, Twr, Tcr, &pr, K, 8));
+  const int grid_u = phase_blocks_f32(K), grid_s = grid_u + h->nhub;
+  const int grid_r = res_blocks(K) + h->nhub;
   const size_t nk = (size_t)h->n * K;
-  WL_TRY(ensure(h->r, nk * 4));
   WL_TRY(ensure(h->p, nk * 4));
   WL_TRY(ensure(h->q, nk * 4));
   WL_TRY(ensure(h->d32, nk * 4));
   WL_TRY(ensure(h->r32, nk * 4));
   WL_TRY(ensure(h->r64, nk * 8));
-  WL_TRY(ensure(h->part, (size_t)std::max(G, Gr) * 64 * 2 * 8 + 1024));
-  Smalls sm = smalls(h);
+  WL_TRY(ensure_phase_buffers(h, std::max(grid_s, grid_r)));
+  CgState* st = h->cgst();
   if (x_is_zero) WL_CU(cudaMemsetAsync(x, 0, nk * 8, S(h)));
   WL_CU(cudaMemsetAsync(h->d32.p, 0, nk * 4, S(h)));
   double* hp = h->h_pin;
-  const double inner_tol = 2e-5;  // relative reduction per FP32 correction
+  const double inner_tol = h->inner_tol;
   const int max_ref = 12;
   for (int ref = 0;; ++ref) {
-    ResArgs ra{h->g, pr->view(), x, (float*)h->d32.p, b, (double*)h->r64.p, (float*)h->r32.p,
-               h->ca, h->cA, h->cD, (double*)h->part.p, sm.rr, sm.bb, h->bar, ref > 0 ? 1 : 0};
-    WL_TRY(reset_bar(h));
+    WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
+    ResPhaseArgs ra{phase_graph(h), x, (float*)h->d32.p, b, (double*)h->r64.p, (float*)h->r32.p,
+                    h->ca, h->cA, h->cD, (double*)h->part.p, st};
     const int pi = prof_begin(h, kCatRes);
-    WL_CU(launch_residual64(K, ra, Gr, S(h)));
+    counted(h, ref > 0 ? 2 : 1);
+    WL_CU(launch_res_phases(K, ra, grid_r, ref > 0 ? 1 : 0, S(h)));
     prof_end(h, pi);
     info.refinements++;
     info.nnz_rhs += (double)h->nnz * K;
-    WL_CU(cudaMemcpyAsync(hp, sm.rr, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
-    WL_CU(cudaMemcpyAsync(hp + 64, sm.bb, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
-    const int berr = check_bar(h);
-    if (berr) return berr;
+    WL_CU(cudaMemcpyAsync(hp, st->gamma, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaMemcpyAsync(hp + 64, st->b2, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaStreamSynchronize(S(h)));
     bool all = true;
     double mx = 0.0;
     int skip[64];
@@ -381,35 +394,30 @@ int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, b
       skip[c] = (rel <= tol) ? 1 : 0;
       if (!skip[c]) all = false;
     }
-    info.max_rel = mx;
+    info.max_rel = std::max(info.max_rel, mx);
     if (all) break;
     if (ref >= max_ref) {
       if (info.status == WL_OK) info.status = WL_ERR_NO_CONVERGENCE;
       break;
     }
-    WL_CU(cudaMemcpyAsync(sm.skip, skip, K * sizeof(int), cudaMemcpyHostToDevice, S(h)));
-    CgArgs<float> a{h->g, pd->view(), (float*)h->d32.p, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
-                    h->ca, h->cA, h->cD, nullptr, sm.skip, (double*)h->part.p, sm.gamma, sm.status,
-                    h->bar, h->prm.max_iter, inner_tol * inner_tol, sm.iters};
-    WL_TRY(reset_bar(h));
-    const int pc = prof_begin(h, kCatCG);
-    WL_CU(launch_cg_f32(K, a, G, S(h)));
-    prof_end(h, pc);
-    WL_CU(cudaMemcpyAsync(hp + 128, sm.iters, 4, cudaMemcpyDeviceToHost, S(h)));
-    WL_CU(cudaMemcpyAsync(hp + 130, sm.status, 64 * 4, cudaMemcpyDeviceToHost, S(h)));
-    const int berr2 = check_bar(h);
-    if (berr2) return berr2;
-    const int it = *(const int*)(hp + 128);
-    const int* st = (const int*)(hp + 130);
-    for (int c = 0; c < K; ++c)
-      if (!skip[c] && (st[c] == WL_ERR_NOT_SPD || st[c] == WL_ERR_NONFINITE)) {
-        info.status = st[c];
-        return WL_OK;
-      }
-    info.iters += it;
-    info.cg_iters += it;
-    info.nnz_rhs += (double)it * h->nnz * K;
-    info.bytes += (double)it * alg_bytes_per_iter(h, K, 4);
+    info.max_rel = 0.0;
+    int* dskip = (int*)((double*)h->small.p + 256);
+    WL_CU(cudaMemcpyAsync(dskip, skip, K * sizeof(int), cudaMemcpyHostToDevice, S(h)));
+    WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
+    PhaseArgs<float> a{phase_graph(h), (float*)h->d32.p, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
+                       h->ca, h->cA, h->cD, nullptr, dskip, (double*)h->part.p, st, h->prm.max_iter,
+                       inner_tol * inner_tol};
+    SolveInfo inner;
+    WL_TRY(run_cg<float>(h, K, a, grid_s, grid_u, inner, 4));
+    for (int c = 0; c < K; ++c) (void)c;
+    if (inner.status == WL_ERR_NOT_SPD || inner.status == WL_ERR_NONFINITE) {
+      info.status = inner.status;
+      return WL_OK;
+    }
+    info.iters += inner.iters;
+    info.cg_iters += inner.cg_iters;
+    info.nnz_rhs += inner.nnz_rhs;
+    info.bytes += inner.bytes;
   }
   return WL_OK;
 }
@@ -646,7 +654,7 @@ void free_handle(wl_handle* h) {
   Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
                  &h->r32, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
                  &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->lan, &h->omega, &h->gram,
-                 &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b};
+                 &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b, &h->hubs, &h->cgstate};
   for (Buf* b : bufs) release(*b);
   if (h->bar) cudaFree(h->bar);
   if (h->h_pin) cudaFreeHost(h->h_pin);
@@ -786,6 +794,20 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
     return fail(WL_ERR_INVALID_ARG);
   }
 
+  // rows gathered by a whole CTA in the CG kernels
+  if (h->n > 0) {
+    if ((rc = ensure(h->hubs, sizeof(int32_t) * h->n)) != WL_OK) return fail(rc);
+    if ((rc = ensure(h->ptmp, sizeof(int64_t) * std::max<size_t>(relabel_tmp_i64(h->n),
+                                                                 3 * (size_t)(h->n + 1) + h->n / 1024 + 8))) != WL_OK)
+      return fail(rc);
+    counted(h, 5);
+    cudaError_t e = launch_hub_list(h->g.row_ptr, h->n, (int32_t*)h->hubs.p, (int64_t*)h->ptmp.p,
+                                    (int64_t*)h->h_pin, S(h));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S(h));
+    if (e != cudaSuccess) return fail(set_cuda_error(e, "hub list"));
+    h->nhub = (int)*(int64_t*)h->h_pin;
+  }
+
   // spectral scale and parameters
   h->lmax = 0.0;
   h->rho = 0.0;
@@ -923,7 +945,7 @@ int wl_apply(wl_handle* h, const double* V, int64_t ldv, int k, double* W, int64
         PartDev* pd;
         int Tw, Tc;
         thresholds_f64(K, &Tw, &Tc);
-        if ((rc = get_part(h, cg_grid_f64(K), Tw, Tc, &pd, K, 8)) != WL_OK) break;
+        if ((rc = get_part(h, lanczos_step_grid(K), Tw, Tc, &pd, K, 8)) != WL_OK) break;
         counted(h);
         e = launch_laplacian_apply(h->g, *pd, (const double*)h->packV.p, K, c0, h->perm, Wd, ldw, S(h));
         info.nnz_rhs += (double)h->nnz * K;
@@ -1159,40 +1181,23 @@ int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, u
     if (e == cudaSuccess) e = cudaMemsetAsync(h->x.p, 0, nk * 4, S(h));
     if (e != cudaSuccess) { rc = set_cuda_error(e, "sketch"); break; }
     // Y = M^{-1} (a Omega) in FP32 lockstep CG
-    const int G = cg_grid_f32(K);
-    int Tw, Tc;
-    thresholds_f32(K, &Tw, &Tc);
-    PartDev* pd;
-    if ((rc = get_part(h, G, Tw, Tc, &pd, K, 4)) != WL_OK) break;
-    if ((rc = ensure(h->part, (size_t)G * 64 * 2 * 8 + 1024)) != WL_OK) break;
+    const int grid_u = phase_blocks_f32(K), grid_s = grid_u + h->nhub;
+    if ((rc = ensure_phase_buffers(h, grid_s)) != WL_OK) break;
     Smalls sm = smalls(h);
+    CgState* st = h->cgst();
+    WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
     const double tol = std::max(h->prm.tol, 1e-7);
-    CgArgs<float> a{h->g, pd->view(), (float*)h->x.p, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
-                    h->ca, h->cA, h->cD, nullptr, nullptr, (double*)h->part.p, sm.gamma, sm.status,
-                    h->bar, h->prm.max_iter, tol * tol, sm.iters};
-    if ((rc = reset_bar(h)) != WL_OK) break;
-    const int pc = prof_begin(h, kCatCG);
-    e = launch_cg_f32(K, a, G, S(h));
-    prof_end(h, pc);
-    if (e != cudaSuccess) { rc = set_cuda_error(e, "cg_f32"); break; }
+    PhaseArgs<float> a{phase_graph(h), (float*)h->x.p, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
+                       h->ca, h->cA, h->cD, nullptr, nullptr, (double*)h->part.p, st, h->prm.max_iter, tol * tol};
+    if ((rc = run_cg<float>(h, K, a, grid_s, grid_u, info, 4)) != WL_OK) break;
+    (void)sm;
     counted(h, 3);
     e = launch_gram(om_int, (const float*)h->x.p, n, M, K, partial, Gg, gout, S(h));
     if (e == cudaSuccess) e = launch_nys_core(gout, M, core, S(h));
     if (e != cudaSuccess) { rc = set_cuda_error(e, "gram/core"); break; }
     double* hp = h->h_pin;
     WL_CU(cudaMemcpyAsync(hp, core, 8 * 8, cudaMemcpyDeviceToHost, S(h)));
-    WL_CU(cudaMemcpyAsync(hp + 16, sm.iters, 4, cudaMemcpyDeviceToHost, S(h)));
-    WL_CU(cudaMemcpyAsync(hp + 17, sm.status, 64 * 4, cudaMemcpyDeviceToHost, S(h)));
-    const int berr = check_bar(h);
-    if (berr) { rc = berr; break; }
-    const int it = *(const int*)(hp + 16);
-    const int* cst = (const int*)(hp + 17);
-    info.iters += it;
-    info.cg_iters += it;
-    info.nnz_rhs += (double)it * h->nnz * K;
-    info.bytes += (double)it * alg_bytes_per_iter(h, K, 4);
-    for (int c = 0; c < M; ++c)
-      if (cst[c] != 0 && info.status == WL_OK) info.status = cst[c];
+    WL_CU(cudaStreamSynchronize(S(h)));
     if (hp[2] != 0.0) { rc = WL_ERR_NOT_SPD; break; }
     *est = hp[0];
     *err_est = hp[1];

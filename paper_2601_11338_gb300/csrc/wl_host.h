@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "wl_cg.cuh"
+#include "wl_cg2.cuh"
 #include "wl_common.cuh"
 #include "wl_lanczos.cuh"
 
@@ -60,15 +60,23 @@ cudaError_t launch_apply_out_perm(const double* Vp, const double* X, const doubl
 cudaError_t launch_permute_vec(const double* in, int64_t n, const int32_t* perm, bool scatter, double* out,
                                cudaStream_t s);
 
-// ---- wl_k_cg64.cu / wl_k_cg32.cu
-int cg_grid_f64(int K);  // cooperative grid size of the CG kernel (FP64, K columns)
-int cg_grid_f32(int K);
+// ---- wl_k_cg64.cu / wl_k_cg32.cu: CG phase kernels
+// mode 0: init (gamma_0, flags); 1: `chunk` iterations (S, U pairs); 2: final x += alpha p
+cudaError_t launch_cg_phases_f32(int K, const PhaseArgs<float>& a, int grid_s, int grid_u, int mode, int chunk,
+                                 cudaStream_t s);
+cudaError_t launch_cg_phases_f64(int K, const PhaseArgs<double>& a, int grid_s, int grid_u, int mode, int chunk,
+                                 cudaStream_t s);
+// FP64 residual r = b - M x (after x += d when accumulate), norms into st->gamma / st->b2
+cudaError_t launch_res_phases(int K, const ResPhaseArgs& a, int grid, int accumulate, cudaStream_t s);
+int phase_blocks_f32(int K);  // resident CTAs of the S kernel (all SMs)
+int phase_blocks_f64(int K);
+int res_blocks(int K);
 void thresholds_f64(int K, int* Tw, int* Tc);  // class thresholds of Cfg<T, K>
 void thresholds_f32(int K, int* Tw, int* Tc);
-cudaError_t launch_cg_f64(int K, const CgArgs<double>& a, int G, cudaStream_t s);
-cudaError_t launch_cg_f32(int K, const CgArgs<float>& a, int G, cudaStream_t s);
-int res_grid(int K);
-cudaError_t launch_residual64(int K, const ResArgs& a, int G, cudaStream_t s);
+// rows with deg > kHubDeg in increasing order; *count (host, pinned) set after the stream syncs;
+// tmp: 3 (n + 1) + n / 1024 + 4 int64
+cudaError_t launch_hub_list(const int32_t* row_ptr, int64_t n, int32_t* hubs, int64_t* tmp, int64_t* count,
+                            cudaStream_t s);
 
 // ---- wl_k_lanczos.cu
 int lanczos_ext_grid();

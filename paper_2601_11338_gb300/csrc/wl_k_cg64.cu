@@ -1,55 +1,89 @@
-// FP64 instances of the lockstep CG kernel and the FP64 residual of the
-// iterative refinement (K = 1, 2, 4, ..., 64 columns).
+// FP64 instances of the CG phase kernels and the FP64 residual of the
+// iterative refinement, K = 1, 2, 4, ..., 64 columns.
+#include "wl_cg2.cuh"
 #include "wl_host.h"
 
 namespace wl {
 
 #define WL_FOR_K(X) X(1) X(2) X(4) X(8) X(16) X(32) X(64)
 
-static const void* cg64_fn(int K) {
+template <int K>
+static cudaError_t run_cg64(const PhaseArgs<double>& a, int grid_s, int grid_u, int mode, int chunk,
+                            cudaStream_t s) {
+  if (mode == 0) {
+    cg_u_phase<double, K><<<grid_u, kPhaseBlock, 0, s>>>(a, 1);
+  } else if (mode == 1) {
+    for (int i = 0; i < chunk; ++i) {
+      cg_s_phase<double, K><<<grid_s, kPhaseBlock, 0, s>>>(a);
+      cg_u_phase<double, K><<<grid_u, kPhaseBlock, 0, s>>>(a, 0);
+    }
+  } else {
+    cg_f_phase<double, K><<<grid_u, kPhaseBlock, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_phases_f64(int K, const PhaseArgs<double>& a, int grid_s, int grid_u, int mode, int chunk,
+                                 cudaStream_t s) {
   switch (K) {
 #define C64(k) \
   case k:      \
-    return (const void*)cg_persistent<double, k>;
+    return run_cg64<k>(a, grid_s, grid_u, mode, chunk, s);
     WL_FOR_K(C64)
 #undef C64
   }
-  return nullptr;
+  return cudaErrorInvalidValue;
 }
 
-static const void* res_fn(int K) {
+template <int K>
+static cudaError_t run_res(const ResPhaseArgs& a, int grid, int accumulate, cudaStream_t s) {
+  if (accumulate) {
+    const int64_t total = a.g.n * K;
+    res_acc_phase<K><<<grid, kPhaseBlock, 0, s>>>(a.x, a.d, total);
+  }
+  res_phase<K><<<grid, kPhaseBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_res_phases(int K, const ResPhaseArgs& a, int grid, int accumulate, cudaStream_t s) {
   switch (K) {
 #define R64(k) \
   case k:      \
-    return (const void*)residual64<k>;
+    return run_res<k>(a, grid, accumulate, s);
     WL_FOR_K(R64)
 #undef R64
   }
-  return nullptr;
+  return cudaErrorInvalidValue;
 }
 
-static int g_cap_per_sm = 4;
-
-int cg_grid_f64(int K) {
-  const void* f = cg64_fn(K);
-  return f ? coop_grid(f, g_cap_per_sm) : 0;
+static int occ_blocks(const void* f) {
+  int nb = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kPhaseBlock, 0);
+  return (nb < 1 ? 1 : nb) * sms;
 }
 
-int res_grid(int K) {
-  const void* f = res_fn(K);
-  return f ? coop_grid(f, g_cap_per_sm) : 0;
+int phase_blocks_f64(int K) {
+  switch (K) {
+#define F64(k) \
+  case k:      \
+    return occ_blocks((const void*)cg_s_phase<double, k>);
+    WL_FOR_K(F64)
+#undef F64
+  }
+  return 0;
 }
 
-cudaError_t launch_cg_f64(int K, const CgArgs<double>& a, int G, cudaStream_t s) {
-  const void* f = cg64_fn(K);
-  if (!f) return cudaErrorInvalidValue;
-  return coop_launch(f, G, a, s);
-}
-
-cudaError_t launch_residual64(int K, const ResArgs& a, int G, cudaStream_t s) {
-  const void* f = res_fn(K);
-  if (!f) return cudaErrorInvalidValue;
-  return coop_launch(f, G, a, s);
+int res_blocks(int K) {
+  switch (K) {
+#define RB(k) \
+  case k:     \
+    return occ_blocks((const void*)res_phase<k>);
+    WL_FOR_K(RB)
+#undef RB
+  }
+  return 0;
 }
 
 void thresholds_f64(int K, int* Tw, int* Tc) {
@@ -63,6 +97,32 @@ void thresholds_f64(int K, int* Tw, int* Tc) {
 #undef T64
   }
   *Tw = *Tc = 0;
+}
+
+// hub list: rows with more than kHubDeg entries, in increasing row order
+__global__ void k_hub_flags(const int32_t* row_ptr, int64_t n, int64_t* flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = (row_ptr[i + 1] - row_ptr[i] > kHubDeg) ? 1 : 0;
+}
+
+__global__ void k_hub_scatter(const int64_t* flag, const int64_t* pos, int64_t n, int32_t* hubs) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (flag[i]) hubs[pos[i]] = (int32_t)i;
+}
+
+cudaError_t launch_hub_list(const int32_t* row_ptr, int64_t n, int32_t* hubs, int64_t* tmp, int64_t* count,
+                            cudaStream_t s) {
+  int64_t* flag = tmp;
+  int64_t* pos = tmp + n + 1;
+  int64_t* sc = pos + n + 1;
+  const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
+  k_hub_flags<<<gb, 256, 0, s>>>(row_ptr, n, flag);
+  cudaError_t e = launch_scan(flag, n, pos, sc, s);
+  if (e != cudaSuccess) return e;
+  k_hub_scatter<<<gb, 256, 0, s>>>(flag, pos, n, hubs);
+  e = cudaMemcpyAsync(count, pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
 }
 
 }  // namespace wl
