@@ -297,9 +297,13 @@ int run_cg(wl_handle* h, int K, const PhaseArgs<T>& a, int grid_s, int grid_u, S
   WL_CU(cudaMemcpyAsync(hd + 64, st->b2, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
   WL_CU(cudaMemcpyAsync(hd + 128, st->status, 64 * 4, cudaMemcpyDeviceToHost, S(h)));
   WL_CU(cudaMemcpyAsync(hd + 160, &st->iters, 4, cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaMemcpyAsync(hd + 192, st->done, 64 * 4, cudaMemcpyDeviceToHost, S(h)));
   WL_CU(cudaStreamSynchronize(S(h)));
   const int it = *(const int*)(hd + 160);
-  const int* cs = (const int*)(hd + 128);
+  int* cs = (int*)(hd + 128);
+  const int* dn = (const int*)(hd + 192);
+  for (int c = 0; c < K; ++c)  // iteration cap reached with this column still iterating
+    if (!dn[c] && cs[c] == 0) cs[c] = WL_ERR_NO_CONVERGENCE;
   info.iters += it;
   info.cg_iters += it;
   info.nnz_rhs += (double)it * h->nnz * K;
