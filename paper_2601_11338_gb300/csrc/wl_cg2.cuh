@@ -23,6 +23,10 @@ namespace wl {
 
 constexpr int kHubDeg = 256;       // rows with more entries get a CTA each
 constexpr int kPhaseBlock = 256;   // threads per CTA of the phase kernels
+#ifndef WL_PHASE_MINB
+#define WL_PHASE_MINB 6
+#endif
+constexpr int kPhaseMinBlocks = WL_PHASE_MINB;  // CTAs per SM the S kernel's registers are sized for
 
 // Per-solve device state (written by the last CTA of each kernel).
 struct CgState {
@@ -148,7 +152,7 @@ __device__ __forceinline__ void sum_partials(const double* part, int nblk, doubl
 
 // ---------------------------------------------------------------- S phase
 template <typename T, int K>
-__global__ void __launch_bounds__(kPhaseBlock) cg_s_phase(PhaseArgs<T> a) {
+__global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) cg_s_phase(PhaseArgs<T> a) {
   using C = Cfg<T, K>;
   constexpr int VW = C::VW, G = C::G, RPB = kPhaseBlock / G;  // rows per CTA pass
   __shared__ __align__(16) T s_red[kPhaseBlock * VW];
@@ -165,9 +169,9 @@ __global__ void __launch_bounds__(kPhaseBlock) cg_s_phase(PhaseArgs<T> a) {
     al[v] = (T)st->alpha[lane_off + v];
     be[v] = (T)st->beta[lane_off + v];
   }
-  double dacc[VW];
+  T dacc[VW];  // per-thread partials in the working precision (FP64 adds are scarce on this GPU)
 #pragma unroll
-  for (int v = 0; v < VW; ++v) dacc[v] = 0.0;
+  for (int v = 0; v < VW; ++v) dacc[v] = T(0);
 
   auto fin = [&](int64_t row, int deg, const T (&nb)[VW]) {
     const size_t o = (size_t)row * K + lane_off;
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(kPhaseBlock) cg_s_phase(PhaseArgs<T> a) {
       stp<T, VW>(a.x + o, xx);
     }
 #pragma unroll
-    for (int v = 0; v < VW; ++v) dacc[v] += (double)(pp.v[v] * qq.v[v]);
+    for (int v = 0; v < VW; ++v) dacc[v] += pp.v[v] * qq.v[v];
     stp<T, VW>(a.p + o, pp);
     stp<T, VW>(a.q + o, qq);
   };
@@ -228,7 +232,10 @@ __global__ void __launch_bounds__(kPhaseBlock) cg_s_phase(PhaseArgs<T> a) {
       fin(row, end - beg, acc);
     }
   }
-  if (!block_partials_last<T, K>(dacc, a.part, &st->ticket)) return;
+  double dd[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) dd[v] = (double)dacc[v];
+  if (!block_partials_last<T, K>(dd, a.part, &st->ticket)) return;
   // last CTA: delta -> alpha, breakdown checks
   sum_partials<K>(a.part, gridDim.x, s_tmp, s_out);
   if (tid < K) {
@@ -254,7 +261,7 @@ __global__ void __launch_bounds__(kPhaseBlock) cg_s_phase(PhaseArgs<T> a) {
 // ---------------------------------------------------------------- U phase (and init)
 // init = 1: gamma_0 = (r, r), convergence reference and flags, no update.
 template <typename T, int K>
-__global__ void __launch_bounds__(kPhaseBlock) cg_u_phase(PhaseArgs<T> a, int init) {
+__global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) cg_u_phase(PhaseArgs<T> a, int init) {
   using C = Cfg<T, K>;
   constexpr int VW = C::VW, G = C::G;
   __shared__ double s_tmp[kPhaseBlock];
@@ -266,10 +273,11 @@ __global__ void __launch_bounds__(kPhaseBlock) cg_u_phase(PhaseArgs<T> a, int in
   T al[VW];
 #pragma unroll
   for (int v = 0; v < VW; ++v) al[v] = init ? T(0) : (T)st->alpha[mycol + v];
-  double acc[VW];
+  T acc[VW];
 #pragma unroll
-  for (int v = 0; v < VW; ++v) acc[v] = 0.0;
+  for (int v = 0; v < VW; ++v) acc[v] = T(0);
   const size_t nv = (size_t)a.g.n * K / VW;
+#pragma unroll 4
   for (size_t e = (size_t)blockIdx.x * kPhaseBlock + tid; e < nv; e += (size_t)gridDim.x * kPhaseBlock) {
     Pack<T, VW> rr = ld_plain<T, VW>(a.r + e * VW);
     if (!init) {
@@ -279,9 +287,12 @@ __global__ void __launch_bounds__(kPhaseBlock) cg_u_phase(PhaseArgs<T> a, int in
       stp<T, VW>(a.r + e * VW, rr);
     }
 #pragma unroll
-    for (int v = 0; v < VW; ++v) acc[v] += (double)(rr.v[v] * rr.v[v]);
+    for (int v = 0; v < VW; ++v) acc[v] += rr.v[v] * rr.v[v];
   }
-  if (!block_partials_last<T, K>(acc, a.part, &st->ticket)) return;
+  double dd[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) dd[v] = (double)acc[v];
+  if (!block_partials_last<T, K>(dd, a.part, &st->ticket)) return;
   sum_partials<K>(a.part, gridDim.x, s_tmp, s_out);
   if (tid < K) {
     const double gn = s_out[tid];
@@ -361,7 +372,7 @@ __global__ void __launch_bounds__(kPhaseBlock) res_acc_phase(double* x, const fl
 }
 
 template <int K>
-__global__ void __launch_bounds__(kPhaseBlock) res_phase(ResPhaseArgs a) {
+__global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) res_phase(ResPhaseArgs a) {
   using C = Cfg<double, K>;
   constexpr int VW = C::VW, G = C::G, RPB = kPhaseBlock / G;
   __shared__ __align__(16) double s_red[kPhaseBlock * VW];
