@@ -24,7 +24,7 @@ namespace wl {
 constexpr int kHubDeg = 256;       // rows with more entries get a CTA each
 constexpr int kPhaseBlock = 256;   // threads per CTA of the phase kernels
 #ifndef WL_PHASE_MINB
-#define WL_PHASE_MINB 6
+#define WL_PHASE_MINB 5
 #endif
 constexpr int kPhaseMinBlocks = WL_PHASE_MINB;  // CTAs per SM the S kernel's registers are sized for
 
@@ -173,9 +173,28 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) cg_s_phase(Phase
 #pragma unroll
   for (int v = 0; v < VW; ++v) dacc[v] = T(0);
 
-  auto fin = [&](int64_t row, int deg, const T (&nb)[VW]) {
+  T* __restrict__ px = a.x;
+  T* __restrict__ pp_ = a.p;
+  T* __restrict__ pq = a.q;
+  const T* __restrict__ pr = a.r;
+  struct Own {
+    Pack<T, VW> r, x, p, q;
+  };
+  // own-row vectors, loaded before the row's gathers so the two overlap
+  auto own = [&](int64_t row) {
+    Own o;
+    const size_t off = (size_t)row * K + lane_off;
+    o.r = ld_plain<T, VW>(pr + off);
+    if (!first) {
+      o.x = ld_plain<T, VW>(px + off);
+      o.p = ld_plain<T, VW>(pp_ + off);
+      o.q = ld_plain<T, VW>(pq + off);
+    }
+    return o;
+  };
+  auto fin = [&](int64_t row, int deg, const T (&nb)[VW], const Own& w) {
     const size_t o = (size_t)row * K + lane_off;
-    const Pack<T, VW> rr = ld_plain<T, VW>(a.r + o);
+    const Pack<T, VW>& rr = w.r;
     Pack<T, VW> pp, qq;
     const T dg = (T)deg;
     if (first) {
@@ -185,22 +204,20 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) cg_s_phase(Phase
         qq.v[v] = ca * rr.v[v] + cA * nb[v] + cD * dg * rr.v[v];
       }
     } else {
-      Pack<T, VW> xx = ld_plain<T, VW>(a.x + o);
-      pp = ld_plain<T, VW>(a.p + o);
-      qq = ld_plain<T, VW>(a.q + o);
+      Pack<T, VW> xx = w.x;
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
         const T s = ca * rr.v[v] + cA * nb[v] + cD * dg * rr.v[v];
-        xx.v[v] += al[v] * pp.v[v];
-        pp.v[v] = rr.v[v] + be[v] * pp.v[v];
-        qq.v[v] = s + be[v] * qq.v[v];
+        xx.v[v] += al[v] * w.p.v[v];
+        pp.v[v] = rr.v[v] + be[v] * w.p.v[v];
+        qq.v[v] = s + be[v] * w.q.v[v];
       }
-      stp<T, VW>(a.x + o, xx);
+      stp<T, VW>(px + o, xx);
     }
 #pragma unroll
     for (int v = 0; v < VW; ++v) dacc[v] += pp.v[v] * qq.v[v];
-    stp<T, VW>(a.p + o, pp);
-    stp<T, VW>(a.q + o, qq);
+    stp<T, VW>(pp_ + o, pp);
+    stp<T, VW>(pq + o, qq);
   };
 
   if ((int)blockIdx.x < a.g.nhub) {
@@ -215,21 +232,23 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) cg_s_phase(Phase
     for (int v = 0; v < VW; ++v) s_red[tid * VW + v] = acc[v];
     __syncthreads();
     if (tid < G) {
+      const Own w = own(row);
       for (int gr = 1; gr < RPB; ++gr)
 #pragma unroll
         for (int v = 0; v < VW; ++v) acc[v] += s_red[(gr * G + sl) * VW + v];
-      fin(row, end - beg, acc);
+      fin(row, end - beg, acc, w);
     }
   } else {
     const int64_t nblk = (int64_t)gridDim.x - a.g.nhub;
     for (int64_t row = ((int64_t)blockIdx.x - a.g.nhub) * RPB + tid / G; row < a.g.n; row += nblk * RPB) {
       const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
       if (end - beg > kHubDeg) continue;  // gathered by a hub CTA
+      const Own w = own(row);
       T acc[VW];
 #pragma unroll
       for (int v = 0; v < VW; ++v) acc[v] = T(0);
       row_gather<T, K, VW>(a.g.col, beg, end, 1, a.r, lane_off, acc);
-      fin(row, end - beg, acc);
+      fin(row, end - beg, acc, w);
     }
   }
   double dd[VW];
