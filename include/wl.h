@@ -191,6 +191,35 @@ const char* wl_status_string(int status);
 /* Text of the last CUDA error seen by the calling thread (or ""). */
 const char* wl_last_error(void);
 
+/* ------------------------------------------------------------ no-allocation variant */
+/* Walk degrees D_f = phi 1 for the resolvent (the computation of wl_degrees
+ * with prec = WL_FP64, without spectral-radius estimation and without node
+ * relabelling) for callers that cannot allocate GPU memory: code that runs
+ * inside a framework step whose memory planner forbids allocation, hosts
+ * that reserve all device memory up front, and plug-ins that only receive
+ * pre-allocated buffers. The paper has no counterpart to this entry point.
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine: every
+ * intermediate vector lives in one fixed array compiled into libwl.so
+ * (about 12 MB of device memory, held by every GPU that loads the library
+ * until the process exits). Limits and rules:
+ *  - A->n must not exceed 262144 nodes; larger graphs return
+ *    WL_ERR_INVALID_ARG because the fixed array cannot hold their vectors.
+ *  - A (row_ptr, col_idx) and Df are DEVICE pointers owned by the caller; Df
+ *    receives n FP64 values. mu is used only with WL_BTDW. alpha is taken
+ *    as given (alpha * rho(Z_mu) >= 1 shows up as WL_ERR_NOT_SPD); tol <= 0
+ *    means 1e-12, max_iter <= 0 means 2000.
+ *  - The first call on each device looks up the array's device address with
+ *    cudaGetSymbolAddress (that device must be current) and caches it; make
+ *    that first call before any stream capture begins.
+ *  - All calls share the one array and each call resets what must start at
+ *    zero. Calls that overlap on the GPU (different streams or host threads
+ *    at the same time) race on the array and corrupt each other's results;
+ *    serialise them.
+ *  - Returns after the device work has completed. `st` may be NULL. */
+int wl_degrees_noalloc(const wl_csr* A, wl_variant v, double mu, double alpha, double tol, int max_iter,
+                       double* Df, void* stream, wl_stats* st);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,9 @@ def lib():
         L.wl_status_string.argtypes = [c_int]
         L.wl_status_string.restype = ctypes.c_char_p
         L.wl_last_error.restype = ctypes.c_char_p
+        L.wl_degrees_noalloc.argtypes = [ctypes.POINTER(wl_csr), c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, c_int, vp, vp, ctypes.POINTER(wl_stats)]
+        L.wl_degrees_noalloc.restype = c_int
         for name in ("wl_build", "wl_set_params", "wl_degrees", "wl_apply", "wl_expmv", "wl_trace",
                      "wl_set_warm_start", "wl_get_info"):
             getattr(L, name).restype = c_int
@@ -184,6 +187,16 @@ def wl_trace(h, M, seed, omega_out=None, stats=None):
     _check(lib().wl_trace(h.ptr, M, seed, ctypes.byref(est), ctypes.byref(err), _ptr(omega_out),
                           ctypes.byref(st)), "wl_trace")
     return est.value, err.value
+
+
+def wl_degrees_noalloc(row_ptr, col_idx, n, nnz, variant, mu, alpha, Df, tol=0.0, max_iter=0, stream=None,
+                       stats=None, allow=()):
+    """Walk degrees without any GPU allocation by the library (device CSR and
+    output; at most 262144 nodes). See include/wl.h."""
+    A = wl_csr(n, nnz, _ptr(row_ptr), _ptr(col_idx))
+    st = stats if stats is not None else wl_stats()
+    return _check(lib().wl_degrees_noalloc(ctypes.byref(A), variant, mu, alpha, tol, max_iter, _ptr(Df), stream,
+                                           ctypes.byref(st)), "wl_degrees_noalloc", allow)
 
 
 def wl_set_warm_start(h, x0):
