@@ -140,7 +140,7 @@ struct wl_handle {
   Buf hubs;               // rows with more than kHubDeg entries (internal order)
   int nhub = 0;
   Buf cgstate;            // CgState of the running solve
-  double inner_tol = 2e-5;  // FP32 correction target of the refined form
+  double inner_tol = 4e-6;  // floor of the FP32 correction target of the refined form
   CgState* cgst() { return (CgState*)cgstate.p; }
   double* h_pin = nullptr;  // pinned host scratch (4096 doubles)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -369,18 +369,20 @@ int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, b
   if (x_is_zero) WL_CU(cudaMemsetAsync(x, 0, nk * 8, S(h)));
   WL_CU(cudaMemsetAsync(h->d32.p, 0, nk * 4, S(h)));
   double* hp = h->h_pin;
-  const double inner_tol = h->inner_tol;
+  // FP32 correction target: two corrections reach tol when tol >= (inner)^2
+  const double inner_tol = std::min(1e-3, std::max(h->inner_tol, 0.5 * std::sqrt(tol)));
   const int max_ref = 12;
   for (int ref = 0;; ++ref) {
     WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
     ResPhaseArgs ra{phase_graph(h), x, (float*)h->d32.p, b, (double*)h->r64.p, (float*)h->r32.p,
                     h->ca, h->cA, h->cD, (double*)h->part.p, st};
+    const int mode = ref > 0 ? 1 : (x_is_zero ? -1 : 0);  // -1: x = 0, no SpMM needed
     const int pi = prof_begin(h, kCatRes);
     counted(h, ref > 0 ? 2 : 1);
-    WL_CU(launch_res_phases(K, ra, grid_r, ref > 0 ? 1 : 0, S(h)));
+    WL_CU(launch_res_phases(K, ra, grid_r, mode, S(h)));
     prof_end(h, pi);
     info.refinements++;
-    info.nnz_rhs += (double)h->nnz * K;
+    if (mode >= 0) info.nnz_rhs += (double)h->nnz * K;
     WL_CU(cudaMemcpyAsync(hp, st->gamma, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
     WL_CU(cudaMemcpyAsync(hp + 64, st->b2, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
     WL_CU(cudaStreamSynchronize(S(h)));

@@ -384,6 +384,36 @@ struct ResPhaseArgs {
   CgState* st;
 };
 
+// x64 = 0: r64 = b needs no SpMM; r32 = (float) b, d32 = 0, ||b||^2 -> gamma and b2
+template <int K>
+__global__ void __launch_bounds__(kPhaseBlock) res_zero_phase(ResPhaseArgs a) {
+  using C = Cfg<double, K>;
+  constexpr int VW = C::VW;
+  __shared__ double s_tmp[kPhaseBlock];
+  __shared__ double s_out[K];
+  const int tid = threadIdx.x;
+  double acc[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) acc[v] = 0.0;
+  const size_t nv = (size_t)a.g.n * K / VW;
+  for (size_t e = (size_t)blockIdx.x * kPhaseBlock + tid; e < nv; e += (size_t)gridDim.x * kPhaseBlock) {
+    const Pack<double, VW> bb = ld_plain<double, VW>(a.b + e * VW);
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      acc[v] += bb.v[v] * bb.v[v];
+      if (a.r32) a.r32[e * VW + v] = (float)bb.v[v];
+      if (a.d) a.d[e * VW + v] = 0.0f;
+    }
+  }
+  if (!block_partials_last<double, K>(acc, a.part, &a.st->ticket)) return;
+  sum_partials<K>(a.part, gridDim.x, s_tmp, s_out);
+  if (tid < K) {
+    a.st->gamma[tid] = s_out[tid];
+    a.st->b2[tid] = s_out[tid];
+  }
+  if (tid == 0) a.st->ticket = 0;
+}
+
 template <int K>
 __global__ void __launch_bounds__(kPhaseBlock) res_acc_phase(double* x, const float* d, int64_t total) {
   for (int64_t e = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; e < total; e += (int64_t)gridDim.x * kPhaseBlock)

@@ -66,7 +66,8 @@ cudaError_t launch_cg_phases_f32(int K, const PhaseArgs<float>& a, int grid_s, i
                                  cudaStream_t s);
 cudaError_t launch_cg_phases_f64(int K, const PhaseArgs<double>& a, int grid_s, int grid_u, int mode, int chunk,
                                  cudaStream_t s);
-// FP64 residual r = b - M x (after x += d when accumulate), norms into st->gamma / st->b2
+// FP64 residual r = b - M x (after x += d when accumulate > 0; accumulate < 0: x = 0, so r = b),
+// norms into st->gamma / st->b2
 cudaError_t launch_res_phases(int K, const ResPhaseArgs& a, int grid, int accumulate, cudaStream_t s);
 int phase_blocks_f32(int K);  // resident CTAs of the S kernel (all SMs)
 int phase_blocks_f64(int K);

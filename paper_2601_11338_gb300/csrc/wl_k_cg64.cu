@@ -37,6 +37,10 @@ cudaError_t launch_cg_phases_f64(int K, const PhaseArgs<double>& a, int grid_s, 
 
 template <int K>
 static cudaError_t run_res(const ResPhaseArgs& a, int grid, int accumulate, cudaStream_t s) {
+  if (accumulate < 0) {  // x = 0
+    res_zero_phase<K><<<grid, kPhaseBlock, 0, s>>>(a);
+    return cudaGetLastError();
+  }
   if (accumulate) {
     const int64_t total = a.g.n * K;
     res_acc_phase<K><<<grid, kPhaseBlock, 0, s>>>(a.x, a.d, total);
