@@ -140,6 +140,7 @@ struct wl_handle {
   Buf hubs;               // rows with more than kHubDeg entries (internal order)
   int nhub = 0;
   Buf cgstate;            // CgState of the running solve
+  Buf lzstate;            // LzState of the spectral-scale Lanczos
   double inner_tol = 4e-6;  // floor of the FP32 correction target of the refined form
   CgState* cgst() { return (CgState*)cgstate.p; }
   double* h_pin = nullptr;  // pinned host scratch (4096 doubles)
@@ -473,26 +474,21 @@ int compute_Df(wl_handle* h, SolveInfo& info) {
 // Extreme eigenvalues of Op = c0 I + cA A + cD D by Lanczos (k = 1).
 int lanczos_ext(wl_handle* h, double c0, double cA, double cD, int m, double* th_max, double* th_min,
                 double* conv) {
-  const int G = lanczos_ext_grid();
-  int Tw, Tc;
-  thresholds_f64(1, &Tw, &Tc);
-  PartDev* pd;
-  WL_TRY(get_part(h, G, Tw, Tc, &pd, 1, 8));
-  WL_TRY(ensure(h->lan, (size_t)h->n * 3 * 8 + 2 * 512 * 8));
-  WL_TRY(ensure(h->part, (size_t)G * 64 * 2 * 8 + 1024));
-  Smalls sm = smalls(h);
+  const int gu = lz_blocks(), gs = gu + h->nhub;
+  WL_TRY(ensure(h->lan, (size_t)h->n * 4 * 8 + 64));
+  WL_TRY(ensure(h->part, (size_t)gs * 64 * 2 * 8 + 1024));
+  WL_TRY(ensure(h->lzstate, sizeof(LzState)));
   double* v = (double*)h->lan.p;
-  double* ab = v + (size_t)h->n * 3;
-  m = std::min<int64_t>(m, std::max<int64_t>(h->n, 1));
-  m = std::min(m, 512);
-  LanczosExtArgs a{h->g, pd->view(), c0, cA, cD, v, ab, ab + 512, (double*)h->part.p, sm.misc, h->bar, m,
-                   std::max(1, m / 8), 0x5EEDull};
-  WL_TRY(reset_bar(h));
-  counted(h);
-  WL_CU(launch_lanczos_extreme(a, G, S(h)));
-  WL_CU(cudaMemcpyAsync(h->h_pin, sm.misc, 5 * 8, cudaMemcpyDeviceToHost, S(h)));
-  const int berr = check_bar(h);
-  if (berr) return berr;
+  LzState* st = (LzState*)h->lzstate.p;
+  m = (int)std::min<int64_t>(m, std::max<int64_t>(h->n, 1));
+  m = std::min(m, 511);
+  LzArgs a{phase_graph(h), c0, cA, cD, {v, v + h->n}, {v + 2 * h->n, v + 3 * h->n}, (double*)h->part.p, st, 0,
+           0x5EEDull};
+  WL_CU(cudaMemsetAsync(st, 0, sizeof(LzState), S(h)));
+  counted(h, 2 * m + 2);
+  WL_CU(launch_lanczos2(a, m, std::max(1, m / 8), gs, gu, S(h)));
+  WL_CU(cudaMemcpyAsync(h->h_pin, st->out, 5 * 8, cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaStreamSynchronize(S(h)));
   const double* o = h->h_pin;
   *th_max = o[0];
   *th_min = o[2];
@@ -503,7 +499,7 @@ int lanczos_ext(wl_handle* h, double c0, double cA, double cD, int m, double* th
 
 int lambda_max_adaptive(wl_handle* h, double c0, double cA, double cD, double* lmax) {
   double mx = 0, mn = 0, cv = 1;
-  int m = 96;
+  int m = 128;
   for (;;) {
     WL_TRY(lanczos_ext(h, c0, cA, cD, m, &mx, &mn, &cv));
     if (cv < 1e-10 || m >= 480 || m >= h->n) break;
@@ -660,7 +656,7 @@ void free_handle(wl_handle* h) {
   Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
                  &h->r32, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
                  &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->lan, &h->omega, &h->gram,
-                 &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b, &h->hubs, &h->cgstate};
+                 &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b, &h->hubs, &h->cgstate, &h->lzstate};
   for (Buf* b : bufs) release(*b);
   if (h->bar) cudaFree(h->bar);
   if (h->h_pin) cudaFreeHost(h->h_pin);

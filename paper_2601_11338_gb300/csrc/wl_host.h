@@ -8,6 +8,7 @@
 #include "wl_cg2.cuh"
 #include "wl_common.cuh"
 #include "wl_lanczos.cuh"
+#include "wl_lanczos2.cuh"
 
 namespace wl {
 
@@ -83,6 +84,9 @@ cudaError_t launch_hub_list(const int32_t* row_ptr, int64_t n, int32_t* hubs, in
 int lanczos_ext_grid();
 int lanczos_step_grid(int K);
 cudaError_t launch_lanczos_extreme(const LanczosExtArgs& a, int G, cudaStream_t s);
+// m Lanczos steps of the phase-kernel form (2 m + 2 launches), extremes of T_m into a.st->out
+cudaError_t launch_lanczos2(const LzArgs& a, int m, int check, int grid_s, int grid_u, cudaStream_t s);
+int lz_blocks();
 cudaError_t launch_lanczos_step(int K, const LanczosStepArgs& a, int G, cudaStream_t s);
 cudaError_t launch_tridiag_exp(const TridiagArgs& a, int K, cudaStream_t s);
 cudaError_t launch_combine(int K, const CombineArgs& a, cudaStream_t s);

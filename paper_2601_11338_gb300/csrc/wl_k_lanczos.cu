@@ -1,7 +1,9 @@
 // Lanczos kernels: extreme eigenvalues (spectral scale), one step of the
 // outer Lanczos on the walk Laplacian, exp of the tridiagonal, combination.
 #define WL_LANCZOS_KERNELS
+#define WL_LANCZOS2_KERNELS
 #include "wl_host.h"
+#include "wl_lanczos2.cuh"
 
 namespace wl {
 
@@ -54,6 +56,27 @@ cudaError_t launch_combine(int K, const CombineArgs& a, cudaStream_t s) {
     default:
       return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+int lz_blocks() {
+  int nb = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)lz_s, kPhaseBlock, 0);
+  return (nb < 1 ? 1 : nb) * sms;
+}
+
+cudaError_t launch_lanczos2(const LzArgs& a0, int m, int check, int grid_s, int grid_u, cudaStream_t s) {
+  LzArgs a = a0;
+  a.j = 0;
+  lz_init<<<grid_u, kPhaseBlock, 0, s>>>(a);
+  for (int j = 0; j < m; ++j) {
+    a.j = j;
+    lz_s<<<grid_s, kPhaseBlock, 0, s>>>(a);
+    lz_u<<<grid_u, kPhaseBlock, 0, s>>>(a, j == m - 1 ? 1 : 0);
+  }
+  lz_eig<<<1, 32, 0, s>>>(a.st, check);
   return cudaGetLastError();
 }
 
