@@ -472,54 +472,82 @@ int compute_Df(wl_handle* h, SolveInfo& info) {
 
 // ------------------------------------------------------------------ spectral scale
 // Extreme eigenvalues of Op = c0 I + cA A + cD D by Lanczos (k = 1).
-int lanczos_ext(wl_handle* h, double c0, double cA, double cD, int m, double* th_max, double* th_min,
-                double* conv) {
+// One Lanczos run on Op = c0 I + cA A + cD D from the seeded start vector,
+// extended in place (doubling m, up to 480 steps) until the largest Ritz
+// value of T_m agrees with that of T_{m - m/8} to rtol. run->cont lets a
+// caller ask for more accuracy later without restarting.
+struct LzRun {
+  double c0, cA, cD;
+  int m = 0;         // steps done so far
+  int m_eff = 0;     // steps before a breakdown (== m without one)
+  double th = 0.0;   // largest Ritz value
+  double conv = 1.0; // relative change of th over the last m/8 steps
+};
+
+int lanczos_run(wl_handle* h, LzRun* run, double rtol) {
   const int gu = lz_blocks(), gs = gu + h->nhub;
   WL_TRY(ensure(h->lan, (size_t)h->n * 4 * 8 + 64));
   WL_TRY(ensure(h->part, (size_t)gs * 64 * 2 * 8 + 1024));
   WL_TRY(ensure(h->lzstate, sizeof(LzState)));
   double* v = (double*)h->lan.p;
   LzState* st = (LzState*)h->lzstate.p;
-  m = (int)std::min<int64_t>(m, std::max<int64_t>(h->n, 1));
-  m = std::min(m, 511);
-  LzArgs a{phase_graph(h), c0, cA, cD, {v, v + h->n}, {v + 2 * h->n, v + 3 * h->n}, (double*)h->part.p, st, 0,
-           0x5EEDull};
-  WL_CU(cudaMemsetAsync(st, 0, sizeof(LzState), S(h)));
-  counted(h, 2 * m + 2);
-  WL_CU(launch_lanczos2(a, m, std::max(1, m / 8), gs, gu, S(h)));
-  WL_CU(cudaMemcpyAsync(h->h_pin, st->out, 5 * 8, cudaMemcpyDeviceToHost, S(h)));
-  WL_CU(cudaStreamSynchronize(S(h)));
-  const double* o = h->h_pin;
-  *th_max = o[0];
-  *th_min = o[2];
-  if (conv) *conv = std::max(std::fabs(o[0] - o[1]) / (std::fabs(o[0]) + 1e-300),
-                             std::fabs(o[2] - o[3]) / (std::fabs(o[2]) + std::fabs(o[0]) + 1e-300));
+  const int m_cap = (int)std::min<int64_t>(480, std::max<int64_t>(h->n, 1));
+  LzArgs a{phase_graph(h), run->c0, run->cA, run->cD, {v, v + h->n}, {v + 2 * h->n, v + 3 * h->n},
+           (double*)h->part.p, st, 0, 0x5EEDull};
+  for (;;) {
+    if (run->m > 0 && (run->conv <= rtol || run->m_eff < run->m || run->m >= m_cap)) break;
+    const int j0 = run->m;
+    const int m = j0 == 0 ? std::min(64, m_cap) : std::min(2 * j0, m_cap);
+    if (j0 == 0) WL_CU(cudaMemsetAsync(st, 0, sizeof(LzState), S(h)));
+    counted(h, 2 * (m - j0) + 2);
+    WL_CU(launch_lanczos2(a, j0, m, std::max(1, m / 8), gs, gu, S(h)));
+    WL_CU(cudaMemcpyAsync(h->h_pin, st->out, 5 * 8, cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaStreamSynchronize(S(h)));
+    const double* o = h->h_pin;
+    run->m = m;
+    run->m_eff = (int)o[4];
+    run->th = o[0];
+    run->conv = run->m_eff < m ? 0.0 : std::fabs(o[0] - o[1]) / (std::fabs(o[0]) + 1e-300);
+  }
   return WL_OK;
 }
 
-int lambda_max_adaptive(wl_handle* h, double c0, double cA, double cD, double* lmax) {
-  double mx = 0, mn = 0, cv = 1;
-  int m = 128;
-  for (;;) {
-    WL_TRY(lanczos_ext(h, c0, cA, cD, m, &mx, &mn, &cv));
-    if (cv < 1e-10 || m >= 480 || m >= h->n) break;
-    m *= 2;
-  }
-  *lmax = mx;
+int lambda_max_adaptive(wl_handle* h, double c0, double cA, double cD, double rtol, double* lmax) {
+  LzRun r;
+  r.c0 = c0;
+  r.cA = cA;
+  r.cD = cD;
+  WL_TRY(lanczos_run(h, &r, rtol));
+  *lmax = r.th;
   return WL_OK;
 }
 
 // rho(Z_mu): largest lambda with lambda_max(A - (mu/lambda)(D - mu I)) = lambda
-// (the quadratic eigenproblem of Eq. Zdef), by a bracketed Illinois iteration.
+// (the quadratic eigenproblem behind Eq. Zdef), by a bracketed Illinois
+// iteration on h(lambda) = lambda_max(...) - lambda. Each evaluation is one
+// Lanczos run made only as accurate as the sign of h needs: it starts loose
+// and is extended until |h| clearly exceeds its error estimate or the
+// estimate reaches 1e-11.
 int rho_companion(wl_handle* h, double mu, double lmaxA, double* rho) {
   if (mu == 0.0 || lmaxA <= 0.0) {
     *rho = lmaxA;
     return WL_OK;
   }
+  constexpr double kTight = 1e-11;
+  bool certain = true;
   auto hfun = [&](double lam, double* val) -> int {
-    double lm;
-    WL_TRY(lambda_max_adaptive(h, mu * mu / lam, 1.0, -mu / lam, &lm));
-    *val = lm - lam;
+    LzRun r;
+    r.c0 = mu * mu / lam;
+    r.cA = 1.0;
+    r.cD = -mu / lam;
+    double rtol = 1e-6;
+    for (;;) {
+      WL_TRY(lanczos_run(h, &r, rtol));
+      *val = r.th - lam;
+      certain = std::fabs(*val) > 10.0 * r.conv * std::fabs(r.th);
+      if (certain || r.conv <= kTight || r.m_eff < r.m || r.m >= 480) break;
+      rtol = std::max(kTight, 1e-3 * std::fabs(*val) / std::fabs(r.th));
+    }
     return WL_OK;
   };
   double hi = lmaxA, fhi;
@@ -547,6 +575,10 @@ int rho_companion(wl_handle* h, double mu, double lmaxA, double* rho) {
     if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
     double fx;
     WL_TRY(hfun(x, &fx));
+    if (!certain) {  // |h(x)| is below what the Lanczos run resolves: x is the root
+      lo = hi = x;
+      break;
+    }
     if (fx > 0) {
       lo = x;
       flo = fx;
@@ -557,10 +589,6 @@ int rho_companion(wl_handle* h, double mu, double lmaxA, double* rho) {
       fhi = fx;
       if (side == -1) flo *= 0.5;
       side = -1;
-    }
-    if (std::fabs(fx) < 1e-13 * x) {
-      lo = hi = x;
-      break;
     }
   }
   *rho = 0.5 * (lo + hi);
@@ -814,7 +842,7 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
   h->lmax = 0.0;
   h->rho = 0.0;
   if (h->n > 0 && h->nnz > 0) {
-    if ((rc = lambda_max_adaptive(h, 0.0, 1.0, 0.0, &h->lmax)) != WL_OK) return fail(rc);
+    if ((rc = lambda_max_adaptive(h, 0.0, 1.0, 0.0, 1e-11, &h->lmax)) != WL_OK) return fail(rc);
     if (p->f == WL_F_RESOLVENT) {
       if ((rc = rho_companion(h, mu, h->lmax, &h->rho)) != WL_OK) return fail(rc);
     } else {

@@ -85,7 +85,10 @@ int lanczos_ext_grid();
 int lanczos_step_grid(int K);
 cudaError_t launch_lanczos_extreme(const LanczosExtArgs& a, int G, cudaStream_t s);
 // m Lanczos steps of the phase-kernel form (2 m + 2 launches), extremes of T_m into a.st->out
-cudaError_t launch_lanczos2(const LzArgs& a, int m, int check, int grid_s, int grid_u, cudaStream_t s);
+// Lanczos steps j0..m-1 (j0 = 0: a fresh run from the seeded start vector;
+// j0 > 0: continue the run held in a.st / a.V / a.W), then the extreme
+// eigenvalues of T_m and T_{m-check}
+cudaError_t launch_lanczos2(const LzArgs& a, int j0, int m, int check, int grid_s, int grid_u, cudaStream_t s);
 int lz_blocks();
 cudaError_t launch_lanczos_step(int K, const LanczosStepArgs& a, int G, cudaStream_t s);
 cudaError_t launch_tridiag_exp(const TridiagArgs& a, int K, cudaStream_t s);

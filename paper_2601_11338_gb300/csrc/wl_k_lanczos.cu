@@ -67,11 +67,14 @@ int lz_blocks() {
   return (nb < 1 ? 1 : nb) * sms;
 }
 
-cudaError_t launch_lanczos2(const LzArgs& a0, int m, int check, int grid_s, int grid_u, cudaStream_t s) {
+cudaError_t launch_lanczos2(const LzArgs& a0, int j0, int m, int check, int grid_s, int grid_u, cudaStream_t s) {
   LzArgs a = a0;
   a.j = 0;
-  lz_init<<<grid_u, kPhaseBlock, 0, s>>>(a);
-  for (int j = 0; j < m; ++j) {
+  if (j0 == 0)
+    lz_init<<<grid_u, kPhaseBlock, 0, s>>>(a);
+  else
+    lz_resume<<<1, 32, 0, s>>>(a.st);
+  for (int j = j0; j < m; ++j) {
     a.j = j;
     lz_s<<<grid_s, kPhaseBlock, 0, s>>>(a);
     lz_u<<<grid_u, kPhaseBlock, 0, s>>>(a, j == m - 1 ? 1 : 0);

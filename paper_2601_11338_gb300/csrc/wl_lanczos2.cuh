@@ -21,7 +21,7 @@ struct LzState {
   int m_eff;         // steps done before an (exact) breakdown, or m
   int stop;
   unsigned ticket;
-  int pad;
+  int brk;           // 1 after an (exact) breakdown: the run cannot be continued
   double out[8];     // theta_max(T_m), theta_max(T_{m-c}), theta_min(T_m), theta_min(T_{m-c}), m_eff
 };
 
@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(kPhaseBlock) lz_init(LzArgs a) {
   if (threadIdx.x == 0) {
     a.st->start_norm = sqrt(s_out[0]);
     a.st->stop = 0;
+    a.st->brk = 0;
     a.st->m_eff = 0;
     a.st->ticket = 0;
   }
@@ -147,9 +148,20 @@ __global__ void __launch_bounds__(kPhaseBlock) lz_u(LzArgs a, int last) {
     st->beta[j] = b;
     st->m_eff = j + 1;
     // invariant subspace reached: T_{j+1} is exact
-    if (!(b > 1e-13 * (fabs(al) + bp + 1e-300)) || last) st->stop = 1;
+    if (!(b > 1e-13 * (fabs(al) + bp + 1e-300))) {
+      st->brk = 1;
+      st->stop = 1;
+    } else if (last) {
+      st->stop = 1;
+    }
     st->ticket = 0;
   }
+}
+
+// re-open a run stopped at its last step (not after a breakdown) so that
+// more steps can be appended
+__global__ void lz_resume(LzState* st) {
+  if (threadIdx.x == 0 && !st->brk) st->stop = 0;
 }
 
 // extreme eigenvalues of T_m and T_{m - check} by bisection (4 threads)
