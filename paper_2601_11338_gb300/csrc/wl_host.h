@@ -77,8 +77,9 @@ void thresholds_f64(int K, int* Tw, int* Tc);  // class thresholds of Cfg<T, K>
 void thresholds_f32(int K, int* Tw, int* Tc);
 // rows with deg > kHubDeg in increasing order; *count (host, pinned) set after the stream syncs;
 // tmp: 3 (n + 1) + n / 1024 + 4 int64
-cudaError_t launch_hub_list(const int32_t* row_ptr, int64_t n, int32_t* hubs, int64_t* tmp, int64_t* count,
-                            cudaStream_t s);
+// rows with lo < deg <= hi in increasing order; *count (host, pinned) after a sync
+cudaError_t launch_row_list(const int32_t* row_ptr, int64_t n, int lo, int hi, int32_t* rows, int64_t* tmp,
+                            int64_t* count, cudaStream_t s);
 
 // ---- wl_k_lanczos.cu
 int lanczos_ext_grid();

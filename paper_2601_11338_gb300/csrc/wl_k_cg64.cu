@@ -103,27 +103,29 @@ void thresholds_f64(int K, int* Tw, int* Tc) {
   *Tw = *Tc = 0;
 }
 
-// hub list: rows with more than kHubDeg entries, in increasing row order
-__global__ void k_hub_flags(const int32_t* row_ptr, int64_t n, int64_t* flag) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    flag[i] = (row_ptr[i + 1] - row_ptr[i] > kHubDeg) ? 1 : 0;
+// row lists: rows with lo < deg <= hi, in increasing row order
+__global__ void k_row_flags(const int32_t* row_ptr, int64_t n, int lo, int hi, int64_t* flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int d = row_ptr[i + 1] - row_ptr[i];
+    flag[i] = (d > lo && d <= hi) ? 1 : 0;
+  }
 }
 
-__global__ void k_hub_scatter(const int64_t* flag, const int64_t* pos, int64_t n, int32_t* hubs) {
+__global__ void k_row_scatter(const int64_t* flag, const int64_t* pos, int64_t n, int32_t* rows) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (flag[i]) hubs[pos[i]] = (int32_t)i;
+    if (flag[i]) rows[pos[i]] = (int32_t)i;
 }
 
-cudaError_t launch_hub_list(const int32_t* row_ptr, int64_t n, int32_t* hubs, int64_t* tmp, int64_t* count,
-                            cudaStream_t s) {
+cudaError_t launch_row_list(const int32_t* row_ptr, int64_t n, int lo, int hi, int32_t* rows, int64_t* tmp,
+                            int64_t* count, cudaStream_t s) {
   int64_t* flag = tmp;
   int64_t* pos = tmp + n + 1;
   int64_t* sc = pos + n + 1;
   const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
-  k_hub_flags<<<gb, 256, 0, s>>>(row_ptr, n, flag);
+  k_row_flags<<<gb, 256, 0, s>>>(row_ptr, n, lo, hi, flag);
   cudaError_t e = launch_scan(flag, n, pos, sc, s);
   if (e != cudaSuccess) return e;
-  k_hub_scatter<<<gb, 256, 0, s>>>(flag, pos, n, hubs);
+  k_row_scatter<<<gb, 256, 0, s>>>(flag, pos, n, rows);
   e = cudaMemcpyAsync(count, pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

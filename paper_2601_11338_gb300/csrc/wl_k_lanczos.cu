@@ -79,7 +79,7 @@ cudaError_t launch_lanczos2(const LzArgs& a0, int j0, int m, int check, int grid
     lz_s<<<grid_s, kPhaseBlock, 0, s>>>(a);
     lz_u<<<grid_u, kPhaseBlock, 0, s>>>(a, j == m - 1 ? 1 : 0);
   }
-  lz_eig<<<1, 32, 0, s>>>(a.st, check);
+  lz_eig<<<1, 4 * kEigT, 0, s>>>(a.st, check);
   return cudaGetLastError();
 }
 

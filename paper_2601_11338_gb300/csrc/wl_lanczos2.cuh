@@ -100,11 +100,24 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) lz_s(LzArgs a) {
       __syncthreads();
     }
     if (tid == 0) fin(row, end - beg, s_red[0]);
-  } else {
-    const int64_t nblk = (int64_t)gridDim.x - a.g.nhub;
-    for (int64_t row = ((int64_t)blockIdx.x - a.g.nhub) * kPhaseBlock + tid; row < a.g.n; row += nblk * kPhaseBlock) {
+  } else if ((int)blockIdx.x < list_blocks(a.g)) {
+    // one mid row per warp
+    const int wi = ((int)blockIdx.x - a.g.nhub) * kWarpsPerBlock + (tid >> 5);
+    if (wi < a.g.nmid) {
+      const int64_t row = a.g.mids[wi];
       const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
-      if (end - beg > kHubDeg) continue;
+      double s = 0.0;
+      for (int e = beg + (tid & 31); e < end; e += 32) s += Wp[__ldg(a.g.col + e)];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if ((tid & 31) == 0) fin(row, end - beg, s);
+    }
+  } else {
+    const int64_t nblk = (int64_t)gridDim.x - list_blocks(a.g);
+    for (int64_t row = ((int64_t)blockIdx.x - list_blocks(a.g)) * kPhaseBlock + tid; row < a.g.n;
+         row += nblk * kPhaseBlock) {
+      const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
+      if (end - beg > a.g.mid_deg) continue;
       double s = 0.0;
       int e = beg;
       for (; e + 3 < end; e += 4) {
@@ -164,15 +177,50 @@ __global__ void lz_resume(LzState* st) {
   if (threadIdx.x == 0 && !st->brk) st->stop = 0;
 }
 
-// extreme eigenvalues of T_m and T_{m - check} by bisection (4 threads)
-__global__ void lz_eig(LzState* st, int check) {
+// Extreme eigenvalues of T_m and T_{m - check} by multisection: four groups
+// of kEigT threads, one group per eigenvalue. Each round evaluates kEigT
+// Sturm counts spread across the group's bracket and keeps the sub-interval
+// where the count passes the eigenvalue's index; 9 rounds shrink the
+// Gershgorin bracket by 129^9 (below the FP64 spacing).
+constexpr int kEigT = 128;
+constexpr int kEigRounds = 9;
+
+__global__ void __launch_bounds__(4 * kEigT) lz_eig(LzState* st, int check) {
+  __shared__ double s_lo[4], s_hi[4];
+  __shared__ int s_cnt[4][kEigT];
   const int m = st->m_eff;
-  const int tid = threadIdx.x;
-  if (tid < 4 && m > 0) {
-    const int mm = (tid & 1) ? (m > check ? m - check : m) : m;
-    st->out[tid] = (tid < 2) ? tridiag_eig(st->alpha, st->beta, mm, mm - 1) : tridiag_eig(st->alpha, st->beta, mm, 0);
+  if (m <= 0) {
+    if (threadIdx.x == 0) st->out[4] = 0.0;
+    return;
   }
-  if (tid == 0) st->out[4] = (double)m;
+  const int grp = threadIdx.x / kEigT, t = threadIdx.x % kEigT;
+  const int mm = (grp & 1) ? (m > check ? m - check : m) : m;
+  const int idx = (grp < 2) ? mm - 1 : 0;
+  if (t == 0) {
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < mm; ++i) {
+      const double r = (i > 0 ? fabs(st->beta[i - 1]) : 0.0) + (i + 1 < mm ? fabs(st->beta[i]) : 0.0);
+      lo = fmin(lo, st->alpha[i] - r);
+      hi = fmax(hi, st->alpha[i] + r);
+    }
+    s_lo[grp] = lo;
+    s_hi[grp] = hi;
+  }
+  __syncthreads();
+  for (int round = 0; round < kEigRounds; ++round) {
+    const double lo = s_lo[grp], w = s_hi[grp] - lo;
+    s_cnt[grp][t] = sturm_count(st->alpha, st->beta, mm, lo + w * (double)(t + 1) / (double)(kEigT + 1));
+    __syncthreads();
+    if (t == 0) {
+      int k = 0;
+      while (k < kEigT && s_cnt[grp][k] <= idx) ++k;
+      s_lo[grp] = lo + w * (double)k / (double)(kEigT + 1);
+      s_hi[grp] = lo + w * (double)(k + 1) / (double)(kEigT + 1);
+    }
+    __syncthreads();
+  }
+  if (t == 0) st->out[grp] = 0.5 * (s_lo[grp] + s_hi[grp]);
+  if (threadIdx.x == 0) st->out[4] = (double)m;
 }
 #endif  // WL_LANCZOS2_KERNELS
 
