@@ -139,8 +139,6 @@ struct wl_handle {
   int32_t* iperm = nullptr;
   Buf hubs;               // rows with more than kHubDeg entries (internal order)
   int nhub = 0;
-  Buf mids;               // rows with kMidDeg < deg <= kHubDeg (internal order)
-  int nmid = 0;
   Buf cgstate;            // CgState of the running solve
   Buf lzstate;            // LzState of the spectral-scale Lanczos
   double inner_tol = 4e-6;  // floor of the FP32 correction target of the refined form
@@ -266,11 +264,8 @@ double alg_bytes_per_iter(wl_handle* h, int K, int s) {
 }
 
 PhaseGraph phase_graph(wl_handle* h) {
-  return PhaseGraph{h->g.row_ptr, h->g.col, h->n, (const int32_t*)h->hubs.p, h->nhub, (const int32_t*)h->mids.p,
-                    h->nmid, h->nmid > 0 ? kMidDeg : kHubDeg};
+  return PhaseGraph{h->g.row_ptr, h->g.col, h->n, (const int32_t*)h->hubs.p, h->nhub};
 }
-// CTAs of a gather kernel beyond its grid-stride part (hub CTAs, mid warps)
-int list_ctas(wl_handle* h) { return list_blocks(phase_graph(h)); }
 
 constexpr int kChunk = 8;  // CG iterations launched between two reads of the device flag
 
@@ -333,19 +328,19 @@ int ensure_phase_buffers(wl_handle* h, int grid) {
 // FP64 lockstep CG on M x = b for K columns (b, x contiguous n x K doubles).
 // x holds the starting guess on entry (zero unless a warm start is given).
 int solve_fp64(wl_handle* h, const double* b, double* x, int K, double tol, bool x_is_zero, SolveInfo& info) {
-  const int grid_u = phase_blocks_f64(K), grid_s = grid_u + list_ctas(h);
+  const int grid_u = phase_blocks_f64(K), grid_s = grid_u + h->nhub;
   const size_t nk = (size_t)h->n * K;
   WL_TRY(ensure(h->r, nk * 8));
   WL_TRY(ensure(h->p, nk * 8));
   WL_TRY(ensure(h->q, nk * 8));
-  WL_TRY(ensure_phase_buffers(h, std::max(grid_s, res_blocks(K) + list_ctas(h))));
+  WL_TRY(ensure_phase_buffers(h, std::max(grid_s, res_blocks(K) + h->nhub)));
   CgState* st = h->cgst();
   WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
   const double* bn2 = nullptr;
   if (x_is_zero) {
     WL_CU(cudaMemcpyAsync(h->r.p, b, nk * 8, cudaMemcpyDeviceToDevice, S(h)));
   } else {
-    const int gr = res_blocks(K) + list_ctas(h);
+    const int gr = res_blocks(K) + h->nhub;
     ResPhaseArgs ra{phase_graph(h), x, nullptr, b, (double*)h->r.p, nullptr, h->ca, h->cA, h->cD,
                     (double*)h->part.p, st};
     const int pi = prof_begin(h, kCatRes);
@@ -364,8 +359,8 @@ int solve_fp64(wl_handle* h, const double* b, double* x, int K, double tol, bool
 
 // Refined solve: FP64 iterate and residual, FP32 inner CG corrections.
 int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, bool x_is_zero, SolveInfo& info) {
-  const int grid_u = phase_blocks_f32(K), grid_s = grid_u + list_ctas(h);
-  const int grid_r = res_blocks(K) + list_ctas(h);
+  const int grid_u = phase_blocks_f32(K), grid_s = grid_u + h->nhub;
+  const int grid_r = res_blocks(K) + h->nhub;
   const size_t nk = (size_t)h->n * K;
   WL_TRY(ensure(h->p, nk * 4));
   WL_TRY(ensure(h->q, nk * 4));
@@ -492,7 +487,7 @@ struct LzRun {
 };
 
 int lanczos_run(wl_handle* h, LzRun* run, double rtol) {
-  const int gu = lz_blocks(), gs = gu + list_ctas(h);
+  const int gu = lz_blocks(), gs = gu + h->nhub;
   WL_TRY(ensure(h->lan, (size_t)h->n * 4 * 8 + 64));
   WL_TRY(ensure(h->part, (size_t)gs * 64 * 2 * 8 + 1024));
   WL_TRY(ensure(h->lzstate, sizeof(LzState)));
@@ -691,7 +686,7 @@ void free_handle(wl_handle* h) {
   Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
                  &h->r32, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
                  &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->lan, &h->omega, &h->gram,
-                 &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b, &h->hubs, &h->mids, &h->cgstate, &h->lzstate};
+                 &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b, &h->hubs, &h->cgstate, &h->lzstate};
   for (Buf* b : bufs) release(*b);
   if (h->bar) cudaFree(h->bar);
   if (h->h_pin) cudaFreeHost(h->h_pin);
@@ -837,16 +832,11 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
     if ((rc = ensure(h->ptmp, sizeof(int64_t) * std::max<size_t>(relabel_tmp_i64(h->n),
                                                                  3 * (size_t)(h->n + 1) + h->n / 1024 + 8))) != WL_OK)
       return fail(rc);
-    if ((rc = ensure(h->mids, sizeof(int32_t) * h->n)) != WL_OK) return fail(rc);
-    counted(h, 10);
+    counted(h, 5);
     cudaError_t e = launch_row_list(h->g.row_ptr, h->n, kHubDeg, INT32_MAX, (int32_t*)h->hubs.p,
                                     (int64_t*)h->ptmp.p, (int64_t*)h->h_pin, S(h));
-    if (e == cudaSuccess)
-      e = launch_row_list(h->g.row_ptr, h->n, kMidDeg, kHubDeg, (int32_t*)h->mids.p, (int64_t*)h->ptmp.p,
-                          (int64_t*)h->h_pin + 1, S(h));
     if (e == cudaSuccess) e = cudaStreamSynchronize(S(h));
-    if (e != cudaSuccess) return fail(set_cuda_error(e, "row lists"));
-    h->nmid = (int)((int64_t*)h->h_pin)[1];
+    if (e != cudaSuccess) return fail(set_cuda_error(e, "hub list"));
     h->nhub = (int)*(int64_t*)h->h_pin;
   }
 
@@ -1223,7 +1213,7 @@ int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, u
     if (e == cudaSuccess) e = cudaMemsetAsync(h->x.p, 0, nk * 4, S(h));
     if (e != cudaSuccess) { rc = set_cuda_error(e, "sketch"); break; }
     // Y = M^{-1} (a Omega) in FP32 lockstep CG
-    const int grid_u = phase_blocks_f32(K), grid_s = grid_u + list_ctas(h);
+    const int grid_u = phase_blocks_f32(K), grid_s = grid_u + h->nhub;
     if ((rc = ensure_phase_buffers(h, grid_s)) != WL_OK) break;
     Smalls sm = smalls(h);
     CgState* st = h->cgst();

@@ -6,9 +6,7 @@
 // The gather of neighbour vectors is latency bound, so these kernels keep
 // the SMs full of warps (G lanes per row, one 16-byte slice each, rows
 // spread over a grid-stride loop) instead of persisting with few warps.
-// Rows with more than kHubDeg entries are gathered by one CTA each, rows
-// with more than mid_deg (and at most kHubDeg) entries by one warp each, so
-// that no lane group walks a long row alone.
+// Rows with more than kHubDeg entries are gathered by one CTA each.
 //
 // One iteration = two kernels:
 //   S: s = M r ; x += alpha p ; p = r + beta p ; q = s + beta q ; delta = (p, q)
@@ -24,8 +22,6 @@
 namespace wl {
 
 constexpr int kHubDeg = 256;       // rows with more entries get a CTA each
-constexpr int kMidDeg = 32;        // rows with more entries (up to kHubDeg) get a warp each
-constexpr int kWarpsPerBlock = 256 / 32;
 constexpr int kPhaseBlock = 256;   // threads per CTA of the phase kernels
 #ifndef WL_PHASE_MINB
 #define WL_PHASE_MINB 5
@@ -48,15 +44,7 @@ struct PhaseGraph {
   int64_t n;
   const int32_t* hubs;  // rows with deg > kHubDeg
   int nhub;
-  const int32_t* mids;  // rows with mid_deg < deg <= kHubDeg (may be empty)
-  int nmid;
-  int mid_deg;          // kHubDeg when there is no mid list
 };
-
-// CTAs a phase kernel spends on the hub and mid lists before its
-// grid-stride part
-__host__ __device__ inline int mid_blocks(const PhaseGraph& g) { return (g.nmid + kWarpsPerBlock - 1) / kWarpsPerBlock; }
-__host__ __device__ inline int list_blocks(const PhaseGraph& g) { return g.nhub + mid_blocks(g); }
 
 template <typename T>
 struct PhaseArgs {
@@ -100,18 +88,6 @@ __device__ __forceinline__ void row_gather(const int32_t* __restrict__ col, int 
 #pragma unroll
     for (int v = 0; v < VW; ++v) acc[v] += a0.v[v];
   }
-}
-
-// One row per warp: the 32 / G lane groups stride over the entries and are
-// combined by shuffles; afterwards every lane holds its slice's full sum.
-template <typename T, int K, int VW, int G>
-__device__ __forceinline__ void warp_row_gather(const int32_t* __restrict__ col, int beg, int end, const T* X,
-                                                int lane, int lane_off, T (&acc)[VW]) {
-  row_gather<T, K, VW>(col, beg + lane / G, end, 32 / G, X, lane_off, acc);
-#pragma unroll
-  for (int off = G; off < 32; off <<= 1)
-#pragma unroll
-    for (int v = 0; v < VW; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
 }
 
 // CTA column sums of per-thread partials (thread t owns columns (t % G) VW + v)
@@ -262,24 +238,11 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) cg_s_phase(Phase
         for (int v = 0; v < VW; ++v) acc[v] += s_red[(gr * G + sl) * VW + v];
       fin(row, end - beg, acc, w);
     }
-  } else if ((int)blockIdx.x < list_blocks(a.g)) {
-    // one mid row per warp
-    const int wi = ((int)blockIdx.x - a.g.nhub) * kWarpsPerBlock + (tid >> 5);
-    if (wi < a.g.nmid) {
-      const int64_t row = a.g.mids[wi];
-      const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
-      const Own w = own(row);
-      T acc[VW];
-#pragma unroll
-      for (int v = 0; v < VW; ++v) acc[v] = T(0);
-      warp_row_gather<T, K, VW, G>(a.g.col, beg, end, a.r, tid & 31, lane_off, acc);
-      if ((tid & 31) < G) fin(row, end - beg, acc, w);
-    }
   } else {
-    const int64_t nblk = (int64_t)gridDim.x - list_blocks(a.g);
-    for (int64_t row = ((int64_t)blockIdx.x - list_blocks(a.g)) * RPB + tid / G; row < a.g.n; row += nblk * RPB) {
+    const int64_t nblk = (int64_t)gridDim.x - a.g.nhub;
+    for (int64_t row = ((int64_t)blockIdx.x - a.g.nhub) * RPB + tid / G; row < a.g.n; row += nblk * RPB) {
       const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
-      if (end - beg > a.g.mid_deg) continue;  // gathered by a hub CTA or a mid warp
+      if (end - beg > kHubDeg) continue;  // gathered by a hub CTA
       const Own w = own(row);
       T acc[VW];
 #pragma unroll
@@ -500,22 +463,11 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) res_phase(ResPha
         for (int v = 0; v < VW; ++v) acc[v] += s_red[(gr * G + sl) * VW + v];
       fin(row, end - beg, acc);
     }
-  } else if ((int)blockIdx.x < list_blocks(a.g)) {
-    const int wi = ((int)blockIdx.x - a.g.nhub) * kWarpsPerBlock + (tid >> 5);
-    if (wi < a.g.nmid) {
-      const int64_t row = a.g.mids[wi];
-      const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
-      double acc[VW];
-#pragma unroll
-      for (int v = 0; v < VW; ++v) acc[v] = 0.0;
-      warp_row_gather<double, K, VW, G>(a.g.col, beg, end, a.x, tid & 31, lane_off, acc);
-      if ((tid & 31) < G) fin(row, end - beg, acc);
-    }
   } else {
-    const int64_t nblk = (int64_t)gridDim.x - list_blocks(a.g);
-    for (int64_t row = ((int64_t)blockIdx.x - list_blocks(a.g)) * RPB + tid / G; row < a.g.n; row += nblk * RPB) {
+    const int64_t nblk = (int64_t)gridDim.x - a.g.nhub;
+    for (int64_t row = ((int64_t)blockIdx.x - a.g.nhub) * RPB + tid / G; row < a.g.n; row += nblk * RPB) {
       const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
-      if (end - beg > a.g.mid_deg) continue;
+      if (end - beg > kHubDeg) continue;
       double acc[VW];
 #pragma unroll
       for (int v = 0; v < VW; ++v) acc[v] = 0.0;

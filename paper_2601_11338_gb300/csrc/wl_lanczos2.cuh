@@ -100,24 +100,11 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) lz_s(LzArgs a) {
       __syncthreads();
     }
     if (tid == 0) fin(row, end - beg, s_red[0]);
-  } else if ((int)blockIdx.x < list_blocks(a.g)) {
-    // one mid row per warp
-    const int wi = ((int)blockIdx.x - a.g.nhub) * kWarpsPerBlock + (tid >> 5);
-    if (wi < a.g.nmid) {
-      const int64_t row = a.g.mids[wi];
-      const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
-      double s = 0.0;
-      for (int e = beg + (tid & 31); e < end; e += 32) s += Wp[__ldg(a.g.col + e)];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-      if ((tid & 31) == 0) fin(row, end - beg, s);
-    }
   } else {
-    const int64_t nblk = (int64_t)gridDim.x - list_blocks(a.g);
-    for (int64_t row = ((int64_t)blockIdx.x - list_blocks(a.g)) * kPhaseBlock + tid; row < a.g.n;
-         row += nblk * kPhaseBlock) {
+    const int64_t nblk = (int64_t)gridDim.x - a.g.nhub;
+    for (int64_t row = ((int64_t)blockIdx.x - a.g.nhub) * kPhaseBlock + tid; row < a.g.n; row += nblk * kPhaseBlock) {
       const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
-      if (end - beg > a.g.mid_deg) continue;
+      if (end - beg > kHubDeg) continue;
       double s = 0.0;
       int e = beg;
       for (; e + 3 < end; e += 4) {

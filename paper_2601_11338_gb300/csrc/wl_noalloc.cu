@@ -175,7 +175,7 @@ extern "C" int wl_degrees_noalloc(const wl_csr* A, wl_variant v, double mu, doub
 
   // M x = a 1, M = a I - alpha A + alpha^2 mu D (FP64 CG from x = 0)
   const double a = 1.0 - m * m * alpha * alpha;
-  const PhaseGraph pg{A->row_ptr, A->col_idx, n, hubs, nhub, nullptr, 0, kHubDeg};
+  const PhaseGraph pg{A->row_ptr, A->col_idx, n, hubs, nhub};
   na_fill<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(r, a, n);
   NA_CU(cudaGetLastError());
   NA_CU(cudaMemsetAsync(Df, 0, (size_t)n * sizeof(double), s));
