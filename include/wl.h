@@ -220,6 +220,47 @@ const char* wl_last_error(void);
 int wl_degrees_noalloc(const wl_csr* A, wl_variant v, double mu, double alpha, double tol, int max_iter,
                        double* Df, void* stream, wl_stats* st);
 
+/* ------------------------------------------------------------ batched executor */
+/* Walk degrees and walk-Laplacian applies for a collection of graphs and a
+ * sweep of backtrack weights, all problems at once (Sec. 4.2 applied to
+ * every (graph, mu) pair; Def. BDTW-Laplacian with theta = 1 - mu, so
+ * mu = 1 is the non-backtracking and mu = 0 the all-walk resolvent).
+ * A problem is one (graph g, mu_j) pair; problem index p = j * ngraph + g. */
+typedef struct wl_batch wl_batch;
+
+/* graphs[0 .. ngraph): CSR graphs as in wl_build (host or device arrays,
+ * copied; each validated like wl_build). mus[0 .. nmu): mu values in [0, 1].
+ * p: f must be WL_F_RESOLVENT; alpha_rel > 0 gives alpha = alpha_rel /
+ * rho(Z_mu) per problem (a graph with no edges gets alpha = 0), otherwise
+ * p->alpha is used for all; every problem must have alpha rho(Z_mu) < 1
+ * (else WL_ERR_ALPHA_RANGE). p->prec is WL_FP64 or WL_REFINED; tol,
+ * max_iter, max_outer and stream as in wl_build. Synchronous. */
+int wl_batch_build(const wl_csr* graphs, int ngraph, const double* mus, int nmu, const wl_params* p,
+                   wl_batch** out, wl_stats* st);
+
+/* For every problem p = (g, mu_j):
+ *   Df[j][row]        = D_f of graph g at mu_j       (nmu x n, n = total rows)
+ *   W[j][row][c]      = (L_mu_j V_g)[row][c]          (nmu x n x k)
+ * V: n x k row-major FP64 (rows of the graphs concatenated in order); the
+ * same V serves every mu. k in {1, 2, 4, 8, 16, 32, 64}. V, Df and W may be
+ * host or device pointers. stepped = 0 runs the whole computation as one
+ * CUDA graph launch (captured on the first call for this k and form, then
+ * replayed); stepped = 1 launches the same kernels one by one with a host
+ * read per iteration (for checking; the results are identical).
+ * Returns the first non-OK problem status (WL_ERR_NO_CONVERGENCE, ...);
+ * outputs hold the last iterates then. Synchronous. st may be NULL:
+ * time_ms, rel_res (largest relative residual), nnz_rhs_iters, launches. */
+int wl_batch_run(wl_batch* b, const double* V, int k, double* Df, double* W, int stepped, wl_stats* st);
+
+/* Per-problem figures of the build and the last run (any pointer may be NULL). */
+int wl_batch_info(const wl_batch* b, int graph, int mu_index, double* alpha, double* rho, double* lambda_max,
+                  int* iters_df, int* iters_v, int* status);
+
+/* Rows per plain tile chosen by the autotuner for width k (0 before the first run). */
+int wl_batch_tile_rows(const wl_batch* b, int k);
+
+void wl_batch_destroy(wl_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1251,3 +1251,40 @@ void wl_destroy(wl_handle* h) {
 }
 
 }  // extern "C"
+
+namespace wl {
+
+int report_cuda_error(cudaError_t e, const char* where) { return set_cuda_error(e, where); }
+void report_error(const std::string& msg) { g_last_error = msg; }
+std::string last_error_copy() { return g_last_error; }
+
+// Spectral scale of one graph for several mu values (Sec. 4.1): validates
+// the CSR as wl_build does, then lambda_max(A) and rho(Z_mu) for each mu
+// (rho(Z_0) = lambda_max(A)).
+int graph_spectral(const wl_csr* A, const double* mus, int nmu, void* stream, double* lmax, double* rho) {
+  wl_params p;
+  memset(&p, 0, sizeof(p));
+  p.f = WL_F_IDENTITY;
+  p.prec = WL_FP64;
+  p.stream = stream;
+  p.reorder = 1;
+  wl_handle* h = nullptr;
+  int rc = wl_build(A, WL_ALLWALK, &p, &h, nullptr);
+  if (rc != WL_OK) return rc;
+  *lmax = h->lmax;
+  for (int i = 0; i < nmu && rc == WL_OK; ++i) {
+    if (!(mus[i] >= 0.0 && mus[i] <= 1.0)) {
+      rc = WL_ERR_INVALID_ARG;
+      break;
+    }
+    if (h->n == 0 || h->nnz == 0) {
+      rho[i] = 0.0;
+      continue;
+    }
+    rc = rho_companion(h, mus[i], h->lmax, &rho[i]);
+  }
+  wl_destroy(h);
+  return rc;
+}
+
+}  // namespace wl

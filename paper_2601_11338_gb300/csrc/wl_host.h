@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "wl_cg2.cuh"
 #include "wl_common.cuh"
 #include "wl_lanczos.cuh"
@@ -125,5 +127,11 @@ inline int coop_grid(const void* fn, int cap_per_sm) {
   if (nb < 1) nb = 1;
   return nb * sms;
 }
+
+// ---- wl_api.cu (shared with the batched executor)
+int report_cuda_error(cudaError_t e, const char* where);
+void report_error(const std::string& msg);
+std::string last_error_copy();
+int graph_spectral(const wl_csr* A, const double* mus, int nmu, void* stream, double* lmax, double* rho);
 
 }  // namespace wl

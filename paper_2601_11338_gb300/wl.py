@@ -94,6 +94,18 @@ def lib():
         L.wl_degrees_noalloc.argtypes = [ctypes.POINTER(wl_csr), c_int, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, c_int, vp, vp, ctypes.POINTER(wl_stats)]
         L.wl_degrees_noalloc.restype = c_int
+        L.wl_batch_build.argtypes = [vp, c_int, vp, c_int, ctypes.POINTER(wl_params), ctypes.POINTER(vp),
+                                     ctypes.POINTER(wl_stats)]
+        L.wl_batch_build.restype = c_int
+        L.wl_batch_run.argtypes = [vp, vp, c_int, vp, vp, c_int, ctypes.POINTER(wl_stats)]
+        L.wl_batch_run.restype = c_int
+        dp, ip = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(c_int)
+        L.wl_batch_info.argtypes = [vp, c_int, c_int, dp, dp, dp, ip, ip, ip]
+        L.wl_batch_info.restype = c_int
+        L.wl_batch_tile_rows.argtypes = [vp, c_int]
+        L.wl_batch_tile_rows.restype = c_int
+        L.wl_batch_destroy.argtypes = [vp]
+        L.wl_batch_destroy.restype = None
         for name in ("wl_build", "wl_set_params", "wl_degrees", "wl_apply", "wl_expmv", "wl_trace",
                      "wl_set_warm_start", "wl_get_info"):
             getattr(L, name).restype = c_int
@@ -207,3 +219,51 @@ def wl_get_info(h):
     st = wl_stats()
     _check(lib().wl_get_info(h.ptr, ctypes.byref(st)), "wl_get_info")
     return st
+
+
+class BatchHandle:
+    """Owns a wl_batch*."""
+
+    def __init__(self, ptr, ngraph, nmu):
+        self.ptr = ptr
+        self.ngraph = ngraph
+        self.nmu = nmu
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        if getattr(self, "ptr", None):
+            lib().wl_batch_destroy(self.ptr)
+            self.ptr = None
+
+
+def wl_batch_build(graphs, mus, params, stats=None):
+    """graphs: list of (row_ptr, col_idx, n, nnz) with host or device arrays."""
+    arr = (wl_csr * len(graphs))(*[wl_csr(n, nnz, _ptr(rp), _ptr(ci)) for rp, ci, n, nnz in graphs])
+    m = np.ascontiguousarray(np.asarray(mus, dtype=np.float64))
+    h = ctypes.c_void_p()
+    st = stats if stats is not None else wl_stats()
+    _check(lib().wl_batch_build(ctypes.cast(arr, ctypes.c_void_p), len(graphs), m.ctypes.data, len(m),
+                                ctypes.byref(params), ctypes.byref(h), ctypes.byref(st)), "wl_batch_build")
+    return BatchHandle(h, len(graphs), len(m))
+
+
+def wl_batch_run(b, V, k, Df, W, stepped=0, stats=None, allow=()):
+    st = stats if stats is not None else wl_stats()
+    return _check(lib().wl_batch_run(b.ptr, _ptr(V), k, _ptr(Df), _ptr(W), int(stepped), ctypes.byref(st)),
+                  "wl_batch_run", allow)
+
+
+def wl_batch_info(b, graph, mu_index):
+    a, r, lm = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    i1, i2, stt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().wl_batch_info(b.ptr, graph, mu_index, ctypes.byref(a), ctypes.byref(r), ctypes.byref(lm),
+                               ctypes.byref(i1), ctypes.byref(i2), ctypes.byref(stt)), "wl_batch_info")
+    return {"alpha": a.value, "rho": r.value, "lambda_max": lm.value, "iters_df": i1.value, "iters_v": i2.value,
+            "status": stt.value}
+
+
+def wl_batch_tile_rows(b, k):
+    return lib().wl_batch_tile_rows(b.ptr, k)
+
