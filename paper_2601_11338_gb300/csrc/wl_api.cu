@@ -484,6 +484,7 @@ struct LzRun {
   int m_eff = 0;     // steps before a breakdown (== m without one)
   double th = 0.0;   // largest Ritz value
   double conv = 1.0; // relative change of th over the last m/8 steps
+  bool spent = false; // no more steps possible (breakdown or the step cap reached)
 };
 
 int lanczos_run(wl_handle* h, LzRun* run, double rtol) {
@@ -497,7 +498,8 @@ int lanczos_run(wl_handle* h, LzRun* run, double rtol) {
   LzArgs a{phase_graph(h), run->c0, run->cA, run->cD, {v, v + h->n}, {v + 2 * h->n, v + 3 * h->n},
            (double*)h->part.p, st, 0, 0x5EEDull};
   for (;;) {
-    if (run->m > 0 && (run->conv <= rtol || run->m_eff < run->m || run->m >= m_cap)) break;
+    run->spent = run->m > 0 && (run->m_eff < run->m || run->m >= m_cap);
+    if (run->m > 0 && (run->conv <= rtol || run->spent)) break;
     const int j0 = run->m;
     const int m = j0 == 0 ? std::min(64, m_cap) : std::min(2 * j0, m_cap);
     if (j0 == 0) WL_CU(cudaMemsetAsync(st, 0, sizeof(LzState), S(h)));
@@ -547,7 +549,7 @@ int rho_companion(wl_handle* h, double mu, double lmaxA, double* rho) {
       WL_TRY(lanczos_run(h, &r, rtol));
       *val = r.th - lam;
       certain = std::fabs(*val) > 10.0 * r.conv * std::fabs(r.th);
-      if (certain || r.conv <= kTight || r.m_eff < r.m || r.m >= 480) break;
+      if (certain || r.conv <= kTight || r.spent) break;
       rtol = std::max(kTight, 1e-3 * std::fabs(*val) / std::fabs(r.th));
     }
     return WL_OK;
