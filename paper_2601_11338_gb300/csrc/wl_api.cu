@@ -511,7 +511,9 @@ int lanczos_run(wl_handle* h, LzRun* run, double rtol) {
     run->m = m;
     run->m_eff = (int)o[4];
     run->th = o[0];
-    run->conv = run->m_eff < m ? 0.0 : std::fabs(o[0] - o[1]) / (std::fabs(o[0]) + 1e-300);
+    // after a breakdown, or with as many steps as nodes, T_m holds the exact
+    // extreme eigenvalue (up to rounding)
+    run->conv = (run->m_eff < m || m >= h->n) ? 0.0 : std::fabs(o[0] - o[1]) / (std::fabs(o[0]) + 1e-300);
   }
   return WL_OK;
 }
