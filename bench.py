@@ -366,6 +366,137 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batched workload
+BATCH_MUS = [1.0, 0.75, 0.5, 0.25, 0.0]  # theta = 1 - mu in {0, .25, .5, .75, 1}
+BATCH_K = 32
+SEED_BATCH = 20260200
+BATCH_METRIC = "nnz*RHS*iters/s (64 graphs x 5 mu: D_f + L V, 32 RHS, refined form, one graph launch)"
+
+
+def run_batch(args):
+    """64 graphs (sizes log-uniform in [1e3, 2e5]; Erdos-Renyi mean degree 10,
+    Barabasi-Albert m = 3, 2D grids) x 5 mu values: walk degrees and L V for
+    32 Gaussian columns per problem, alpha = 0.5 / rho(Z_mu) per problem.
+    A step is one wl_batch_run (one CUDA graph launch). Baseline: the same
+    320 problems as a per-problem loop of single-graph FP64 calls."""
+    import torch
+
+    import wlgen
+    from paper_2601_11338_gb300 import wl
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    gs = wlgen.batch_graphs(64, 1e3, 2e5, seed=SEED_BATCH)
+    n = sum(g.n for g in gs)
+    nnz = sum(g.nnz for g in gs)
+    graphs = [(torch.as_tensor(g.row_ptr.astype(np.int32), device="cuda"), torch.as_tensor(g.col_idx, device="cuda"),
+               g.n, g.nnz) for g in gs]
+    Vh = wlgen.gaussian_block(n, BATCH_K, SEED_BATCH + 1)
+    V = torch.as_tensor(Vh, device="cuda")
+    nmu = len(BATCH_MUS)
+    Df = torch.empty((nmu, n), dtype=torch.float64, device="cuda")
+    W = torch.empty((nmu, n, BATCH_K), dtype=torch.float64, device="cuda")
+    log(f"batch: {len(gs)} graphs, n={n} nnz={nnz}, {nmu} mu values, k={BATCH_K}")
+
+    def build(prec):
+        p = wl.make_params(f=wl.WL_F_RESOLVENT, alpha_rel=0.5, prec=prec, tol=1e-10, stream=stream.cuda_stream)
+        sb = wl.wl_stats()
+        b = wl.wl_batch_build(graphs, BATCH_MUS, p, sb)
+        return b, sb.time_ms
+
+    b, build_ms = build(wl.WL_REFINED)
+    st = wl.wl_stats()
+    for _ in range(args.warmup):
+        wl.wl_batch_run(b, V, BATCH_K, Df, W, 0, st)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    units = 0.0
+    e0.record(stream)
+    for _ in range(args.steps):
+        wl.wl_batch_run(b, V, BATCH_K, Df, W, 0, st)
+        units += st.nnz_rhs_iters
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    value = units / args.steps / (ms / 1000.0)
+    iters = [wl.wl_batch_info(b, g, j) for j in range(nmu) for g in range(len(gs))]
+    tile = wl.wl_batch_tile_rows(b, BATCH_K)
+    # algorithmic bytes of the inner CG iterations: 4 nnz + 4 (n + 1) + 11 n K s per
+    # iteration of a problem (index streams; x, p, q, r vectors in FP32 with the x
+    # update in the U kernel)
+    alg = 0.0
+    for j in range(nmu):
+        for gi, g in enumerate(gs):
+            it = iters[j * len(gs) + gi]
+            alg += it["iters_df"] * (4 * g.nnz + 4 * (g.n + 1) + 11 * g.n * 1 * 4)
+            alg += it["iters_v"] * (4 * g.nnz + 4 * (g.n + 1) + 11 * g.n * BATCH_K * 4)
+    peak, peak_kind = peaks()
+    achieved = alg / (ms / 1000.0) / 1e9
+    # e2e: host V in, host D_f and W out, through the same call
+    Dh = np.empty((nmu, n))
+    Wh = np.empty((nmu, n, BATCH_K))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    wl.wl_batch_run(b, Vh, BATCH_K, Dh, Wh, 0, st)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": st.nnz_rhs_iters / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(Vh.nbytes),
+           "d2h_bytes_per_step": int(Dh.nbytes + Wh.nbytes), "ms": e2e_s * 1000.0}
+    # same batch in the FP64 form (one graph launch)
+    b64, _ = build(wl.WL_FP64)
+    wl.wl_batch_run(b64, V, BATCH_K, Df, W, 0, st)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    wl.wl_batch_run(b64, V, BATCH_K, Df, W, 0, st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_batch_ms = e0.elapsed_time(e1)
+    # per-problem loop of single-graph FP64 calls (handles built outside the timing)
+    from paper_2601_11338_gb300.api import WalkLaplacian
+    loop_ms = None
+    if not args.no_loop:
+        hs = []
+        off = np.concatenate([[0], np.cumsum([g.n for g in gs])])
+        for j, mu in enumerate(BATCH_MUS):
+            for gi, g in enumerate(gs):
+                a = iters[j * len(gs) + gi]["alpha"]
+                hs.append((WalkLaplacian(graphs[gi][0], graphs[gi][1], g.n, variant="btdw", mu=mu, alpha=a,
+                                         prec="fp64", tol=1e-10), slice(int(off[gi]), int(off[gi + 1]))))
+        Vs = [V[sl].contiguous() for _, sl in hs]
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for (w, sl), Vg in zip(hs, Vs):
+            w.degrees()
+            w.apply(Vg)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        loop_ms = e0.elapsed_time(e1)
+        del hs
+    line = {
+        "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "batch64_er_ba_grid_5mu_k32", "graphs": len(gs), "n": n, "nnz": nnz,
+                   "sizes": "log-uniform [1e3, 2e5]", "generators": "ER(mean deg 10) / BA(m=3) / 2D grid",
+                   "mus": BATCH_MUS, "rhs": BATCH_K, "alpha": "0.5/rho(Z_mu) per problem", "tol": 1e-10,
+                   "form": "refined (FP32 CG + FP64 residual/update)", "tile_rows": tile,
+                   "l2": "per-step working set > 3 GB (> L2)", "seed": SEED_BATCH},
+        "build_ms": build_ms,
+        "iters": {"df_max": max(i["iters_df"] for i in iters), "v_max": max(i["iters_v"] for i in iters),
+                  "v_mean": float(np.mean([i["iters_v"] for i in iters]))},
+        "roofline": {"bound": "hbm", "kernel": "whole graph launch (all batch kernels)", "achieved": achieved,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "bytes_alg_per_step": alg},
+        "fp64": {"batch_graph_ms": fp64_batch_ms, "per_problem_loop_ms": loop_ms,
+                 "speedup_refined_batch_vs_fp64_loop": (loop_ms / ms) if loop_ms else None},
+        "e2e": e2e, "gpu_launches": 1, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,11 +504,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--workload", default="chung_lu_1e6", choices=["chung_lu_1e6", "batch64"],
+                    help="chung_lu_1e6: the headline diffusion step; batch64: the batched executor")
+    ap.add_argument("--no-loop", action="store_true", help="batch64: skip the per-problem FP64 loop baseline")
     ap.add_argument("--timed-only", action="store_true",
                     help="profiling aid: run the warm-up and timed steps only (no time-to-1e-8, e2e or CPU legs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

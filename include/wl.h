@@ -252,7 +252,9 @@ int wl_batch_build(const wl_csr* graphs, int ngraph, const double* mus, int nmu,
  * time_ms, rel_res (largest relative residual), nnz_rhs_iters, launches. */
 int wl_batch_run(wl_batch* b, const double* V, int k, double* Df, double* W, int stepped, wl_stats* st);
 
-/* Per-problem figures of the build and the last run (any pointer may be NULL). */
+/* Per-problem figures of the build and the last run (any pointer may be NULL):
+ * alpha, rho(Z_mu), lambda_max(A), the CG iterations of the D_f solve and of
+ * the K-column solve (summed over refinement steps), the problem's status. */
 int wl_batch_info(const wl_batch* b, int graph, int mu_index, double* alpha, double* rho, double* lambda_max,
                   int* iters_df, int* iters_v, int* status);
 

@@ -91,7 +91,7 @@ struct SolveBufs {
   DBuf part;            // [nslab][ntile][2K] doubles
   DBuf colstate;        // gamma, alpha, beta, b2, rn2, bn2 (doubles) per problem-column
   DBuf colint;          // done, status, skip, ostatus (ints) per problem-column
-  DBuf probint;         // active, iters, outer_active, outer_iters (ints) per problem
+  DBuf probint;         // active, iters, outer_active, outer_iters, total iters (ints) per problem
   DBuf flags;           // any_inner, any_outer, host copy, loop counters (ints)
 };
 
@@ -174,7 +174,7 @@ int alloc_solve(wl_batch* b, SolveBufs& s, int K) {
   BT_CU(dalloc(s.part, (size_t)b->nslab * std::max(max_tiles(b), 1) * 2 * K * 8));
   BT_CU(dalloc(s.colstate, nc * 6 * 8));
   BT_CU(dalloc(s.colint, nc * 4 * 4));
-  BT_CU(dalloc(s.probint, np * 4 * 4));
+  BT_CU(dalloc(s.probint, np * 5 * 4));
   BT_CU(dalloc(s.flags, 64 * 4));
   return WL_OK;
 }
@@ -186,7 +186,7 @@ BatchState bstate(const wl_batch* b, SolveBufs& s) {
   int* ci = (int*)s.colint.p;
   int* pi = (int*)s.probint.p;
   int* fl = (int*)s.flags.p;
-  return BatchState{cs, cs + nc, cs + 2 * nc, cs + 3 * nc, ci, ci + nc, pi, pi + np, fl + 0};
+  return BatchState{cs, cs + nc, cs + 2 * nc, cs + 3 * nc, ci, ci + nc, pi, pi + np, pi + 4 * np, fl + 0};
 }
 
 BatchOuter bouter(const wl_batch* b, SolveBufs& s) {
@@ -387,6 +387,7 @@ int emit_solve(wl_batch* b, Emitter& em, SolveBufs& sb, const TileSet& ts, const
   const double tol2 = b->prm.tol * b->prm.tol;
   cudaStream_t s = em.s();
   BT_CU(cudaMemsetAsync(sb.flags.p, 0, sb.flags.bytes, s));
+  BT_CU(cudaMemsetAsync(st.total, 0, sizeof(int) * np, s));
   if (b->prm.prec == WL_FP64) {
     BatchArgs<double> a{g, (double*)sb.x.p, (double*)sb.r.p, (double*)sb.p.p, (double*)sb.q.p,
                         (const double*)b->ca.p, (const double*)b->cA.p, (const double*)b->cD.p, rhs, bscale,
@@ -791,7 +792,7 @@ int wl_batch_run(wl_batch* b, const double* V, int k, double* Df, double* W, int
     SolveBufs& sb = which_solve == 0 ? b->sb1 : b->sbk;
     const int K = sb.K;
     const size_t nc = (size_t)np * K;
-    std::vector<int> pi(np * 4), ci(nc * 4);
+    std::vector<int> pi(np * 5), ci(nc * 4);
     std::vector<double> cs(nc * 6);
     BT_CU(cudaMemcpy(pi.data(), sb.probint.p, sizeof(int) * pi.size(), cudaMemcpyDeviceToHost));
     BT_CU(cudaMemcpy(ci.data(), sb.colint.p, sizeof(int) * ci.size(), cudaMemcpyDeviceToHost));
@@ -800,7 +801,7 @@ int wl_batch_run(wl_batch* b, const double* V, int k, double* Df, double* W, int
       const int g = pr % b->ngraph;
       const int64_t gn = b->goff_h[g + 1] - b->goff_h[g];
       const int64_t gnnz = b->rp_h[b->goff_h[g + 1]] - b->rp_h[b->goff_h[g]];
-      int it = pi[np + pr], outer = refined ? pi[3 * np + pr] : 0;
+      int it = pi[4 * np + pr], outer = refined ? pi[3 * np + pr] : 0;
       double rel = 0.0;
       int stat = WL_OK;
       for (int c = 0; c < K; ++c) {

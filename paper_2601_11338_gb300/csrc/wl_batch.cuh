@@ -50,7 +50,8 @@ struct BatchState {
   int* done;
   int* status;
   int* active;   // per problem
-  int* iters;    // per problem
+  int* iters;    // per problem: iterations of the current solve
+  int* total;    // per problem: iterations summed over the refinement steps
   int* any;      // one flag: some problem still iterates
 };
 
@@ -310,7 +311,10 @@ __global__ void __launch_bounds__(kPhaseBlock) bred_s(BatchGraph g, BatchState s
       st.alpha[i] = 0.0;
     }
   }
-  if (tid == 0) st.iters[pr] += 1;
+  if (tid == 0) {
+    st.iters[pr] += 1;
+    st.total[pr] += 1;
+  }
 }
 
 // ---------------------------------------------------------------- U
