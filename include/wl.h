@@ -220,6 +220,49 @@ const char* wl_last_error(void);
 int wl_degrees_noalloc(const wl_csr* A, wl_variant v, double mu, double alpha, double tol, int max_iter,
                        double* Df, void* stream, wl_stats* st);
 
+/* ------------------------------------------------------------ learned warm start */
+/* A small perceptron supplies the starting guess of the walk-degree solve
+ * (wl_degrees); the paper has no learned part. Features per node i:
+ *   f0 = log(1 + d_i), f1 = log(1 + (A d)_i), f2 = log(1 + t_i) (triangles
+ *   through i), f3 = log(1 + (A d - d)_i) (nonbacktracking 2-walks).
+ * Guess: x0 = x_an * exp(y), x_an = 1 + B 1 + B^2 1 with
+ * B = (alpha A - alpha^2 mu D) / (1 - mu^2 alpha^2) (two terms of the
+ * Neumann series of D_f), y = W3 tanh(W2 tanh(W1 s + b1) + b2) + b3 on the
+ * standardised features s = (f - mean) / std.
+ * Parameter vector (wl_mlp_param_count() = 4553 floats): mean[4], std[4],
+ * W1[64][4], b1[64], W2[64][64], b2[64], W3[64], b3. */
+int wl_mlp_param_count(void);
+
+/* Features (n x 4 FP32, row-major) and x_an (n FP64) of the handle's graph
+ * and parameters (f = WL_F_RESOLVENT), in the caller's node order; either
+ * output may be NULL; host or device pointers. Synchronous. */
+int wl_mlp_features(wl_handle* h, float* feats, double* xan, wl_stats* st);
+
+/* Trains the network on rows (feats[r], target[r]) with the MSE loss and
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8, step size lr): `steps` updates on
+ * consecutive slices of `batch` rows (batch <= 0: all rows). standardize = 1
+ * first sets mean/std from the rows. params: in = initial values, out =
+ * trained values (host or device). final_loss: MSE of the trained network
+ * over all rows. Synchronous. */
+int wl_mlp_train(float* params, const float* feats, const float* target, int64_t rows, int steps, int64_t batch,
+                 float lr, int standardize, double* final_loss, void* stream);
+
+/* MSE loss over all rows and its gradient (layout of the parameter vector,
+ * zero for mean/std), FP32 accumulation per 128 rows, FP64 across them. */
+int wl_mlp_loss_grad(const float* params, const float* feats, const float* target, int64_t rows, double* loss,
+                     float* grad, void* stream);
+
+/* out[r] = xan[r] * exp(y_r) (xan NULL: out[r] = y_r). */
+int wl_mlp_predict(const float* params, const float* feats, int64_t rows, const double* xan, double* out,
+                   void* stream);
+
+/* Training target[r] = log(Df[r] / xan[r]) (FP32). */
+int wl_mlp_targets(const double* Df, const double* xan, int64_t rows, float* target, void* stream);
+
+/* Features, x_an and x0 on the device for the handle's graph; x0 becomes
+ * the starting guess of the next wl_degrees (as wl_set_warm_start). */
+int wl_mlp_warm_start(wl_handle* h, const float* params, wl_stats* st);
+
 /* ------------------------------------------------------------ batched executor */
 /* Walk degrees and walk-Laplacian applies for a collection of graphs and a
  * sweep of backtrack weights, all problems at once (Sec. 4.2 applied to

@@ -81,3 +81,11 @@ class WalkLaplacian:
 
     def close(self):
         self.h.destroy()
+
+
+def mlp_features(w: "WalkLaplacian"):
+    """Node features (n x 4, FP32) and the analytic guess x_an (n, FP64) of a handle's graph."""
+    F = torch.empty((w.n, 4), dtype=torch.float32, device=w.device)
+    X = torch.empty(w.n, dtype=torch.float64, device=w.device)
+    wl.wl_mlp_features(w.h, F, X)
+    return F, X

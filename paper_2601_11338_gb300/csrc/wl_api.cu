@@ -932,6 +932,68 @@ int wl_set_warm_start(wl_handle* h, const double* x0) {
   return WL_OK;
 }
 
+// Node features of the warm-start network and the analytic guess x_an,
+// in the caller's node order.
+int wl_mlp_features(wl_handle* h, float* feats, double* xan, wl_stats* st) {
+  if (st) memset(st, 0, sizeof(*st));
+  if (!h || (!feats && !xan)) return WL_ERR_INVALID_ARG;
+  if (h->prm.f != WL_F_RESOLVENT) return WL_ERR_UNSUPPORTED;
+  if (h->n == 0) return WL_OK;
+  begin_timer(h);
+  const size_t n = (size_t)h->n;
+  WL_TRY(ensure(h->ptmp, std::max(h->ptmp.bytes, features_tmp_bytes(h->n, h->nnz))));
+  float* F = feats;
+  double* X = xan;
+  const bool fdev = !feats || is_device_ptr(feats), xdev = !xan || is_device_ptr(xan);
+  if (!fdev || !xdev) {
+    WL_TRY(ensure(h->stage_b, n * 4 * sizeof(float) + n * 8));
+    if (!fdev) F = (float*)h->stage_b.p;
+    if (!xdev) X = (double*)((char*)h->stage_b.p + n * 4 * sizeof(float));
+  }
+  counted(h, 8);
+  WL_CU(launch_features(h->g.row_ptr, h->g.col, h->n, h->nnz, h->alpha, h->mu, h->perm, F, X, h->ptmp.p, S(h)));
+  if (!fdev) WL_CU(cudaMemcpyAsync(feats, F, n * 4 * sizeof(float), cudaMemcpyDeviceToHost, S(h)));
+  if (!xdev) WL_CU(cudaMemcpyAsync(xan, X, n * 8, cudaMemcpyDeviceToHost, S(h)));
+  const double ms = end_timer(h);
+  if (st) {
+    st->time_ms = ms;
+    st->launches = h->launches;
+  }
+  prof_reset(h);
+  return WL_OK;
+}
+
+// Warm start of the walk-degree solve from the network: features, x_an and
+// x0 = x_an * exp(y) on the device, kept as the handle's starting guess.
+int wl_mlp_warm_start(wl_handle* h, const float* params, wl_stats* st) {
+  if (st) memset(st, 0, sizeof(*st));
+  if (!h || !params) return WL_ERR_INVALID_ARG;
+  if (h->prm.f != WL_F_RESOLVENT) return WL_ERR_UNSUPPORTED;
+  if (h->n == 0) return WL_OK;
+  begin_timer(h);
+  const size_t n = (size_t)h->n;
+  const int np = wl_mlp_param_count();
+  WL_TRY(ensure(h->ptmp, std::max(h->ptmp.bytes, features_tmp_bytes(h->n, h->nnz))));
+  WL_TRY(ensure(h->stage_b, n * 4 * sizeof(float) + n * 8 + (size_t)np * sizeof(float) + 256));
+  WL_TRY(ensure(h->warm, std::max<size_t>(n, 1) * 8));
+  float* F = (float*)h->stage_b.p;
+  double* X = (double*)((char*)h->stage_b.p + n * 4 * sizeof(float));
+  float* P = (float*)((char*)X + n * 8);
+  WL_CU(cudaMemcpyAsync(P, params, (size_t)np * sizeof(float), cudaMemcpyDefault, S(h)));
+  counted(h, 9);
+  WL_CU(launch_features(h->g.row_ptr, h->g.col, h->n, h->nnz, h->alpha, h->mu, nullptr, F, X, h->ptmp.p, S(h)));
+  WL_CU(launch_mlp_predict(P, F, h->n, X, (double*)h->warm.p, S(h)));
+  const double ms = end_timer(h);
+  h->have_warm = true;
+  h->have_Df = false;
+  if (st) {
+    st->time_ms = ms;
+    st->launches = h->launches;
+  }
+  prof_reset(h);
+  return WL_OK;
+}
+
 int wl_degrees(wl_handle* h, double* Df, wl_stats* st) {
   if (!h || (!Df && h->n > 0)) return WL_ERR_INVALID_ARG;
   SolveInfo info;

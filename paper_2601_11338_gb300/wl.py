@@ -104,6 +104,18 @@ def lib():
         L.wl_batch_info.restype = c_int
         L.wl_batch_tile_rows.argtypes = [vp, c_int]
         L.wl_batch_tile_rows.restype = c_int
+        L.wl_mlp_param_count.restype = c_int
+        L.wl_mlp_param_count.argtypes = []
+        L.wl_mlp_features.argtypes = [vp, vp, vp, ctypes.POINTER(wl_stats)]
+        L.wl_mlp_train.argtypes = [vp, vp, vp, i64, c_int, i64, ctypes.c_float, c_int,
+                                   ctypes.POINTER(ctypes.c_double), vp]
+        L.wl_mlp_loss_grad.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctypes.c_double), vp, vp]
+        L.wl_mlp_predict.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.wl_mlp_targets.argtypes = [vp, vp, i64, vp, vp]
+        L.wl_mlp_warm_start.argtypes = [vp, vp, ctypes.POINTER(wl_stats)]
+        for name in ("wl_mlp_features", "wl_mlp_train", "wl_mlp_loss_grad", "wl_mlp_predict", "wl_mlp_targets",
+                     "wl_mlp_warm_start"):
+            getattr(L, name).restype = c_int
         L.wl_batch_destroy.argtypes = [vp]
         L.wl_batch_destroy.restype = None
         for name in ("wl_build", "wl_set_params", "wl_degrees", "wl_apply", "wl_expmv", "wl_trace",
@@ -266,4 +278,42 @@ def wl_batch_info(b, graph, mu_index):
 
 def wl_batch_tile_rows(b, k):
     return lib().wl_batch_tile_rows(b.ptr, k)
+
+
+# ------------------------------------------------------------ learned warm start
+def wl_mlp_param_count():
+    return lib().wl_mlp_param_count()
+
+
+def wl_mlp_features(h, feats=None, xan=None, stats=None):
+    st = stats if stats is not None else wl_stats()
+    _check(lib().wl_mlp_features(h.ptr, _ptr(feats), _ptr(xan), ctypes.byref(st)), "wl_mlp_features")
+
+
+def wl_mlp_train(params, feats, target, rows, steps, batch=0, lr=1e-3, standardize=1, stream=None):
+    loss = ctypes.c_double()
+    _check(lib().wl_mlp_train(_ptr(params), _ptr(feats), _ptr(target), rows, steps, batch, lr, standardize,
+                              ctypes.byref(loss), stream), "wl_mlp_train")
+    return loss.value
+
+
+def wl_mlp_loss_grad(params, feats, target, rows, grad, stream=None):
+    loss = ctypes.c_double()
+    _check(lib().wl_mlp_loss_grad(_ptr(params), _ptr(feats), _ptr(target), rows, ctypes.byref(loss), _ptr(grad),
+                                  stream), "wl_mlp_loss_grad")
+    return loss.value
+
+
+def wl_mlp_predict(params, feats, rows, xan, out, stream=None):
+    _check(lib().wl_mlp_predict(_ptr(params), _ptr(feats), rows, _ptr(xan), _ptr(out), stream), "wl_mlp_predict")
+
+
+def wl_mlp_targets(Df, xan, rows, target, stream=None):
+    _check(lib().wl_mlp_targets(_ptr(Df), _ptr(xan), rows, _ptr(target), stream), "wl_mlp_targets")
+
+
+def wl_mlp_warm_start(h, params, stats=None):
+    st = stats if stats is not None else wl_stats()
+    _check(lib().wl_mlp_warm_start(h.ptr, _ptr(params), ctypes.byref(st)), "wl_mlp_warm_start")
+    return st
 
