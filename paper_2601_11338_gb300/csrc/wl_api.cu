@@ -951,7 +951,8 @@ int wl_mlp_features(wl_handle* h, float* feats, double* xan, wl_stats* st) {
     if (!xdev) X = (double*)((char*)h->stage_b.p + n * 4 * sizeof(float));
   }
   counted(h, 8);
-  WL_CU(launch_features(h->g.row_ptr, h->g.col, h->n, h->nnz, h->alpha, h->mu, h->perm, F, X, h->ptmp.p, S(h)));
+  WL_CU(launch_features(h->g.row_ptr, h->g.col, h->n, h->nnz, h->alpha, h->mu, h->perm, h->perm, F, X, h->ptmp.p,
+                        S(h)));
   if (!fdev) WL_CU(cudaMemcpyAsync(feats, F, n * 4 * sizeof(float), cudaMemcpyDeviceToHost, S(h)));
   if (!xdev) WL_CU(cudaMemcpyAsync(xan, X, n * 8, cudaMemcpyDeviceToHost, S(h)));
   const double ms = end_timer(h);
@@ -981,7 +982,8 @@ int wl_mlp_warm_start(wl_handle* h, const float* params, wl_stats* st) {
   float* P = (float*)((char*)X + n * 8);
   WL_CU(cudaMemcpyAsync(P, params, (size_t)np * sizeof(float), cudaMemcpyDefault, S(h)));
   counted(h, 9);
-  WL_CU(launch_features(h->g.row_ptr, h->g.col, h->n, h->nnz, h->alpha, h->mu, nullptr, F, X, h->ptmp.p, S(h)));
+  WL_CU(launch_features(h->g.row_ptr, h->g.col, h->n, h->nnz, h->alpha, h->mu, nullptr, h->perm, F, X, h->ptmp.p,
+                        S(h)));
   WL_CU(launch_mlp_predict(P, F, h->n, X, (double*)h->warm.p, S(h)));
   const double ms = end_timer(h);
   h->have_warm = true;

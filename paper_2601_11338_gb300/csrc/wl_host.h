@@ -129,10 +129,13 @@ inline int coop_grid(const void* fn, int cap_per_sm) {
 }
 
 // ---- wl_mlp.cu
-// node features (n x 4, FP32, row perm[i] for internal row i) and the
-// analytic guess x_an (n, FP64); tmp holds features_tmp_bytes(n, nnz)
+// node features (n x 4, FP32, row perm[i] for internal row i, perm NULL: i)
+// and the analytic guess x_an (n, FP64); perm_key: the caller's index of
+// each internal node (NULL when not relabelled), the order of the columns
+// in each row; tmp holds features_tmp_bytes(n, nnz)
 cudaError_t launch_features(const int32_t* rp, const int32_t* col, int64_t n, int64_t nnz, double alpha, double mu,
-                            const int32_t* perm, float* F, double* xan, void* tmp, cudaStream_t s);
+                            const int32_t* perm, const int32_t* perm_key, float* F, double* xan, void* tmp,
+                            cudaStream_t s);
 size_t features_tmp_bytes(int64_t n, int64_t nnz);
 // out = x_an * exp(y) per row (xan NULL: out = y)
 cudaError_t launch_mlp_predict(const float* P, const float* F, int64_t rows, const double* xan, double* out,

@@ -104,10 +104,11 @@ __global__ void k_feat_orient(const int32_t* __restrict__ rp, const int32_t* __r
 }
 
 // every triangle once: for i, each oriented neighbour j (one per lane) and
-// each w in N+(i) and N+(j) (merge of two ascending lists) adds one to t_i,
-// t_j and t_w
+// each w in N+(i) and N+(j) (merge of two lists ascending in key) adds one
+// to t_i, t_j and t_w. The key is the caller's node index (key[j], NULL:
+// j): relabelled rows keep their columns in the caller's order.
 __global__ void k_feat_triangles(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol, int64_t n,
-                                 unsigned long long* __restrict__ t) {
+                                 const int32_t* __restrict__ key, unsigned long long* __restrict__ t) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -121,12 +122,13 @@ __global__ void k_feat_triangles(const int64_t* __restrict__ orp, const int32_t*
       unsigned long long tj = 0;
       while (a < ie && b < be) {
         const int x = ocol[a], y = ocol[b];
-        if (x == y) {
+        const int kx = key ? key[x] : x, ky = key ? key[y] : y;
+        if (kx == ky) {
           ++tj;
           atomicAdd(t + x, 1ull);
           ++a;
           ++b;
-        } else if (x < y) {
+        } else if (kx < ky) {
           ++a;
         } else {
           ++b;
@@ -388,7 +390,8 @@ cudaError_t grad_setup() {
 
 // ------------------------------------------------------------------ launchers (wl_host.h)
 cudaError_t launch_features(const int32_t* rp, const int32_t* col, int64_t n, int64_t nnz, double alpha, double mu,
-                            const int32_t* perm, float* F, double* xan, void* tmp, cudaStream_t s) {
+                            const int32_t* perm, const int32_t* perm_key, float* F, double* xan, void* tmp,
+                            cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   // tmp: ad (n doubles), t (n u64), outdeg / orp (n + 1 int64 each), scan scratch, ocol (nnz / 2 + 1 int32)
   double* ad = (double*)tmp;
@@ -406,7 +409,7 @@ cudaError_t launch_features(const int32_t* rp, const int32_t* col, int64_t n, in
   e = launch_scan(outdeg, n, orp, sc, s);  // orp[0..n]: exclusive prefix, orp[n] = total
   if (e != cudaSuccess) return e;
   k_feat_orient<<<gw, 256, 0, s>>>(rp, col, n, orp, ocol);
-  k_feat_triangles<<<gw, 256, 0, s>>>(orp, ocol, n, t);
+  k_feat_triangles<<<gw, 256, 0, s>>>(orp, ocol, n, perm_key, t);
   k_feat_out<<<g1, 256, 0, s>>>(rp, ad, t, n, alpha, mu, perm, F, xan);
   (void)nnz;
   return cudaGetLastError();
