@@ -124,8 +124,11 @@ def test_predict_matches_oracle_forward_with_standardisation():
 
 def test_training_reduces_loss_and_warm_start_cuts_iterations():
     """Trained on walk degrees of small ER / Chung-Lu / BA / grid graphs, the
-    network's guess starts the NBT walk-degree CG closer to D_f than x = 0
-    on a held-out graph, so the solve needs fewer iterations."""
+    network's guess x0 = x_an exp(y) on a held-out Chung-Lu graph is closer
+    to D_f than the analytic two-term guess x_an, and the NBT walk-degree CG
+    started from it needs fewer iterations than from x = 0. (The analytic
+    guess, whose error is a smooth Krylov remainder, still needs fewer
+    iterations than the learned one; the test records all three.)"""
     from paper_2601_11338_gb300 import warmstart, wl
     from paper_2601_11338_gb300.api import WalkLaplacian, mlp_features
     train = [wlgen.erdos_renyi(3000, 10.0, 51), wlgen.chung_lu(5000, seed=52), wlgen.barabasi_albert(4000, 3, 53),
@@ -137,21 +140,28 @@ def test_training_reduces_loss_and_warm_start_cuts_iterations():
     loss = wl.wl_mlp_train(p, F, T, F.shape[0], 1500, 0, 3e-3, 1)
     assert loss < 0.5 * loss0
     g = wlgen.chung_lu(20000, seed=56)
-    iters = {}
+    iters, err = {}, {}
+    Dref = None
     for mode in ("cold", "analytic", "mlp"):
         w = WalkLaplacian(g.row_ptr.astype(np.int32), g.col_idx, g.n, variant="nbt", alpha_rel=0.5, prec="fp64",
                           tol=1e-10)
+        Fg, X = mlp_features(w)
+        x0 = None
         if mode == "analytic":
-            _, X = mlp_features(w)
             wl.wl_set_warm_start(w.h, X)
+            x0 = X
         elif mode == "mlp":
             wl.wl_mlp_warm_start(w.h, p)
+            x0 = torch.empty_like(X)
+            wl.wl_mlp_predict(p, Fg, g.n, X, x0)
         D = w.degrees()
         iters[mode] = w.last.iters
         if mode == "cold":
             Dref = D.clone()
         else:
             assert rel(D.cpu().numpy(), Dref.cpu().numpy()) <= 1e-9
+            err[mode] = rel(x0.cpu().numpy(), Dref.cpu().numpy())
         w.close()
-    print("walk-degree CG iterations", iters)
+    print("walk-degree CG iterations", iters, "guess errors", err)
+    assert err["mlp"] < err["analytic"]
     assert iters["mlp"] < iters["cold"]
