@@ -497,6 +497,145 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ trace workload
+def run_trace(args):
+    """XNysTrace of the all-walk resolvent (I - alpha A)^{-1}, alpha = 0.5 /
+    lambda_max(A), on R-MAT scale 22 (a = .57, b = c = .19, edge factor 16):
+    M = 64 Philox Gaussian BF16 test vectors, FP32 block CG (k = 64), Gram,
+    FP64 leave-one-out core. A step is one wl_trace on a built handle."""
+    import torch
+
+    import wlgen
+    from paper_2601_11338_gb300 import wl
+    from paper_2601_11338_gb300.api import WalkLaplacian
+
+    torch.cuda.set_device(0)
+    scale = args.scale or 22
+    t0 = time.perf_counter()
+    g = wlgen.rmat(scale, 16, 0.57, 0.19, 0.19, seed=20260300 + scale)
+    gen_s = time.perf_counter() - t0
+    log(f"trace: R-MAT scale {scale}: n={g.n} nnz={g.nnz} (generated in {gen_s:.1f} s)")
+    w = WalkLaplacian(g.row_ptr.astype(np.int32), g.col_idx, g.n, variant="allwalk", alpha_rel=0.5, prec="refined",
+                      tol=1e-7)
+    build_ms = w.build_stats.time_ms
+    for i in range(args.warmup):
+        w.trace(64, 1000 + i)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms, units, res = [], 0.0, []
+    kcg_ms = kcg_bytes = 0.0
+    kcg_iters = 0
+    for i in range(args.steps):
+        est, err = w.trace(64, 1 + i)
+        st = w.last
+        ms.append(st.time_ms)
+        units += st.nnz_rhs_iters
+        kcg_ms += st.k_cg_ms
+        kcg_bytes += st.k_cg_bytes
+        kcg_iters += st.k_cg_iters
+        res.append((est, err))
+    clk = clocks.stop()
+    tot_ms = sum(ms)
+    peak, peak_kind = peaks()
+    achieved = (kcg_bytes / (kcg_ms / 1000.0)) / 1e9 if kcg_ms > 0 else 0.0
+    line = {
+        "metric": "nnz*RHS*iters/s (XNysTrace, all-walk resolvent, M = 64)", "value": units / (tot_ms / 1000.0),
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32+f64",
+        "data": "synthetic",
+        "config": {"workload": f"rmat{scale}_xnystrace_m64", "n": g.n, "nnz": g.nnz, "a": 0.57, "b": 0.19,
+                   "c": 0.19, "edge_factor": 16, "alpha": "0.5/lambda_max(A)", "cg_tol": 1e-7,
+                   "l2": "per-step working set > 2 GB (> L2)"},
+        "build_ms": build_ms, "estimates": res,
+        "roofline": {"bound": "hbm", "kernel": "block CG iteration kernels (FP32, k = 64)", "achieved": achieved,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "cg_ms_per_step": kcg_ms / args.steps, "cg_iters_per_step": kcg_iters / args.steps},
+        "gpu_launches": int(w.last.launches), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ warm-start workload
+def run_warmstart(args):
+    """Walk degrees of R-MAT scale 24 (all-walk and NBT resolvent, alpha = 0.5 /
+    rho(Z_mu)), refined form to relative residual 1e-8, from x = 0, from the
+    analytic two-term guess and from the learned guess (network trained on
+    walk degrees of Erdos-Renyi / Chung-Lu / Barabasi-Albert / grid graphs of
+    1e3 - 2e5 nodes). Times include features and inference for the guesses."""
+    import torch
+
+    import wlgen
+    from paper_2601_11338_gb300 import warmstart, wl
+    from paper_2601_11338_gb300.api import WalkLaplacian, mlp_features
+
+    torch.cuda.set_device(0)
+    scale = args.scale or 24
+    rng = np.random.default_rng(20260400)
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(2e5), size=16)).astype(int)
+    train = []
+    for i, sz in enumerate(sizes):
+        kind = i % 4
+        if kind == 0:
+            train.append(wlgen.erdos_renyi(int(sz), 10.0, 20260410 + i))
+        elif kind == 1:
+            train.append(wlgen.chung_lu(int(sz), seed=20260410 + i))
+        elif kind == 2:
+            train.append(wlgen.barabasi_albert(int(sz), 3, 20260410 + i))
+        else:
+            r = max(2, int(round(np.sqrt(sz))))
+            train.append(wlgen.grid2d(r, max(2, int(round(sz / r)))))
+    t0 = time.perf_counter()
+    g = wlgen.rmat(scale, 16, 0.57, 0.19, 0.19, seed=20260400 + scale)
+    log(f"warm start: R-MAT scale {scale}: n={g.n} nnz={g.nnz} (generated in {time.perf_counter() - t0:.1f} s)")
+    rp = torch.as_tensor(g.row_ptr.astype(np.int32), device="cuda")
+    ci = torch.as_tensor(g.col_idx, device="cuda")
+    out = {}
+    for variant in ("allwalk", "nbt"):
+        t0 = time.perf_counter()
+        p, loss = warmstart.train(train, variant, steps=1500, lr=3e-3)
+        train_s = time.perf_counter() - t0
+        w = WalkLaplacian(rp, ci, g.n, variant=variant, alpha_rel=0.5, prec="refined", tol=1e-8)
+        res = {"train_s": train_s, "train_loss": loss}
+        Dref = None
+        for mode in ("cold", "analytic", "mlp", "cold"):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            guess_ms = 0.0
+            if mode == "analytic":
+                st = wl.wl_stats()
+                X = torch.empty(g.n, dtype=torch.float64, device="cuda")
+                wl.wl_mlp_features(w.h, None, X, st)
+                wl.wl_set_warm_start(w.h, X)
+                guess_ms = st.time_ms
+            elif mode == "mlp":
+                st = wl.wl_mlp_warm_start(w.h, p)
+                guess_ms = st.time_ms
+            else:
+                wl.wl_set_warm_start(w.h, None)
+            D = w.degrees()
+            e1.record()
+            torch.cuda.synchronize()
+            r = {"iters": int(w.last.k_cg_iters), "refinements": int(w.last.refinements),
+                 "ms_total": e0.elapsed_time(e1), "guess_ms": guess_ms, "rel_res": w.last.rel_res}
+            if Dref is None:
+                Dref = D.clone()
+            else:
+                r["rel_diff_vs_cold"] = float(torch.linalg.norm(D - Dref) / torch.linalg.norm(Dref))
+            res[mode] = r  # the second cold run (warm caches) overwrites the first
+        out[variant] = res
+        w.close()
+    line = {"metric": "time to relative residual 1e-8 of the walk degrees (ms)", "value": out["nbt"]["mlp"]["ms_total"],
+            "unit": "ms", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"rmat{scale}_walk_degrees_warm_start", "n": g.n, "nnz": g.nnz,
+                       "train_graphs": len(train), "train_sizes": "log-uniform [1e3, 2e5]",
+                       "form": "refined", "tol": 1e-8},
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -504,9 +643,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
-    ap.add_argument("--workload", default="chung_lu_1e6", choices=["chung_lu_1e6", "batch64"],
+    ap.add_argument("--workload", default="chung_lu_1e6", choices=["chung_lu_1e6", "batch64", "trace_rmat", "warmstart_rmat"],
                     help="chung_lu_1e6: the headline diffusion step; batch64: the batched executor")
     ap.add_argument("--no-loop", action="store_true", help="batch64: skip the per-problem FP64 loop baseline")
+    ap.add_argument("--scale", type=int, default=0, help="trace_rmat / warmstart_rmat: R-MAT scale (22 / 24)")
     ap.add_argument("--timed-only", action="store_true",
                     help="profiling aid: run the warm-up and timed steps only (no time-to-1e-8, e2e or CPU legs)")
     args = ap.parse_args()
@@ -514,6 +654,10 @@ def main():
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)
+    elif args.workload == "trace_rmat":
+        run_trace(args)
+    elif args.workload == "warmstart_rmat":
+        run_warmstart(args)
     else:
         run_ours(args)
 
