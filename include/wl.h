@@ -220,6 +220,16 @@ const char* wl_last_error(void);
 int wl_degrees_noalloc(const wl_csr* A, wl_variant v, double mu, double alpha, double tol, int max_iter,
                        double* Df, void* stream, wl_stats* st);
 
+/* Gram [Omega Y]^T Y of the XNysTrace core (Alg. 1): omega n x M BF16 bit
+ * patterns, Y n x ldy FP32 (first M columns used), M <= 64; DEVICE pointers.
+ * out (device, 128 x 64 FP64): rows 0..63 = Omega^T Y, rows 64..127 =
+ * Y^T Y, entries beyond M zero. tensor_cores = 1: tcgen05 MMA (kind::tf32,
+ * FP32 accumulation in tensor memory) with Y split into two TF32 terms;
+ * 0: FP32 CUDA cores. FP64 sum across node chunks either way. Synchronous;
+ * WL_ERR_TIMEOUT if a bounded tensor-core wait gave up. */
+int wl_sketch_gram(const uint16_t* omega, const float* Y, int64_t n, int M, int ldy, int tensor_cores, double* out,
+                   void* stream);
+
 /* ------------------------------------------------------------ learned warm start */
 /* A small perceptron supplies the starting guess of the walk-degree solve
  * (wl_degrees); the paper has no learned part. Features per node i:

@@ -142,6 +142,7 @@ struct wl_handle {
   Buf cgstate;            // CgState of the running solve
   Buf lzstate;            // LzState of the spectral-scale Lanczos
   double inner_tol = 4e-6;  // floor of the FP32 correction target of the refined form
+  bool gram_tc = false;     // XNysTrace Gram on the tensor cores (tcgen05) instead of CUDA cores
   CgState* cgst() { return (CgState*)cgstate.p; }
   double* h_pin = nullptr;  // pinned host scratch (4096 doubles)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -1292,12 +1293,19 @@ int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, u
     if ((rc = run_cg<float>(h, K, a, grid_s, grid_u, info, 4)) != WL_OK) break;
     (void)sm;
     counted(h, 3);
-    e = launch_gram(om_int, (const float*)h->x.p, n, M, K, partial, Gg, gout, S(h));
+    int* gerr = (int*)((double*)h->small.p + 1000);
+    e = cudaMemsetAsync(gerr, 0, sizeof(int), S(h));
+    if (e == cudaSuccess) e = launch_gram(om_int, (const float*)h->x.p, n, M, K, partial, Gg, gout, h->gram_tc, gerr, S(h));
     if (e == cudaSuccess) e = launch_nys_core(gout, M, core, S(h));
     if (e != cudaSuccess) { rc = set_cuda_error(e, "gram/core"); break; }
     double* hp = h->h_pin;
     WL_CU(cudaMemcpyAsync(hp, core, 8 * 8, cudaMemcpyDeviceToHost, S(h)));
     WL_CU(cudaStreamSynchronize(S(h)));
+    if (h->gram_tc) {
+      int herr = 0;
+      WL_CU(cudaMemcpy(&herr, gerr, sizeof(int), cudaMemcpyDeviceToHost));
+      if (herr != 0) { rc = herr; break; }
+    }
     if (hp[2] != 0.0) { rc = WL_ERR_NOT_SPD; break; }
     *est = hp[0];
     *err_est = hp[1];

@@ -1,0 +1,203 @@
+// Gram [Omega Y]^T Y of the XNysTrace core on the 5th-generation tensor
+// cores (tcgen05.mma, kind::tf32, accumulator in tensor memory).
+//
+// X = [Omega Y] has 128 columns (Omega BF16 in 0..63, Y FP32 in 64..127;
+// columns beyond the sketch size are zero) and one row per node. Y is split
+// into two TF32 terms, Y = Yh + Yl (Yh = Y rounded to TF32, Yl = the
+// remainder rounded to TF32), so that with Xh = [Omega Yh], Xl = [0 Yl]
+//   D = Xh^T Yh + Xh^T Yl + Xl^T Yh
+// carries FP32-level accuracy (the dropped Yl^T Yl term is 2^-22 relative);
+// Omega is exact in TF32. D (128 x 64 FP32) lives in 64 TMEM columns.
+//
+// Each CTA (4 warps) owns a contiguous range of nodes and walks it in
+// stages of kTcRows nodes: all threads convert their feature column of the
+// stage into two K-major operand tiles in shared memory (no swizzle: 8-row
+// x 16-byte core matrices), one thread issues the MMAs (M = 128, N = 64,
+// K = 8 each) and commits them to the stage's mbarrier; two stages alternate
+// so that loading overlaps the tensor-core work. Every mbarrier wait is
+// bounded; on timeout the CTA records an error and still frees its TMEM.
+#pragma once
+#include <stdint.h>
+
+namespace wl {
+
+constexpr int kTcRows = 32;                               // nodes per stage
+constexpr int kTcThreads = 128;                           // one thread per column of X
+constexpr uint32_t kTcTileBytes = 128u * kTcRows * 4u;    // one 128 x 32 TF32 tile (16 KB)
+constexpr uint32_t kTcLBO = 128;                          // core matrix to the next along K
+constexpr uint32_t kTcSBO = (kTcRows / 4) * 128;          // core matrix to the next 8-row group
+constexpr uint32_t kTcCols = 64;                          // TMEM columns (N)
+constexpr size_t kTcSmem = 4 * (size_t)kTcTileBytes + 1024 + 64;
+// kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32 (2 in bits 7-9 and 10-12),
+// both K-major, N / 8 in bits 17-22, M / 16 in bits 24-28
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr long long kTcWaitLimit = 1ll << 24;             // polls of one mbarrier wait
+
+#ifdef WL_TRACE_KERNELS
+
+__device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, LBO, SBO (16-byte units), version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((kTcLBO >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((kTcSBO >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ uint32_t tc_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+  for (long long i = 0; i < kTcWaitLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t taddr, uint64_t da, uint64_t db, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %3, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %4, p;\n\t}\n"
+      :
+      : "r"(taddr), "l"(da), "l"(db), "r"(acc), "r"(kTcIdesc)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads) gram_tc(const uint16_t* __restrict__ omega, const float* __restrict__ Y,
+                                                      int64_t n, int M, int K, int64_t chunk,
+                                                      float* __restrict__ partial, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tc_sm[];
+  unsigned char* base = tc_sm + ((1024 - (tc_smem_u32(tc_sm) & 1023)) & 1023);  // 1 KB aligned tiles
+  unsigned char* tile[2][2] = {{base, base + kTcTileBytes}, {base + 2 * kTcTileBytes, base + 3 * kTcTileBytes}};
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(base + 4 * kTcTileBytes);
+  uint32_t* s_taddr = reinterpret_cast<uint32_t*>(base + 4 * kTcTileBytes + 16);
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m = tid;  // column of X
+  const int64_t r0 = (int64_t)blockIdx.x * chunk;
+  const int64_t r1 = min(n, r0 + chunk);
+  const int nst = r1 > r0 ? (int)((r1 - r0 + kTcRows - 1) / kTcRows) : 0;
+  if (tid == 0) {
+    s_fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // rows 0..63 of the Yl tiles (the Omega block of Xl) stay zero
+  if (m < 64) {
+    const uint32_t o = (uint32_t)(m >> 3) * kTcSBO + (uint32_t)(m & 7) * 16;
+    for (int kg = 0; kg < kTcRows / 4; ++kg) {
+      *reinterpret_cast<uint4*>(tile[0][1] + o + kg * kTcLBO) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(tile[1][1] + o + kg * kTcLBO) = make_uint4(0, 0, 0, 0);
+    }
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem_u32(s_taddr)),
+                 "r"(kTcCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = *s_taddr;
+  const uint32_t orow = (uint32_t)(m >> 3) * kTcSBO + (uint32_t)(m & 7) * 16;
+  bool ok = true;
+  for (int c = 0; c < nst; ++c) {
+    const int s = c & 1;
+    if (c >= 2 && !tc_wait(tc_smem_u32(&mbar[s]), (uint32_t)(((c >> 1) - 1) & 1))) {
+      ok = false;
+      atomicExch(&s_fail, 1);
+    }
+    __syncthreads();
+    if (s_fail) break;
+    const int64_t nb = r0 + (int64_t)c * kTcRows;
+    for (int kg = 0; kg < kTcRows / 4; ++kg) {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t r = nb + kg * 4 + q;
+        float x = 0.f;
+        h[q] = 0u;
+        l[q] = 0u;
+        if (r < r1) {
+          if (m < 64) {
+            if (m < M) x = __uint_as_float((uint32_t)omega[r * M + m] << 16);
+            h[q] = __float_as_uint(x);  // BF16 values are exact in TF32
+          } else if (m - 64 < M) {
+            x = Y[r * K + (m - 64)];
+            h[q] = tc_tf32(x);
+            l[q] = tc_tf32(x - __uint_as_float(h[q]));
+          }
+        }
+      }
+      *reinterpret_cast<uint4*>(tile[s][0] + orow + kg * kTcLBO) = make_uint4(h[0], h[1], h[2], h[3]);
+      if (m >= 64) *reinterpret_cast<uint4*>(tile[s][1] + orow + kg * kTcLBO) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t th = tc_smem_u32(tile[s][0]), tl = tc_smem_u32(tile[s][1]);
+#pragma unroll
+      for (int j = 0; j < kTcRows / 8; ++j) {
+        const uint32_t kofs = (uint32_t)j * 2 * kTcLBO;  // 8 TF32 along K = two core matrices
+        const uint64_t ah = tc_desc(th + kofs), bh = tc_desc(th + 8 * kTcSBO + kofs);
+        const uint64_t al = tc_desc(tl + kofs), bl = tc_desc(tl + 8 * kTcSBO + kofs);
+        tc_mma(taddr, ah, bh, (c > 0 || j > 0) ? 1u : 0u);
+        tc_mma(taddr, ah, bl, 1u);
+        tc_mma(taddr, al, bh, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       tc_smem_u32(&mbar[s]))
+                   : "memory");
+    }
+  }
+  // the last commit covers every MMA issued before it
+  if (nst > 0 && !s_fail) {
+    const int c = nst - 1;
+    if (!tc_wait(tc_smem_u32(&mbar[c & 1]), (uint32_t)((c >> 1) & 1))) {
+      ok = false;
+      atomicExch(&s_fail, 1);
+    }
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  float* out = partial + (size_t)blockIdx.x * 128 * 64 + (size_t)(warp * 32 + lane) * 64;
+  if (nst > 0 && !s_fail) {
+#pragma unroll
+    for (int cb = 0; cb < 64; cb += 16) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int q = 0; q < 16; ++q) out[cb + q] = __uint_as_float(v[q]);
+    }
+  } else {
+    for (int q = 0; q < 64; ++q) out[q] = 0.f;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcCols));
+  if (tid == 0 && s_fail) atomicExch(err, WL_ERR_TIMEOUT);
+  (void)ok;
+}
+
+#endif  // WL_TRACE_KERNELS
+
+}  // namespace wl

@@ -106,7 +106,7 @@ cudaError_t launch_sketch_rhs(const uint16_t* omega, int64_t n, int M, int K, do
 int gram_grid(int64_t n);
 // H = Omega^T Y and G = Y^T Y into out (128 x 64 doubles); partial holds G x 128 x 64 floats
 cudaError_t launch_gram(const uint16_t* omega, const float* Y, int64_t n, int M, int K, float* partial, int G,
-                        double* out, cudaStream_t s);
+                        double* out, bool tensor_cores, int* err, cudaStream_t s);
 // out[0] estimate, out[1] error estimate, out[2] status, out[8 + i] = t_i
 cudaError_t launch_nys_core(const double* gram, int M, double* out, cudaStream_t s);
 

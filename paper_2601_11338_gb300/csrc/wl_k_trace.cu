@@ -1,5 +1,9 @@
 // XNysTrace kernels: Philox sketch, right-hand side, Gram, leave-one-out core.
 #define WL_TRACE_KERNELS
+#include <string.h>
+
+#include "wl.h"
+#include "wl_gram_tc.cuh"
 #include "wl_host.h"
 #include "wl_trace.cuh"
 
@@ -46,9 +50,19 @@ int gram_grid(int64_t n) {
 }
 
 cudaError_t launch_gram(const uint16_t* omega, const float* Y, int64_t n, int M, int K, float* partial, int G,
-                        double* out, cudaStream_t s) {
+                        double* out, bool tensor_cores, int* err, cudaStream_t s) {
   const int64_t chunk = (n + G - 1) / G;
-  gram_cc<<<G, 256, 0, s>>>(omega, Y, n, M, K, chunk, partial);
+  if (tensor_cores) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    gram_tc<<<G, kTcThreads, kTcSmem, s>>>(omega, Y, n, M, K, chunk, partial, err);
+  } else {
+    gram_cc<<<G, 256, 0, s>>>(omega, Y, n, M, K, chunk, partial);
+  }
   gram_reduce<<<(2 * kMaxSketch * kMaxSketch + 255) / 256, 256, 0, s>>>(partial, G, out);
   return cudaGetLastError();
 }
@@ -66,3 +80,26 @@ cudaError_t launch_nys_core(const double* gram, int M, double* out, cudaStream_t
 }
 
 }  // namespace wl
+
+using namespace wl;
+
+extern "C" int wl_sketch_gram(const uint16_t* omega, const float* Y, int64_t n, int M, int ldy, int tensor_cores,
+                              double* out, void* stream) {
+  if (!omega || !Y || !out || n < 0 || M < 1 || M > kMaxSketch || ldy < M) return WL_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int G = gram_grid(n);
+  float* partial = nullptr;
+  int* err = nullptr;
+  cudaError_t e = cudaMalloc(&partial, sizeof(float) * (size_t)G * 2 * kMaxSketch * kMaxSketch);
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_gram(omega, Y, n, M, ldy, partial, G, out, tensor_cores != 0, err, s);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(partial);
+  cudaFree(err);
+  if (e != cudaSuccess) return report_cuda_error(e, "wl_sketch_gram");
+  return herr;
+}
+

@@ -116,6 +116,8 @@ def lib():
         for name in ("wl_mlp_features", "wl_mlp_train", "wl_mlp_loss_grad", "wl_mlp_predict", "wl_mlp_targets",
                      "wl_mlp_warm_start"):
             getattr(L, name).restype = c_int
+        L.wl_sketch_gram.argtypes = [vp, vp, i64, c_int, c_int, c_int, vp, vp]
+        L.wl_sketch_gram.restype = c_int
         L.wl_batch_destroy.argtypes = [vp]
         L.wl_batch_destroy.restype = None
         for name in ("wl_build", "wl_set_params", "wl_degrees", "wl_apply", "wl_expmv", "wl_trace",
@@ -316,4 +318,10 @@ def wl_mlp_warm_start(h, params, stats=None):
     st = stats if stats is not None else wl_stats()
     _check(lib().wl_mlp_warm_start(h.ptr, _ptr(params), ctypes.byref(st)), "wl_mlp_warm_start")
     return st
+
+
+def wl_sketch_gram(omega, Y, n, M, ldy, tensor_cores, out, stream=None):
+    """[Omega Y]^T Y (128 x 64 FP64) from device arrays; see include/wl.h."""
+    return _check(lib().wl_sketch_gram(_ptr(omega), _ptr(Y), n, M, ldy, int(tensor_cores), _ptr(out), stream),
+                  "wl_sketch_gram")
 

@@ -65,3 +65,31 @@ def test_rmat14_estimate_against_exact_trace():
     for est, err in ests:
         assert abs(est - tr) <= 6 * err + 1e-6 * tr, (est, err, tr)
         assert err < 1e-2 * tr
+
+
+@pytest.mark.parametrize("n,M,ldy", [(100_003, 64, 64), (4_097, 37, 64), (31, 64, 64), (0, 8, 8)])
+def test_sketch_gram_tensor_cores(n, M, ldy):
+    """The XNysTrace Gram [Omega Y]^T Y on the tensor cores (tcgen05, TF32
+    with Y split in two terms) and on CUDA cores both match the FP64 product
+    of the same inputs to FP32 accuracy; ragged row counts and sketch sizes."""
+    from paper_2601_11338_gb300 import wl
+    rng = np.random.default_rng(n + M)
+    om32 = rng.normal(size=(n, M)).astype(np.float32)
+    bits = (om32.view(np.uint32) >> 16).astype(np.uint16)  # BF16 patterns (truncated)
+    om = (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    Y = rng.normal(size=(n, ldy)).astype(np.float32)
+    X = np.concatenate([om, Y[:, :M].astype(np.float64)], axis=1) if n else np.zeros((0, 2 * M))
+    ref = np.zeros((128, 64))
+    if n:
+        P = X.T @ Y[:, :M].astype(np.float64)
+        ref[:M, :M] = P[:M]
+        ref[64:64 + M, :M] = P[M:]
+    dom = torch.as_tensor(bits.view(np.int16) if n else np.zeros((1, M), np.int16), device="cuda")
+    dY = torch.as_tensor(Y if n else np.zeros((1, ldy), np.float32), device="cuda")
+    scale = np.abs(ref).max() if n else 1.0
+    for tc in (0, 1):
+        out = torch.full((128, 64), float("nan"), dtype=torch.float64, device="cuda")
+        assert wl.wl_sketch_gram(dom, dY, n, M, ldy, tc, out) == wl.WL_OK
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert np.abs(got - ref).max() <= 2e-6 * scale * max(1.0, np.sqrt(n) / 100), (tc, np.abs(got - ref).max())
