@@ -7,7 +7,11 @@
 // remainder rounded to TF32), so that with Xh = [Omega Yh], Xl = [0 Yl]
 //   D = Xh^T Yh + Xh^T Yl + Xl^T Yh
 // carries FP32-level accuracy (the dropped Yl^T Yl term is 2^-22 relative);
-// Omega is exact in TF32. D (128 x 64 FP32) lives in 64 TMEM columns.
+// Omega is exact in TF32. D (128 x 64 FP32) lives in TMEM, one accumulator
+// per stage (2 x 64 columns): each stage's 12 MMAs start a fresh sum, and
+// once they have completed every thread adds its row of D into FP64
+// registers. The tensor core's FP32 accumulation thus never runs over more
+// than kTcRows nodes (over thousands it drifts by ~1e-5 relative).
 //
 // Each CTA (4 warps) owns a contiguous range of nodes and walks it in
 // stages of kTcRows nodes: all threads convert their feature column of the
@@ -26,7 +30,8 @@ constexpr int kTcThreads = 128;                           // one thread per colu
 constexpr uint32_t kTcTileBytes = 128u * kTcRows * 4u;    // one 128 x 32 TF32 tile (16 KB)
 constexpr uint32_t kTcLBO = 128;                          // core matrix to the next along K
 constexpr uint32_t kTcSBO = (kTcRows / 4) * 128;          // core matrix to the next 8-row group
-constexpr uint32_t kTcCols = 64;                          // TMEM columns (N)
+constexpr uint32_t kTcN = 64;                             // N of the MMA (TMEM columns per accumulator)
+constexpr uint32_t kTcCols = 2 * kTcN;                    // two accumulators
 constexpr size_t kTcSmem = 4 * (size_t)kTcTileBytes + 1024 + 64;
 // kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32 (2 in bits 7-9 and 10-12),
 // both K-major, N / 8 in bits 17-22, M / 16 in bits 24-28
@@ -74,6 +79,23 @@ __device__ __forceinline__ void tc_mma(uint32_t taddr, uint64_t da, uint64_t db,
       : "memory");
 }
 
+// adds this warp's 32 rows x 64 columns of the accumulator at column col0 to acc
+__device__ __forceinline__ void tc_drain(uint32_t taddr, int warp, uint32_t col0, double (&acc)[kTcN]) {
+#pragma unroll
+  for (int cb = 0; cb < (int)kTcN; cb += 16) {
+    uint32_t v[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr + ((uint32_t)(warp * 32) << 16) + col0 + (uint32_t)cb));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[cb + q] += (double)__uint_as_float(v[q]);
+  }
+}
+
 __global__ void __launch_bounds__(kTcThreads) gram_tc(const uint16_t* __restrict__ omega, const float* __restrict__ Y,
                                                       int64_t n, int M, int K, int64_t chunk,
                                                       float* __restrict__ partial, int* __restrict__ err) {
@@ -112,15 +134,21 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc(const uint16_t* __restrict
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t taddr = *s_taddr;
   const uint32_t orow = (uint32_t)(m >> 3) * kTcSBO + (uint32_t)(m & 7) * 16;
-  bool ok = true;
+  double acc[kTcN];
+#pragma unroll
+  for (int q = 0; q < (int)kTcN; ++q) acc[q] = 0.0;
   for (int c = 0; c < nst; ++c) {
     const int s = c & 1;
-    if (c >= 2 && !tc_wait(tc_smem_u32(&mbar[s]), (uint32_t)(((c >> 1) - 1) & 1))) {
-      ok = false;
-      atomicExch(&s_fail, 1);
+    if (c >= 2) {
+      // the MMAs of chunk c - 2 (this stage's tiles and accumulator) are done: drain D[s]
+      if (!tc_wait(tc_smem_u32(&mbar[s]), (uint32_t)(((c >> 1) - 1) & 1))) atomicExch(&s_fail, 1);
+      __syncthreads();
+      if (s_fail) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      tc_drain(taddr, warp, (uint32_t)s * kTcN, acc);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
     __syncthreads();
-    if (s_fail) break;
     const int64_t nb = r0 + (int64_t)c * kTcRows;
     for (int kg = 0; kg < kTcRows / 4; ++kg) {
       uint32_t h[4], l[4];
@@ -154,48 +182,34 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc(const uint16_t* __restrict
         const uint32_t kofs = (uint32_t)j * 2 * kTcLBO;  // 8 TF32 along K = two core matrices
         const uint64_t ah = tc_desc(th + kofs), bh = tc_desc(th + 8 * kTcSBO + kofs);
         const uint64_t al = tc_desc(tl + kofs), bl = tc_desc(tl + 8 * kTcSBO + kofs);
-        tc_mma(taddr, ah, bh, (c > 0 || j > 0) ? 1u : 0u);
-        tc_mma(taddr, ah, bl, 1u);
-        tc_mma(taddr, al, bh, 1u);
+        const uint32_t d = taddr + (uint32_t)s * kTcN;  // this stage's accumulator, restarted per stage
+        tc_mma(d, ah, bh, j > 0 ? 1u : 0u);
+        tc_mma(d, ah, bl, 1u);
+        tc_mma(d, al, bh, 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        tc_smem_u32(&mbar[s]))
                    : "memory");
     }
   }
-  // the last commit covers every MMA issued before it
+  // the last commit covers every MMA issued before it: drain the last one or two accumulators
   if (nst > 0 && !s_fail) {
     const int c = nst - 1;
-    if (!tc_wait(tc_smem_u32(&mbar[c & 1]), (uint32_t)((c >> 1) & 1))) {
-      ok = false;
-      atomicExch(&s_fail, 1);
-    }
+    if (!tc_wait(tc_smem_u32(&mbar[c & 1]), (uint32_t)((c >> 1) & 1))) atomicExch(&s_fail, 1);
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  float* out = partial + (size_t)blockIdx.x * 128 * 64 + (size_t)(warp * 32 + lane) * 64;
   if (nst > 0 && !s_fail) {
-#pragma unroll
-    for (int cb = 0; cb < 64; cb += 16) {
-      uint32_t v[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-          "%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int q = 0; q < 16; ++q) out[cb + q] = __uint_as_float(v[q]);
-    }
-  } else {
-    for (int q = 0; q < 64; ++q) out[q] = 0.f;
+    if (nst >= 2) tc_drain(taddr, warp, (uint32_t)((nst - 2) & 1) * kTcN, acc);
+    tc_drain(taddr, warp, (uint32_t)((nst - 1) & 1) * kTcN, acc);
   }
+  float* out = partial + (size_t)blockIdx.x * 128 * 64 + (size_t)(warp * 32 + lane) * 64;
+#pragma unroll
+  for (int q = 0; q < (int)kTcN; ++q) out[q] = s_fail ? 0.f : (float)acc[q];
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcCols));
   if (tid == 0 && s_fail) atomicExch(err, WL_ERR_TIMEOUT);
-  (void)ok;
 }
 
 #endif  // WL_TRACE_KERNELS
