@@ -142,7 +142,7 @@ struct wl_handle {
   Buf cgstate;            // CgState of the running solve
   Buf lzstate;            // LzState of the spectral-scale Lanczos
   double inner_tol = 4e-6;  // floor of the FP32 correction target of the refined form
-  bool gram_tc = false;     // XNysTrace Gram on the tensor cores (tcgen05) instead of CUDA cores
+  bool gram_tc = true;      // XNysTrace Gram on the tensor cores (tcgen05); false: CUDA cores
   CgState* cgst() { return (CgState*)cgstate.p; }
   double* h_pin = nullptr;  // pinned host scratch (4096 doubles)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
