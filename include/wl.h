@@ -41,6 +41,7 @@
 #ifndef WL_H
 #define WL_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -190,6 +191,14 @@ const char* wl_status_string(int status);
 
 /* Text of the last CUDA error seen by the calling thread (or ""). */
 const char* wl_last_error(void);
+
+/* ------------------------------------------------------------ device memory cache */
+/* The library keeps freed device and pinned host blocks for reuse by later
+ * handles (building and destroying handles then costs no cudaMalloc /
+ * cudaFree). wl_pool_release returns every cached block to the driver;
+ * wl_pool_cached_bytes reports how much is held. Live handles keep theirs. */
+void wl_pool_release(void);
+size_t wl_pool_cached_bytes(void);
 
 /* ------------------------------------------------------------ no-allocation variant */
 /* Walk degrees D_f = phi 1 for the resolvent (the computation of wl_degrees

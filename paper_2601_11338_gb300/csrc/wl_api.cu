@@ -48,13 +48,33 @@ int set_cuda_error(cudaError_t e, const char* where) {
     if (s__ != WL_OK) return s__; \
   } while (0)
 
+// Blocks released while a call is running may still be read by work queued
+// on the handle's stream: they are kept on the handle until it is destroyed
+// (after its stream has been synchronised) instead of going back to the
+// allocator's cache, where another stream could pick them up.
+thread_local std::vector<void*>* t_retired = nullptr;
+
+struct CallScope {
+  std::vector<void*>* prev;
+  explicit CallScope(std::vector<void*>* r) : prev(t_retired) { t_retired = r; }
+  ~CallScope() { t_retired = prev; }
+};
+
+void retire(void* p) {
+  if (!p) return;
+  if (t_retired)
+    t_retired->push_back(p);
+  else
+    pool_free(p);
+}
+
 int ensure(Buf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return WL_OK;
-  if (b.p) cudaFree(b.p);
+  retire(b.p);
   b.p = nullptr;
   b.bytes = 0;
-  cudaError_t e = cudaMalloc(&b.p, bytes);
+  cudaError_t e = pool_malloc(&b.p, bytes);
   if (e != cudaSuccess) {
     b.p = nullptr;
     return set_cuda_error(e, "cudaMalloc");
@@ -64,7 +84,7 @@ int ensure(Buf& b, size_t bytes) {
 }
 
 void release(Buf& b) {
-  if (b.p) cudaFree(b.p);
+  retire(b.p);
   b.p = nullptr;
   b.bytes = 0;
 }
@@ -139,6 +159,7 @@ struct wl_handle {
   int32_t* iperm = nullptr;
   Buf hubs;               // rows with more than kHubDeg entries (internal order)
   int nhub = 0;
+  std::vector<void*> retired;  // blocks released during calls, returned to the allocator at destroy
   Buf cgstate;            // CgState of the running solve
   Buf lzstate;            // LzState of the spectral-scale Lanczos
   double inner_tol = 4e-6;  // floor of the FP32 correction target of the refined form
@@ -210,9 +231,9 @@ int get_part(wl_handle* h, int G, int Tw, int Tc, PartDev** out, int K = 16, int
   p.Tc = Tc;
   p.row_bytes = 10 * K * vbytes;
   p.entry_bytes = 4 + K * vbytes;
-  WL_CU(cudaMalloc(&p.rb, sizeof(int32_t) * (G + 1)));
-  WL_CU(cudaMalloc(&p.seg, sizeof(int32_t) * 4 * G));
-  WL_CU(cudaMalloc(&p.meta, sizeof(int4) * std::max<int64_t>(h->n, 1)));
+  WL_CU(pool_malloc((void**)&p.rb, sizeof(int32_t) * (G + 1)));
+  WL_CU(pool_malloc((void**)&p.seg, sizeof(int32_t) * 4 * G));
+  WL_CU(pool_malloc((void**)&p.meta, sizeof(int4) * std::max<int64_t>(h->n, 1)));
   WL_TRY(ensure(h->ptmp, sizeof(int64_t) * (2 * (size_t)(h->n + 1) + (size_t)h->n / 1024 + 8)));
   counted(h, 4);
   WL_CU(launch_partition_weighted(h->g, p, (int64_t*)h->ptmp.p, S(h)));
@@ -683,18 +704,23 @@ int copy_out_vec(wl_handle* h, const double* src, double* dst) {
 
 void free_handle(wl_handle* h) {
   if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  (void)cudaGetLastError();
+  CallScope none(nullptr);  // everything below goes straight back to the allocator
   for (auto& kv : h->parts) {
-    cudaFree(kv.second.rb);
-    cudaFree(kv.second.seg);
-    cudaFree(kv.second.meta);
+    pool_free(kv.second.rb);
+    pool_free(kv.second.seg);
+    pool_free(kv.second.meta);
   }
   Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
                  &h->r32, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
                  &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->lan, &h->omega, &h->gram,
                  &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b, &h->hubs, &h->cgstate, &h->lzstate};
   for (Buf* b : bufs) release(*b);
-  if (h->bar) cudaFree(h->bar);
-  if (h->h_pin) cudaFreeHost(h->h_pin);
+  for (void* p : h->retired) pool_free(p);
+  h->retired.clear();
+  if (h->bar) pool_free(h->bar);
+  if (h->h_pin) pool_free_host(h->h_pin);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -750,6 +776,7 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
   if (p->f == WL_F_EXP) return WL_ERR_UNSUPPORTED;  // exponential variant: not provided by this build
 
   wl_handle* h = new wl_handle();
+  CallScope cs__(&h->retired);
   h->n = A->n;
   h->nnz = A->nnz;
   h->variant = v;
@@ -768,9 +795,10 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
   };
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess)
     return fail(set_cuda_error(cudaGetLastError(), "cudaEventCreate"));
-  if (cudaMallocHost(&h->h_pin, 4096 * sizeof(double)) != cudaSuccess)
+  if (pool_malloc_host((void**)&h->h_pin, 4096 * sizeof(double)) != cudaSuccess)
     return fail(set_cuda_error(cudaGetLastError(), "cudaMallocHost"));
-  if (cudaMalloc(&h->bar, sizeof(GridBar)) != cudaSuccess) return fail(set_cuda_error(cudaGetLastError(), "cudaMalloc"));
+  if (pool_malloc((void**)&h->bar, sizeof(GridBar)) != cudaSuccess)
+    return fail(set_cuda_error(cudaGetLastError(), "cudaMalloc"));
   if ((rc = ensure(h->small, 8192)) != WL_OK) return fail(rc);
   if ((rc = ensure(h->csr_rp, sizeof(int32_t) * (A->n + 1))) != WL_OK) return fail(rc);
   if ((rc = ensure(h->csr_col, sizeof(int32_t) * std::max<int64_t>(A->nnz, 1))) != WL_OK) return fail(rc);
@@ -911,6 +939,7 @@ int wl_get_info(const wl_handle* h, wl_stats* info) {
 }
 
 int wl_set_warm_start(wl_handle* h, const double* x0) {
+  CallScope cs__(h ? &h->retired : nullptr);
   if (!h) return WL_ERR_INVALID_ARG;
   if (!x0) {
     h->have_warm = false;
@@ -936,6 +965,7 @@ int wl_set_warm_start(wl_handle* h, const double* x0) {
 // Node features of the warm-start network and the analytic guess x_an,
 // in the caller's node order.
 int wl_mlp_features(wl_handle* h, float* feats, double* xan, wl_stats* st) {
+  CallScope cs__(h ? &h->retired : nullptr);
   if (st) memset(st, 0, sizeof(*st));
   if (!h || (!feats && !xan)) return WL_ERR_INVALID_ARG;
   if (h->prm.f != WL_F_RESOLVENT) return WL_ERR_UNSUPPORTED;
@@ -968,6 +998,7 @@ int wl_mlp_features(wl_handle* h, float* feats, double* xan, wl_stats* st) {
 // Warm start of the walk-degree solve from the network: features, x_an and
 // x0 = x_an * exp(y) on the device, kept as the handle's starting guess.
 int wl_mlp_warm_start(wl_handle* h, const float* params, wl_stats* st) {
+  CallScope cs__(h ? &h->retired : nullptr);
   if (st) memset(st, 0, sizeof(*st));
   if (!h || !params) return WL_ERR_INVALID_ARG;
   if (h->prm.f != WL_F_RESOLVENT) return WL_ERR_UNSUPPORTED;
@@ -998,6 +1029,7 @@ int wl_mlp_warm_start(wl_handle* h, const float* params, wl_stats* st) {
 }
 
 int wl_degrees(wl_handle* h, double* Df, wl_stats* st) {
+  CallScope cs__(h ? &h->retired : nullptr);
   if (!h || (!Df && h->n > 0)) return WL_ERR_INVALID_ARG;
   SolveInfo info;
   begin_timer(h);
@@ -1014,6 +1046,7 @@ int wl_degrees(wl_handle* h, double* Df, wl_stats* st) {
 }
 
 int wl_apply(wl_handle* h, const double* V, int64_t ldv, int k, double* W, int64_t ldw, wl_stats* st) {
+  CallScope cs__(h ? &h->retired : nullptr);
   if (!h || k < 0 || (k > 0 && h->n > 0 && (!V || !W || ldv < k || ldw < k))) return WL_ERR_INVALID_ARG;
   SolveInfo info;
   begin_timer(h);
@@ -1076,6 +1109,7 @@ int wl_apply(wl_handle* h, const double* V, int64_t ldv, int k, double* W, int64
 
 int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* taus, int ntau, double* U,
              int64_t ldo, wl_stats* st) {
+  CallScope cs__(h ? &h->retired : nullptr);
   if (!h || k < 0 || ntau < 0 || ntau > kMaxTau) return WL_ERR_INVALID_ARG;
   if (k > 0 && h->n > 0 && (!U0 || !U || !taus || ldu < k || ldo < k)) return WL_ERR_INVALID_ARG;
   for (int t = 0; t < ntau; ++t)
@@ -1241,6 +1275,7 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
 }
 
 int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, uint16_t* omega_out, wl_stats* st) {
+  CallScope cs__(h ? &h->retired : nullptr);
   if (!h || !est || !err_est || M < 2 || M > kMaxSketch) return WL_ERR_INVALID_ARG;
   if (h->prm.f != WL_F_RESOLVENT) return WL_ERR_UNSUPPORTED;
   SolveInfo info;

@@ -45,19 +45,20 @@ struct DBuf {
   size_t bytes = 0;
 };
 
+// growth and release happen only between runs (every run ends synchronised)
 cudaError_t dalloc(DBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return cudaSuccess;
-  if (b.p) cudaFree(b.p);
+  pool_free(b.p);
   b.p = nullptr;
   b.bytes = 0;
-  cudaError_t e = cudaMalloc(&b.p, bytes);
+  cudaError_t e = pool_malloc(&b.p, bytes);
   if (e == cudaSuccess) b.bytes = bytes;
   return e;
 }
 
 void dfree(DBuf& b) {
-  if (b.p) cudaFree(b.p);
+  pool_free(b.p);
   b.p = nullptr;
   b.bytes = 0;
 }
@@ -507,6 +508,8 @@ void free_exec(Exec& x) {
 
 void free_batch(wl_batch* b) {
   if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  (void)cudaGetLastError();
   for (auto& kv : b->execs) free_exec(kv.second);
   for (auto& t : b->tilesets) {
     dfree(t.tiles);
@@ -521,7 +524,7 @@ void free_batch(wl_batch* b) {
   for (DBuf* d : bufs) dfree(*d);
   for (cudaStream_t& c : b->cap)
     if (c) cudaStreamDestroy(c);
-  if (b->h_pin) cudaFreeHost(b->h_pin);
+  if (b->h_pin) pool_free_host(b->h_pin);
   delete b;
 }
 
@@ -693,7 +696,7 @@ int wl_batch_build(const wl_csr* graphs, int ngraph, const double* mus, int nmu,
   for (int i = 0; i < 3; ++i)
     if (cudaStreamCreateWithFlags(&b->cap[i], cudaStreamNonBlocking) != cudaSuccess)
       return fail(cuerr(cudaGetLastError(), "cudaStreamCreate"));
-  if (cudaMallocHost(&b->h_pin, 64 * sizeof(int)) != cudaSuccess)
+  if (pool_malloc_host((void**)&b->h_pin, 64 * sizeof(int)) != cudaSuccess)
     return fail(cuerr(cudaGetLastError(), "cudaMallocHost"));
   cudaEventRecord(t1, b->stream);
   cudaEventSynchronize(t1);

@@ -128,6 +128,12 @@ inline int coop_grid(const void* fn, int cap_per_sm) {
   return nb * sms;
 }
 
+// ---- wl_pool.cu: caching allocator (free only blocks no queued work can touch)
+cudaError_t pool_malloc(void** out, size_t bytes);
+void pool_free(void* p);
+cudaError_t pool_malloc_host(void** out, size_t bytes);
+void pool_free_host(void* p);
+
 // ---- wl_mlp.cu
 // node features (n x 4, FP32, row perm[i] for internal row i, perm NULL: i)
 // and the analytic guess x_an (n, FP64); perm_key: the caller's index of

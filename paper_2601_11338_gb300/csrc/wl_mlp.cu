@@ -81,7 +81,8 @@ __global__ void k_feat_outdeg(const int32_t* __restrict__ rp, const int32_t* __r
 
 // oriented lists (ascending index order kept by an ordered warp compaction)
 __global__ void k_feat_orient(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t n,
-                              const int64_t* __restrict__ orp, int32_t* __restrict__ ocol) {
+                              const int64_t* __restrict__ orp, const int32_t* __restrict__ key,
+                              int32_t* __restrict__ ocol, int32_t* __restrict__ okey) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -97,18 +98,33 @@ __global__ void k_feat_orient(const int32_t* __restrict__ rp, const int32_t* __r
         keep = ranks_above(rp[j + 1] - rp[j], j, di, (int)i);
       }
       const unsigned m = __ballot_sync(0xffffffffu, keep);
-      if (keep) ocol[o + __popc(m & ((1u << lane) - 1u))] = j;
+      if (keep) {
+        const int64_t q = o + __popc(m & ((1u << lane) - 1u));
+        ocol[q] = j;
+        okey[q] = key ? key[j] : j;
+      }
       o += __popc(m);
     }
   }
 }
 
-// every triangle once: for i, each oriented neighbour j (one per lane) and
-// each w in N+(i) and N+(j) (merge of two lists ascending in key) adds one
-// to t_i, t_j and t_w. The key is the caller's node index (key[j], NULL:
-// j): relabelled rows keep their columns in the caller's order.
-__global__ void k_feat_triangles(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol, int64_t n,
-                                 const int32_t* __restrict__ key, unsigned long long* __restrict__ t) {
+// position in okey[lo, end) (ascending) holding k, or -1
+__device__ __forceinline__ int64_t find_key(const int32_t* __restrict__ okey, int64_t lo, int64_t end, int k) {
+  int64_t hi = end;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (okey[mid] < k) lo = mid + 1; else hi = mid;
+  }
+  return (lo < end && okey[lo] == k) ? lo : -1;
+}
+
+// Every triangle once: for i, each oriented neighbour j (one per lane) and
+// each w in N+(i) and N+(j) adds one to t_i, t_j and t_w. The lists are
+// ascending in key (the caller's node index, which is the column order of
+// every row); two lists of similar length are merged, a much shorter one is
+// looked up element by element in the longer one by binary search.
+__global__ void k_feat_triangles(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                 const int32_t* __restrict__ okey, int64_t n, unsigned long long* __restrict__ t) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -117,21 +133,39 @@ __global__ void k_feat_triangles(const int64_t* __restrict__ orp, const int32_t*
     unsigned long long ti = 0;
     for (int64_t e = ib + lane; e < ie; e += 32) {
       const int j = ocol[e];
-      int64_t a = ib, b = orp[j];
-      const int64_t be = orp[j + 1];
+      const int64_t jb = orp[j], je = orp[j + 1];
+      const int64_t la = ie - ib, lb = je - jb;
       unsigned long long tj = 0;
-      while (a < ie && b < be) {
-        const int x = ocol[a], y = ocol[b];
-        const int kx = key ? key[x] : x, ky = key ? key[y] : y;
-        if (kx == ky) {
-          ++tj;
-          atomicAdd(t + x, 1ull);
-          ++a;
-          ++b;
-        } else if (kx < ky) {
-          ++a;
-        } else {
-          ++b;
+      if (la > 16 * lb) {  // look up N+(j) in N+(i)
+        for (int64_t b = jb; b < je; ++b) {
+          const int64_t pos = find_key(okey, ib, ie, okey[b]);
+          if (pos >= 0) {
+            ++tj;
+            atomicAdd(t + ocol[b], 1ull);
+          }
+        }
+      } else if (lb > 16 * la) {  // look up N+(i) in N+(j)
+        for (int64_t a = ib; a < ie; ++a) {
+          const int64_t pos = find_key(okey, jb, je, okey[a]);
+          if (pos >= 0) {
+            ++tj;
+            atomicAdd(t + ocol[a], 1ull);
+          }
+        }
+      } else {
+        int64_t a = ib, b = jb;
+        while (a < ie && b < je) {
+          const int kx = okey[a], ky = okey[b];
+          if (kx == ky) {
+            ++tj;
+            atomicAdd(t + ocol[a], 1ull);
+            ++a;
+            ++b;
+          } else if (kx < ky) {
+            ++a;
+          } else {
+            ++b;
+          }
         }
       }
       if (tj) atomicAdd(t + j, tj);
@@ -400,23 +434,25 @@ cudaError_t launch_features(const int32_t* rp, const int32_t* col, int64_t n, in
   int64_t* orp = outdeg + n + 1;
   int64_t* sc = orp + n + 1;
   int32_t* ocol = (int32_t*)(sc + n / 1024 + 64);
+  int32_t* okey = ocol + nnz / 2 + 1;
   const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n * 32 + 255) / 256, 152 * 64));
   const unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
   k_feat_ad<<<gw, 256, 0, s>>>(rp, col, n, ad);
-  cudaError_t e = cudaMemsetAsync(t, 0, sizeof(unsigned long long) * n, s);
-  if (e != cudaSuccess) return e;
-  k_feat_outdeg<<<gw, 256, 0, s>>>(rp, col, n, outdeg);
-  e = launch_scan(outdeg, n, orp, sc, s);  // orp[0..n]: exclusive prefix, orp[n] = total
-  if (e != cudaSuccess) return e;
-  k_feat_orient<<<gw, 256, 0, s>>>(rp, col, n, orp, ocol);
-  k_feat_triangles<<<gw, 256, 0, s>>>(orp, ocol, n, perm_key, t);
+  if (F) {  // triangles only for the network's inputs (x_an needs d and A d alone)
+    cudaError_t e = cudaMemsetAsync(t, 0, sizeof(unsigned long long) * n, s);
+    if (e != cudaSuccess) return e;
+    k_feat_outdeg<<<gw, 256, 0, s>>>(rp, col, n, outdeg);
+    e = launch_scan(outdeg, n, orp, sc, s);  // orp[0..n]: exclusive prefix, orp[n] = total
+    if (e != cudaSuccess) return e;
+    k_feat_orient<<<gw, 256, 0, s>>>(rp, col, n, orp, perm_key, ocol, okey);
+    k_feat_triangles<<<gw, 256, 0, s>>>(orp, ocol, okey, n, t);
+  }
   k_feat_out<<<g1, 256, 0, s>>>(rp, ad, t, n, alpha, mu, perm, F, xan);
-  (void)nnz;
   return cudaGetLastError();
 }
 
 size_t features_tmp_bytes(int64_t n, int64_t nnz) {
-  return (size_t)n * 8 * 2 + (size_t)(n + 1) * 8 * 2 + (size_t)(n / 1024 + 64) * 8 + (size_t)(nnz / 2 + 1) * 4 + 256;
+  return (size_t)n * 8 * 2 + (size_t)(n + 1) * 8 * 2 + (size_t)(n / 1024 + 64) * 8 + (size_t)(nnz / 2 + 1) * 8 + 256;
 }
 
 cudaError_t launch_mlp_predict(const float* P, const float* F, int64_t rows, const double* xan, double* out,
@@ -441,12 +477,17 @@ int mlp_err(cudaError_t e, const char* where) { return report_cuda_error(e, wher
     if (e__ != cudaSuccess) return mlp_err(e__, #call);   \
   } while (0)
 
+// staging and scratch of one synchronous call: released after the call's
+// stream has been synchronised (or, on an early error, after a device sync)
 struct DevBuf {
   void* p = nullptr;
   ~DevBuf() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaDeviceSynchronize();
+      pool_free(p);
+    }
   }
-  cudaError_t alloc(size_t b) { return cudaMalloc(&p, b ? b : 16); }
+  cudaError_t alloc(size_t b) { return pool_malloc(&p, b ? b : 16); }
 };
 
 bool dev_ptr(const void* p) {

@@ -118,6 +118,10 @@ def lib():
             getattr(L, name).restype = c_int
         L.wl_sketch_gram.argtypes = [vp, vp, i64, c_int, c_int, c_int, vp, vp]
         L.wl_sketch_gram.restype = c_int
+        L.wl_pool_release.argtypes = []
+        L.wl_pool_release.restype = None
+        L.wl_pool_cached_bytes.argtypes = []
+        L.wl_pool_cached_bytes.restype = ctypes.c_size_t
         L.wl_batch_destroy.argtypes = [vp]
         L.wl_batch_destroy.restype = None
         for name in ("wl_build", "wl_set_params", "wl_degrees", "wl_apply", "wl_expmv", "wl_trace",
@@ -324,4 +328,12 @@ def wl_sketch_gram(omega, Y, n, M, ldy, tensor_cores, out, stream=None):
     """[Omega Y]^T Y (128 x 64 FP64) from device arrays; see include/wl.h."""
     return _check(lib().wl_sketch_gram(_ptr(omega), _ptr(Y), n, M, ldy, int(tensor_cores), _ptr(out), stream),
                   "wl_sketch_gram")
+
+
+def wl_pool_release():
+    lib().wl_pool_release()
+
+
+def wl_pool_cached_bytes():
+    return int(lib().wl_pool_cached_bytes())
 
