@@ -101,35 +101,19 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) lz_s(LzArgs a) {
     }
     if (tid == 0) fin(row, end - beg, s_red[0]);
   } else {
-    // four lanes per row (16 gathers in flight per row), rows taken a warp
-    // (8 rows) at a time so that every lane reaches the group shuffles
-    constexpr int kL = 4;
     const int64_t nblk = (int64_t)gridDim.x - a.g.nhub;
-    const int64_t gwarp = ((int64_t)blockIdx.x - a.g.nhub) * (kPhaseBlock / 32) + (tid >> 5);
-    const int64_t nwarps = nblk * (kPhaseBlock / 32);
-    const int lane = tid & 31, sub = lane & (kL - 1);
-    for (int64_t wrow = gwarp * (32 / kL); wrow < a.g.n; wrow += nwarps * (32 / kL)) {
-      const int64_t row = wrow + (lane / kL);
-      int beg = 0, end = 0;
-      if (row < a.g.n) {
-        beg = a.g.row_ptr[row];
-        end = a.g.row_ptr[row + 1];
-        if (end - beg > kHubDeg) end = beg;  // gathered by a hub CTA
-      }
+    for (int64_t row = ((int64_t)blockIdx.x - a.g.nhub) * kPhaseBlock + tid; row < a.g.n; row += nblk * kPhaseBlock) {
+      const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
+      if (end - beg > kHubDeg) continue;
       double s = 0.0;
-      int e = beg + sub;
-      for (; e + 3 * kL < end; e += 4 * kL) {
-        const int j0 = __ldg(a.g.col + e), j1 = __ldg(a.g.col + e + kL);
-        const int j2 = __ldg(a.g.col + e + 2 * kL), j3 = __ldg(a.g.col + e + 3 * kL);
+      int e = beg;
+      for (; e + 3 < end; e += 4) {
+        const int j0 = __ldg(a.g.col + e), j1 = __ldg(a.g.col + e + 1);
+        const int j2 = __ldg(a.g.col + e + 2), j3 = __ldg(a.g.col + e + 3);
         s += (Wp[j0] + Wp[j1]) + (Wp[j2] + Wp[j3]);
       }
-      for (; e < end; e += kL) s += Wp[__ldg(a.g.col + e)];
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      if (sub == 0 && row < a.g.n) {
-        const int d = a.g.row_ptr[row + 1] - a.g.row_ptr[row];
-        if (d <= kHubDeg) fin(row, d, s);
-      }
+      for (; e < end; ++e) s += Wp[__ldg(a.g.col + e)];
+      fin(row, end - beg, s);
     }
   }
   if (!block_partials_last<double, 1>(acc, a.part, &st->ticket)) return;
