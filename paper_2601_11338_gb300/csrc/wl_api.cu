@@ -139,6 +139,7 @@ struct wl_handle {
   Buf x, r, p, q;         // CG vectors (FP64 or FP32), n * 64 doubles each at most
   Buf x64, b64, r64;      // refinement
   Buf d32, r32;
+  Buf xh, xl;             // refined form: the iterate as two FP32 terms (x = xh + xl)
   Buf part;               // partial sums
   Buf small;              // per-column scalars
   Buf Df;
@@ -388,10 +389,20 @@ int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, b
   WL_TRY(ensure(h->q, nk * 4));
   WL_TRY(ensure(h->d32, nk * 4));
   WL_TRY(ensure(h->r32, nk * 4));
-  WL_TRY(ensure(h->r64, nk * 8));
+  WL_TRY(ensure(h->xh, nk * 4));
+  WL_TRY(ensure(h->xl, nk * 4));
   WL_TRY(ensure_phase_buffers(h, std::max(grid_s, grid_r)));
   CgState* st = h->cgst();
-  if (x_is_zero) WL_CU(cudaMemsetAsync(x, 0, nk * 8, S(h)));
+  // the iterate lives as two FP32 terms during the refinement (x = xh + xl)
+  float* xh = (float*)h->xh.p;
+  float* xl = (float*)h->xl.p;
+  if (x_is_zero) {
+    WL_CU(cudaMemsetAsync(xh, 0, nk * 4, S(h)));
+    WL_CU(cudaMemsetAsync(xl, 0, nk * 4, S(h)));
+  } else {
+    counted(h);
+    WL_CU(launch_split_x(x, (int64_t)nk, xh, xl, false, nullptr, S(h)));
+  }
   WL_CU(cudaMemsetAsync(h->d32.p, 0, nk * 4, S(h)));
   double* hp = h->h_pin;
   // FP32 correction target: two corrections reach tol when tol >= (inner)^2
@@ -399,8 +410,8 @@ int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, b
   const int max_ref = 12;
   for (int ref = 0;; ++ref) {
     WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
-    ResPhaseArgs ra{phase_graph(h), x, (float*)h->d32.p, b, (double*)h->r64.p, (float*)h->r32.p,
-                    h->ca, h->cA, h->cD, (double*)h->part.p, st};
+    ResPhaseArgs ra{phase_graph(h), x, (float*)h->d32.p, b, nullptr, (float*)h->r32.p,
+                    h->ca, h->cA, h->cD, (double*)h->part.p, st, xh, xl};
     const int mode = ref > 0 ? 1 : (x_is_zero ? -1 : 0);  // -1: x = 0, no SpMM needed
     const int pi = prof_begin(h, kCatRes);
     counted(h, ref > 0 ? 2 : 1);
@@ -416,17 +427,14 @@ int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, b
     int skip[64];
     for (int c = 0; c < K; ++c) {
       const double rr = hp[c], bb = hp[64 + c];
-      if (!std::isfinite(rr)) {
-        info.status = WL_ERR_NONFINITE;
-        return WL_OK;
-      }
+      if (!std::isfinite(rr)) info.status = WL_ERR_NONFINITE;
       const double rel = bb > 0 ? std::sqrt(rr / bb) : 0.0;
       mx = std::max(mx, rel);
       skip[c] = (rel <= tol) ? 1 : 0;
       if (!skip[c]) all = false;
     }
     info.max_rel = std::max(info.max_rel, mx);
-    if (all) break;
+    if (all || info.status == WL_ERR_NONFINITE) break;
     if (ref >= max_ref) {
       if (info.status == WL_OK) info.status = WL_ERR_NO_CONVERGENCE;
       break;
@@ -443,13 +451,15 @@ int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, b
     for (int c = 0; c < K; ++c) (void)c;
     if (inner.status == WL_ERR_NOT_SPD || inner.status == WL_ERR_NONFINITE) {
       info.status = inner.status;
-      return WL_OK;
+      break;
     }
     info.iters += inner.iters;
     info.cg_iters += inner.cg_iters;
     info.nnz_rhs += inner.nnz_rhs;
     info.bytes += inner.bytes;
   }
+  counted(h);
+  WL_CU(launch_split_x(nullptr, (int64_t)nk, xh, xl, true, x, S(h)));
   return WL_OK;
 }
 
@@ -713,7 +723,7 @@ void free_handle(wl_handle* h) {
     pool_free(kv.second.meta);
   }
   Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
-                 &h->r32, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
+                 &h->r32, &h->xh, &h->xl, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
                  &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->lan, &h->omega, &h->gram,
                  &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b, &h->hubs, &h->cgstate, &h->lzstate};
   for (Buf* b : bufs) release(*b);

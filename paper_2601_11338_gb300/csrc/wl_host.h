@@ -72,6 +72,9 @@ cudaError_t launch_cg_phases_f64(int K, const PhaseArgs<double>& a, int grid_s, 
 // FP64 residual r = b - M x (after x += d when accumulate > 0; accumulate < 0: x = 0, so r = b),
 // norms into st->gamma / st->b2
 cudaError_t launch_res_phases(int K, const ResPhaseArgs& a, int grid, int accumulate, cudaStream_t s);
+// x (n K doubles) -> (xh, xl) FP32 terms, or (join) xh + xl -> xout
+cudaError_t launch_split_x(const double* x, int64_t total, float* xh, float* xl, bool join, double* xout,
+                           cudaStream_t s);
 int phase_blocks_f32(int K);  // resident CTAs of the S kernel (all SMs)
 int phase_blocks_f64(int K);
 int res_blocks(int K);

@@ -41,11 +41,38 @@ static cudaError_t run_res(const ResPhaseArgs& a, int grid, int accumulate, cuda
     res_zero_phase<K><<<grid, kPhaseBlock, 0, s>>>(a);
     return cudaGetLastError();
   }
-  if (accumulate) {
-    const int64_t total = a.g.n * K;
-    res_acc_phase<K><<<grid, kPhaseBlock, 0, s>>>(a.x, a.d, total);
+  const int64_t total = a.g.n * K;
+  if (a.xh) {  // iterate held as two FP32 terms
+    if (accumulate) res_acc_split<K><<<grid, kPhaseBlock, 0, s>>>(a.xh, a.xl, a.d, total);
+    res_phase_split<K><<<grid, kPhaseBlock, 0, s>>>(a);
+    return cudaGetLastError();
   }
+  if (accumulate) res_acc_phase<K><<<grid, kPhaseBlock, 0, s>>>(a.x, a.d, total);
   res_phase<K><<<grid, kPhaseBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// x64 <-> (xh, xl)
+__global__ void __launch_bounds__(kPhaseBlock) split_x(const double* x, int64_t total, float* xh, float* xl) {
+  for (int64_t e = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; e < total; e += (int64_t)gridDim.x * kPhaseBlock) {
+    const float h = (float)x[e];
+    xh[e] = h;
+    xl[e] = (float)(x[e] - (double)h);
+  }
+}
+
+__global__ void __launch_bounds__(kPhaseBlock) join_x(const float* xh, const float* xl, int64_t total, double* x) {
+  for (int64_t e = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; e < total; e += (int64_t)gridDim.x * kPhaseBlock)
+    x[e] = (double)xh[e] + (double)xl[e];
+}
+
+cudaError_t launch_split_x(const double* x, int64_t total, float* xh, float* xl, bool join, double* xout,
+                           cudaStream_t s) {
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + kPhaseBlock - 1) / kPhaseBlock, 152 * 16));
+  if (join)
+    join_x<<<g, kPhaseBlock, 0, s>>>(xh, xl, total, xout);
+  else
+    split_x<<<g, kPhaseBlock, 0, s>>>(x, total, xh, xl);
   return cudaGetLastError();
 }
 
