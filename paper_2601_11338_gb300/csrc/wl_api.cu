@@ -138,8 +138,10 @@ struct wl_handle {
   Buf csr_rp, csr_col;
   Buf x, r, p, q;         // CG vectors (FP64 or FP32), n * 64 doubles each at most
   Buf x64, b64, r64;      // refinement
-  Buf d32, r32;
+  Buf d32, d32b, r32;     // refined form: FP32 corrections (two, alternating) and inner right-hand side
   Buf xh, xl;             // refined form: the iterate as two FP32 terms (x = xh + xl)
+  Buf bh, bl, rh, rl;     // refined form: right-hand side and residual as two FP32 terms
+  Buf dfdf, ydf;          // refined form: D_f and the Lanczos coefficients y(tau) as two FP32 terms
   Buf part;               // partial sums
   Buf small;              // per-column scalars
   Buf Df;
@@ -380,48 +382,64 @@ int solve_fp64(wl_handle* h, const double* b, double* x, int K, double tol, bool
   return WL_OK;
 }
 
-// Refined solve: FP64 iterate and residual, FP32 inner CG corrections.
-int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, bool x_is_zero, SolveInfo& info) {
+// Refined solve of M X = B for K columns with B, the residual and the
+// iterate held in double-float form (two FP32 arrays each) and FP32 inner
+// CG corrections M d = fl32(r); the residual is carried by r <- r - M d in
+// double-float arithmetic (one gather of the 4-byte correction per step).
+// (bh, bl): right-hand side; |B|^2 per column in bn2 (device, K doubles).
+// On return (xh, xl) holds X. x0 (FP64, or NULL for X0 = 0) is a warm start.
+int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const double* bn2, float* xh, float* xl,
+                     const double* x0, int K, double tol, SolveInfo& info) {
   const int grid_u = phase_blocks_f32(K), grid_s = grid_u + h->nhub;
-  const int grid_r = res_blocks(K) + h->nhub;
+  const int grid_r = df_res_blocks(K) + h->nhub;
   const size_t nk = (size_t)h->n * K;
   WL_TRY(ensure(h->p, nk * 4));
   WL_TRY(ensure(h->q, nk * 4));
   WL_TRY(ensure(h->d32, nk * 4));
+  WL_TRY(ensure(h->d32b, nk * 4));
   WL_TRY(ensure(h->r32, nk * 4));
-  WL_TRY(ensure(h->xh, nk * 4));
-  WL_TRY(ensure(h->xl, nk * 4));
+  WL_TRY(ensure(h->rh, nk * 4));
+  WL_TRY(ensure(h->rl, nk * 4));
   WL_TRY(ensure_phase_buffers(h, std::max(grid_s, grid_r)));
   CgState* st = h->cgst();
-  // the iterate lives as two FP32 terms during the refinement (x = xh + xl)
-  float* xh = (float*)h->xh.p;
-  float* xl = (float*)h->xl.p;
-  if (x_is_zero) {
-    WL_CU(cudaMemsetAsync(xh, 0, nk * 4, S(h)));
-    WL_CU(cudaMemsetAsync(xl, 0, nk * 4, S(h)));
-  } else {
-    counted(h);
-    WL_CU(launch_split_x(x, (int64_t)nk, xh, xl, false, nullptr, S(h)));
-  }
-  WL_CU(cudaMemsetAsync(h->d32.p, 0, nk * 4, S(h)));
+  float* rh = (float*)h->rh.p;
+  float* rl = (float*)h->rl.p;
+  float* dcur = (float*)h->d32.p;
+  float* dnext = (float*)h->d32b.p;
+  const df ca = df_from_double(h->ca), cA = df_from_double(h->cA), cD = df_from_double(h->cD);
   double* hp = h->h_pin;
+  // current residual: B itself while X = 0
+  const float* rch = bh;
+  const float* rcl = bl;
+  bool x_zero = (x0 == nullptr);
+  WL_CU(cudaMemsetAsync(dcur, 0, nk * 4, S(h)));
+  WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
+  if (x_zero) {
+    counted(h);
+    WL_CU(cudaMemcpyAsync(h->r32.p, bh, nk * 4, cudaMemcpyDeviceToDevice, S(h)));
+    WL_CU(cudaMemcpyAsync(st->gamma, bn2, K * 8, cudaMemcpyDeviceToDevice, S(h)));
+  } else {
+    // r = B - M x0 (x0 split into two FP32 terms and gathered whole)
+    counted(h, 2);
+    WL_CU(launch_split_x(x0, (int64_t)nk, xh, xl, false, nullptr, S(h)));
+    DfResArgs ra{phase_graph(h), xh, xl, bh, bl, rh, rl, (float*)h->r32.p, nullptr, nullptr, nullptr,
+                 ca, cA, cD, (double*)h->part.p, st, 0};
+    const int pi = prof_begin(h, kCatRes);
+    WL_CU(launch_df_res(K, ra, grid_r, true, S(h)));
+    prof_end(h, pi);
+    info.nnz_rhs += (double)h->nnz * K;
+    rch = rh;
+    rcl = rl;
+  }
   // FP32 correction target: two corrections reach tol when tol >= (inner)^2
   const double inner_tol = std::min(1e-3, std::max(h->inner_tol, 0.5 * std::sqrt(tol)));
   const int max_ref = 12;
+  int ndf = 0;
   for (int ref = 0;; ++ref) {
-    WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
-    ResPhaseArgs ra{phase_graph(h), x, (float*)h->d32.p, b, nullptr, (float*)h->r32.p,
-                    h->ca, h->cA, h->cD, (double*)h->part.p, st, xh, xl};
-    const int mode = ref > 0 ? 1 : (x_is_zero ? -1 : 0);  // -1: x = 0, no SpMM needed
-    const int pi = prof_begin(h, kCatRes);
-    counted(h, ref > 0 ? 2 : 1);
-    WL_CU(launch_res_phases(K, ra, grid_r, mode, S(h)));
-    prof_end(h, pi);
-    info.refinements++;
-    if (mode >= 0) info.nnz_rhs += (double)h->nnz * K;
-    WL_CU(cudaMemcpyAsync(hp, st->gamma, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
-    WL_CU(cudaMemcpyAsync(hp + 64, st->b2, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaMemcpyAsync(hp, st->gamma, K * 8, cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaMemcpyAsync(hp + 64, bn2, K * 8, cudaMemcpyDeviceToHost, S(h)));
     WL_CU(cudaStreamSynchronize(S(h)));
+    info.refinements++;
     bool all = true;
     double mx = 0.0;
     int skip[64];
@@ -433,22 +451,20 @@ int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, b
       skip[c] = (rel <= tol) ? 1 : 0;
       if (!skip[c]) all = false;
     }
-    info.max_rel = std::max(info.max_rel, mx);
+    info.max_rel = mx;
     if (all || info.status == WL_ERR_NONFINITE) break;
     if (ref >= max_ref) {
       if (info.status == WL_OK) info.status = WL_ERR_NO_CONVERGENCE;
       break;
     }
-    info.max_rel = 0.0;
     int* dskip = (int*)((double*)h->small.p + 256);
     WL_CU(cudaMemcpyAsync(dskip, skip, K * sizeof(int), cudaMemcpyHostToDevice, S(h)));
     WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
-    PhaseArgs<float> a{phase_graph(h), (float*)h->d32.p, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
+    PhaseArgs<float> a{phase_graph(h), dcur, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
                        h->ca, h->cA, h->cD, nullptr, dskip, (double*)h->part.p, st, h->prm.max_iter,
                        inner_tol * inner_tol};
     SolveInfo inner;
     WL_TRY(run_cg<float>(h, K, a, grid_s, grid_u, inner, 4));
-    for (int c = 0; c < K; ++c) (void)c;
     if (inner.status == WL_ERR_NOT_SPD || inner.status == WL_ERR_NONFINITE) {
       info.status = inner.status;
       break;
@@ -457,9 +473,48 @@ int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, b
     info.cg_iters += inner.cg_iters;
     info.nnz_rhs += inner.nnz_rhs;
     info.bytes += inner.bytes;
+    // r <- r - M d, x <- x + d, next correction buffer zeroed
+    WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
+    DfResArgs ra{phase_graph(h), dcur, nullptr, rch, rcl, rh, rl, (float*)h->r32.p, xh, xl, dnext,
+                 ca, cA, cD, (double*)h->part.p, st, x_zero ? 1 : 0};
+    const int pi = prof_begin(h, kCatRes);
+    counted(h);
+    WL_CU(launch_df_res(K, ra, grid_r, false, S(h)));
+    prof_end(h, pi);
+    info.nnz_rhs += (double)h->nnz * K;
+    ++ndf;
+    x_zero = false;
+    rch = rh;
+    rcl = rl;
+    std::swap(dcur, dnext);
   }
+  if (x_zero) {  // converged before any correction: X = 0
+    WL_CU(cudaMemsetAsync(xh, 0, nk * 4, S(h)));
+    WL_CU(cudaMemsetAsync(xl, 0, nk * 4, S(h)));
+  }
+  return WL_OK;
+}
+
+// Refined solve with FP64 B and X: B -> double-float once, X back to FP64.
+int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, bool x_is_zero, SolveInfo& info) {
+  const size_t nk = (size_t)h->n * K;
+  const int grid_u = phase_blocks_f32(K);
+  WL_TRY(ensure(h->bh, nk * 4));
+  WL_TRY(ensure(h->bl, nk * 4));
+  WL_TRY(ensure(h->xh, nk * 4));
+  WL_TRY(ensure(h->xl, nk * 4));
+  WL_TRY(ensure(h->r32, nk * 4));
+  WL_TRY(ensure_phase_buffers(h, grid_u + h->nhub));
+  CgState* st = h->cgst();
+  double* bn2 = (double*)h->small.p + 600;
+  WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
   counted(h);
-  WL_CU(launch_split_x(nullptr, (int64_t)nk, xh, xl, true, x, S(h)));
+  WL_CU(launch_df_from_f64(K, b, 1.0, h->n, (float*)h->bh.p, (float*)h->bl.p, nullptr, (double*)h->part.p, st, bn2,
+                           grid_u, S(h)));
+  WL_TRY(solve_refined_df(h, (const float*)h->bh.p, (const float*)h->bl.p, bn2, (float*)h->xh.p,
+                          (float*)h->xl.p, x_is_zero ? nullptr : x, K, tol, info));
+  counted(h);
+  WL_CU(launch_split_x(nullptr, (int64_t)nk, (float*)h->xh.p, (float*)h->xl.p, true, x, S(h)));
   return WL_OK;
 }
 
@@ -723,7 +778,7 @@ void free_handle(wl_handle* h) {
     pool_free(kv.second.meta);
   }
   Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
-                 &h->r32, &h->xh, &h->xl, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
+                 &h->r32, &h->xh, &h->xl, &h->d32b, &h->bh, &h->bl, &h->rh, &h->rl, &h->dfdf, &h->ydf, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
                  &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->lan, &h->omega, &h->gram,
                  &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b, &h->hubs, &h->cgstate, &h->lzstate};
   for (Buf* b : bufs) release(*b);
@@ -1139,8 +1194,15 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
   const int ldT = 512;
   const int maxm = std::min(h->prm.max_outer, ldT - 1);
   const int check = 4;
+  // refined resolvent form: double-float outer recurrence (FP32 instructions only)
+  const bool dfp = h->prm.prec == WL_REFINED && h->prm.f == WL_F_RESOLVENT;
   do {
     if (h->prm.f != WL_F_IDENTITY && !h->have_Df && (rc = compute_Df(h, info)) != WL_OK) break;
+    if (dfp) {  // D_f as two FP32 terms for the double-float outer recurrence
+      if ((rc = ensure(h->dfdf, (size_t)n * 8)) != WL_OK) break;
+      counted(h);
+      WL_CU(launch_df_split((const double*)h->Df.p, (size_t)n, (float*)h->dfdf.p, (float*)h->dfdf.p + n, S(h)));
+    }
     if ((rc = stage_in(h, h->stage_a, U0, (size_t)n * ldu * 8, (const void**)&U0d)) != WL_OK) break;
     if (!u_dev) {
       if ((rc = ensure(h->stage_b, (size_t)ntau * n * ldo * 8)) != WL_OK) break;
@@ -1176,20 +1238,32 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
       cudaError_t e = h->perm ? launch_pack_perm(U0d, ldu, c0, K, n, 1.0, h->perm, (double*)h->packX.p, S(h))
                               : launch_pack(U0d, ldu, c0, K, n, 1.0, h->packX.p, false, S(h));
       if (e == cudaSuccess) e = launch_colnorms((const double*)h->packX.p, n, K, nrm, S(h));
-      if (e == cudaSuccess) e = launch_scale_cols((const double*)h->packX.p, n, K, nrm, basis, S(h));
+      if (e == cudaSuccess)
+        e = dfp ? launch_df_scale_cols((const double*)h->packX.p, n, K, nrm, (float*)basis, (float*)basis + blk, S(h))
+                : launch_scale_cols((const double*)h->packX.p, n, K, nrm, basis, S(h));
       if (e != cudaSuccess) { rc = set_cuda_error(e, "expmv init"); break; }
       // done flags: zero columns
       WL_CU(cudaMemcpyAsync(h->h_pin, nrm, K * 8, cudaMemcpyDeviceToHost, S(h)));
       WL_CU(cudaStreamSynchronize(S(h)));
       std::vector<int> hdone(K), hzero(K, 0);
-      for (int c = 0; c < K; ++c) hdone[c] = (h->h_pin[c] > 0.0) ? 0 : 1;
+      std::vector<double> hb2(K);
+      for (int c = 0; c < K; ++c) {
+        hdone[c] = (h->h_pin[c] > 0.0) ? 0 : 1;
+        hb2[c] = hdone[c] ? 0.0 : 1.0;
+      }
       WL_CU(cudaMemcpyAsync(done, hdone.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
       WL_CU(cudaMemcpyAsync(mprev, hzero.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
-      const int Gs = lanczos_step_grid(K);
+      double* bn2 = (double*)h->small.p + 664;  // |v_j|^2 per column for the double-float solves
+      if (dfp) {
+        WL_CU(cudaMemcpyAsync(bn2, hb2.data(), K * 8, cudaMemcpyHostToDevice, S(h)));
+        if ((rc = ensure(h->xh, blk * 4)) != WL_OK) break;
+        if ((rc = ensure(h->xl, blk * 4)) != WL_OK) break;
+      }
+      const int Gs = dfp ? df_lanczos_grid(K) : lanczos_step_grid(K);
       int Tw, Tc;
       thresholds_f64(K, &Tw, &Tc);
-      PartDev* pd;
-      if ((rc = get_part(h, Gs, Tw, Tc, &pd, K, 8)) != WL_OK) break;
+      PartDev* pd = nullptr;
+      if (!dfp && (rc = get_part(h, Gs, Tw, Tc, &pd, K, 8)) != WL_OK) break;
       if ((rc = ensure(h->part, (size_t)std::max(Gs, 1) * 64 * 2 * 8 + 1024)) != WL_OK) break;
       int m = 0;
       bool converged = false;
@@ -1207,28 +1281,51 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
           cap_blocks = nbk;
           basis = (double*)h->basis.p;
         }
-        double* vj = basis + (size_t)j * blk;
-        double* vjm1 = j > 0 ? basis + (size_t)(j - 1) * blk : nullptr;
-        double* vjp1 = basis + (size_t)(j + 1) * blk;
-        LanczosStepArgs la{h->g, pd->view(), vj, vjm1, nullptr, (const double*)h->Df.p, 0, 0, 0, vjp1,
-                           Ta, Tb, done, (double*)h->part.p, h->bar, j, ldT, 0};
-        if (h->prm.f == WL_F_IDENTITY) {
-          la.mode = 1;
-          la.c0 = 0.0;
-          la.cA = -1.0;
-          la.cD = 1.0;
-          info.nnz_rhs += (double)h->nnz * K;
-          info.iters += 1;
-        } else {
-          if ((rc = phi_apply(h, vj, (double*)h->packX.p, K, info)) != WL_OK) break;
+        if (dfp) {
+          // double-float basis: block j holds hi then lo terms
+          float* vjh = (float*)basis + (size_t)2 * j * blk;
+          float* vmh = j > 0 ? (float*)basis + (size_t)2 * (j - 1) * blk : nullptr;
+          float* vph = (float*)basis + (size_t)2 * (j + 1) * blk;
+          if ((rc = solve_refined_df(h, vjh, vjh + blk, bn2, (float*)h->xh.p, (float*)h->xl.p, nullptr, K,
+                                     h->prm.tol, info)) != WL_OK)
+            break;
           if (info.status != WL_OK) break;
-          la.X = (const double*)h->packX.p;
+          if ((rc = ensure(h->part, (size_t)std::max(Gs, 1) * 64 * 2 * 8 + 1024)) != WL_OK) break;
+          DfLanczosArgs la{vjh, vjh + blk, vmh, vmh ? vmh + blk : nullptr, (const float*)h->xh.p,
+                           (const float*)h->xl.p, (const float*)h->dfdf.p, (const float*)h->dfdf.p + n,
+                           df_from_double(h->a_scale), vph, vph + blk, Ta, Tb, done, bn2, (double*)h->part.p,
+                           h->bar, n, j, ldT};
+          if ((rc = reset_bar(h)) != WL_OK) break;
+          const int pl = prof_begin(h, kCatLan);
+          counted(h);
+          e = launch_df_lanczos_step(K, la, Gs, S(h));
+          prof_end(h, pl);
+          if (e != cudaSuccess) { rc = set_cuda_error(e, "df_lanczos_step"); break; }
+        } else {
+          double* vj = basis + (size_t)j * blk;
+          double* vjm1 = j > 0 ? basis + (size_t)(j - 1) * blk : nullptr;
+          double* vjp1 = basis + (size_t)(j + 1) * blk;
+          LanczosStepArgs la{h->g, pd->view(), vj, vjm1, nullptr, (const double*)h->Df.p, 0, 0, 0, vjp1,
+                             Ta, Tb, done, (double*)h->part.p, h->bar, j, ldT, 0};
+          if (h->prm.f == WL_F_IDENTITY) {
+            la.mode = 1;
+            la.c0 = 0.0;
+            la.cA = -1.0;
+            la.cD = 1.0;
+            info.nnz_rhs += (double)h->nnz * K;
+            info.iters += 1;
+          } else {
+            if ((rc = phi_apply(h, vj, (double*)h->packX.p, K, info)) != WL_OK) break;
+            if (info.status != WL_OK) break;
+            la.X = (const double*)h->packX.p;
+            la.part = (double*)h->part.p;
+          }
+          if ((rc = reset_bar(h)) != WL_OK) break;
+          const int pl = prof_begin(h, kCatLan);
+          e = launch_lanczos_step(K, la, Gs, S(h));
+          prof_end(h, pl);
+          if (e != cudaSuccess) { rc = set_cuda_error(e, "lanczos_step"); break; }
         }
-        if ((rc = reset_bar(h)) != WL_OK) break;
-        const int pl = prof_begin(h, kCatLan);
-        e = launch_lanczos_step(K, la, Gs, S(h));
-        prof_end(h, pl);
-        if (e != cudaSuccess) { rc = set_cuda_error(e, "lanczos_step"); break; }
         m = j + 1;
         ++outer_total;
         if (m % check == 0 || m == maxm) {
@@ -1266,9 +1363,19 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
         std::vector<int> hm(K, m);
         WL_CU(cudaMemcpyAsync(mcol, hm.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
       }
-      CombineArgs ca{basis, (const double*)h->ybuf.p, mcol, nrm, Ud, n, ldo, n * ldo, c0, ldT, ntau, h->perm};
-      counted(h);
-      e = launch_combine(K, ca, S(h));
+      if (dfp) {
+        const size_t ny = (size_t)K * ntau * ldT;
+        if ((rc = ensure(h->ydf, ny * 8)) != WL_OK) break;
+        counted(h, 2);
+        e = launch_df_split((const double*)h->ybuf.p, ny, (float*)h->ydf.p, (float*)h->ydf.p + ny, S(h));
+        DfCombineArgs ca{(const float*)basis, (const float*)h->ydf.p, (const float*)h->ydf.p + ny, mcol, nrm, Ud,
+                         n, ldo, n * ldo, c0, ldT, ntau, h->perm};
+        if (e == cudaSuccess) e = launch_df_combine(K, ca, S(h));
+      } else {
+        CombineArgs ca{basis, (const double*)h->ybuf.p, mcol, nrm, Ud, n, ldo, n * ldo, c0, ldT, ntau, h->perm};
+        counted(h);
+        e = launch_combine(K, ca, S(h));
+      }
       if (e != cudaSuccess) { rc = set_cuda_error(e, "combine"); break; }
       c0 += K;
     }

@@ -382,8 +382,6 @@ struct ResPhaseArgs {
   double ca, cA, cD;
   double* part;  // 2 * gridDim.x * K
   CgState* st;
-  float* xh;     // split iterate x = xh + xl (two FP32 terms), or NULL: x is FP64
-  float* xl;
 };
 
 // x64 = 0: r64 = b needs no SpMM; r32 = (float) b, d32 = 0, ||b||^2 -> gamma and b2
@@ -420,177 +418,6 @@ template <int K>
 __global__ void __launch_bounds__(kPhaseBlock) res_acc_phase(double* x, const float* d, int64_t total) {
   for (int64_t e = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; e < total; e += (int64_t)gridDim.x * kPhaseBlock)
     x[e] += (double)d[e];
-}
-
-// ---------------------------------------------------------------- split-FP32 residual
-// The refined form keeps its FP64-accurate iterate as two FP32 terms,
-// x = xh + xl (xh = fl32(x), xl = fl32(x - xh): 48 significant bits). The
-// residual gathers both terms (the same 8 bytes per value as FP64) and sums
-// them in FP32 arithmetic without losing accuracy: the xh terms with the
-// error-free two-sum (s, e) <- s + a (Knuth), the xl terms plainly, so that
-// the neighbour sum carries ~2^-48 relative error while every add is an FP32
-// operation (FP64 adds run at 1/64 of the FP32 rate on this GPU).
-__device__ __forceinline__ void two_sum_acc(float& s, float& e, float a) {
-  const float t = s + a;
-  const float bb = t - s;
-  e += (s - (t - bb)) + (a - bb);
-  s = t;
-}
-
-template <int K, int VW>
-__device__ __forceinline__ void row_gather_split(const int32_t* __restrict__ col, int beg, int end, int step,
-                                                 const float* XH, const float* XL, int lane_off, float (&sh)[VW],
-                                                 float (&se)[VW], float (&sl)[VW]) {
-  int e = beg;
-  for (; e + step < end; e += 2 * step) {
-    const int j0 = __ldg(col + e), j1 = __ldg(col + e + step);
-    const Pack<float, VW> h0 = ld_plain<float, VW>(XH + (size_t)j0 * K + lane_off);
-    const Pack<float, VW> h1 = ld_plain<float, VW>(XH + (size_t)j1 * K + lane_off);
-    const Pack<float, VW> l0 = ld_plain<float, VW>(XL + (size_t)j0 * K + lane_off);
-    const Pack<float, VW> l1 = ld_plain<float, VW>(XL + (size_t)j1 * K + lane_off);
-#pragma unroll
-    for (int v = 0; v < VW; ++v) {
-      two_sum_acc(sh[v], se[v], h0.v[v]);
-      two_sum_acc(sh[v], se[v], h1.v[v]);
-      sl[v] += l0.v[v] + l1.v[v];
-    }
-  }
-  for (; e < end; e += step) {
-    const int j0 = __ldg(col + e);
-    const Pack<float, VW> h0 = ld_plain<float, VW>(XH + (size_t)j0 * K + lane_off);
-    const Pack<float, VW> l0 = ld_plain<float, VW>(XL + (size_t)j0 * K + lane_off);
-#pragma unroll
-    for (int v = 0; v < VW; ++v) {
-      two_sum_acc(sh[v], se[v], h0.v[v]);
-      sl[v] += l0.v[v];
-    }
-  }
-}
-
-// r = b - M x with x = xh + xl; r32 = (float) r, d32 = 0, r64 if a.r;
-// ||r||^2 -> st->gamma, ||b||^2 -> st->b2 (last CTA)
-template <int K>
-__global__ void __launch_bounds__(kPhaseBlock, 4) res_phase_split(ResPhaseArgs a) {
-  using C = Cfg<float, K>;
-  constexpr int VW = C::VW, G = C::G, RPB = kPhaseBlock / G;
-  __shared__ __align__(16) double s_red[kPhaseBlock * VW];
-  __shared__ double s_tmp[kPhaseBlock];
-  __shared__ double s_out[K];
-  const int tid = threadIdx.x, sl_ = tid % G, lane_off = sl_ * VW;
-  const double ca = a.ca, cA = a.cA, cD = a.cD;
-  double racc[2 * VW];  // (r, r) then (b, b)
-#pragma unroll
-  for (int v = 0; v < 2 * VW; ++v) racc[v] = 0.0;
-  auto fin = [&](int64_t row, int deg, const double (&nb)[VW]) {
-    const size_t o = (size_t)row * K + lane_off;
-    const Pack<float, VW> xh = ld_plain<float, VW>(a.xh + o);
-    const Pack<float, VW> xl = ld_plain<float, VW>(a.xl + o);
-#pragma unroll
-    for (int v = 0; v < VW; ++v) {
-      const double bb = a.b[o + v];
-      const double xx = (double)xh.v[v] + (double)xl.v[v];
-      const double rr = bb - (ca * xx + cA * nb[v] + cD * (double)deg * xx);
-      racc[v] += rr * rr;
-      racc[VW + v] += bb * bb;
-      a.r32[o + v] = (float)rr;
-      if (a.d) a.d[o + v] = 0.0f;
-      if (a.r) a.r[o + v] = rr;
-    }
-  };
-  if ((int)blockIdx.x < a.g.nhub) {
-    const int64_t row = a.g.hubs[blockIdx.x];
-    const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
-    float sh[VW], se[VW], sl[VW];
-#pragma unroll
-    for (int v = 0; v < VW; ++v) sh[v] = se[v] = sl[v] = 0.f;
-    row_gather_split<K, VW>(a.g.col, beg + tid / G, end, RPB, a.xh, a.xl, lane_off, sh, se, sl);
-#pragma unroll
-    for (int v = 0; v < VW; ++v) s_red[tid * VW + v] = (double)sh[v] + ((double)se[v] + (double)sl[v]);
-    __syncthreads();
-    if (tid < G) {
-      double acc[VW];
-#pragma unroll
-      for (int v = 0; v < VW; ++v) acc[v] = s_red[tid * VW + v];
-      for (int gr = 1; gr < RPB; ++gr)
-#pragma unroll
-        for (int v = 0; v < VW; ++v) acc[v] += s_red[(gr * G + sl_) * VW + v];
-      fin(row, end - beg, acc);
-    }
-  } else {
-    const int64_t nblk = (int64_t)gridDim.x - a.g.nhub;
-    for (int64_t row = ((int64_t)blockIdx.x - a.g.nhub) * RPB + tid / G; row < a.g.n; row += nblk * RPB) {
-      const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
-      if (end - beg > kHubDeg) continue;
-      float sh[VW], se[VW], sl[VW];
-#pragma unroll
-      for (int v = 0; v < VW; ++v) sh[v] = se[v] = sl[v] = 0.f;
-      row_gather_split<K, VW>(a.g.col, beg, end, 1, a.xh, a.xl, lane_off, sh, se, sl);
-      double nb[VW];
-#pragma unroll
-      for (int v = 0; v < VW; ++v) nb[v] = (double)sh[v] + ((double)se[v] + (double)sl[v]);
-      fin(row, end - beg, nb);
-    }
-  }
-  // column sums of (r, r) and (b, b): per-thread partials, then CTA and grid
-  double rp[VW], bp[VW];
-#pragma unroll
-  for (int v = 0; v < VW; ++v) {
-    rp[v] = racc[v];
-    bp[v] = racc[VW + v];
-  }
-  double* part_b = a.part + (size_t)gridDim.x * K;
-  {
-    constexpr int NW = kPhaseBlock / 32;
-    __shared__ double s_w[2 * NW * K];
-    const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int off = G; off < 32; off <<= 1)
-#pragma unroll
-      for (int v = 0; v < VW; ++v) {
-        rp[v] += __shfl_xor_sync(0xffffffffu, rp[v], off);
-        bp[v] += __shfl_xor_sync(0xffffffffu, bp[v], off);
-      }
-    if (lane < G)
-#pragma unroll
-      for (int v = 0; v < VW; ++v) {
-        s_w[warp * K + lane * VW + v] = rp[v];
-        s_w[NW * K + warp * K + lane * VW + v] = bp[v];
-      }
-    __syncthreads();
-    if (tid < K) {
-      double t = 0.0, u = 0.0;
-      for (int w = 0; w < NW; ++w) {
-        t += s_w[w * K + tid];
-        u += s_w[NW * K + w * K + tid];
-      }
-      a.part[(size_t)blockIdx.x * K + tid] = t;
-      part_b[(size_t)blockIdx.x * K + tid] = u;
-      __threadfence();
-    }
-    __syncthreads();
-  }
-  __shared__ int s_last;
-  if (tid == 0) s_last = (atomicAdd(&a.st->ticket, 1u) == gridDim.x - 1) ? 1 : 0;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  sum_partials<K>(a.part, gridDim.x, s_tmp, s_out);
-  if (tid < K) a.st->gamma[tid] = s_out[tid];
-  __syncthreads();
-  sum_partials<K>(part_b, gridDim.x, s_tmp, s_out);
-  if (tid < K) a.st->b2[tid] = s_out[tid];
-  if (tid == 0) a.st->ticket = 0;
-}
-
-// (xh, xl) += d, re-split in FP64
-template <int K>
-__global__ void __launch_bounds__(kPhaseBlock) res_acc_split(float* xh, float* xl, const float* d, int64_t total) {
-  for (int64_t e = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; e < total; e += (int64_t)gridDim.x * kPhaseBlock) {
-    const double x = ((double)xh[e] + (double)xl[e]) + (double)d[e];
-    const float h = (float)x;
-    xh[e] = h;
-    xl[e] = (float)(x - (double)h);
-  }
 }
 
 template <int K>

@@ -11,6 +11,8 @@
 #include "wl_common.cuh"
 #include "wl_lanczos.cuh"
 #include "wl_lanczos2.cuh"
+#include "wl_expdf.cuh"
+#include "wl_res.cuh"
 
 namespace wl {
 
@@ -75,6 +77,22 @@ cudaError_t launch_res_phases(int K, const ResPhaseArgs& a, int grid, int accumu
 // x (n K doubles) -> (xh, xl) FP32 terms, or (join) xh + xl -> xout
 cudaError_t launch_split_x(const double* x, int64_t total, float* xh, float* xl, bool join, double* xout,
                            cudaStream_t s);
+// ---- wl_k_res.cu: double-float residual of the refined form
+// r_out = r_in - M y (y gathered: the correction d; x += d) or, full, r_out = b - M x (x = yh + yl)
+cudaError_t launch_df_res(int K, const DfResArgs& a, int grid, bool full, cudaStream_t s);
+// (bh, bl) = scale * b (b: n x K FP64, contiguous), r32 = bh (if not NULL), |b|^2 per column -> b2
+cudaError_t launch_df_from_f64(int K, const double* b, double scale, int64_t n, float* bh, float* bl, float* r32,
+                               double* part, CgState* st, double* b2, int grid, cudaStream_t s);
+int df_res_blocks(int K);
+// outer Lanczos of the refined form on double-float vectors (cooperative launch)
+int df_lanczos_grid(int K);
+cudaError_t launch_df_lanczos_step(int K, const DfLanczosArgs& a, int G, cudaStream_t s);
+cudaError_t launch_df_combine(int K, const DfCombineArgs& a, cudaStream_t s);
+// hi + lo = X[:, c] / nrm[c] (X: n x K FP64, contiguous)
+cudaError_t launch_df_scale_cols(const double* X, int64_t n, int K, const double* nrm, float* hi, float* lo,
+                                 cudaStream_t s);
+// hi + lo = x (total FP64 values)
+cudaError_t launch_df_split(const double* x, size_t total, float* hi, float* lo, cudaStream_t s);
 int phase_blocks_f32(int K);  // resident CTAs of the S kernel (all SMs)
 int phase_blocks_f64(int K);
 int res_blocks(int K);

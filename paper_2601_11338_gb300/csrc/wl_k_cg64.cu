@@ -42,11 +42,6 @@ static cudaError_t run_res(const ResPhaseArgs& a, int grid, int accumulate, cuda
     return cudaGetLastError();
   }
   const int64_t total = a.g.n * K;
-  if (a.xh) {  // iterate held as two FP32 terms
-    if (accumulate) res_acc_split<K><<<grid, kPhaseBlock, 0, s>>>(a.xh, a.xl, a.d, total);
-    res_phase_split<K><<<grid, kPhaseBlock, 0, s>>>(a);
-    return cudaGetLastError();
-  }
   if (accumulate) res_acc_phase<K><<<grid, kPhaseBlock, 0, s>>>(a.x, a.d, total);
   res_phase<K><<<grid, kPhaseBlock, 0, s>>>(a);
   return cudaGetLastError();
