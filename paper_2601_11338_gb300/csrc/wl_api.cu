@@ -153,7 +153,6 @@ struct wl_handle {
   Buf Tab, ybuf, yprev, errb;
   Buf stage_a, stage_b;   // host <-> device staging
   Buf packV, packX;
-  Buf lan;                // Lanczos extreme vectors
   Buf omega, gram;        // sketch and Gram workspace
   Buf omega_int;          // sketch rows in the internal node order
   Buf ptmp;               // partition / relabel scratch (int64)
@@ -164,7 +163,12 @@ struct wl_handle {
   int nhub = 0;
   std::vector<void*> retired;  // blocks released during calls, returned to the allocator at destroy
   Buf cgstate;            // CgState of the running solve
-  Buf lzstate;            // LzState of the spectral-scale Lanczos
+  Buf spV, spW;           // spectral-scale Lanczos: basis (double-float, float2 per node) and raw w vectors
+  Buf spstate;            // SpState of the spectral-scale Lanczos
+  Buf mid;                // rows with kSpWarpDeg < deg <= kHubDeg (a warp each in the spectral Lanczos)
+  int nmid = 0, nmid_blk = 0;
+  double sp_c0 = 0.0, sp_cD = 0.0, sp_theta = 0.0;  // operator and Ritz value of the basis held in spV
+  bool sp_ritz_ready = false;                        // W[1] holds that run's Ritz vector
   double inner_tol = 4e-6;  // floor of the FP32 correction target of the refined form
   bool gram_tc = true;      // XNysTrace Gram on the tensor cores (tcgen05); false: CUDA cores
   CgState* cgst() { return (CgState*)cgstate.p; }
@@ -560,131 +564,191 @@ int compute_Df(wl_handle* h, SolveInfo& info) {
 }
 
 // ------------------------------------------------------------------ spectral scale
-// Extreme eigenvalues of Op = c0 I + cA A + cD D by Lanczos (k = 1).
-// One Lanczos run on Op = c0 I + cA A + cD D from the seeded start vector,
-// extended in place (doubling m, up to 480 steps) until the largest Ritz
-// value of T_m agrees with that of T_{m - m/8} to rtol. run->cont lets a
-// caller ask for more accuracy later without restarting.
-struct LzRun {
-  double c0, cA, cD;
-  int m = 0;         // steps done so far
-  int m_eff = 0;     // steps before a breakdown (== m without one)
-  double th = 0.0;   // largest Ritz value
-  double conv = 1.0; // relative change of th over the last m/8 steps
-  bool spent = false; // no more steps possible (breakdown or the step cap reached)
+// Largest eigenpair of Op = c0 I + A + cD D by Lanczos on a stored
+// double-float basis (k = 1). A run stops once the error bound of its
+// largest Ritz value is below rtol |theta|; a full basis restarts from the
+// Ritz vector. The Ritz vector of the last run starts the next one.
+struct SpRun {
+  double c0 = 0.0, cD = 0.0;
+  int m = 0;            // steps of the current run (held in the basis)
+  int total = 0;        // steps over all runs of this operator
+  double theta = 0.0;   // largest Ritz value
+  double bound = 1e300; // its error bound
+  bool exact = false;   // breakdown, or as many steps as nodes
 };
 
-int lanczos_run(wl_handle* h, LzRun* run, double rtol) {
-  const int gu = lz_blocks(), gs = gu + h->nhub;
-  WL_TRY(ensure(h->lan, (size_t)h->n * 4 * 8 + 64));
+int sp_cap(wl_handle* h) {
+  const int64_t n = std::max<int64_t>(h->n, 1);
+  const int64_t by_mem = (int64_t)(4.0e9 / (8.0 * (double)n));  // basis up to about 4 GB
+  return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(kSpMax, std::max<int64_t>(by_mem, 16)), n));
+}
+
+SpArgs sp_args(wl_handle* h, double c0, double cD) {
+  float2* W = (float2*)h->spW.p;
+  return SpArgs{phase_graph(h), (const int32_t*)h->mid.p, h->nmid, h->nmid_blk, c0, 1.0, cD, (float2*)h->spV.p,
+                {W, W + h->n}, (double*)h->part.p, (SpState*)h->spstate.p, 0, 0x5EEDull};
+}
+
+int sp_buffers(wl_handle* h, int gs) {
+  WL_TRY(ensure(h->spV, (size_t)sp_cap(h) * h->n * 8));
+  WL_TRY(ensure(h->spW, (size_t)2 * h->n * 8));
   WL_TRY(ensure(h->part, (size_t)gs * 64 * 2 * 8 + 1024));
-  WL_TRY(ensure(h->lzstate, sizeof(LzState)));
-  double* v = (double*)h->lan.p;
-  LzState* st = (LzState*)h->lzstate.p;
-  const int m_cap = (int)std::min<int64_t>(480, std::max<int64_t>(h->n, 1));
-  LzArgs a{phase_graph(h), run->c0, run->cA, run->cD, {v, v + h->n}, {v + 2 * h->n, v + 3 * h->n},
-           (double*)h->part.p, st, 0, 0x5EEDull};
-  for (;;) {
-    run->spent = run->m > 0 && (run->m_eff < run->m || run->m >= m_cap);
-    if (run->m > 0 && (run->conv <= rtol || run->spent)) break;
-    const int j0 = run->m;
-    const int m = j0 == 0 ? std::min(64, m_cap) : std::min(2 * j0, m_cap);
-    if (j0 == 0) WL_CU(cudaMemsetAsync(st, 0, sizeof(LzState), S(h)));
-    counted(h, 2 * (m - j0) + 2);
-    WL_CU(launch_lanczos2(a, j0, m, std::max(1, m / 8), gs, gu, S(h)));
-    WL_CU(cudaMemcpyAsync(h->h_pin, st->out, 5 * 8, cudaMemcpyDeviceToHost, S(h)));
+  WL_TRY(ensure(h->spstate, sizeof(SpState)));
+  return WL_OK;
+}
+
+// Extend the run of r (or start one: seeded, or from the vector in W[1]
+// when r->m == 0) until its bound is below rtol |theta| or it is exact.
+int sp_run(wl_handle* h, SpRun* r, double rtol, bool seeded) {
+  const int cap = sp_cap(h), gu = sp_blocks(), gs = gu + h->nhub + h->nmid_blk;
+  WL_TRY(sp_buffers(h, gs));
+  const SpArgs a = sp_args(h, r->c0, r->cD);
+  SpState* st = (SpState*)h->spstate.p;
+  for (int guard = 0; guard < 256; ++guard) {
+    if (r->exact || (r->m > 0 && r->bound <= rtol * std::fabs(r->theta))) break;
+    int mode = 2;
+    if (r->m == 0) {
+      mode = (seeded && r->total == 0) ? 0 : 1;
+    } else if (r->m >= cap) {  // basis full: restart from the Ritz vector
+      counted(h);
+      WL_CU(launch_sp_ritz(a, gu, S(h)));
+      r->m = 0;
+      mode = 1;
+    }
+    const int j0 = r->m, j1 = std::min(cap, j0 + 16);
+    if (mode == 0) WL_CU(cudaMemsetAsync(st, 0, sizeof(SpState), S(h)));  // tickets and flags start at zero
+    counted(h, 1 + 2 * (j1 - j0) + (j1 - j0 + 7) / 8);
+    WL_CU(launch_sp_start(a, mode, gu, S(h)));
+    WL_CU(launch_sp_steps(a, j0, j1, cap, 8, rtol, gs, gu, S(h)));
+    WL_CU(cudaMemcpyAsync(h->h_pin, &st->start_norm, 9 * 8 + 4 * 4, cudaMemcpyDeviceToHost, S(h)));
     WL_CU(cudaStreamSynchronize(S(h)));
-    const double* o = h->h_pin;
-    run->m = m;
-    run->m_eff = (int)o[4];
-    run->th = o[0];
-    // after a breakdown, or with as many steps as nodes, T_m holds the exact
-    // extreme eigenvalue (up to rounding)
-    run->conv = (run->m_eff < m || m >= h->n) ? 0.0 : std::fabs(o[0] - o[1]) / (std::fabs(o[0]) + 1e-300);
+    const double* o = h->h_pin + 1;
+    const int* ints = (const int*)(h->h_pin + 9);
+    const int m_eff = ints[0], brk = ints[2];
+    r->total += m_eff - j0;
+    r->m = m_eff;
+    r->theta = o[0];
+    r->bound = o[3];
+    r->exact = brk != 0 || (int64_t)m_eff >= h->n;
+    if (m_eff < j1 && !brk && r->bound > rtol * std::fabs(r->theta)) break;  // defensive: no progress
   }
+  h->sp_c0 = r->c0;
+  h->sp_cD = r->cD;
+  h->sp_theta = r->theta;
+  h->sp_ritz_ready = false;
   return WL_OK;
 }
 
-int lambda_max_adaptive(wl_handle* h, double c0, double cA, double cD, double rtol, double* lmax) {
-  LzRun r;
-  r.c0 = c0;
-  r.cA = cA;
-  r.cD = cD;
-  WL_TRY(lanczos_run(h, &r, rtol));
-  *lmax = r.th;
+// Ritz vector of the last run into W[1]; q = u^T D u / |u|^2 and
+// u^T A u / |u|^2 from the run's Ritz value.
+int sp_ritz_q(wl_handle* h, double* q, double* uAu) {
+  const int gu = sp_blocks();
+  const SpArgs a = sp_args(h, h->sp_c0, h->sp_cD);
+  SpState* st = (SpState*)h->spstate.p;
+  if (!h->sp_ritz_ready) {
+    counted(h);
+    WL_CU(launch_sp_ritz(a, gu, S(h)));
+  }
+  WL_CU(cudaMemcpyAsync(h->h_pin, &st->out[5], 2 * 8, cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaStreamSynchronize(S(h)));
+  const double n2 = h->h_pin[0];
+  *q = n2 > 0 ? h->h_pin[1] / n2 : 0.0;
+  *uAu = h->sp_theta - h->sp_c0 - h->sp_cD * (*q);
+  h->sp_ritz_ready = true;
   return WL_OK;
 }
 
-// rho(Z_mu): largest lambda with lambda_max(A - (mu/lambda)(D - mu I)) = lambda
-// (the quadratic eigenproblem behind Eq. Zdef), by a bracketed Illinois
-// iteration on h(lambda) = lambda_max(...) - lambda. Each evaluation is one
-// Lanczos run made only as accurate as the sign of h needs: it starts loose
-// and is extended until |h| clearly exceeds its error estimate or the
-// estimate reaches 1e-11.
+int lambda_max_adaptive(wl_handle* h, double rtol, double* lmax) {
+  SpRun r;
+  WL_TRY(sp_run(h, &r, rtol, true));
+  *lmax = r.theta;
+  return WL_OK;
+}
+
+// rho(Z_mu): the largest lambda with lambda_max(A - (mu/lambda)(D - mu I)) =
+// lambda (the quadratic eigenproblem lambda^2 u = lambda A u - mu (D - mu I) u
+// behind Eq. Zdef). Each evaluation of h(lambda) = lambda_max(...) - lambda is
+// one Lanczos run from the previous Ritz vector u, made only as accurate as
+// the sign of h needs. The next lambda is the Rayleigh functional of u (the
+// root of lambda^2 - lambda u^T A u + mu u^T (D - mu I) u = 0 nearest the
+// current one, quadratically convergent), kept inside the bracket of signs
+// seen so far; outside it, regula falsi (Illinois) or halving.
 int rho_companion(wl_handle* h, double mu, double lmaxA, double* rho) {
   if (mu == 0.0 || lmaxA <= 0.0) {
     *rho = lmaxA;
     return WL_OK;
   }
   constexpr double kTight = 1e-11;
+  double q = 0.0, uAu = 0.0;
+  WL_TRY(sp_ritz_q(h, &q, &uAu));
+  auto rf = [&](double near) {
+    const double c = mu * (q - mu), disc = uAu * uAu - 4.0 * c;
+    if (!(disc >= 0.0)) return std::nan("");
+    const double sq = std::sqrt(disc);
+    const double r1 = 0.5 * (uAu + sq), r2 = 0.5 * (uAu - sq);
+    return std::fabs(r1 - near) <= std::fabs(r2 - near) ? r1 : r2;
+  };
   bool certain = true;
   auto hfun = [&](double lam, double* val) -> int {
-    LzRun r;
+    SpRun r;
     r.c0 = mu * mu / lam;
-    r.cA = 1.0;
     r.cD = -mu / lam;
     double rtol = 1e-6;
     for (;;) {
-      WL_TRY(lanczos_run(h, &r, rtol));
-      *val = r.th - lam;
-      certain = std::fabs(*val) > 10.0 * r.conv * std::fabs(r.th);
-      if (certain || r.conv <= kTight || r.spent) break;
-      rtol = std::max(kTight, 1e-3 * std::fabs(*val) / std::fabs(r.th));
+      WL_TRY(sp_run(h, &r, rtol, false));
+      *val = r.theta - lam;
+      certain = std::fabs(*val) > 10.0 * r.bound;
+      if (certain || r.exact || r.bound <= kTight * std::fabs(r.theta)) break;
+      rtol = std::max(kTight, 1e-3 * std::fabs(*val) / std::fabs(r.theta));
     }
-    return WL_OK;
+    return sp_ritz_q(h, &q, &uAu);
   };
-  double hi = lmaxA, fhi;
-  WL_TRY(hfun(hi, &fhi));
-  if (fhi > 0) {  // can only happen through rounding; widen
-    hi *= 1.01;
-    WL_TRY(hfun(hi, &fhi));
-  }
-  double lo = 0.5 * hi, flo;
-  WL_TRY(hfun(lo, &flo));
-  int guard = 0;
-  while (flo <= 0 && guard++ < 40) {
-    hi = lo;
-    fhi = flo;
-    lo *= 0.5;
-    WL_TRY(hfun(lo, &flo));
-  }
-  if (flo <= 0) {
-    *rho = 0.0;
-    return WL_OK;
-  }
+  // h(lambda_max(A)) <= 0: there lambda_max(A - (mu/lambda)(D - mu I)) <= lambda_max(A)
+  // (D - mu I >= 0 on nodes with an edge; isolated nodes give mu^2 / lambda <= 1 <= lambda)
+  double hi = lmaxA * (1.0 + 1e-12), lo = 0.0, fhi = 0.0, flo = 0.0;
+  bool have_lo = false, have_fhi = false;
+  double lam = rf(lmaxA);
+  if (!(lam > 0.0 && lam < hi)) lam = 0.5 * hi;
   int side = 0;
-  for (int it = 0; it < 60 && (hi - lo) > 1e-12 * hi; ++it) {
-    double x = (lo * fhi - hi * flo) / (fhi - flo);
-    if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
+  for (int it = 0; it < 60; ++it) {
     double fx;
-    WL_TRY(hfun(x, &fx));
-    if (!certain) {  // |h(x)| is below what the Lanczos run resolves: x is the root
-      lo = hi = x;
-      break;
+    WL_TRY(hfun(lam, &fx));
+    if (!certain) {  // |h| is below what the Lanczos run resolves: lam is the root
+      *rho = lam;
+      return WL_OK;
     }
     if (fx > 0) {
-      lo = x;
+      lo = lam;
       flo = fx;
-      if (side == 1) fhi *= 0.5;
+      have_lo = true;
+      if (side == 1 && have_fhi) fhi *= 0.5;
       side = 1;
     } else {
-      hi = x;
+      hi = lam;
       fhi = fx;
-      if (side == -1) flo *= 0.5;
+      have_fhi = true;
+      if (side == -1 && have_lo) flo *= 0.5;
       side = -1;
     }
+    if (hi - lo <= 1e-12 * hi) break;
+    if (!have_lo && hi < 1e-12 * lmaxA) {  // no positive side found: rho is 0
+      *rho = 0.0;
+      return WL_OK;
+    }
+    double nxt = rf(lam);
+    if (!(nxt > lo && nxt < hi)) {
+      if (have_lo && have_fhi) {
+        nxt = (lo * fhi - hi * flo) / (fhi - flo);
+        if (!(nxt > lo && nxt < hi)) nxt = 0.5 * (lo + hi);
+      } else if (have_lo) {
+        nxt = 0.5 * (lo + hi);
+      } else {
+        nxt = 0.5 * hi;
+      }
+    }
+    lam = nxt;
   }
-  *rho = 0.5 * (lo + hi);
+  *rho = have_lo ? 0.5 * (lo + hi) : lam;
   return WL_OK;
 }
 
@@ -779,8 +843,8 @@ void free_handle(wl_handle* h) {
   }
   Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
                  &h->r32, &h->xh, &h->xl, &h->d32b, &h->bh, &h->bl, &h->rh, &h->rl, &h->dfdf, &h->ydf, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
-                 &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->lan, &h->omega, &h->gram,
-                 &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b, &h->hubs, &h->cgstate, &h->lzstate};
+                 &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->spV, &h->spW, &h->spstate, &h->mid, &h->omega, &h->gram,
+                 &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b, &h->hubs, &h->cgstate};
   for (Buf* b : bufs) release(*b);
   for (void* p : h->retired) pool_free(p);
   h->retired.clear();
@@ -936,13 +1000,22 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
     if (e == cudaSuccess) e = cudaStreamSynchronize(S(h));
     if (e != cudaSuccess) return fail(set_cuda_error(e, "hub list"));
     h->nhub = (int)*(int64_t*)h->h_pin;
+    // rows gathered by a warp each in the spectral-scale Lanczos
+    if ((rc = ensure(h->mid, sizeof(int32_t) * h->n)) != WL_OK) return fail(rc);
+    counted(h, 5);
+    e = launch_row_list(h->g.row_ptr, h->n, kSpWarpDeg, kHubDeg, (int32_t*)h->mid.p, (int64_t*)h->ptmp.p,
+                        (int64_t*)h->h_pin, S(h));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S(h));
+    if (e != cudaSuccess) return fail(set_cuda_error(e, "mid-row list"));
+    h->nmid = (int)*(int64_t*)h->h_pin;
+    h->nmid_blk = h->nmid > 0 ? (int)std::min<int64_t>((h->nmid + 31) / 32, 2 * 152) : 0;
   }
 
   // spectral scale and parameters
   h->lmax = 0.0;
   h->rho = 0.0;
   if (h->n > 0 && h->nnz > 0) {
-    if ((rc = lambda_max_adaptive(h, 0.0, 1.0, 0.0, 1e-11, &h->lmax)) != WL_OK) return fail(rc);
+    if ((rc = lambda_max_adaptive(h, 1e-12, &h->lmax)) != WL_OK) return fail(rc);
     if (p->f == WL_F_RESOLVENT) {
       if ((rc = rho_companion(h, mu, h->lmax, &h->rho)) != WL_OK) return fail(rc);
     } else {

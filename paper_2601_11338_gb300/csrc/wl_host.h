@@ -10,9 +10,9 @@
 #include "wl_cg2.cuh"
 #include "wl_common.cuh"
 #include "wl_lanczos.cuh"
-#include "wl_lanczos2.cuh"
 #include "wl_expdf.cuh"
 #include "wl_res.cuh"
+#include "wl_spec.cuh"
 
 namespace wl {
 
@@ -105,18 +105,22 @@ cudaError_t launch_row_list(const int32_t* row_ptr, int64_t n, int lo, int hi, i
                             int64_t* count, cudaStream_t s);
 
 // ---- wl_k_lanczos.cu
-int lanczos_ext_grid();
 int lanczos_step_grid(int K);
-cudaError_t launch_lanczos_extreme(const LanczosExtArgs& a, int G, cudaStream_t s);
-// m Lanczos steps of the phase-kernel form (2 m + 2 launches), extremes of T_m into a.st->out
-// Lanczos steps j0..m-1 (j0 = 0: a fresh run from the seeded start vector;
-// j0 > 0: continue the run held in a.st / a.V / a.W), then the extreme
-// eigenvalues of T_m and T_{m-check}
-cudaError_t launch_lanczos2(const LzArgs& a, int j0, int m, int check, int grid_s, int grid_u, cudaStream_t s);
-int lz_blocks();
 cudaError_t launch_lanczos_step(int K, const LanczosStepArgs& a, int G, cudaStream_t s);
 cudaError_t launch_tridiag_exp(const TridiagArgs& a, int K, cudaStream_t s);
 cudaError_t launch_combine(int K, const CombineArgs& a, cudaStream_t s);
+
+// ---- wl_k_spec.cu: spectral-scale Lanczos (double-float basis, k = 1)
+int sp_blocks();  // resident CTAs of the step kernels (all SMs)
+// mode 0: a fresh run from the seeded start vector; 1: a new run from the
+// vector in W[1] (a Ritz vector); 2: continue the current run
+cudaError_t launch_sp_start(const SpArgs& a, int mode, int grid_u, cudaStream_t s);
+// steps j0..j1-1 (the run stops by itself at cap - 1, on breakdown, or when the
+// error bound checked every `check` steps and at j1 is below rtol |theta_1|)
+cudaError_t launch_sp_steps(const SpArgs& a, int j0, int j1, int cap, int check, double rtol, int grid_s,
+                            int grid_u, cudaStream_t s);
+// Ritz vector of the run into W[1], |u|^2 and u^T D u into st->out[5], out[6]
+cudaError_t launch_sp_ritz(const SpArgs& a, int grid_u, cudaStream_t s);
 
 // ---- wl_k_trace.cu
 cudaError_t launch_philox_sketch(uint16_t* omega, int64_t n, int M, uint64_t seed, cudaStream_t s);

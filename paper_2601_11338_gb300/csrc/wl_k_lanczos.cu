@@ -1,9 +1,7 @@
-// Lanczos kernels: extreme eigenvalues (spectral scale), one step of the
-// outer Lanczos on the walk Laplacian, exp of the tridiagonal, combination.
+// Lanczos kernels: one step of the outer Lanczos on the walk Laplacian,
+// exp of the tridiagonal, combination.
 #define WL_LANCZOS_KERNELS
-#define WL_LANCZOS2_KERNELS
 #include "wl_host.h"
-#include "wl_lanczos2.cuh"
 
 namespace wl {
 
@@ -20,15 +18,9 @@ static const void* step_fn(int K) {
   return nullptr;
 }
 
-int lanczos_ext_grid() { return coop_grid((const void*)lanczos_extreme, 2); }
-
 int lanczos_step_grid(int K) {
   const void* f = step_fn(K);
   return f ? coop_grid(f, 4) : 0;
-}
-
-cudaError_t launch_lanczos_extreme(const LanczosExtArgs& a, int G, cudaStream_t s) {
-  return coop_launch((const void*)lanczos_extreme, G, a, s);
 }
 
 cudaError_t launch_lanczos_step(int K, const LanczosStepArgs& a, int G, cudaStream_t s) {
@@ -56,30 +48,6 @@ cudaError_t launch_combine(int K, const CombineArgs& a, cudaStream_t s) {
     default:
       return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
-}
-
-int lz_blocks() {
-  int nb = 0, dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)lz_s, kPhaseBlock, 0);
-  return (nb < 1 ? 1 : nb) * sms;
-}
-
-cudaError_t launch_lanczos2(const LzArgs& a0, int j0, int m, int check, int grid_s, int grid_u, cudaStream_t s) {
-  LzArgs a = a0;
-  a.j = 0;
-  if (j0 == 0)
-    lz_init<<<grid_u, kPhaseBlock, 0, s>>>(a);
-  else
-    lz_resume<<<1, 32, 0, s>>>(a.st);
-  for (int j = j0; j < m; ++j) {
-    a.j = j;
-    lz_s<<<grid_s, kPhaseBlock, 0, s>>>(a);
-    lz_u<<<grid_u, kPhaseBlock, 0, s>>>(a, j == m - 1 ? 1 : 0);
-  }
-  lz_eig<<<1, 4 * kEigT, 0, s>>>(a.st, check);
   return cudaGetLastError();
 }
 

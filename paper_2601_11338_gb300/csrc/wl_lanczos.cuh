@@ -1,10 +1,6 @@
 // Lanczos kernels (Sec. 4.1: f(A) v ~ |v| Q_k f(H_k) e_1 with the Lanczos
 // process for symmetric operators), all FP64.
 //
-//  lanczos_extreme : m Lanczos steps on Op = c0 I + cA A + cD D (k = 1) in one
-//                    persistent kernel, then the extreme eigenvalues of T_m by
-//                    Sturm-count bisection. Used for lambda_max(A) and for the
-//                    spectral-radius search of Z_mu (Prop. whe-we-converge).
 //  lanczos_step    : one step of K lockstep Lanczos recurrences on the walk
 //                    Laplacian, w = D_f (.) v - X (X = phi v from a CG solve) or
 //                    w = Op v; alpha, beta, and the next basis block.
@@ -17,155 +13,6 @@
 #include "wl_common.cuh"
 
 namespace wl {
-
-// ------------------------------------------------------------------ Sturm bisection
-// Number of eigenvalues of the symmetric tridiagonal (a[0..m), b[0..m-1)) that
-// are < x (LDL^T inertia).
-__device__ inline int sturm_count(const double* a, const double* b, int m, double x) {
-  int cnt = 0;
-  double q = a[0] - x;
-  if (q < 0.0) ++cnt;
-  for (int i = 1; i < m; ++i) {
-    const double qq = (q == 0.0) ? 1e-300 : q;
-    q = a[i] - x - b[i - 1] * b[i - 1] / qq;
-    if (q < 0.0) ++cnt;
-  }
-  return cnt;
-}
-
-// idx-th smallest eigenvalue (0-based) by bisection on [lo, hi].
-__device__ inline double tridiag_eig(const double* a, const double* b, int m, int idx) {
-  double lo = 1e300, hi = -1e300;
-  for (int i = 0; i < m; ++i) {
-    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < m ? fabs(b[i]) : 0.0);
-    lo = fmin(lo, a[i] - r);
-    hi = fmax(hi, a[i] + r);
-  }
-  for (int it = 0; it < 100 && hi - lo > 1e-15 * fmax(fabs(lo), fabs(hi)) + 1e-300; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (sturm_count(a, b, m, mid) > idx) hi = mid; else lo = mid;
-  }
-  return 0.5 * (lo + hi);
-}
-
-// ------------------------------------------------------------------ extreme Lanczos
-struct LanczosExtArgs {
-  Graph g;
-  Part pt;
-  double c0, cA, cD;
-  double* v;       // 3 * n doubles: three rotating basis vectors
-  double* alpha;   // m
-  double* beta;    // m
-  double* part;    // 2 * G
-  double* out;     // [0] theta_max(T_m), [1] theta_max(T_{m-check}), [2] theta_min(T_m), [3] theta_min(T_{m-check}), [4] m_eff
-  GridBar* bar;
-  int m;
-  int check;
-  uint64_t seed;
-};
-
-__device__ inline double start_component(int64_t i, uint64_t seed) {
-  uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + seed;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  return 1.0 + 0.25 * ((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
-}
-
-#ifdef WL_LANCZOS_KERNELS
-__global__ void __launch_bounds__(kBlock) lanczos_extreme(LanczosExtArgs a) {
-  constexpr int K = 1;
-  constexpr int VW = 1;
-  constexpr int NW = kBlock / 32;
-  __shared__ double s_tmp[kBlock];
-  __shared__ double s_w[NW * K];
-  __shared__ double s_red[K];
-  __shared__ __align__(16) double s_gath[kBlock];
-  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
-  const int r0 = a.pt.rb[cta], r1 = a.pt.rb[cta + 1];
-  const int64_t n = a.g.n;
-  double* vp = a.v;          // v_{j-1}
-  double* vc = a.v + n;      // v_j
-  double* w = a.v + 2 * n;   // w
-  int buf = 0;
-
-  // start vector: positive, mildly perturbed, normalised
-  {
-    double acc[1] = {0.0};
-    for (int i = r0 + tid; i < r1; i += kBlock) {
-      const double x = start_component(i, a.seed);
-      w[i] = x;
-      vp[i] = 0.0;
-      acc[0] += x * x;
-    }
-    cta_column_sums<double, K>(acc, s_w, a.part + (size_t)buf * G + cta);
-  }
-  if (!grid_sync(a.bar, G)) return;
-  reduce_partials<K>(a.part + (size_t)buf * G, G, s_tmp, s_red);
-  buf ^= 1;
-  {
-    const double inv = 1.0 / sqrt(s_red[0]);
-    for (int i = r0 + tid; i < r1; i += kBlock) vc[i] = __ldcg(w + i) * inv;
-  }
-  if (!grid_sync(a.bar, G)) return;
-  double beta_prev = 0.0;
-  int m_eff = a.m;
-  for (int j = 0; j < a.m; ++j) {
-    // w = Op v_j ; alpha = (v_j, w)
-    double acc[1] = {0.0};
-    auto pre = [&](int row, int lane_off) { return __ldcg(vc + row); };
-    auto fin = [&](int row, int deg, int lane_off, const double (&nb)[VW], const double vi) {
-      const double wi = a.c0 * vi + a.cA * nb[0] + a.cD * (double)deg * vi;
-      w[row] = wi;
-      acc[0] += vi * wi;
-    };
-    for_rows_gather<double, K>(a.g, a.pt, vc, s_gath, pre, fin);
-    cta_column_sums<double, K>(acc, s_w, a.part + (size_t)buf * G + cta);
-    if (!grid_sync(a.bar, G)) return;
-    reduce_partials<K>(a.part + (size_t)buf * G, G, s_tmp, s_red);
-    buf ^= 1;
-    const double alpha = s_red[0];
-    // w -= alpha v_j + beta_{j-1} v_{j-1}; beta = |w|
-    double acc2[1] = {0.0};
-    for (int i = r0 + tid; i < r1; i += kBlock) {
-      const double wi = __ldcg(w + i) - alpha * __ldcg(vc + i) - beta_prev * __ldcg(vp + i);
-      w[i] = wi;
-      acc2[0] += wi * wi;
-    }
-    cta_column_sums<double, K>(acc2, s_w, a.part + (size_t)buf * G + cta);
-    if (!grid_sync(a.bar, G)) return;
-    reduce_partials<K>(a.part + (size_t)buf * G, G, s_tmp, s_red);
-    buf ^= 1;
-    const double beta = sqrt(s_red[0]);
-    if (cta == 0 && tid == 0) {
-      a.alpha[j] = alpha;
-      a.beta[j] = beta;
-    }
-    if (!(beta > 1e-13 * (fabs(alpha) + beta_prev + 1e-300)) || j + 1 == a.m) {
-      m_eff = j + 1;
-      break;
-    }
-    // v_{j+1} = w / beta into the v_{j-1} slot, then rotate
-    const double inv = 1.0 / beta;
-    for (int i = r0 + tid; i < r1; i += kBlock) vp[i] = __ldcg(w + i) * inv;
-    double* t = vp; vp = vc; vc = t;
-    beta_prev = beta;
-    if (!grid_sync(a.bar, G)) return;
-  }
-  if (cta == 0) {
-    __syncthreads();
-    if (tid < 4) {
-      const int mm = (tid & 1) ? (m_eff > a.check ? m_eff - a.check : m_eff) : m_eff;
-      double* al = a.alpha;
-      double* be = a.beta;
-      const double th = (tid < 2) ? tridiag_eig(al, be, mm, mm - 1) : tridiag_eig(al, be, mm, 0);
-      a.out[tid] = th;
-    }
-    if (tid == 0) a.out[4] = (double)m_eff;
-  }
-}
-
-#endif  // WL_LANCZOS_KERNELS
 
 // ------------------------------------------------------------------ one Lanczos step on L
 struct LanczosStepArgs {

@@ -1,0 +1,402 @@
+// Spectral scale (Sec. 4.1 and Prop. whe-we-converge): the largest
+// eigenpair of Op = c0 I + cA A + cD D (k = 1) by Lanczos, for lambda_max(A)
+// and for the spectral-radius search of Z_mu.
+//
+// The basis is stored (double-float, one float2 per node: hi, lo), so a run
+// can end with its Ritz vector, which then starts the next run (the search
+// over lambda evaluates nearby operators; a warm start needs few steps).
+// Every element operation is FP32 arithmetic on double-float values (GB300
+// runs FP64 at 1/64 of the FP32 rate); the scalars are FP64.
+//
+// Step j (two kernels, no host synchronisation between steps):
+//   S: v_j = w_{j-1} / beta_{j-1} (stored in V_j), w_j = Op v_j computed from
+//      the raw w_{j-1} gathered and scaled once per row; alpha_j = (v_j, w_j)
+//   U: w_j -= alpha_j v_j + beta_{j-1} v_{j-1}; beta_j = |w_j|
+// Rows: more than kHubDeg entries -> one CTA each; kSpWarpDeg < deg <=
+// kHubDeg -> one warp each (listed at build time); the rest one thread each.
+// After every few steps one CTA finds the two largest eigenvalues of T_m
+// (Sturm multisection), the top eigenvector y of T_m (inverse iteration) and
+// the error bound min(r, r^2 / gap), r = beta_m |y_m|, and stops the run once
+// the bound is below rtol |theta_1|.
+#pragma once
+#include "wl_cg2.cuh"
+#include "wl_df.cuh"
+
+namespace wl {
+
+constexpr int kSpMax = 256;     // Lanczos steps held per run
+constexpr int kSpWarpDeg = 32;  // rows with more entries (up to kHubDeg) get a warp each
+
+struct SpState {
+  double alpha[kSpMax];
+  double beta[kSpMax];
+  double y[kSpMax];     // top eigenvector of T_m (unit)
+  double start_norm;    // |w_{-1}|: norm of the raw start vector
+  double out[8];        // theta_1, theta_2, r = beta_m |y_m|, bound, m, |u|^2, u^T D u
+  int m_eff;            // steps done (before a breakdown)
+  int stop;             // the run is finished (converged, broken down or at its cap)
+  int brk;              // exact breakdown: T_m holds exact eigenvalues
+  unsigned ticket;
+};
+
+struct SpArgs {
+  PhaseGraph g;
+  const int32_t* mid;  // rows with kSpWarpDeg < deg <= kHubDeg
+  int nmid;
+  int nmid_blk;        // CTAs that walk the mid rows (after the hub CTAs)
+  double c0, cA, cD;
+  float2* V;           // basis, V_j at V + j n
+  float2* W[2];        // raw w vectors (ping-pong): step j writes W[j & 1], gathers W[(j - 1) & 1]
+  double* part;
+  SpState* st;
+  int j;
+  uint64_t seed;
+};
+
+#ifdef WL_SPEC_KERNELS
+__device__ __forceinline__ df ld_df2(const float2* p) {
+  const float2 v = *p;
+  return df{v.x, v.y};
+}
+
+__device__ __forceinline__ void st_df2(float2* p, df v) { *p = make_float2(v.hi, v.lo); }
+
+__device__ inline double sp_start(int64_t i, uint64_t seed) {
+  uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + seed;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return 1.0 + 0.25 * ((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+}
+
+// fresh run: seeded positive start vector into W[1], its norm, state reset
+__global__ void __launch_bounds__(kPhaseBlock) sp_init(SpArgs a) {
+  __shared__ double s_tmp[kPhaseBlock];
+  __shared__ double s_out[1];
+  double acc[1] = {0.0};
+  float2* W = a.W[1];
+  for (int64_t i = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; i < a.g.n; i += (int64_t)gridDim.x * kPhaseBlock) {
+    const float x = (float)sp_start(i, a.seed);  // any start vector will do: keep it exactly representable
+    W[i] = make_float2(x, 0.f);
+    acc[0] += (double)x * (double)x;
+  }
+  if (!block_partials_last<double, 1>(acc, a.part, &a.st->ticket)) return;
+  sum_partials<1>(a.part, gridDim.x, s_tmp, s_out);
+  if (threadIdx.x == 0) {
+    a.st->start_norm = sqrt(s_out[0]);
+    a.st->stop = 0;
+    a.st->brk = 0;
+    a.st->m_eff = 0;
+    a.st->ticket = 0;
+  }
+}
+
+// resume = 0: a new run from the vector in W[1] (whose norm is start_norm);
+// resume = 1: continue the current run (unless it broke down)
+__global__ void sp_restart(SpState* st, int resume) {
+  if (threadIdx.x == 0) {
+    if (resume) {
+      if (!st->brk) st->stop = 0;
+    } else {
+      st->stop = 0;
+      st->brk = 0;
+      st->m_eff = 0;
+      st->ticket = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPhaseBlock) sp_s(SpArgs a) {
+  __shared__ float s_red[3][kPhaseBlock];
+  __shared__ double s_tmp[kPhaseBlock];
+  __shared__ double s_out[1];
+  SpState* st = a.st;
+  if (*(volatile int*)&st->stop) return;
+  const int j = a.j;
+  const double bprev = (j == 0) ? st->start_norm : st->beta[j - 1];
+  const df inv = df_from_double(1.0 / bprev);
+  const df c0 = df_from_double(a.c0), cA = df_from_double(a.cA), cD = df_from_double(a.cD);
+  const float2* __restrict__ Wp = a.W[(j + 1) & 1];
+  float2* Wc = a.W[j & 1];
+  float2* Vj = a.V + (size_t)j * a.g.n;
+  const int tid = threadIdx.x;
+  float aS = 0.f, aC = 0.f;
+  // neighbour sum (s, c, l) of the raw previous vector -> this row's v, w
+  auto fin = [&](int64_t row, int deg, float s, float c, float l) {
+    const df nb = df_mul(two_sum(s, c + l), inv);
+    const df v = df_mul(ld_df2(Wp + row), inv);
+    const df crow = df_add(c0, df_mul_f(cD, (float)deg));
+    const df w = df_add(df_mul(crow, v), df_mul(cA, nb));
+    st_df2(Vj + row, v);
+    st_df2(Wc + row, w);
+    df_acc2(aS, aC, df_mul(v, w));
+  };
+  auto gather = [&](int beg, int end, int step, float& s, float& c, float& l) {
+    int e = beg;
+    for (; e + 3 * step < end; e += 4 * step) {
+      const int j0 = __ldg(a.g.col + e), j1 = __ldg(a.g.col + e + step);
+      const int j2 = __ldg(a.g.col + e + 2 * step), j3 = __ldg(a.g.col + e + 3 * step);
+      const float2 x0 = Wp[j0], x1 = Wp[j1], x2 = Wp[j2], x3 = Wp[j3];
+      df_acc(s, c, x0.x);
+      df_acc(s, c, x1.x);
+      df_acc(s, c, x2.x);
+      df_acc(s, c, x3.x);
+      l += (x0.y + x1.y) + (x2.y + x3.y);
+    }
+    for (; e < end; e += step) {
+      const float2 x0 = Wp[__ldg(a.g.col + e)];
+      df_acc(s, c, x0.x);
+      l += x0.y;
+    }
+  };
+  const int b = blockIdx.x;
+  if (b < a.g.nhub) {
+    const int64_t row = a.g.hubs[b];
+    const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
+    float s = 0.f, c = 0.f, l = 0.f;
+    gather(beg + tid, end, kPhaseBlock, s, c, l);
+    s_red[0][tid] = s;
+    s_red[1][tid] = c;
+    s_red[2][tid] = l;
+    __syncthreads();
+    if (tid == 0) {
+      for (int t = 1; t < kPhaseBlock; ++t) {
+        const df u = two_sum(s, s_red[0][t]);
+        s = u.hi;
+        c += u.lo + s_red[1][t];
+        l += s_red[2][t];
+      }
+      fin(row, end - beg, s, c, l);
+    }
+  } else if (b < a.g.nhub + a.nmid_blk) {
+    const int lane = tid & 31;
+    const int wg = (b - a.g.nhub) * (kPhaseBlock / 32) + (tid >> 5);
+    for (int r = wg; r < a.nmid; r += a.nmid_blk * (kPhaseBlock / 32)) {
+      const int64_t row = a.mid[r];
+      const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
+      float s = 0.f, c = 0.f, l = 0.f;
+      for (int e = beg + lane; e < end; e += 32) {
+        const float2 x = Wp[__ldg(a.g.col + e)];
+        df_acc(s, c, x.x);
+        l += x.y;
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s, off);
+        const float co = __shfl_xor_sync(0xffffffffu, c, off);
+        const float lo = __shfl_xor_sync(0xffffffffu, l, off);
+        const df u = two_sum(s, so);
+        s = u.hi;
+        c += u.lo + co;
+        l += lo;
+      }
+      if (lane == 0) fin(row, end - beg, s, c, l);
+    }
+  } else {
+    const int64_t nblk = (int64_t)gridDim.x - a.g.nhub - a.nmid_blk;
+    const int bt = b - a.g.nhub - a.nmid_blk;
+    const int lim = a.nmid_blk > 0 ? kSpWarpDeg : kHubDeg;
+    for (int64_t row = (int64_t)bt * kPhaseBlock + tid; row < a.g.n; row += nblk * kPhaseBlock) {
+      const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
+      if (end - beg > lim) continue;
+      float s = 0.f, c = 0.f, l = 0.f;
+      gather(beg, end, 1, s, c, l);
+      fin(row, end - beg, s, c, l);
+    }
+  }
+  double acc[1] = {(double)aS + (double)aC};
+  if (!block_partials_last<double, 1>(acc, a.part, &st->ticket)) return;
+  sum_partials<1>(a.part, gridDim.x, s_tmp, s_out);
+  if (tid == 0) {
+    st->alpha[j] = s_out[0];
+    st->ticket = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kPhaseBlock) sp_u(SpArgs a, int last) {
+  __shared__ double s_tmp[kPhaseBlock];
+  __shared__ double s_out[1];
+  SpState* st = a.st;
+  if (*(volatile int*)&st->stop) return;
+  const int j = a.j;
+  const double al = st->alpha[j];
+  const double bp = (j == 0) ? 0.0 : st->beta[j - 1];
+  const df dal = df_from_double(al), dbp = df_from_double(bp);
+  float2* Wc = a.W[j & 1];
+  const float2* Vj = a.V + (size_t)j * a.g.n;
+  const float2* Vm = a.V + (size_t)(j > 0 ? j - 1 : 0) * a.g.n;
+  float aS = 0.f, aC = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; i < a.g.n; i += (int64_t)gridDim.x * kPhaseBlock) {
+    df w = df_sub(ld_df2(Wc + i), df_mul(dal, ld_df2(Vj + i)));
+    if (j > 0) w = df_sub(w, df_mul(dbp, ld_df2(Vm + i)));
+    st_df2(Wc + i, w);
+    df_acc2(aS, aC, df_mul(w, w));
+  }
+  double acc[1] = {(double)aS + (double)aC};
+  if (!block_partials_last<double, 1>(acc, a.part, &st->ticket)) return;
+  sum_partials<1>(a.part, gridDim.x, s_tmp, s_out);
+  if (threadIdx.x == 0) {
+    const double b = sqrt(fmax(s_out[0], 0.0));
+    st->beta[j] = b;
+    st->m_eff = j + 1;
+    // invariant subspace reached: T_{j+1} is exact
+    if (!(b > 1e-13 * (fabs(al) + bp + 1e-300))) {
+      st->brk = 1;
+      st->stop = 1;
+    } else if (last) {
+      st->stop = 1;
+    }
+    st->ticket = 0;
+  }
+}
+
+// Number of eigenvalues of T_m below x from the signs of the leading
+// principal minors p_i(x) (Sturm sequence), with no division: p_{i+1} =
+// (alpha_i - x) p_i - beta_{i-1}^2 p_{i-1}, rescaled by powers of two to
+// stay in range; a zero minor takes the sign opposite to its predecessor.
+__device__ inline int sturm_count_poly(const double* a, const double* b, int m, double x) {
+  double pm = 1.0, p = a[0] - x;
+  int cnt = (p < 0.0) ? 1 : 0;
+  double sprev = (p == 0.0) ? -1.0 : p;
+  for (int i = 1; i < m; ++i) {
+    const double pn = (a[i] - x) * p - (b[i - 1] * b[i - 1]) * pm;
+    pm = p;
+    p = pn;
+    const double ap = fabs(p);
+    if (ap > 0x1p500) {
+      p *= 0x1p-500;
+      pm *= 0x1p-500;
+    } else if (ap < 0x1p-500 && fabs(pm) < 0x1p-500) {
+      p *= 0x1p500;
+      pm *= 0x1p500;
+    }
+    const double sc = (p == 0.0) ? -sprev : p;
+    if ((sc < 0.0) != (sprev < 0.0)) ++cnt;
+    sprev = sc;
+  }
+  return cnt;
+}
+
+// Two largest eigenvalues of T_m by multisection (a group of kSpEigT threads
+// per eigenvalue, kSpEigRounds rounds of kSpEigT Sturm counts: 129^7 > 1e14),
+// then the top eigenvector by inverse iteration and the error bound; stops
+// the run when the bound is below rtol |theta_1| (or after a breakdown).
+constexpr int kSpEigT = 128;
+constexpr int kSpEigRounds = 7;
+
+__global__ void __launch_bounds__(2 * kSpEigT) sp_eig(SpState* st, double rtol) {
+  __shared__ double s_lo[2], s_hi[2];
+  __shared__ int s_cnt[2][kSpEigT];
+  const int m = st->m_eff;
+  if (m <= 0 || m > kSpMax) return;
+  const int grp = threadIdx.x / kSpEigT, t = threadIdx.x % kSpEigT;
+  const int idx = grp == 0 ? m - 1 : (m >= 2 ? m - 2 : m - 1);
+  if (t == 0) {
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < m; ++i) {
+      const double r = (i > 0 ? fabs(st->beta[i - 1]) : 0.0) + (i + 1 < m ? fabs(st->beta[i]) : 0.0);
+      lo = fmin(lo, st->alpha[i] - r);
+      hi = fmax(hi, st->alpha[i] + r);
+    }
+    s_lo[grp] = lo;
+    s_hi[grp] = hi;
+  }
+  __syncthreads();
+  for (int round = 0; round < kSpEigRounds; ++round) {
+    const double lo = s_lo[grp], w = s_hi[grp] - lo;
+    s_cnt[grp][t] = sturm_count_poly(st->alpha, st->beta, m, lo + w * (double)(t + 1) / (double)(kSpEigT + 1));
+    __syncthreads();
+    if (t == 0) {
+      int k = 0;
+      while (k < kSpEigT && s_cnt[grp][k] <= idx) ++k;
+      s_lo[grp] = lo + w * (double)k / (double)(kSpEigT + 1);
+      s_hi[grp] = lo + w * (double)(k + 1) / (double)(kSpEigT + 1);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double th1 = 0.5 * (s_lo[0] + s_hi[0]);
+  const double th2 = 0.5 * (s_lo[1] + s_hi[1]);
+  // inverse iteration on T_m - sigma I (Thomas algorithm, tiny pivots
+  // replaced), sigma just above theta_1
+  double* y = st->y;
+  double tn = 0.0;
+  for (int i = 0; i < m; ++i) tn = fmax(tn, fabs(st->alpha[i]) + (i > 0 ? fabs(st->beta[i - 1]) : 0.0) +
+                                             (i + 1 < m ? fabs(st->beta[i]) : 0.0));
+  const double sigma = th1 + 1e-13 * (tn + 1e-300);
+  const double tiny = 1e-300 + 1e-15 * tn;
+  for (int i = 0; i < m; ++i) y[i] = 1.0 + 0.01 * (double)(i % 7);
+  double cp[kSpMax];
+  for (int it = 0; it < 2; ++it) {
+    // forward sweep: T - sigma I = L U, solve in place (one division a row)
+    double piv = st->alpha[0] - sigma;
+    if (fabs(piv) < tiny) piv = tiny;
+    double rp = 1.0 / piv;
+    cp[0] = (m > 1 ? st->beta[0] : 0.0) * rp;
+    y[0] = y[0] * rp;
+    for (int i = 1; i < m; ++i) {
+      const double bl = st->beta[i - 1];
+      piv = (st->alpha[i] - sigma) - bl * cp[i - 1];
+      if (fabs(piv) < tiny) piv = tiny;
+      rp = 1.0 / piv;
+      cp[i] = (i + 1 < m ? st->beta[i] : 0.0) * rp;
+      y[i] = (y[i] - bl * y[i - 1]) * rp;
+    }
+    for (int i = m - 2; i >= 0; --i) y[i] -= cp[i] * y[i + 1];
+    double nn = 0.0;
+    for (int i = 0; i < m; ++i) nn += y[i] * y[i];
+    const double s = 1.0 / sqrt(nn);
+    for (int i = 0; i < m; ++i) y[i] *= s;
+  }
+  const double r = fabs(st->beta[m - 1] * y[m - 1]);
+  const double gap = th1 - th2;
+  double bound = r;
+  if (gap > 0.0) bound = fmin(r, r * r / gap);
+  if (st->brk) bound = 0.0;
+  st->out[0] = th1;
+  st->out[1] = th2;
+  st->out[2] = r;
+  st->out[3] = bound;
+  st->out[4] = (double)m;
+  if (bound <= rtol * fabs(th1)) st->stop = 1;
+}
+
+// Ritz vector u = V_m y into W[1] (the start of the next run), |u|^2 and
+// u^T D u into out[5], out[6], start_norm = |u|
+__global__ void __launch_bounds__(kPhaseBlock) sp_ritz(SpArgs a) {
+  __shared__ double s_tmp[kPhaseBlock];
+  __shared__ double s_out[2];
+  __shared__ float s_y[2][kSpMax];
+  SpState* st = a.st;
+  const int m = min(max(st->m_eff, 0), kSpMax);
+  for (int j = threadIdx.x; j < m; j += kPhaseBlock) {
+    const df yy = df_from_double(st->y[j]);
+    s_y[0][j] = yy.hi;
+    s_y[1][j] = yy.lo;
+  }
+  __syncthreads();
+  float nS = 0.f, nC = 0.f, dS = 0.f, dC = 0.f;
+  float2* U = a.W[1];
+  for (int64_t i = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; i < a.g.n; i += (int64_t)gridDim.x * kPhaseBlock) {
+    float s = 0.f, c = 0.f;
+    for (int j = 0; j < m; ++j) df_acc2(s, c, df_mul(df{s_y[0][j], s_y[1][j]}, ld_df2(a.V + (size_t)j * a.g.n + i)));
+    const df u = two_sum(s, c);
+    st_df2(U + i, u);
+    const df u2 = df_mul(u, u);
+    df_acc2(nS, nC, u2);
+    df_acc2(dS, dC, df_mul_f(u2, (float)(a.g.row_ptr[i + 1] - a.g.row_ptr[i])));
+  }
+  // two column sums through the K = 2 reduction (deterministic)
+  double acc[2] = {(double)nS + (double)nC, (double)dS + (double)dC};
+  if (!block_partials_last<double, 2>(acc, a.part, &st->ticket)) return;
+  sum_partials<2>(a.part, gridDim.x, s_tmp, s_out);
+  if (threadIdx.x == 0) {
+    st->out[5] = s_out[0];
+    st->out[6] = s_out[1];
+    st->start_norm = sqrt(s_out[0]);
+    st->ticket = 0;
+  }
+}
+#endif  // WL_SPEC_KERNELS
+
+}  // namespace wl
