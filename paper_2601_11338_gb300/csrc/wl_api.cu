@@ -167,6 +167,7 @@ struct wl_handle {
   Buf spstate;            // SpState of the spectral-scale Lanczos
   Buf mid;                // rows with kSpWarpDeg < deg <= kHubDeg (a warp each in the spectral Lanczos)
   int nmid = 0, nmid_blk = 0;
+  double mid_share = 0.0; // share of the S kernels' CTAs that walk the mid rows
   double sp_c0 = 0.0, sp_cD = 0.0, sp_theta = 0.0;  // operator and Ritz value of the basis held in spV
   bool sp_ritz_ready = false;                        // W[1] holds that run's Ritz vector
   double inner_tol = 4e-6;  // floor of the FP32 correction target of the refined form
@@ -296,6 +297,18 @@ PhaseGraph phase_graph(wl_handle* h) {
   return PhaseGraph{h->g.row_ptr, h->g.col, h->n, (const int32_t*)h->hubs.p, h->nhub};
 }
 
+// the graph as seen by an S kernel of grid_u CTAs (plus the hub CTAs) that
+// walks the mid rows with a warp each
+PhaseGraph phase_graph_mid(wl_handle* h, int grid_u) {
+  PhaseGraph g = phase_graph(h);
+  if (h->nmid > 0 && grid_u > 1) {
+    g.mids = (const int32_t*)h->mid.p;
+    g.nmid = h->nmid;
+    g.nmid_blk = (int)std::min<long>(grid_u - 1, std::max<long>(1, std::lround(h->mid_share * grid_u)));
+  }
+  return g;
+}
+
 constexpr int kChunk = 8;  // CG iterations launched between two reads of the device flag
 
 // Runs the CG iterations of an initialised solve state to completion (or the
@@ -379,7 +392,7 @@ int solve_fp64(wl_handle* h, const double* b, double* x, int K, double tol, bool
     bn2 = st->b2;
     info.nnz_rhs += (double)h->nnz * K;
   }
-  PhaseArgs<double> a{phase_graph(h), x, (double*)h->r.p, (double*)h->p.p, (double*)h->q.p, h->ca, h->cA, h->cD,
+  PhaseArgs<double> a{phase_graph_mid(h, grid_u), x, (double*)h->r.p, (double*)h->p.p, (double*)h->q.p, h->ca, h->cA, h->cD,
                       bn2, nullptr, (double*)h->part.p, st, h->prm.max_iter, tol * tol};
   WL_TRY(run_cg<double>(h, K, a, grid_s, grid_u, info, 8));
   info.max_rel = std::max(info.max_rel, info.last_rel);
@@ -426,7 +439,7 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
     // r = B - M x0 (x0 split into two FP32 terms and gathered whole)
     counted(h, 2);
     WL_CU(launch_split_x(x0, (int64_t)nk, xh, xl, false, nullptr, S(h)));
-    DfResArgs ra{phase_graph(h), xh, xl, bh, bl, rh, rl, (float*)h->r32.p, nullptr, nullptr, nullptr,
+    DfResArgs ra{phase_graph_mid(h, grid_r - h->nhub), xh, xl, bh, bl, rh, rl, (float*)h->r32.p, nullptr, nullptr, nullptr,
                  ca, cA, cD, (double*)h->part.p, st, 0};
     const int pi = prof_begin(h, kCatRes);
     WL_CU(launch_df_res(K, ra, grid_r, true, S(h)));
@@ -464,7 +477,7 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
     int* dskip = (int*)((double*)h->small.p + 256);
     WL_CU(cudaMemcpyAsync(dskip, skip, K * sizeof(int), cudaMemcpyHostToDevice, S(h)));
     WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
-    PhaseArgs<float> a{phase_graph(h), dcur, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
+    PhaseArgs<float> a{phase_graph_mid(h, grid_u), dcur, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
                        h->ca, h->cA, h->cD, nullptr, dskip, (double*)h->part.p, st, h->prm.max_iter,
                        inner_tol * inner_tol};
     SolveInfo inner;
@@ -479,7 +492,7 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
     info.bytes += inner.bytes;
     // r <- r - M d, x <- x + d, next correction buffer zeroed
     WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
-    DfResArgs ra{phase_graph(h), dcur, nullptr, rch, rcl, rh, rl, (float*)h->r32.p, xh, xl, dnext,
+    DfResArgs ra{phase_graph_mid(h, grid_r - h->nhub), dcur, nullptr, rch, rcl, rh, rl, (float*)h->r32.p, xh, xl, dnext,
                  ca, cA, cD, (double*)h->part.p, st, x_zero ? 1 : 0};
     const int pi = prof_begin(h, kCatRes);
     counted(h);
@@ -1009,6 +1022,30 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
     if (e != cudaSuccess) return fail(set_cuda_error(e, "mid-row list"));
     h->nmid = (int)*(int64_t*)h->h_pin;
     h->nmid_blk = h->nmid > 0 ? (int)std::min<int64_t>((h->nmid + 31) / 32, 2 * 152) : 0;
+    // share of the S kernels' CTAs for the mid rows: a warp takes about 32
+    // entries per round on either path, but a mid row pays the fixed cost of
+    // a row (pointers, own-row vectors, finish: ~3 rounds) for a whole warp,
+    // a short row for a lane group (1/8 of a warp at K = 16 FP32)
+    h->mid_share = 0.0;
+    if (h->nmid > 0) {
+      unsigned long long* cnt = (unsigned long long*)h->h_pin;
+      unsigned long long* dsum = (unsigned long long*)((double*)h->small.p + 900);
+      double ent[2];
+      const int32_t* lists[2] = {(const int32_t*)h->mid.p, (const int32_t*)h->hubs.p};
+      const int64_t counts[2] = {h->nmid, h->nhub};
+      for (int li = 0; li < 2; ++li) {
+        e = launch_list_entries(h->g.row_ptr, lists[li], counts[li], dsum, S(h));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, dsum, 8, cudaMemcpyDeviceToHost, S(h));
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S(h));
+        if (e != cudaSuccess) return fail(set_cuda_error(e, "mid-row entries"));
+        ent[li] = (double)*cnt;
+      }
+      counted(h, 4);
+      const double e_mid = ent[0], e_low = (double)h->nnz - ent[0] - ent[1];
+      const double n_low = (double)(h->n - h->nhub - h->nmid);
+      const double w_mid = e_mid / 32.0 + 3.0 * h->nmid, w_low = e_low / 32.0 + 0.375 * n_low;
+      h->mid_share = w_mid / std::max(w_mid + w_low, 1e-300);
+    }
   }
 
   // spectral scale and parameters
@@ -1513,8 +1550,9 @@ int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, u
     CgState* st = h->cgst();
     WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
     const double tol = std::max(h->prm.tol, 1e-7);
-    PhaseArgs<float> a{phase_graph(h), (float*)h->x.p, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
-                       h->ca, h->cA, h->cD, nullptr, nullptr, (double*)h->part.p, st, h->prm.max_iter, tol * tol};
+    PhaseArgs<float> a{phase_graph_mid(h, grid_u), (float*)h->x.p, (float*)h->r32.p, (float*)h->p.p,
+                       (float*)h->q.p, h->ca, h->cA, h->cD, nullptr, nullptr, (double*)h->part.p, st,
+                       h->prm.max_iter, tol * tol};
     if ((rc = run_cg<float>(h, K, a, grid_s, grid_u, info, 4)) != WL_OK) break;
     (void)sm;
     counted(h, 3);

@@ -6,7 +6,11 @@
 // The gather of neighbour vectors is latency bound, so these kernels keep
 // the SMs full of warps (G lanes per row, one 16-byte slice each, rows
 // spread over a grid-stride loop) instead of persisting with few warps.
-// Rows with more than kHubDeg entries are gathered by one CTA each.
+// Rows with more than kHubDeg entries are gathered by one CTA each; when the
+// graph carries a list of mid rows (kMidDeg < deg <= kHubDeg), the S kernel
+// spends a share of its CTAs (proportional to those rows' entries) on them,
+// one warp per row, so that no lane group walks a long row alone, and the
+// remaining CTAs take the short rows; the grid stays one wave.
 //
 // One iteration = two kernels:
 //   S: s = M r ; x += alpha p ; p = r + beta p ; q = s + beta q ; delta = (p, q)
@@ -22,6 +26,7 @@
 namespace wl {
 
 constexpr int kHubDeg = 256;       // rows with more entries get a CTA each
+constexpr int kMidDeg = 30;        // rows with more entries (up to kHubDeg) get a warp each in the S kernels
 constexpr int kPhaseBlock = 256;   // threads per CTA of the phase kernels
 #ifndef WL_PHASE_MINB
 #define WL_PHASE_MINB 5
@@ -44,6 +49,9 @@ struct PhaseGraph {
   int64_t n;
   const int32_t* hubs;  // rows with deg > kHubDeg
   int nhub;
+  const int32_t* mids = nullptr;  // rows with kMidDeg < deg <= kHubDeg
+  int nmid = 0;
+  int nmid_blk = 0;               // CTAs (after the hub CTAs) that walk the mid rows; 0: no mid path
 };
 
 template <typename T>
@@ -238,11 +246,33 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) cg_s_phase(Phase
         for (int v = 0; v < VW; ++v) acc[v] += s_red[(gr * G + sl) * VW + v];
       fin(row, end - beg, acc, w);
     }
-  } else {
-    const int64_t nblk = (int64_t)gridDim.x - a.g.nhub;
-    for (int64_t row = ((int64_t)blockIdx.x - a.g.nhub) * RPB + tid / G; row < a.g.n; row += nblk * RPB) {
+  } else if ((int)blockIdx.x < a.g.nhub + a.g.nmid_blk) {
+    // mid rows, one warp each: the 32 / G lane groups stride over the entries
+    // and are combined by shuffles; lane group 0 finishes the row
+    const int lane = tid & 31;
+    constexpr int WPB = kPhaseBlock / 32;
+    for (int r = ((int)blockIdx.x - a.g.nhub) * WPB + (tid >> 5); r < a.g.nmid; r += a.g.nmid_blk * WPB) {
+      const int64_t row = a.g.mids[r];
       const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
-      if (end - beg > kHubDeg) continue;  // gathered by a hub CTA
+      Own w;
+      if (lane < G) w = own(row);
+      T acc[VW];
+#pragma unroll
+      for (int v = 0; v < VW; ++v) acc[v] = T(0);
+      row_gather<T, K, VW>(a.g.col, beg + lane / G, end, 32 / G, a.r, lane_off, acc);
+#pragma unroll
+      for (int off = G; off < 32; off <<= 1)
+#pragma unroll
+        for (int v = 0; v < VW; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+      if (lane < G) fin(row, end - beg, acc, w);
+    }
+  } else {
+    const int nlist = a.g.nhub + a.g.nmid_blk;
+    const int lim = a.g.nmid_blk > 0 ? kMidDeg : kHubDeg;  // longer rows: hub CTAs or mid warps
+    const int64_t nblk = (int64_t)gridDim.x - nlist;
+    for (int64_t row = ((int64_t)blockIdx.x - nlist) * RPB + tid / G; row < a.g.n; row += nblk * RPB) {
+      const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
+      if (end - beg > lim) continue;
       const Own w = own(row);
       T acc[VW];
 #pragma unroll

@@ -104,6 +104,10 @@ void thresholds_f32(int K, int* Tw, int* Tc);
 cudaError_t launch_row_list(const int32_t* row_ptr, int64_t n, int lo, int hi, int32_t* rows, int64_t* tmp,
                             int64_t* count, cudaStream_t s);
 
+// sum of the degrees of the listed rows into *out (device)
+cudaError_t launch_list_entries(const int32_t* row_ptr, const int32_t* rows, int64_t count, unsigned long long* out,
+                                cudaStream_t s);
+
 // ---- wl_k_lanczos.cu
 int lanczos_step_grid(int K);
 cudaError_t launch_lanczos_step(int K, const LanczosStepArgs& a, int G, cudaStream_t s);

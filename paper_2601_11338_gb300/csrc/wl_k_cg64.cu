@@ -125,6 +125,24 @@ void thresholds_f64(int K, int* Tw, int* Tc) {
   *Tw = *Tc = 0;
 }
 
+// entries of the rows in a list (sum of their degrees)
+__global__ void k_list_entries(const int32_t* row_ptr, const int32_t* rows, int64_t count, unsigned long long* out) {
+  unsigned long long s = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    s += (unsigned long long)(row_ptr[rows[i] + 1] - row_ptr[rows[i]]);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+cudaError_t launch_list_entries(const int32_t* row_ptr, const int32_t* rows, int64_t count, unsigned long long* out,
+                                cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess || count <= 0) return e;
+  const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152 * 8));
+  k_list_entries<<<gb, 256, 0, s>>>(row_ptr, rows, count, out);
+  return cudaGetLastError();
+}
+
 // row lists: rows with lo < deg <= hi, in increasing row order
 __global__ void k_row_flags(const int32_t* row_ptr, int64_t n, int lo, int hi, int64_t* flag) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {

@@ -173,11 +173,38 @@ __global__ void __launch_bounds__(kPhaseBlock, 4) df_res(DfResArgs a) {
         }
       fin(row, end - beg, s, c, l);
     }
-  } else {
-    const int64_t nblk = (int64_t)gridDim.x - a.g.nhub;
-    for (int64_t row = ((int64_t)blockIdx.x - a.g.nhub) * RPB + tid / G; row < a.g.n; row += nblk * RPB) {
+  } else if ((int)blockIdx.x < a.g.nhub + a.g.nmid_blk) {
+    // mid rows, one warp each (as in the CG S kernel)
+    const int lane = tid & 31;
+    constexpr int WPB = kPhaseBlock / 32;
+    for (int r = ((int)blockIdx.x - a.g.nhub) * WPB + (tid >> 5); r < a.g.nmid; r += a.g.nmid_blk * WPB) {
+      const int64_t row = a.g.mids[r];
       const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
-      if (end - beg > kHubDeg) continue;  // gathered by a hub CTA
+      float s[VW], c[VW], l[VW];
+#pragma unroll
+      for (int v = 0; v < VW; ++v) s[v] = c[v] = l[v] = 0.f;
+      df_row_gather<K, VW, FULL>(a.g.col, beg + lane / G, end, 32 / G, a.yh, a.yl, lane_off, s, c, l);
+#pragma unroll
+      for (int off = G; off < 32; off <<= 1)
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          const float so = __shfl_xor_sync(0xffffffffu, s[v], off);
+          const float co = __shfl_xor_sync(0xffffffffu, c[v], off);
+          const float lo = __shfl_xor_sync(0xffffffffu, l[v], off);
+          const df t = two_sum(s[v], so);
+          s[v] = t.hi;
+          c[v] += t.lo + co;
+          l[v] += lo;
+        }
+      if (lane < G) fin(row, end - beg, s, c, l);
+    }
+  } else {
+    const int nlist = a.g.nhub + a.g.nmid_blk;
+    const int lim = a.g.nmid_blk > 0 ? kMidDeg : kHubDeg;  // longer rows: hub CTAs or mid warps
+    const int64_t nblk = (int64_t)gridDim.x - nlist;
+    for (int64_t row = ((int64_t)blockIdx.x - nlist) * RPB + tid / G; row < a.g.n; row += nblk * RPB) {
+      const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
+      if (end - beg > lim) continue;
       float s[VW], c[VW], l[VW];
 #pragma unroll
       for (int v = 0; v < VW; ++v) s[v] = c[v] = l[v] = 0.f;

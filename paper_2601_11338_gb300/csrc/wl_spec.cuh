@@ -25,7 +25,7 @@
 namespace wl {
 
 constexpr int kSpMax = 256;     // Lanczos steps held per run
-constexpr int kSpWarpDeg = 32;  // rows with more entries (up to kHubDeg) get a warp each
+constexpr int kSpWarpDeg = kMidDeg;  // rows with more entries (up to kHubDeg) get a warp each
 
 struct SpState {
   double alpha[kSpMax];
