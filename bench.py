@@ -281,7 +281,7 @@ def run_ours(args):
     peak, peak_kind = peaks()
     fams = {"cg": kcg_ms, "residual64": kres_ms, "lanczos_step": klan_ms}
     achieved = (kcg_bytes / (kcg_ms / 1000.0)) / 1e9 if kcg_ms > 0 else 0.0
-    traffic = recorded_traffic("cg_persistent_f32_k16")
+    traffic = recorded_traffic("cg_phase_f32_k16")
     roof = {"bound": "hbm", "kernel": "CG iteration kernels cg_s_phase<float,16> + cg_u_phase<float,16>", "achieved": achieved, "peak": peak,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
             "traffic": (traffic * kcg_iters / max(kcg_launches, 1)) if traffic else None,

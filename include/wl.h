@@ -61,7 +61,7 @@ extern "C" {
 #define WL_ERR_TIMEOUT        -9  /* a bounded device-side wait expired; kernel returned early */
 #define WL_ERR_OOM           -10  /* device allocation failed */
 #define WL_ERR_CUDA          -11  /* other CUDA runtime error (message via wl_last_error) */
-#define WL_ERR_UNSUPPORTED   -12  /* combination not provided (e.g. exp with mu > 0) */
+#define WL_ERR_UNSUPPORTED   -12  /* combination not provided (e.g. the trace of the exponential) */
 
 /* ------------------------------------------------------------ enums */
 typedef enum {
@@ -72,7 +72,8 @@ typedef enum {
 
 typedef enum {
   WL_F_RESOLVENT = 0, /* c_k = alpha^k, f(x) = (1 - alpha x)^{-1}  (Sec. 3.2.1) */
-  WL_F_EXP       = 1, /* c_k = beta^k / k!, f(x) = exp(beta x); all-walk (mu = 0) only */
+  WL_F_EXP       = 1, /* c_k = beta^k / k!, f(x) = exp(beta x) (Def. BDTW-Laplacian), any mu:
+                         phi V is summed term by term over the walk counts of Eq. qrec */
   WL_F_IDENTITY  = 2  /* c = (0, 1, 0, ...): phi = A, L = D - A (Sec. 3.1) */
 } wl_func;
 
@@ -165,6 +166,21 @@ int wl_apply(wl_handle* h, const double* V, int64_t ldv, int k, double* W, int64
  * ldo. taus is a host array of ntau values >= 0. */
 int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* taus, int ntau,
              double* U, int64_t ldo, wl_stats* st);
+
+/* Discrete-time diffusion (Sec. 3.3, Eq. let_there_be_markov): the chain
+ * p_{s+1} = p_s P with P = I - D^{-1} L = D^{-1} phi, where D = diag(phi 1)
+ * holds the walk degrees D_f (the reading under which the chain needs one
+ * evaluation of the matrix function and reproduces the stationary
+ * distributions printed in Fig. 1: pi = D_f / 1^T D_f). In column form one
+ * step is p <- phi (p / D_f): a diagonal scale and one resolvent solve for
+ * all k columns (for WL_F_IDENTITY, phi = A: the simple random walk).
+ * P0 is n x k (ld ldp, columns are start distributions, host or device);
+ * steps is a host array of nsteps non-decreasing step counts >= 0; out
+ * (host or device) holds nsteps blocks, block t at out + t * n * ldo, each
+ * n x k with leading dimension ldo: the distributions after steps[t] steps.
+ * 1 <= nsteps <= 64. */
+int wl_markov(wl_handle* h, const double* P0, int64_t ldp, int k, const int* steps, int nsteps, double* out,
+              int64_t ldo, wl_stats* st);
 
 /* XNysTrace estimate of tr(phi) with M Gaussian test vectors (Alg. 1,
  * "XNysTrace(Y, Omega)"). Omega (n x M) is drawn on the device by

@@ -143,3 +143,19 @@ def markov_stationary(phi):
     i = int(np.argmin(np.abs(w - 1.0)))
     pi = np.real(V[:, i])
     return pi / pi.sum()
+
+
+def markov_evolve(phi, P0, steps):
+    """Distributions of the discrete-time chain p_{s+1} = p_s P of Sec. 3.3
+    (Eq. let_there_be_markov) with D = diag(phi 1), i.e. P = D^{-1} phi, after
+    each step count in `steps` (non-decreasing). P0 holds start distributions
+    as columns; in column form a step is p <- P^T p."""
+    d = walk_degrees(phi)
+    P = phi / d[:, None]
+    out, cur, s = [], np.array(P0, dtype=np.float64), 0
+    for t in steps:
+        while s < t:
+            cur = P.T @ cur
+            s += 1
+        out.append(cur.copy())
+    return out

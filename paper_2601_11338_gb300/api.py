@@ -24,7 +24,7 @@ class WalkLaplacian:
 
     def __init__(self, row_ptr, col_idx, n, variant="allwalk", f="resolvent", alpha=0.0, alpha_rel=0.0,
                  mu=0.0, prec="fp64", tol=1e-12, max_iter=0, max_outer=0, outer_tol=0.0, device="cuda",
-                 stream=None, reorder=1):
+                 stream=None, reorder=1, beta=0.0):
         self.device = torch.device(device)
         if isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda:
             self.row_ptr, self.col_idx = row_ptr, col_idx
@@ -33,7 +33,7 @@ class WalkLaplacian:
         self.n = int(n)
         self.nnz = int(self.col_idx.numel())
         s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
-        self.params = wl.make_params(f=FUNCS[f], alpha=alpha, alpha_rel=alpha_rel, mu=mu, prec=PRECS[prec],
+        self.params = wl.make_params(f=FUNCS[f], alpha=alpha, alpha_rel=alpha_rel, beta=beta, mu=mu, prec=PRECS[prec],
                                      tol=tol, max_iter=max_iter, max_outer=max_outer, outer_tol=outer_tol,
                                      stream=s, reorder=reorder)
         self.build_stats = wl.wl_stats()
@@ -72,6 +72,17 @@ class WalkLaplacian:
                                                     device=U0.device)
         wl.wl_expmv(self.h, U0, k, k, taus, U, k, self.last, allow)
         return U
+
+    def markov(self, P0, steps, out=None, allow=()):
+        """Distributions of the chain P = D_f^{-1} phi after each of `steps` steps
+        (columns of P0 are start distributions)."""
+        P0 = P0.contiguous()
+        k = P0.shape[1]
+        steps = np.asarray(steps, dtype=np.int32)
+        P = out if out is not None else torch.empty((len(steps), self.n, k), dtype=torch.float64,
+                                                    device=P0.device)
+        wl.wl_markov(self.h, P0, k, k, steps, P, k, self.last, allow)
+        return P
 
     def trace(self, M, seed, omega_out=None):
         return wl.wl_trace(self.h, M, seed, omega_out, self.last)

@@ -142,6 +142,7 @@ struct wl_handle {
   Buf xh, xl;             // refined form: the iterate as two FP32 terms (x = xh + xl)
   Buf bh, bl, rh, rl;     // refined form: right-hand side and residual as two FP32 terms
   Buf dfdf, ydf;          // refined form: D_f and the Lanczos coefficients y(tau) as two FP32 terms
+  Buf ew;                 // exponential series: w_{k-1}, w_k, w_{k+1} and the sum (double-float)
   Buf part;               // partial sums
   Buf small;              // per-column scalars
   Buf Df;
@@ -448,8 +449,11 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
     rch = rh;
     rcl = rl;
   }
-  // FP32 correction target: two corrections reach tol when tol >= (inner)^2
-  const double inner_tol = std::min(1e-3, std::max(h->inner_tol, 0.5 * std::sqrt(tol)));
+  // FP32 correction target: the first correction goes as deep as FP32 CG
+  // reliably gets (the inner_tol floor) unless tol is loose; a later one only
+  // as deep as the current relative residual rel needs to reach tol (0.5 tol /
+  // rel, with the same floor)
+  const double inner0 = std::min(1e-3, std::max(h->inner_tol, 0.5 * std::sqrt(tol)));
   const int max_ref = 12;
   int ndf = 0;
   for (int ref = 0;; ++ref) {
@@ -474,6 +478,7 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
       if (info.status == WL_OK) info.status = WL_ERR_NO_CONVERGENCE;
       break;
     }
+    const double inner_tol = ref == 0 && x_zero ? inner0 : std::min(1e-3, std::max(h->inner_tol, 0.5 * tol / mx));
     int* dskip = (int*)((double*)h->small.p + 256);
     WL_CU(cudaMemcpyAsync(dskip, skip, K * sizeof(int), cudaMemcpyHostToDevice, S(h)));
     WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
@@ -542,9 +547,65 @@ int solve(wl_handle* h, const double* b, double* x, int K, bool x_is_zero, Solve
   return solve_fp64(h, b, x, K, tol, x_is_zero, info);
 }
 
+// phi V for the exponential, c_k = beta^k / k! (Def. BDTW-Laplacian): the
+// series sum_k c_k q_k V with the q_k of Eq. qrec applied term by term
+// (exp_term kernels, double-float), V and X n x K FP64 in the internal order.
+int exp_series(wl_handle* h, const double* V, double* X, int K, SolveInfo& info) {
+  const size_t nk = (size_t)h->n * K;
+  const int gu = exp_blocks(K), gs = gu + h->nhub;
+  WL_TRY(ensure(h->ew, nk * 4 * 8));
+  WL_TRY(ensure_phase_buffers(h, gs));
+  float* b = (float*)h->ew.p;
+  float* W[3][2] = {{b, b + nk}, {b + 2 * nk, b + 3 * nk}, {b + 4 * nk, b + 5 * nk}};
+  float* Ah = b + 6 * nk;
+  float* Al = b + 7 * nk;
+  CgState* st = h->cgst();
+  WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
+  const int one = 1;
+  WL_CU(cudaMemcpyAsync(&st->active, &one, sizeof(int), cudaMemcpyHostToDevice, S(h)));
+  counted(h);
+  WL_CU(launch_df_split(V, nk, W[0][0], W[0][1], S(h)));  // w_0 = V
+  WL_CU(cudaMemcpyAsync(Ah, W[0][0], nk * 4, cudaMemcpyDeviceToDevice, S(h)));  // acc = c_0 w_0
+  WL_CU(cudaMemcpyAsync(Al, W[0][1], nk * 4, cudaMemcpyDeviceToDevice, S(h)));
+  const PhaseGraph pg = phase_graph_mid(h, gu);
+  const int max_terms = std::max(h->prm.max_iter, 8);
+  const int pc = prof_begin(h, kCatCG);
+  double ck = 1.0;
+  int k = 0;
+  int* hp = (int*)h->h_pin;
+  for (;;) {
+    for (int i = 0; i < kChunk && k < max_terms; ++i, ++k) {
+      ck *= h->beta / (double)(k + 1);  // c_{k+1}
+      ExpArgs a{pg, W[k % 3][0], W[k % 3][1], W[(k + 2) % 3][0], W[(k + 2) % 3][1], W[(k + 1) % 3][0],
+                W[(k + 1) % 3][1], Ah, Al, df_from_double(h->mu), df_from_double(ck), k, max_terms,
+                (double*)h->part.p, st};
+      counted(h);
+      WL_CU(launch_exp_term(K, a, gs, S(h)));
+    }
+    WL_CU(cudaMemcpyAsync(hp, &st->active, 2 * sizeof(int), cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaStreamSynchronize(S(h)));
+    if (!hp[0] || k >= max_terms) break;
+  }
+  prof_end(h, pc);
+  WL_CU(cudaMemcpyAsync(hp, st->status, 64 * sizeof(int), cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaMemcpyAsync(hp + 64, &st->iters, sizeof(int), cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaMemcpyAsync(hp + 65, &st->active, sizeof(int), cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaStreamSynchronize(S(h)));
+  const int terms = hp[64];
+  for (int c = 0; c < K; ++c)
+    if (hp[c] != 0 && info.status == WL_OK) info.status = hp[c];
+  if (hp[65] && info.status == WL_OK) info.status = WL_ERR_NO_CONVERGENCE;  // term cap reached
+  info.iters += terms;
+  info.nnz_rhs += (double)terms * h->nnz * K;
+  counted(h);
+  WL_CU(launch_split_x(nullptr, (int64_t)nk, Ah, Al, true, X, S(h)));
+  return WL_OK;
+}
+
 // phi X for a packed block V (n x K, device): X = M^{-1} (a V) for the
 // resolvent; the result goes to X (n x K).
 int phi_apply(wl_handle* h, const double* Vp, double* X, int K, SolveInfo& info) {
+  if (h->prm.f == WL_F_EXP) return exp_series(h, Vp, X, K, info);
   const size_t nk = (size_t)h->n * K;
   WL_TRY(ensure(h->b64, nk * 8));
   // b = a V
@@ -559,6 +620,11 @@ int compute_Df(wl_handle* h, SolveInfo& info) {
   if (h->prm.f == WL_F_IDENTITY) {
     counted(h);
     WL_CU(launch_degree_vector(h->g, Df, S(h)));
+  } else if (h->prm.f == WL_F_EXP) {
+    WL_TRY(ensure(h->b64, (size_t)h->n * 8));
+    counted(h);
+    WL_CU(launch_fill((double*)h->b64.p, 1.0, h->n, S(h)));
+    WL_TRY(exp_series(h, (const double*)h->b64.p, Df, 1, info));
   } else if (h->prm.f == WL_F_RESOLVENT) {
     WL_TRY(ensure(h->b64, (size_t)h->n * 8));
     counted(h);
@@ -855,7 +921,7 @@ void free_handle(wl_handle* h) {
     pool_free(kv.second.meta);
   }
   Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
-                 &h->r32, &h->xh, &h->xl, &h->d32b, &h->bh, &h->bl, &h->rh, &h->rl, &h->dfdf, &h->ydf, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
+                 &h->r32, &h->xh, &h->xl, &h->d32b, &h->bh, &h->bl, &h->rh, &h->rl, &h->dfdf, &h->ydf, &h->ew, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
                  &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->spV, &h->spW, &h->spstate, &h->mid, &h->omega, &h->gram,
                  &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b, &h->hubs, &h->cgstate};
   for (Buf* b : bufs) release(*b);
@@ -914,8 +980,6 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
   if (p->prec != WL_FP64 && p->prec != WL_REFINED) return WL_ERR_INVALID_ARG;
   double mu = (v == WL_ALLWALK) ? 0.0 : (v == WL_NBT ? 1.0 : p->mu);
   if (!(mu >= 0.0 && mu <= 1.0)) return WL_ERR_INVALID_ARG;
-  if (p->f == WL_F_EXP && mu != 0.0) return WL_ERR_UNSUPPORTED;
-  if (p->f == WL_F_EXP) return WL_ERR_UNSUPPORTED;  // exponential variant: not provided by this build
 
   wl_handle* h = new wl_handle();
   CallScope cs__(&h->retired);
@@ -1079,6 +1143,11 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
     h->cD = 1.0;
   }
   h->beta = 0.0;
+  if (p->f == WL_F_EXP) {
+    // beta <= 0: 1 / lambda_max(A) (Sec. 4.1.2), so that the series terms fall from the start
+    h->beta = p->beta > 0.0 ? p->beta : (h->lmax > 0.0 ? 1.0 / h->lmax : 1.0);
+    if (!std::isfinite(h->beta)) return fail(WL_ERR_INVALID_ARG);
+  }
   const double ms = end_timer(h);
   if (st) {
     SolveInfo none;
@@ -1498,6 +1567,86 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
   const double ms = end_timer(h);
   if (rc == WL_OK) rc = info.status;
   fill_stats(h, st, info, rc, ms, outer_total);
+  return rc;
+}
+
+int wl_markov(wl_handle* h, const double* P0, int64_t ldp, int k, const int* steps, int nsteps, double* out,
+              int64_t ldo, wl_stats* st) {
+  CallScope cs__(h ? &h->retired : nullptr);
+  if (!h || k < 0 || nsteps < 1 || nsteps > 64 || !steps) return WL_ERR_INVALID_ARG;
+  if (k > 0 && h->n > 0 && (!P0 || !out || ldp < k || ldo < k)) return WL_ERR_INVALID_ARG;
+  for (int t = 0; t < nsteps; ++t)
+    if (steps[t] < 0 || (t > 0 && steps[t] < steps[t - 1])) return WL_ERR_INVALID_ARG;
+  SolveInfo info;
+  begin_timer(h);
+  if (k == 0 || h->n == 0) {
+    fill_stats(h, st, info, WL_OK, end_timer(h), 0);
+    return WL_OK;
+  }
+  const int64_t n = h->n;
+  int rc = WL_OK;
+  const bool o_dev = is_device_ptr(out);
+  const double* P0d = nullptr;
+  double* Od = out;
+  int nstep = 0;  // chain steps of the last column block
+  do {
+    if (!h->have_Df && (rc = compute_Df(h, info)) != WL_OK) break;
+    if ((rc = stage_in(h, h->stage_a, P0, (size_t)n * ldp * 8, (const void**)&P0d)) != WL_OK) break;
+    if (!o_dev) {
+      if ((rc = ensure(h->stage_b, (size_t)nsteps * n * ldo * 8)) != WL_OK) break;
+      Od = (double*)h->stage_b.p;
+      if (ldo != k) cudaMemcpyAsync(Od, out, (size_t)nsteps * n * ldo * 8, cudaMemcpyHostToDevice, S(h));
+    }
+    int c0 = 0;
+    for (int K : column_blocks(k)) {
+      if ((rc = ensure(h->packV, (size_t)n * K * 8)) != WL_OK) break;
+      if ((rc = ensure(h->packX, (size_t)n * K * 8)) != WL_OK) break;
+      double* cur = (double*)h->packX.p;  // p_s of this block (internal node order)
+      double* y = (double*)h->packV.p;    // p_s / D_f
+      counted(h);
+      cudaError_t e = h->perm ? launch_pack_perm(P0d, ldp, c0, K, n, 1.0, h->perm, cur, S(h))
+                              : launch_pack(P0d, ldp, c0, K, n, 1.0, cur, false, S(h));
+      if (e != cudaSuccess) { rc = set_cuda_error(e, "markov pack"); break; }
+      int s = 0;
+      nstep = 0;
+      for (int t = 0; t < nsteps && rc == WL_OK; ++t) {
+        for (; s < steps[t]; ++s) {
+          counted(h);
+          if ((e = launch_row_div(cur, (const double*)h->Df.p, n, K, y, S(h))) != cudaSuccess) {
+            rc = set_cuda_error(e, "markov scale");
+            break;
+          }
+          if (h->prm.f == WL_F_IDENTITY) {
+            counted(h);
+            if ((e = launch_adj_apply(h->g, y, K, cur, S(h))) != cudaSuccess) {
+              rc = set_cuda_error(e, "markov step");
+              break;
+            }
+            info.nnz_rhs += (double)h->nnz * K;
+            info.iters += 1;
+          } else {
+            if ((rc = phi_apply(h, y, cur, K, info)) != WL_OK) break;
+            if (info.status != WL_OK) break;
+          }
+          ++nstep;
+        }
+        if (rc != WL_OK || info.status != WL_OK) break;
+        counted(h);
+        e = launch_unpack(cur, n, K, c0, h->perm, Od + (size_t)t * n * ldo, ldo, S(h));
+        if (e != cudaSuccess) { rc = set_cuda_error(e, "markov out"); break; }
+      }
+      if (rc != WL_OK || info.status != WL_OK) break;
+      c0 += K;
+    }
+    if (rc != WL_OK) break;
+    if (!o_dev) {
+      cudaError_t e = cudaMemcpyAsync(out, Od, (size_t)nsteps * n * ldo * 8, cudaMemcpyDeviceToHost, S(h));
+      if (e != cudaSuccess) { rc = set_cuda_error(e, "copy out"); break; }
+    }
+  } while (0);
+  const double ms = end_timer(h);
+  if (rc == WL_OK) rc = info.status;
+  fill_stats(h, st, info, rc, ms, nstep);
   return rc;
 }
 

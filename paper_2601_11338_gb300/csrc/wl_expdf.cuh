@@ -188,9 +188,28 @@ __global__ void __launch_bounds__(kBlock) df_lanczos_step(DfLanczosArgs a) {
 
 // U(tau) = |u0| V_m y(tau) over a double-float basis, all tau from one read
 // of the basis; y in double-float (yh, yl: K x ntau x ldT), output FP64.
+// The coefficients of the CTA's columns are staged in shared memory (layout
+// [j][tau][c]) when they fit; four basis blocks are read per round so that
+// eight independent loads are in flight per thread.
+constexpr int kCombSmemFloats = 10240;  // 40 KB of staged coefficients
+
 template <int K>
 __global__ void __launch_bounds__(kBlock) df_combine(DfCombineArgs a) {
+  __shared__ float s_y[kCombSmemFloats];
   const size_t total = (size_t)a.n * K;
+  int mmax = 0;
+  for (int c = 0; c < K; ++c) mmax = max(mmax, a.mcol[c]);
+  const bool staged = (size_t)mmax * a.ntau * K * 2 <= (size_t)kCombSmemFloats;
+  if (staged) {
+    const int cnt = mmax * a.ntau * K;
+    for (int q = threadIdx.x; q < cnt; q += kBlock) {
+      const int c = q % K, t = (q / K) % a.ntau, j = q / (K * a.ntau);
+      const size_t src = ((size_t)c * a.ntau + t) * a.ldT + j;
+      s_y[2 * q] = __ldg(a.yh + src);
+      s_y[2 * q + 1] = __ldg(a.yl + src);
+    }
+  }
+  __syncthreads();
   for (size_t e = (size_t)blockIdx.x * kBlock + threadIdx.x; e < total; e += (size_t)gridDim.x * kBlock) {
     const int c = (int)(e % K);
     const size_t i = e / K;
@@ -198,20 +217,38 @@ __global__ void __launch_bounds__(kBlock) df_combine(DfCombineArgs a) {
     float S[kMaxTau], Cc[kMaxTau];
 #pragma unroll
     for (int t = 0; t < kMaxTau; ++t) S[t] = Cc[t] = 0.f;
-    const size_t yo = (size_t)c * a.ntau * a.ldT;
-    for (int j = 0; j < m; ++j) {
-      const df v{__ldcs(a.basis + (size_t)(2 * j) * total + e), __ldcs(a.basis + (size_t)(2 * j + 1) * total + e)};
+    auto ycoef = [&](int j, int t) -> df {
+      if (staged) {
+        const int q = (j * a.ntau + t) * K + c;
+        return df{s_y[2 * q], s_y[2 * q + 1]};
+      }
+      const size_t src = ((size_t)c * a.ntau + t) * a.ldT + j;
+      return df{__ldg(a.yh + src), __ldg(a.yl + src)};
+    };
+    int j = 0;
+    for (; j + 3 < m; j += 4) {
+      df v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        v[u] = df{__ldcs(a.basis + (size_t)(2 * (j + u)) * total + e),
+                  __ldcs(a.basis + (size_t)(2 * (j + u) + 1) * total + e)};
 #pragma unroll
       for (int t = 0; t < kMaxTau; ++t)
         if (t < a.ntau) {
-          const size_t q = yo + (size_t)t * a.ldT + j;
-          df_acc2(S[t], Cc[t], df_mul(v, df{__ldg(a.yh + q), __ldg(a.yl + q)}));
+#pragma unroll
+          for (int u = 0; u < 4; ++u) df_acc2(S[t], Cc[t], df_mul(v[u], ycoef(j + u, t)));
         }
     }
-    const double s = a.nrm[c];
+    for (; j < m; ++j) {
+      const df v{__ldcs(a.basis + (size_t)(2 * j) * total + e), __ldcs(a.basis + (size_t)(2 * j + 1) * total + e)};
+#pragma unroll
+      for (int t = 0; t < kMaxTau; ++t)
+        if (t < a.ntau) df_acc2(S[t], Cc[t], df_mul(v, ycoef(j, t)));
+    }
+    const double sc = a.nrm[c];
     const size_t io = a.perm ? (size_t)a.perm[i] : i;
     for (int t = 0; t < a.ntau; ++t)
-      a.out[(size_t)t * a.tstride + io * a.ld + a.c0 + c] = s * ((double)S[t] + (double)Cc[t]);
+      a.out[(size_t)t * a.tstride + io * a.ld + a.c0 + c] = sc * ((double)S[t] + (double)Cc[t]);
   }
 }
 

@@ -12,6 +12,7 @@
 #include "wl_lanczos.cuh"
 #include "wl_expdf.cuh"
 #include "wl_res.cuh"
+#include "wl_exps.cuh"
 #include "wl_spec.cuh"
 
 namespace wl {
@@ -46,6 +47,11 @@ cudaError_t launch_colnorms(const double* X, int64_t n, int K, double* out, cuda
 // Y[:, c] = X[:, c] * inv[c]
 cudaError_t launch_scale_cols(const double* X, int64_t n, int K, const double* inv, double* Y, cudaStream_t s);
 cudaError_t launch_f2d_acc(const float* src, double* dst, int64_t count, cudaStream_t s);
+// discrete-time chain: Y = X / D_f per row; Y = A X; scatter a packed block into caller columns
+cudaError_t launch_row_div(const double* X, const double* Df, int64_t n, int K, double* Y, cudaStream_t s);
+cudaError_t launch_adj_apply(const Graph& g, const double* X, int K, double* Y, cudaStream_t s);
+cudaError_t launch_unpack(const double* src, int64_t n, int K, int c0, const int32_t* perm, double* dst, int64_t ld,
+                          cudaStream_t s);
 // identity-function apply: W[:, c0:c0+K] = d (.) V - A V for V packed n x K
 cudaError_t launch_laplacian_apply(const Graph& g, const PartDev& p, const double* Vp, int K, int c0,
                                    const int32_t* perm, double* W, int64_t ldw, cudaStream_t s);
@@ -91,6 +97,9 @@ cudaError_t launch_df_combine(int K, const DfCombineArgs& a, cudaStream_t s);
 // hi + lo = X[:, c] / nrm[c] (X: n x K FP64, contiguous)
 cudaError_t launch_df_scale_cols(const double* X, int64_t n, int K, const double* nrm, float* hi, float* lo,
                                  cudaStream_t s);
+// one term of the exponential series (the kernel returns at once once st->active is 0)
+cudaError_t launch_exp_term(int K, const ExpArgs& a, int grid, cudaStream_t s);
+int exp_blocks(int K);
 // hi + lo = x (total FP64 values)
 cudaError_t launch_df_split(const double* x, size_t total, float* hi, float* lo, cudaStream_t s);
 int phase_blocks_f32(int K);  // resident CTAs of the S kernel (all SMs)

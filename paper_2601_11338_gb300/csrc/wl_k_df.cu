@@ -1,11 +1,13 @@
 // Double-float kernels of the refined form (refinement residual, outer
 // Lanczos step and basis combination), K = 1, 2, 4, ..., 64.
 #define WL_EXPDF_KERNELS
+#define WL_EXPS_KERNELS
 #include <algorithm>
 
 #include "wl_expdf.cuh"
 #include "wl_host.h"
 #include "wl_res.cuh"
+#include "wl_exps.cuh"
 
 namespace wl {
 
@@ -96,6 +98,35 @@ cudaError_t launch_df_scale_cols(const double* X, int64_t n, int K, const double
   const int64_t blocks = std::min<int64_t>(((int64_t)n * K + kBlock - 1) / kBlock, 152 * 16);
   df_scale_cols<<<(unsigned)std::max<int64_t>(blocks, 1), kBlock, 0, s>>>(X, n, K, nrm, hi, lo);
   return cudaGetLastError();
+}
+
+cudaError_t launch_exp_term(int K, const ExpArgs& a, int grid, cudaStream_t s) {
+  switch (K) {
+#define ET(k)                                            \
+  case k:                                                \
+    exp_term<k><<<grid, kPhaseBlock, 0, s>>>(a);         \
+    return cudaGetLastError();
+    WL_FOR_K(ET)
+#undef ET
+  }
+  return cudaErrorInvalidValue;
+}
+
+int exp_blocks(int K) {
+  const void* f = nullptr;
+  switch (K) {
+#define EB(k)                              \
+  case k:                                  \
+    f = (const void*)exp_term<k>;          \
+    break;
+    WL_FOR_K(EB)
+#undef EB
+  }
+  int nb = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kPhaseBlock, 0);
+  return (nb < 1 ? 1 : nb) * sms;
 }
 
 cudaError_t launch_df_split(const double* x, size_t total, float* hi, float* lo, cudaStream_t s) {

@@ -243,6 +243,54 @@ cudaError_t launch_f2d_acc(const float* src, double* dst, int64_t count, cudaStr
   return cudaGetLastError();
 }
 
+// ---- discrete-time chain P = D_f^{-1} phi (Sec. 3.3, with D = diag(phi 1)):
+// one step in column form is p <- phi (p / D_f)
+__global__ void k_row_div(const double* X, const double* Df, int64_t n, int K, double* Y) {
+  const int64_t total = n * K;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const double d = Df[e / K];
+    Y[e] = d > 0.0 ? X[e] / d : 0.0;
+  }
+}
+
+cudaError_t launch_row_div(const double* X, const double* Df, int64_t n, int K, double* Y, cudaStream_t s) {
+  k_row_div<<<grid_for(n * K), 256, 0, s>>>(X, Df, n, K, Y);
+  return cudaGetLastError();
+}
+
+// Y = A X for n x K blocks (FP64, one thread per row and column)
+__global__ void k_adj_apply(const int32_t* row_ptr, const int32_t* col, const double* X, int64_t n, int K, double* Y) {
+  const int64_t total = n * K;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / K;
+    const int c = (int)(e % K);
+    double acc = 0.0;
+    for (int j = row_ptr[i]; j < row_ptr[i + 1]; ++j) acc += X[(int64_t)col[j] * K + c];
+    Y[e] = acc;
+  }
+}
+
+cudaError_t launch_adj_apply(const Graph& g, const double* X, int K, double* Y, cudaStream_t s) {
+  k_adj_apply<<<grid_for(g.n * K), 256, 0, s>>>(g.row_ptr, g.col, X, g.n, K, Y);
+  return cudaGetLastError();
+}
+
+// dst[row(i) * ld + c0 + c] = src[i * K + c], row(i) = perm[i] (perm NULL: i)
+__global__ void k_unpack(const double* src, int64_t n, int K, int c0, const int32_t* perm, double* dst, int64_t ld) {
+  const int64_t total = n * K;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / K;
+    const int c = (int)(e % K);
+    dst[(perm ? (int64_t)perm[i] : i) * ld + c0 + c] = src[e];
+  }
+}
+
+cudaError_t launch_unpack(const double* src, int64_t n, int K, int c0, const int32_t* perm, double* dst, int64_t ld,
+                          cudaStream_t s) {
+  k_unpack<<<grid_for(n * K), 256, 0, s>>>(src, n, K, c0, perm, dst, ld);
+  return cudaGetLastError();
+}
+
 // W[:, c0:c0+K] = d (.) V - A V (identity function: L = D - A, Sec. 3.1)
 template <int K>
 __global__ void __launch_bounds__(kBlock) k_laplacian_apply(Graph g, Part pt, const double* Vp, int c0,

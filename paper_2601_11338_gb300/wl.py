@@ -84,6 +84,7 @@ def lib():
         L.wl_apply.argtypes = [vp, vp, i64, c_int, vp, i64, ctypes.POINTER(wl_stats)]
         L.wl_expmv.argtypes = [vp, vp, i64, c_int, vp, c_int, vp, i64, ctypes.POINTER(wl_stats)]
         L.wl_trace.argtypes = [vp, c_int, ctypes.c_uint64, vp, vp, vp, ctypes.POINTER(wl_stats)]
+        L.wl_markov.argtypes = [vp, vp, i64, c_int, vp, c_int, vp, i64, ctypes.POINTER(wl_stats)]
         L.wl_set_warm_start.argtypes = [vp, vp]
         L.wl_get_info.argtypes = [vp, ctypes.POINTER(wl_stats)]
         L.wl_destroy.argtypes = [vp]
@@ -125,7 +126,7 @@ def lib():
         L.wl_batch_destroy.argtypes = [vp]
         L.wl_batch_destroy.restype = None
         for name in ("wl_build", "wl_set_params", "wl_degrees", "wl_apply", "wl_expmv", "wl_trace",
-                     "wl_set_warm_start", "wl_get_info"):
+                     "wl_markov", "wl_set_warm_start", "wl_get_info"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -208,6 +209,13 @@ def wl_expmv(h, U0, ldu, k, taus, U, ldo, stats=None, allow=()):
     taus = np.ascontiguousarray(taus, dtype=np.float64)
     return _check(lib().wl_expmv(h.ptr, _ptr(U0), ldu, k, taus.ctypes.data, len(taus), _ptr(U), ldo,
                                  ctypes.byref(st)), "wl_expmv", allow)
+
+
+def wl_markov(h, P0, ldp, k, steps, out, ldo, stats=None, allow=()):
+    st = stats if stats is not None else wl_stats()
+    steps = np.ascontiguousarray(steps, dtype=np.int32)
+    return _check(lib().wl_markov(h.ptr, _ptr(P0), ldp, k, steps.ctypes.data, len(steps), _ptr(out), ldo,
+                                  ctypes.byref(st)), "wl_markov", allow)
 
 
 def wl_trace(h, M, seed, omega_out=None, stats=None):

@@ -51,9 +51,9 @@ def test_build_rejects_bad_arguments_before_touching_the_gpu():
     assert L.wl_build(ctypes.byref(A), 7, ctypes.byref(p), ctypes.byref(h), None) == wl.WL_ERR_INVALID_ARG
     p2 = wl.make_params(mu=1.5)
     assert L.wl_build(ctypes.byref(A), wl.WL_BTDW, ctypes.byref(p2), ctypes.byref(h), None) == wl.WL_ERR_INVALID_ARG
-    # exponential with backtrack downweighting is not provided
-    p3 = wl.make_params(f=wl.WL_F_EXP)
-    assert L.wl_build(ctypes.byref(A), wl.WL_NBT, ctypes.byref(p3), ctypes.byref(h), None) == wl.WL_ERR_UNSUPPORTED
+    # unknown matrix function
+    p3 = wl.make_params(f=9)
+    assert L.wl_build(ctypes.byref(A), wl.WL_NBT, ctypes.byref(p3), ctypes.byref(h), None) == wl.WL_ERR_INVALID_ARG
     assert h.value is None
 
 

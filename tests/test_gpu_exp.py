@@ -1,0 +1,74 @@
+"""The exponential walk function f(x) = exp(beta x) (Def. BDTW-Laplacian with
+c_k = beta^k / k!) for mu in [0, 1]: walk degrees, Laplacian action,
+diffusion and the discrete-time chain through the C ABI, against the CPU FP64
+oracle's series (and, for mu = 0, the spectral form exp(beta A)).
+
+The series runs in double-float arithmetic in both precision forms;
+tolerance 1e-10 relative per column.
+"""
+import numpy as np
+import pytest
+
+import wlgen
+from oracle import graph, spectral, walks
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def dense(g):
+    return graph.dense_adjacency(g.row_ptr, g.col_idx, g.n)
+
+
+def WL(g, **kw):
+    from paper_2601_11338_gb300.api import WalkLaplacian
+    return WalkLaplacian(g.row_ptr[:].astype(np.int32), g.col_idx, g.n, f="exp", **kw)
+
+
+def relerr(got, want):
+    got, want = np.asarray(got), np.asarray(want)
+    if want.ndim == 1:
+        return np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-300)
+    return (np.linalg.norm(got - want, axis=0) / np.maximum(np.linalg.norm(want, axis=0), 1e-300)).max()
+
+
+@pytest.mark.parametrize("variant,mu", [("allwalk", 0.0), ("btdw", 0.5), ("nbt", 1.0)])
+@pytest.mark.parametrize("beta", [0.0, 0.35])
+@pytest.mark.parametrize("prec,reorder", [("fp64", 1), ("refined", 0)])
+def test_exp_degrees_apply_diffusion(variant, mu, beta, prec, reorder):
+    g = wlgen.erdos_renyi(300, 6, 41)
+    A = dense(g)
+    w = WL(g, variant=variant, mu=mu, beta=beta, prec=prec, tol=1e-13, outer_tol=1e-12, reorder=reorder)
+    b = w.info["beta"]
+    want_b = beta if beta > 0 else 1.0 / spectral.lambda_max(A)
+    assert abs(b - want_b) <= 1e-9 * want_b
+    phi = walks.phi_series(A, mu, walks.exp_coeffs(b))
+    if mu == 0.0:  # two independent forms agree
+        np.testing.assert_allclose(phi, walks.phi_allwalk_exp_eig(A, b), rtol=0, atol=1e-12 * np.abs(phi).max())
+    Df = w.degrees().cpu().numpy()
+    assert relerr(Df, walks.walk_degrees(phi)) <= TOL
+    V = wlgen.gaussian_block(g.n, 5, 42)
+    W = w.apply(torch.as_tensor(V, device="cuda")).cpu().numpy()
+    assert relerr(W, walks.apply_laplacian(phi, V)) <= TOL
+    U0 = wlgen.unit_block(g.n, np.array([3, 100]))
+    U = w.expmv(torch.as_tensor(U0, device="cuda"), [0.5, 3.0]).cpu().numpy()
+    want = walks.diffusion(walks.walk_laplacian(phi), U0, [0.5, 3.0])
+    for t in range(2):
+        assert relerr(U[t], want[t]) <= TOL
+    P = w.markov(torch.as_tensor(U0, device="cuda"), [4]).cpu().numpy()[0]
+    assert relerr(P, walks.markov_evolve(phi, U0, [4])[0]) <= TOL
+    w.close()
+
+
+def test_exp_on_a_tree_with_nbt_walks():
+    """On a tree the nonbacktracking counts vanish beyond the diameter, so the
+    NBT series is a polynomial in A; the library's result still matches the
+    oracle's series."""
+    g = wlgen.path(25)
+    A = dense(g)
+    w = WL(g, variant="nbt", beta=0.9)
+    phi = walks.phi_series(A, 1.0, walks.exp_coeffs(0.9))
+    assert relerr(w.degrees().cpu().numpy(), walks.walk_degrees(phi)) <= TOL
+    w.close()

@@ -272,3 +272,44 @@ def test_sparse_companion_radius_matches_dense(mu):
     A = dense(g)
     got = krylov.rho_companion_sparse(krylov.adjacency(g.row_ptr, g.col_idx, g.n), mu)
     assert abs(got - spectral.rho_companion(A, mu)) <= 1e-8 * got
+
+
+# ---------------------------------------------------------------- discrete-time chain
+def test_markov_evolve_simple_random_walk_on_cycle():
+    """With phi = A (the combinatorial Laplacian D - A) the chain of Sec. 3.3 is
+    the simple random walk: on C_n, from node 0, after s < n/2 steps the walk
+    sits at offset j with probability C(s, (s + j)/2) / 2^s (j = s mod 2)."""
+    n, s = 40, 13
+    A = dense(wlgen.cycle(n))
+    P0 = np.zeros((n, 1))
+    P0[0, 0] = 1.0
+    got = walks.markov_evolve(A, P0, [s])[0][:, 0]
+    want = np.zeros(n)
+    for j in range(-s, s + 1):
+        if (s + j) % 2 == 0:
+            want[j % n] = math.comb(s, (s + j) // 2) / 2 ** s
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-16)
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.5, 1.0])
+def test_markov_evolve_conserves_mass_and_reaches_stationary(mu):
+    """p_{s+1} = p_s P with P = D_f^{-1} phi: 1^T p is conserved (this fixes the
+    orientation: P p would not conserve it on an irregular graph), p stays
+    nonnegative, and the chain converges to the stationary distribution that
+    Fig. 1 pins (markov_stationary)."""
+    A = dense(wlgen.g58())
+    alpha = 0.5 / spectral.rho_companion(A, mu) if mu > 0 else 0.5 / spectral.lambda_max(A)
+    phi = walks.phi_resolvent_closed(A, mu, alpha)
+    P0 = np.zeros((A.shape[0], 2))
+    P0[0, 0] = 1.0
+    P0[7, 1] = 1.0
+    out = walks.markov_evolve(phi, P0, [1, 3, 400])
+    for p in out:
+        np.testing.assert_allclose(p.sum(axis=0), 1.0, rtol=0, atol=1e-14)
+        assert p.min() >= 0.0
+    pi = walks.markov_stationary(phi)
+    for c in range(2):
+        np.testing.assert_allclose(out[-1][:, c], pi, rtol=0, atol=1e-12)
+    # the wrong orientation breaks conservation on this irregular graph
+    P = phi / walks.walk_degrees(phi)[:, None]
+    assert abs((P @ P0[:, 0]).sum() - 1.0) > 1e-3
