@@ -194,6 +194,19 @@ int wl_markov(wl_handle* h, const double* P0, int64_t ldp, int k, const int* ste
 int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, uint16_t* omega_out,
              wl_stats* st);
 
+/* Average return probability p(t) = tr(exp(-t L)) / n (Sec. 4.4, Eq.
+ * average_return_probabilities) with its randomized estimate, Alg. 1
+ * ("XNysTrace-exp"): the M Gaussian test vectors Omega are drawn as in
+ * wl_trace (Philox4x32-10 from `seed`, rounded to bfloat16); Y(t) =
+ * exp(-t L) Omega comes from one lockstep Lanczos run on L per column
+ * (Sec. 4.1) evaluated at every t; XNysTrace(Y(t), Omega) / n gives
+ * p_est[t] and the error estimate p_err[t] (host arrays of nt values).
+ * ts: host array of nt time points >= 0, 1 <= nt <= 256; 2 <= M <= 64.
+ * A polynomial Krylov basis replaces the paper's block rational one (one
+ * apply of L per step instead of shifted solves with L). */
+int wl_return_prob(wl_handle* h, int M, uint64_t seed, const double* ts, int nt, double* p_est, double* p_err,
+                   wl_stats* st);
+
 /* Optional starting guess x0 (n FP64 values, host or device) for the D_f
  * solve of wl_degrees; NULL clears it (start from 0). Copied. */
 int wl_set_warm_start(wl_handle* h, const double* x0);

@@ -37,3 +37,24 @@ def xnystrace(A, Omega):
         w = Omega[:, i]
         t[i] = np.trace(Ah) + w @ (A @ w) - w @ (Ah @ w)
     return float(t.mean()), float(t.std(ddof=1) / np.sqrt(M)), t
+
+
+def return_probability(Lap, ts):
+    """p(t) = tr(exp(-t L)) / n (Sec. 4.4, Eq. average_return_probabilities),
+    from the eigenvalues of the symmetric L."""
+    lam = np.linalg.eigvalsh(Lap)
+    return np.array([np.exp(-t * lam).sum() / len(lam) for t in ts])
+
+
+def xnys_return_probability(Lap, Omega, ts):
+    """Alg. 1 with exact Y(t): the literal leave-one-out XNysTrace of
+    exp(-t L) with the test vectors Omega, divided by n, for each t.
+    Returns a list of (estimate, error estimate)."""
+    lam, Q = np.linalg.eigh(Lap)
+    n = len(lam)
+    out = []
+    for t in ts:
+        E = (Q * np.exp(-t * lam)) @ Q.T
+        est, err, _ = xnystrace(E, Omega)
+        out.append((est / n, err / n))
+    return out

@@ -84,6 +84,10 @@ class WalkLaplacian:
         wl.wl_markov(self.h, P0, k, k, steps, P, k, self.last, allow)
         return P
 
+    def return_prob(self, M, seed, ts, allow=()):
+        """Estimates of tr(exp(-t L)) / n and their error estimates at each t."""
+        return wl.wl_return_prob(self.h, M, seed, ts, self.last, allow)
+
     def trace(self, M, seed, omega_out=None):
         return wl.wl_trace(self.h, M, seed, omega_out, self.last)
 

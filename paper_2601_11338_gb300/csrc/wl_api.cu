@@ -143,6 +143,9 @@ struct wl_handle {
   Buf bh, bl, rh, rl;     // refined form: right-hand side and residual as two FP32 terms
   Buf dfdf, ydf;          // refined form: D_f and the Lanczos coefficients y(tau) as two FP32 terms
   Buf ew;                 // exponential series: w_{k-1}, w_k, w_{k+1} and the sum (double-float)
+  Buf taus;               // time points of the outer Lanczos (device copy)
+  Buf ybig;               // Y(t) = exp(-t L) Omega for a batch of time points (return probability)
+  bool have_dfdf = false; // dfdf holds the current D_f
   Buf part;               // partial sums
   Buf small;              // per-column scalars
   Buf Df;
@@ -639,6 +642,7 @@ int compute_Df(wl_handle* h, SolveInfo& info) {
     return WL_ERR_UNSUPPORTED;
   }
   h->have_Df = true;
+  h->have_dfdf = false;
   return WL_OK;
 }
 
@@ -892,6 +896,225 @@ void fill_stats(wl_handle* h, wl_stats* st, const SolveInfo& in, int status, dou
 }
 
 // internal-order n-vector -> caller's array (host or device), undoing the relabelling
+// taus (host) into a device array of the handle
+int stage_taus(wl_handle* h, const double* taus, int ntau, const double** dtaus) {
+  WL_TRY(ensure(h->taus, (size_t)std::max(ntau, 1) * 8));
+  WL_CU(cudaMemcpyAsync(h->taus.p, taus, (size_t)ntau * 8, cudaMemcpyHostToDevice, S(h)));
+  *dtaus = (const double*)h->taus.p;
+  return WL_OK;
+}
+
+// ------------------------------------------------------------------ outer Lanczos on L (Sec. 4.1)
+// One column block of the Krylov evaluation exp(-tau L) U0: the packed block
+// (n x K FP64, internal order) in h->packX starts K lockstep Lanczos
+// recurrences on L, one apply of L per step; every `check` steps y(tau) =
+// exp(-tau T_m) e_1 is recomputed for all tau and the run stops when no
+// (column, tau) changed by more than outer_tol since the last check. The
+// basis, T, the column norms and m stay in the handle for outer_combine.
+struct OuterRun {
+  int K = 0, m = 0, ntau = 0;
+  bool converged = false, dfp = false;
+  size_t blk = 0;
+  const double* dtaus = nullptr;
+};
+
+constexpr int kLdT = 512;  // T and y leading dimension (Lanczos steps per column at most kLdT - 1)
+constexpr int kMaxReturnT = 256;  // time points per wl_return_prob call
+
+int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& info, OuterRun& o, int& outer_total) {
+  const int64_t n = h->n;
+  const int ldT = kLdT;
+  const int maxm = std::min(h->prm.max_outer, ldT - 1);
+  const int check = 4;
+  // refined resolvent form: double-float outer recurrence (FP32 instructions only)
+  const bool dfp = h->prm.prec == WL_REFINED && h->prm.f == WL_F_RESOLVENT;
+  o = OuterRun{};
+  o.K = K;
+  o.ntau = ntau;
+  o.dfp = dfp;
+  o.dtaus = dtaus;
+  if (h->prm.f != WL_F_IDENTITY && !h->have_Df) WL_TRY(compute_Df(h, info));
+  if (info.status != WL_OK) return WL_OK;
+  if (dfp && !h->have_dfdf) {  // D_f as two FP32 terms for the double-float outer recurrence
+    WL_TRY(ensure(h->dfdf, (size_t)n * 8));
+    counted(h);
+    WL_CU(launch_df_split((const double*)h->Df.p, (size_t)n, (float*)h->dfdf.p, (float*)h->dfdf.p + n, S(h)));
+    h->have_dfdf = true;
+  }
+  const size_t blk = (size_t)n * K;
+  o.blk = blk;
+  size_t want_blocks = (size_t)std::min(maxm + 1, 160);
+  if (h->basis_blocks < want_blocks || h->basis.bytes < want_blocks * blk * 8) {
+    WL_TRY(ensure(h->basis, want_blocks * blk * 8));
+    h->basis_blocks = want_blocks;
+  }
+  size_t cap_blocks = h->basis.bytes / (blk * 8);
+  WL_TRY(ensure(h->Tab, (size_t)2 * K * ldT * 8 + 64 * 8 * 4));
+  WL_TRY(ensure(h->ybuf, (size_t)K * ntau * ldT * 8));
+  WL_TRY(ensure(h->yprev, (size_t)K * ntau * ldT * 8));
+  WL_TRY(ensure(h->errb, (size_t)K * ntau * 8 * 2 + 64 * 4 * 4));
+  double* basis = (double*)h->basis.p;
+  double* Ta = (double*)h->Tab.p;
+  double* Tb = Ta + (size_t)K * ldT;
+  double* nrm = Tb + (size_t)K * ldT;
+  int* done = (int*)((double*)h->errb.p + (size_t)K * ntau * 2);
+  int* mcol = done + 64;
+  int* mprev = done + 128;
+  double* errd = (double*)h->errb.p;
+  // V_0 = U0 block / |U0 block| (per column)
+  counted(h, 2);
+  cudaError_t e = launch_colnorms((const double*)h->packX.p, n, K, nrm, S(h));
+  if (e == cudaSuccess)
+    e = dfp ? launch_df_scale_cols((const double*)h->packX.p, n, K, nrm, (float*)basis, (float*)basis + blk, S(h))
+            : launch_scale_cols((const double*)h->packX.p, n, K, nrm, basis, S(h));
+  if (e != cudaSuccess) return set_cuda_error(e, "expmv init");
+  // done flags: zero columns
+  WL_CU(cudaMemcpyAsync(h->h_pin, nrm, K * 8, cudaMemcpyDeviceToHost, S(h)));
+  WL_CU(cudaStreamSynchronize(S(h)));
+  std::vector<int> hdone(K), hzero(K, 0);
+  std::vector<double> hb2(K);
+  for (int c = 0; c < K; ++c) {
+    hdone[c] = (h->h_pin[c] > 0.0) ? 0 : 1;
+    hb2[c] = hdone[c] ? 0.0 : 1.0;
+  }
+  WL_CU(cudaMemcpyAsync(done, hdone.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
+  WL_CU(cudaMemcpyAsync(mprev, hzero.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
+  double* bn2 = (double*)h->small.p + 664;  // |v_j|^2 per column for the double-float solves
+  if (dfp) {
+    WL_CU(cudaMemcpyAsync(bn2, hb2.data(), K * 8, cudaMemcpyHostToDevice, S(h)));
+    WL_TRY(ensure(h->xh, blk * 4));
+    WL_TRY(ensure(h->xl, blk * 4));
+  }
+  const int Gs = dfp ? df_lanczos_grid(K) : lanczos_step_grid(K);
+  int Tw, Tc;
+  thresholds_f64(K, &Tw, &Tc);
+  PartDev* pd = nullptr;
+  if (!dfp) WL_TRY(get_part(h, Gs, Tw, Tc, &pd, K, 8));
+  WL_TRY(ensure(h->part, (size_t)std::max(Gs, 1) * 64 * 2 * 8 + 1024));
+  int m = 0;
+  bool converged = false;
+  for (int j = 0; j < maxm; ++j) {
+    if ((size_t)(j + 2) > cap_blocks) {
+      // grow the basis (double), keeping the blocks computed so far
+      Buf nb;
+      size_t nbk = std::min<size_t>((size_t)maxm + 1, cap_blocks * 2);
+      WL_TRY(ensure(nb, nbk * blk * 8));
+      WL_CU(cudaMemcpyAsync(nb.p, h->basis.p, cap_blocks * blk * 8, cudaMemcpyDeviceToDevice, S(h)));
+      WL_CU(cudaStreamSynchronize(S(h)));
+      release(h->basis);
+      h->basis = nb;
+      h->basis_blocks = nbk;
+      cap_blocks = nbk;
+      basis = (double*)h->basis.p;
+    }
+    if (dfp) {
+      // double-float basis: block j holds hi then lo terms
+      float* vjh = (float*)basis + (size_t)2 * j * blk;
+      float* vmh = j > 0 ? (float*)basis + (size_t)2 * (j - 1) * blk : nullptr;
+      float* vph = (float*)basis + (size_t)2 * (j + 1) * blk;
+      WL_TRY(solve_refined_df(h, vjh, vjh + blk, bn2, (float*)h->xh.p, (float*)h->xl.p, nullptr, K, h->prm.tol, info));
+      if (info.status != WL_OK) return WL_OK;
+      WL_TRY(ensure(h->part, (size_t)std::max(Gs, 1) * 64 * 2 * 8 + 1024));
+      DfLanczosArgs la{vjh, vjh + blk, vmh, vmh ? vmh + blk : nullptr, (const float*)h->xh.p,
+                       (const float*)h->xl.p, (const float*)h->dfdf.p, (const float*)h->dfdf.p + n,
+                       df_from_double(h->a_scale), vph, vph + blk, Ta, Tb, done, bn2, (double*)h->part.p,
+                       h->bar, n, j, ldT};
+      WL_TRY(reset_bar(h));
+      const int pl = prof_begin(h, kCatLan);
+      counted(h);
+      e = launch_df_lanczos_step(K, la, Gs, S(h));
+      prof_end(h, pl);
+      if (e != cudaSuccess) return set_cuda_error(e, "df_lanczos_step");
+    } else {
+      double* vj = basis + (size_t)j * blk;
+      double* vjm1 = j > 0 ? basis + (size_t)(j - 1) * blk : nullptr;
+      double* vjp1 = basis + (size_t)(j + 1) * blk;
+      LanczosStepArgs la{h->g, pd->view(), vj, vjm1, nullptr, (const double*)h->Df.p, 0, 0, 0, vjp1,
+                         Ta, Tb, done, (double*)h->part.p, h->bar, j, ldT, 0};
+      if (h->prm.f == WL_F_IDENTITY) {
+        la.mode = 1;
+        la.c0 = 0.0;
+        la.cA = -1.0;
+        la.cD = 1.0;
+        info.nnz_rhs += (double)h->nnz * K;
+        info.iters += 1;
+      } else {
+        WL_TRY(phi_apply(h, vj, (double*)h->packX.p, K, info));
+        if (info.status != WL_OK) return WL_OK;
+        la.X = (const double*)h->packX.p;
+        la.part = (double*)h->part.p;
+      }
+      WL_TRY(reset_bar(h));
+      const int pl = prof_begin(h, kCatLan);
+      e = launch_lanczos_step(K, la, Gs, S(h));
+      prof_end(h, pl);
+      if (e != cudaSuccess) return set_cuda_error(e, "lanczos_step");
+    }
+    m = j + 1;
+    ++outer_total;
+    if (m % check == 0 || m == maxm) {
+      std::vector<int> hm(K, m);
+      WL_CU(cudaMemcpyAsync(mcol, hm.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
+      TridiagArgs ta{Ta, Tb, mcol, dtaus, (double*)h->ybuf.p, (double*)h->yprev.p, mprev, errd, ldT, ntau, 1,
+                     kChebMax};
+      counted(h);
+      e = launch_tridiag_exp(ta, K, S(h));
+      if (e != cudaSuccess) return set_cuda_error(e, "tridiag_exp");
+      WL_CU(cudaMemcpyAsync(mprev, mcol, K * 4, cudaMemcpyDeviceToDevice, S(h)));
+      WL_CU(cudaMemcpyAsync(h->h_pin, errd, (size_t)K * ntau * 8, cudaMemcpyDeviceToHost, S(h)));
+      const int berr = check_bar(h);
+      if (berr) return berr;
+      bool all = true;
+      for (int c = 0; c < K && all; ++c)
+        for (int t = 0; t < ntau; ++t)
+          if (!(h->h_pin[c * ntau + t] <= h->prm.outer_tol)) { all = false; break; }
+      if (all) { converged = true; break; }
+    }
+  }
+  o.m = m;
+  o.converged = converged;
+  return WL_OK;
+}
+
+// U(tau) = |u0| V_m y(tau) for taus [t0, t0 + nt) of an outer run, nt <=
+// kMaxTau: block t at out + t * tstride, row perm[i] (or i), columns c0..c0+K.
+int outer_combine(wl_handle* h, const OuterRun& o, int t0, int nt, double* out, int64_t ld, int64_t tstride, int c0,
+                  const int32_t* perm) {
+  const int K = o.K, ldT = kLdT;
+  const int64_t n = h->n;
+  double* Ta = (double*)h->Tab.p;
+  double* Tb = Ta + (size_t)K * ldT;
+  double* nrm = Tb + (size_t)K * ldT;
+  int* done = (int*)((double*)h->errb.p + (size_t)K * o.ntau * 2);
+  int* mcol = done + 64;
+  int* mzero = done + 192;  // no previous y: the change estimate is not used here
+  double* errd = (double*)h->errb.p;
+  std::vector<int> hm(K, o.m), hz(K, 0);
+  WL_CU(cudaMemcpyAsync(mcol, hm.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
+  WL_CU(cudaMemcpyAsync(mzero, hz.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
+  TridiagArgs ta{Ta, Tb, mcol, o.dtaus + t0, (double*)h->ybuf.p, (double*)h->yprev.p, mzero, errd, ldT, nt, 1,
+                 kChebMax};
+  counted(h);
+  cudaError_t e = launch_tridiag_exp(ta, K, S(h));
+  if (e != cudaSuccess) return set_cuda_error(e, "tridiag_exp");
+  if (o.dfp) {
+    const size_t ny = (size_t)K * nt * ldT;
+    WL_TRY(ensure(h->ydf, ny * 8));
+    counted(h, 2);
+    e = launch_df_split((const double*)h->ybuf.p, ny, (float*)h->ydf.p, (float*)h->ydf.p + ny, S(h));
+    DfCombineArgs ca{(const float*)h->basis.p, (const float*)h->ydf.p, (const float*)h->ydf.p + ny, mcol, nrm, out,
+                     n, ld, tstride, c0, ldT, nt, perm};
+    if (e == cudaSuccess) e = launch_df_combine(K, ca, S(h));
+  } else {
+    CombineArgs ca{(const double*)h->basis.p, (const double*)h->ybuf.p, mcol, nrm, out, n, ld, tstride, c0, ldT, nt,
+                   perm};
+    counted(h);
+    e = launch_combine(K, ca, S(h));
+  }
+  if (e != cudaSuccess) return set_cuda_error(e, "combine");
+  return WL_OK;
+}
+
 int copy_out_vec(wl_handle* h, const double* src, double* dst) {
   const size_t bytes = (size_t)h->n * 8;
   if (!h->perm) {
@@ -921,7 +1144,7 @@ void free_handle(wl_handle* h) {
     pool_free(kv.second.meta);
   }
   Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
-                 &h->r32, &h->xh, &h->xl, &h->d32b, &h->bh, &h->bl, &h->rh, &h->rl, &h->dfdf, &h->ydf, &h->ew, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
+                 &h->r32, &h->xh, &h->xl, &h->d32b, &h->bh, &h->bl, &h->rh, &h->rl, &h->dfdf, &h->ydf, &h->ew, &h->taus, &h->ybig, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
                  &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->spV, &h->spW, &h->spstate, &h->mid, &h->omega, &h->gram,
                  &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b, &h->hubs, &h->cgstate};
   for (Buf* b : bufs) release(*b);
@@ -1203,6 +1426,7 @@ int wl_set_warm_start(wl_handle* h, const double* x0) {
   WL_CU(cudaStreamSynchronize(S(h)));
   h->have_warm = true;
   h->have_Df = false;
+  h->have_dfdf = false;
   return WL_OK;
 }
 
@@ -1264,6 +1488,7 @@ int wl_mlp_warm_start(wl_handle* h, const float* params, wl_stats* st) {
   const double ms = end_timer(h);
   h->have_warm = true;
   h->have_Df = false;
+  h->have_dfdf = false;
   if (st) {
     st->time_ms = ms;
     st->launches = h->launches;
@@ -1280,6 +1505,7 @@ int wl_degrees(wl_handle* h, double* Df, wl_stats* st) {
   int rc = WL_OK;
   if (h->n > 0) {
     h->have_Df = false;
+  h->have_dfdf = false;
     rc = compute_Df(h, info);
     if (rc == WL_OK) rc = copy_out_vec(h, (const double*)h->Df.p, Df);
   }
@@ -1370,192 +1596,27 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
   const bool u_dev = is_device_ptr(U);
   const double* U0d = nullptr;
   double* Ud = U;
-  const int ldT = 512;
-  const int maxm = std::min(h->prm.max_outer, ldT - 1);
-  const int check = 4;
-  // refined resolvent form: double-float outer recurrence (FP32 instructions only)
-  const bool dfp = h->prm.prec == WL_REFINED && h->prm.f == WL_F_RESOLVENT;
   do {
-    if (h->prm.f != WL_F_IDENTITY && !h->have_Df && (rc = compute_Df(h, info)) != WL_OK) break;
-    if (dfp) {  // D_f as two FP32 terms for the double-float outer recurrence
-      if ((rc = ensure(h->dfdf, (size_t)n * 8)) != WL_OK) break;
-      counted(h);
-      WL_CU(launch_df_split((const double*)h->Df.p, (size_t)n, (float*)h->dfdf.p, (float*)h->dfdf.p + n, S(h)));
-    }
     if ((rc = stage_in(h, h->stage_a, U0, (size_t)n * ldu * 8, (const void**)&U0d)) != WL_OK) break;
     if (!u_dev) {
       if ((rc = ensure(h->stage_b, (size_t)ntau * n * ldo * 8)) != WL_OK) break;
       Ud = (double*)h->stage_b.p;
       if (ldo != k) cudaMemcpyAsync(Ud, U, (size_t)ntau * n * ldo * 8, cudaMemcpyHostToDevice, S(h));
     }
-    double* dtaus = (double*)h->small.p + 512;
-    if (cudaMemcpyAsync(dtaus, taus, ntau * 8, cudaMemcpyHostToDevice, S(h)) != cudaSuccess) { rc = WL_ERR_CUDA; break; }
+    const double* dtaus = nullptr;
+    if ((rc = stage_taus(h, taus, ntau, &dtaus)) != WL_OK) break;
     int c0 = 0;
     for (int K : column_blocks(k)) {
-      const size_t blk = (size_t)n * K;
-      size_t want_blocks = (size_t)std::min(maxm + 1, 160);
-      if (h->basis_blocks < want_blocks || h->basis.bytes < want_blocks * blk * 8) {
-        if ((rc = ensure(h->basis, want_blocks * blk * 8)) != WL_OK) break;
-        h->basis_blocks = want_blocks;
-      }
-      size_t cap_blocks = h->basis.bytes / (blk * 8);
-      if ((rc = ensure(h->Tab, (size_t)2 * K * ldT * 8 + 64 * 8 * 4)) != WL_OK) break;
-      if ((rc = ensure(h->ybuf, (size_t)K * ntau * ldT * 8)) != WL_OK) break;
-      if ((rc = ensure(h->yprev, (size_t)K * ntau * ldT * 8)) != WL_OK) break;
-      if ((rc = ensure(h->errb, (size_t)K * ntau * 8 * 2 + 64 * 4 * 3)) != WL_OK) break;
-      if ((rc = ensure(h->packX, blk * 8)) != WL_OK) break;
-      double* basis = (double*)h->basis.p;
-      double* Ta = (double*)h->Tab.p;
-      double* Tb = Ta + (size_t)K * ldT;
-      double* nrm = Tb + (size_t)K * ldT;
-      int* done = (int*)((double*)h->errb.p + (size_t)K * ntau * 2);
-      int* mcol = done + 64;
-      int* mprev = done + 128;
-      double* errd = (double*)h->errb.p;
-      // V_0 = U0 block / |U0 block| (per column)
-      counted(h, 3);
+      if ((rc = ensure(h->packX, (size_t)n * K * 8)) != WL_OK) break;
+      counted(h);
       cudaError_t e = h->perm ? launch_pack_perm(U0d, ldu, c0, K, n, 1.0, h->perm, (double*)h->packX.p, S(h))
                               : launch_pack(U0d, ldu, c0, K, n, 1.0, h->packX.p, false, S(h));
-      if (e == cudaSuccess) e = launch_colnorms((const double*)h->packX.p, n, K, nrm, S(h));
-      if (e == cudaSuccess)
-        e = dfp ? launch_df_scale_cols((const double*)h->packX.p, n, K, nrm, (float*)basis, (float*)basis + blk, S(h))
-                : launch_scale_cols((const double*)h->packX.p, n, K, nrm, basis, S(h));
-      if (e != cudaSuccess) { rc = set_cuda_error(e, "expmv init"); break; }
-      // done flags: zero columns
-      WL_CU(cudaMemcpyAsync(h->h_pin, nrm, K * 8, cudaMemcpyDeviceToHost, S(h)));
-      WL_CU(cudaStreamSynchronize(S(h)));
-      std::vector<int> hdone(K), hzero(K, 0);
-      std::vector<double> hb2(K);
-      for (int c = 0; c < K; ++c) {
-        hdone[c] = (h->h_pin[c] > 0.0) ? 0 : 1;
-        hb2[c] = hdone[c] ? 0.0 : 1.0;
-      }
-      WL_CU(cudaMemcpyAsync(done, hdone.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
-      WL_CU(cudaMemcpyAsync(mprev, hzero.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
-      double* bn2 = (double*)h->small.p + 664;  // |v_j|^2 per column for the double-float solves
-      if (dfp) {
-        WL_CU(cudaMemcpyAsync(bn2, hb2.data(), K * 8, cudaMemcpyHostToDevice, S(h)));
-        if ((rc = ensure(h->xh, blk * 4)) != WL_OK) break;
-        if ((rc = ensure(h->xl, blk * 4)) != WL_OK) break;
-      }
-      const int Gs = dfp ? df_lanczos_grid(K) : lanczos_step_grid(K);
-      int Tw, Tc;
-      thresholds_f64(K, &Tw, &Tc);
-      PartDev* pd = nullptr;
-      if (!dfp && (rc = get_part(h, Gs, Tw, Tc, &pd, K, 8)) != WL_OK) break;
-      if ((rc = ensure(h->part, (size_t)std::max(Gs, 1) * 64 * 2 * 8 + 1024)) != WL_OK) break;
-      int m = 0;
-      bool converged = false;
-      for (int j = 0; j < maxm; ++j) {
-        if ((size_t)(j + 2) > cap_blocks) {
-          // grow the basis (double), keeping the blocks computed so far
-          Buf nb;
-          size_t nbk = std::min<size_t>((size_t)maxm + 1, cap_blocks * 2);
-          if ((rc = ensure(nb, nbk * blk * 8)) != WL_OK) break;
-          WL_CU(cudaMemcpyAsync(nb.p, h->basis.p, cap_blocks * blk * 8, cudaMemcpyDeviceToDevice, S(h)));
-          WL_CU(cudaStreamSynchronize(S(h)));
-          release(h->basis);
-          h->basis = nb;
-          h->basis_blocks = nbk;
-          cap_blocks = nbk;
-          basis = (double*)h->basis.p;
-        }
-        if (dfp) {
-          // double-float basis: block j holds hi then lo terms
-          float* vjh = (float*)basis + (size_t)2 * j * blk;
-          float* vmh = j > 0 ? (float*)basis + (size_t)2 * (j - 1) * blk : nullptr;
-          float* vph = (float*)basis + (size_t)2 * (j + 1) * blk;
-          if ((rc = solve_refined_df(h, vjh, vjh + blk, bn2, (float*)h->xh.p, (float*)h->xl.p, nullptr, K,
-                                     h->prm.tol, info)) != WL_OK)
-            break;
-          if (info.status != WL_OK) break;
-          if ((rc = ensure(h->part, (size_t)std::max(Gs, 1) * 64 * 2 * 8 + 1024)) != WL_OK) break;
-          DfLanczosArgs la{vjh, vjh + blk, vmh, vmh ? vmh + blk : nullptr, (const float*)h->xh.p,
-                           (const float*)h->xl.p, (const float*)h->dfdf.p, (const float*)h->dfdf.p + n,
-                           df_from_double(h->a_scale), vph, vph + blk, Ta, Tb, done, bn2, (double*)h->part.p,
-                           h->bar, n, j, ldT};
-          if ((rc = reset_bar(h)) != WL_OK) break;
-          const int pl = prof_begin(h, kCatLan);
-          counted(h);
-          e = launch_df_lanczos_step(K, la, Gs, S(h));
-          prof_end(h, pl);
-          if (e != cudaSuccess) { rc = set_cuda_error(e, "df_lanczos_step"); break; }
-        } else {
-          double* vj = basis + (size_t)j * blk;
-          double* vjm1 = j > 0 ? basis + (size_t)(j - 1) * blk : nullptr;
-          double* vjp1 = basis + (size_t)(j + 1) * blk;
-          LanczosStepArgs la{h->g, pd->view(), vj, vjm1, nullptr, (const double*)h->Df.p, 0, 0, 0, vjp1,
-                             Ta, Tb, done, (double*)h->part.p, h->bar, j, ldT, 0};
-          if (h->prm.f == WL_F_IDENTITY) {
-            la.mode = 1;
-            la.c0 = 0.0;
-            la.cA = -1.0;
-            la.cD = 1.0;
-            info.nnz_rhs += (double)h->nnz * K;
-            info.iters += 1;
-          } else {
-            if ((rc = phi_apply(h, vj, (double*)h->packX.p, K, info)) != WL_OK) break;
-            if (info.status != WL_OK) break;
-            la.X = (const double*)h->packX.p;
-            la.part = (double*)h->part.p;
-          }
-          if ((rc = reset_bar(h)) != WL_OK) break;
-          const int pl = prof_begin(h, kCatLan);
-          e = launch_lanczos_step(K, la, Gs, S(h));
-          prof_end(h, pl);
-          if (e != cudaSuccess) { rc = set_cuda_error(e, "lanczos_step"); break; }
-        }
-        m = j + 1;
-        ++outer_total;
-        if (m % check == 0 || m == maxm) {
-          std::vector<int> hm(K, m);
-          WL_CU(cudaMemcpyAsync(mcol, hm.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
-          TridiagArgs ta{Ta, Tb, mcol, dtaus, (double*)h->ybuf.p, (double*)h->yprev.p, mprev, errd, ldT, ntau, 1,
-                         kChebMax};
-          counted(h);
-          e = launch_tridiag_exp(ta, K, S(h));
-          if (e != cudaSuccess) { rc = set_cuda_error(e, "tridiag_exp"); break; }
-          WL_CU(cudaMemcpyAsync(mprev, mcol, K * 4, cudaMemcpyDeviceToDevice, S(h)));
-          WL_CU(cudaMemcpyAsync(h->h_pin, errd, (size_t)K * ntau * 8, cudaMemcpyDeviceToHost, S(h)));
-          const int berr = check_bar(h);
-          if (berr) { rc = berr; break; }
-          bool all = true;
-          for (int c = 0; c < K && all; ++c)
-            for (int t = 0; t < ntau; ++t)
-              if (!(h->h_pin[c * ntau + t] <= h->prm.outer_tol)) { all = false; break; }
-          if (all) { converged = true; break; }
-        }
-      }
-      if (rc != WL_OK || info.status != WL_OK) break;
-      if (!converged) info.status = WL_ERR_NO_CONVERGENCE;
-      // final y for all columns at m (recompute if the last step was not a check)
-      if (m % check != 0 && m != maxm) {
-        std::vector<int> hm(K, m);
-        WL_CU(cudaMemcpyAsync(mcol, hm.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
-        TridiagArgs ta{Ta, Tb, mcol, dtaus, (double*)h->ybuf.p, (double*)h->yprev.p, mprev, errd, ldT, ntau, 1,
-                       kChebMax};
-        counted(h);
-        e = launch_tridiag_exp(ta, K, S(h));
-        if (e != cudaSuccess) { rc = set_cuda_error(e, "tridiag_exp"); break; }
-      }
-      {
-        std::vector<int> hm(K, m);
-        WL_CU(cudaMemcpyAsync(mcol, hm.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
-      }
-      if (dfp) {
-        const size_t ny = (size_t)K * ntau * ldT;
-        if ((rc = ensure(h->ydf, ny * 8)) != WL_OK) break;
-        counted(h, 2);
-        e = launch_df_split((const double*)h->ybuf.p, ny, (float*)h->ydf.p, (float*)h->ydf.p + ny, S(h));
-        DfCombineArgs ca{(const float*)basis, (const float*)h->ydf.p, (const float*)h->ydf.p + ny, mcol, nrm, Ud,
-                         n, ldo, n * ldo, c0, ldT, ntau, h->perm};
-        if (e == cudaSuccess) e = launch_df_combine(K, ca, S(h));
-      } else {
-        CombineArgs ca{basis, (const double*)h->ybuf.p, mcol, nrm, Ud, n, ldo, n * ldo, c0, ldT, ntau, h->perm};
-        counted(h);
-        e = launch_combine(K, ca, S(h));
-      }
-      if (e != cudaSuccess) { rc = set_cuda_error(e, "combine"); break; }
+      if (e != cudaSuccess) { rc = set_cuda_error(e, "expmv pack"); break; }
+      OuterRun o;
+      if ((rc = outer_run(h, K, dtaus, ntau, info, o, outer_total)) != WL_OK) break;
+      if (info.status != WL_OK) break;
+      if ((rc = outer_combine(h, o, 0, ntau, Ud, ldo, n * ldo, c0, h->perm)) != WL_OK) break;
+      if (!o.converged) info.status = WL_ERR_NO_CONVERGENCE;
       c0 += K;
     }
     if (rc != WL_OK) break;
@@ -1729,6 +1790,86 @@ int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, u
   const double ms = end_timer(h);
   if (rc == WL_OK) rc = info.status;
   fill_stats(h, st, info, rc, ms, 0);
+  return rc;
+}
+
+int wl_return_prob(wl_handle* h, int M, uint64_t seed, const double* ts, int nt, double* p_est, double* p_err,
+                   wl_stats* st) {
+  CallScope cs__(h ? &h->retired : nullptr);
+  if (!h || !ts || !p_est || !p_err || M < 2 || M > kMaxSketch || nt < 1 || nt > kMaxReturnT) return WL_ERR_INVALID_ARG;
+  for (int t = 0; t < nt; ++t)
+    if (!(ts[t] >= 0.0) || !std::isfinite(ts[t])) return WL_ERR_INVALID_ARG;
+  SolveInfo info;
+  begin_timer(h);
+  for (int t = 0; t < nt; ++t) p_est[t] = p_err[t] = 0.0;
+  if (h->n == 0) {
+    fill_stats(h, st, info, WL_OK, end_timer(h), 0);
+    return WL_OK;
+  }
+  const int64_t n = h->n;
+  int K = 1;
+  while (K < M) K <<= 1;
+  int rc = WL_OK;
+  int outer_total = 0;
+  do {
+    const size_t nk = (size_t)n * K;
+    if ((rc = ensure(h->omega, (size_t)n * M * sizeof(uint16_t))) != WL_OK) break;
+    if ((rc = ensure(h->x, nk * 4)) != WL_OK) break;      // Y(t) in FP32 for the Gram
+    if ((rc = ensure(h->packX, nk * 8)) != WL_OK) break;  // Omega as the FP64 start block
+    if ((rc = ensure(h->ybig, (size_t)kMaxTau * nk * 8)) != WL_OK) break;
+    const int Gg = gram_grid(n);
+    if ((rc = ensure(h->gram, (size_t)Gg * 2 * kMaxSketch * kMaxSketch * 4 + 2 * kMaxSketch * kMaxSketch * 8 +
+                                 128 * 8)) != WL_OK) break;
+    uint16_t* omega = (uint16_t*)h->omega.p;
+    float* partial = (float*)h->gram.p;
+    double* gout = (double*)((char*)h->gram.p + (size_t)Gg * 2 * kMaxSketch * kMaxSketch * 4);
+    double* core = gout + 2 * kMaxSketch * kMaxSketch;
+    counted(h, 2);
+    cudaError_t e = launch_philox_sketch(omega, n, M, seed, S(h));
+    uint16_t* om_int = omega;  // sketch rows in the internal node order
+    if (e == cudaSuccess && h->perm) {
+      if ((rc = ensure(h->omega_int, (size_t)n * M * sizeof(uint16_t))) != WL_OK) break;
+      om_int = (uint16_t*)h->omega_int.p;
+      counted(h);
+      e = launch_permute_rows_u16(omega, n, M, h->perm, om_int, S(h));
+    }
+    if (e == cudaSuccess) e = launch_sketch_block_f64(om_int, n, M, K, (double*)h->packX.p, S(h));
+    if (e != cudaSuccess) { rc = set_cuda_error(e, "sketch"); break; }
+    const double* dtaus = nullptr;
+    if ((rc = stage_taus(h, ts, nt, &dtaus)) != WL_OK) break;
+    // Y(t) = exp(-t L) Omega for every t from one Lanczos run per column
+    OuterRun o;
+    if ((rc = outer_run(h, K, dtaus, nt, info, o, outer_total)) != WL_OK) break;
+    if (info.status != WL_OK) break;
+    if (!o.converged) info.status = WL_ERR_NO_CONVERGENCE;
+    int* gerr = (int*)((double*)h->small.p + 1000);
+    double* hp = h->h_pin;
+    double* Y = (double*)h->ybig.p;
+    for (int t0 = 0; t0 < nt && rc == WL_OK; t0 += kMaxTau) {
+      const int nb = std::min(kMaxTau, nt - t0);
+      if ((rc = outer_combine(h, o, t0, nb, Y, K, (int64_t)nk, 0, nullptr)) != WL_OK) break;
+      for (int i = 0; i < nb; ++i) {
+        // XNysTrace of exp(-t L) from Y(t) and Omega (Alg. 1, last step)
+        counted(h, 3);
+        e = launch_to_f32(Y + (size_t)i * nk, (int64_t)nk, (float*)h->x.p, S(h));
+        if (e == cudaSuccess) e = cudaMemsetAsync(gerr, 0, sizeof(int), S(h));
+        if (e == cudaSuccess)
+          e = launch_gram(om_int, (const float*)h->x.p, n, M, K, partial, Gg, gout, h->gram_tc, gerr, S(h));
+        if (e == cudaSuccess) e = launch_nys_core(gout, M, core, S(h));
+        if (e != cudaSuccess) { rc = set_cuda_error(e, "return probability gram/core"); break; }
+        WL_CU(cudaMemcpyAsync(hp, core, 8 * 8, cudaMemcpyDeviceToHost, S(h)));
+        WL_CU(cudaMemcpyAsync(hp + 8, gerr, sizeof(int), cudaMemcpyDeviceToHost, S(h)));
+        WL_CU(cudaStreamSynchronize(S(h)));
+        if (h->gram_tc && *(int*)(hp + 8) != 0) { rc = *(int*)(hp + 8); break; }
+        if (hp[2] != 0.0 && info.status == WL_OK) info.status = WL_ERR_NOT_SPD;
+        p_est[t0 + i] = hp[0] / (double)n;
+        p_err[t0 + i] = hp[1] / (double)n;
+      }
+    }
+  } while (0);
+  const double ms = end_timer(h);
+  if (rc == WL_OK) rc = info.status;
+  fill_stats(h, st, info, rc, ms, outer_total);
   return rc;
 }
 

@@ -141,6 +141,9 @@ cudaError_t launch_philox_sketch(uint16_t* omega, int64_t n, int M, uint64_t see
 cudaError_t launch_permute_rows_u16(const uint16_t* src, int64_t n, int M, const int32_t* perm, uint16_t* dst,
                                     cudaStream_t s);
 cudaError_t launch_sketch_rhs(const uint16_t* omega, int64_t n, int M, int K, double a, float* B, cudaStream_t s);
+// Omega (bf16, n x M) as FP64 n x K with zero columns M..K-1; FP64 -> FP32 copy
+cudaError_t launch_sketch_block_f64(const uint16_t* omega, int64_t n, int M, int K, double* B, cudaStream_t s);
+cudaError_t launch_to_f32(const double* X, int64_t total, float* Y, cudaStream_t s);
 int gram_grid(int64_t n);
 // H = Omega^T Y and G = Y^T Y into out (128 x 64 doubles); partial holds G x 128 x 64 floats
 cudaError_t launch_gram(const uint16_t* omega, const float* Y, int64_t n, int M, int K, float* partial, int G,

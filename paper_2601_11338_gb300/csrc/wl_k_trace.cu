@@ -41,6 +41,16 @@ cudaError_t launch_sketch_rhs(const uint16_t* omega, int64_t n, int M, int K, do
   return cudaGetLastError();
 }
 
+cudaError_t launch_sketch_block_f64(const uint16_t* omega, int64_t n, int M, int K, double* B, cudaStream_t s) {
+  sketch_block_f64<<<grid_cap(n * K, 256, 152 * 32), 256, 0, s>>>(omega, n, M, K, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double* X, int64_t total, float* Y, cudaStream_t s) {
+  to_f32<<<grid_cap(total, 256, 152 * 32), 256, 0, s>>>(X, total, Y);
+  return cudaGetLastError();
+}
+
 int gram_grid(int64_t n) {
   // about 4096 rows per chunk, at most 8 CTAs per SM worth of chunks
   int64_t g = (n + 4095) / 4096;

@@ -99,6 +99,23 @@ __global__ void sketch_rhs(const uint16_t* omega, int64_t n, int M, int K, float
   }
 }
 
+// Omega as an FP64 n x K block (zero-padded columns): the start block of the
+// return-probability Lanczos
+__global__ void sketch_block_f64(const uint16_t* omega, int64_t n, int M, int K, double* B) {
+  const int64_t total = n * K;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / K;
+    const int j = (int)(e % K);
+    B[e] = (j < M) ? (double)bf16_to_f32(omega[i * M + j]) : 0.0;
+  }
+}
+
+// FP64 -> FP32 (the Gram of the estimator takes FP32 Y)
+__global__ void to_f32(const double* X, int64_t total, float* Y) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    Y[e] = (float)X[e];
+}
+
 // ---------------------------------------------------------------- Gram on CUDA cores
 // Grid of G CTAs, CTA g sums rows [g * chunk, min(n, (g+1) * chunk)).
 // Thread t owns output pairs (r, c) for r in {rt, rt + 16, ...} x c in {ct, ct + 16, ...}

@@ -85,6 +85,7 @@ def lib():
         L.wl_expmv.argtypes = [vp, vp, i64, c_int, vp, c_int, vp, i64, ctypes.POINTER(wl_stats)]
         L.wl_trace.argtypes = [vp, c_int, ctypes.c_uint64, vp, vp, vp, ctypes.POINTER(wl_stats)]
         L.wl_markov.argtypes = [vp, vp, i64, c_int, vp, c_int, vp, i64, ctypes.POINTER(wl_stats)]
+        L.wl_return_prob.argtypes = [vp, c_int, ctypes.c_uint64, vp, c_int, vp, vp, ctypes.POINTER(wl_stats)]
         L.wl_set_warm_start.argtypes = [vp, vp]
         L.wl_get_info.argtypes = [vp, ctypes.POINTER(wl_stats)]
         L.wl_destroy.argtypes = [vp]
@@ -126,7 +127,7 @@ def lib():
         L.wl_batch_destroy.argtypes = [vp]
         L.wl_batch_destroy.restype = None
         for name in ("wl_build", "wl_set_params", "wl_degrees", "wl_apply", "wl_expmv", "wl_trace",
-                     "wl_markov", "wl_set_warm_start", "wl_get_info"):
+                     "wl_markov", "wl_return_prob", "wl_set_warm_start", "wl_get_info"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -216,6 +217,17 @@ def wl_markov(h, P0, ldp, k, steps, out, ldo, stats=None, allow=()):
     steps = np.ascontiguousarray(steps, dtype=np.int32)
     return _check(lib().wl_markov(h.ptr, _ptr(P0), ldp, k, steps.ctypes.data, len(steps), _ptr(out), ldo,
                                   ctypes.byref(st)), "wl_markov", allow)
+
+
+def wl_return_prob(h, M, seed, ts, stats=None, allow=()):
+    """Average return probability estimates (p(t), error estimate) for each t."""
+    st = stats if stats is not None else wl_stats()
+    ts = np.ascontiguousarray(ts, dtype=np.float64)
+    p = np.zeros(len(ts))
+    e = np.zeros(len(ts))
+    _check(lib().wl_return_prob(h.ptr, M, seed, ts.ctypes.data, len(ts), p.ctypes.data, e.ctypes.data,
+                                ctypes.byref(st)), "wl_return_prob", allow)
+    return p, e
 
 
 def wl_trace(h, M, seed, omega_out=None, stats=None):

@@ -1,0 +1,68 @@
+"""Average return probability tr(exp(-t L)) / n and its XNysTrace estimate
+(Sec. 4.4, Alg. 1) through the C ABI.
+
+Against the oracle's Alg. 1 with exact Y(t) = exp(-t L) Omega and the same
+bit-exact Omega: the GPU's Y(t) carries the Lanczos error (outer_tol) and is
+rounded to FP32 for the Gram, like wl_trace's Y, so estimates agree within
+1e-5 relative and error estimates within 1e-2 relative (a spread of nearly
+equal t_i). Against the exact p(t): within a few error estimates."""
+import numpy as np
+import pytest
+
+import wlgen
+from oracle import graph, philox, walks, xnys
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def WL(g, **kw):
+    from paper_2601_11338_gb300.api import WalkLaplacian
+    return WalkLaplacian(g.row_ptr.astype(np.int32), g.col_idx, g.n, **kw)
+
+
+@pytest.mark.parametrize("variant,mu,prec,M,reorder", [("allwalk", 0.0, "fp64", 16, 1), ("nbt", 1.0, "refined", 7, 0),
+                                                        ("btdw", 0.5, "refined", 32, 1)])
+def test_estimates_match_oracle_alg1(variant, mu, prec, M, reorder):
+    g = wlgen.erdos_renyi(500, 8, 51)
+    A = graph.dense_adjacency(g.row_ptr, g.col_idx, g.n)
+    w = WL(g, variant=variant, mu=mu, alpha_rel=0.5, prec=prec, tol=1e-12, outer_tol=1e-11, reorder=reorder)
+    L = walks.walk_laplacian(walks.phi_resolvent_closed(A, mu, w.info["alpha"]))
+    ts = [0.0, 0.3, 1.0, 2.5]
+    seed = 9001 + M
+    p, e = w.return_prob(M, seed, ts)
+    Om, _ = philox.gaussian_sketch(g.n, M, seed)
+    want = xnys.xnys_return_probability(L, Om, ts)
+    exact = xnys.return_probability(L, ts)
+    for i, (pe, ee) in enumerate(want):
+        assert abs(p[i] - pe) <= 1e-5 * abs(pe), (ts[i], p[i], pe)
+        assert abs(e[i] - ee) <= 1e-2 * ee + 1e-12, (ts[i], e[i], ee)
+        assert abs(p[i] - exact[i]) <= 8 * e[i] + 1e-12, (ts[i], p[i], exact[i], e[i])
+    w.close()
+
+
+def test_many_time_points_and_identity_function():
+    """Combinatorial Laplacian (identity f) on a cycle: 90 time points in
+    [0, 5] (several batches of the combination); the estimates follow the
+    Bessel closed form e^{-2t} I_0(2t) of tr(exp(-t L)) / n within their error
+    estimates, and decrease from 1."""
+    from scipy.special import iv
+    n = 600
+    g = wlgen.cycle(n)
+    w = WL(g, f="identity", outer_tol=1e-11)
+    ts = np.linspace(0.0, 5.0, 90)
+    p, e = w.return_prob(24, 77, ts)
+    exact = np.exp(-2 * ts) * iv(0, 2 * ts)
+    assert np.all(np.abs(p - exact) <= 8 * e + 1e-12)
+    assert abs(p[0] - 1.0) < 0.05 and p[-1] < p[0]
+    w.close()
+
+
+def test_argument_checks():
+    from paper_2601_11338_gb300 import wl
+    g = wlgen.erdos_renyi(50, 4, 3)
+    w = WL(g, alpha_rel=0.5)
+    for M, ts in ((1, [0.5]), (65, [0.5]), (8, [-1.0]), (8, [])):
+        with pytest.raises(wl.WLError):
+            w.return_prob(M, 1, ts)
+    w.close()

@@ -145,3 +145,40 @@ def test_triangles_two_ways():
     A = graph.dense_adjacency(g.row_ptr, g.col_idx, g.n)
     np.testing.assert_allclose(np.expm1(features.raw_features(A)[:, 2]),
                                features.triangles_by_intersection(g.row_ptr, g.col_idx, g.n), atol=1e-9)
+
+
+# ---------------------------------------------------------------- average return probability
+def test_return_probability_cycle_closed_form():
+    """On C_n with the combinatorial Laplacian the eigenvalues are
+    2 - 2 cos(2 pi j / n), and by Poisson summation
+    tr(exp(-t L)) / n = e^{-2t} sum_m I_{m n}(2t) (modified Bessel functions);
+    for n = 40 and t <= 3 the terms |m| >= 2 are below 1e-30."""
+    from scipy.special import iv
+    n = 40
+    A = graph.dense_adjacency(*_cycle_csr(n), n)
+    L = np.diag(A.sum(axis=1)) - A
+    ts = [0.0, 0.1, 1.0, 3.0]
+    got = xnys.return_probability(L, ts)
+    want = [np.exp(-2 * t) * (iv(0, 2 * t) + 2 * iv(n, 2 * t)) for t in ts]
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=0)
+
+
+def test_return_probability_limits():
+    """p(0) = 1; for large t only the null space of L survives: p -> c / n
+    with c connected components (two here)."""
+    A = np.zeros((7, 7))
+    for i, j in [(0, 1), (1, 2), (2, 0), (3, 4), (4, 5), (5, 6)]:
+        A[i, j] = A[j, i] = 1.0
+    L = np.diag(A.sum(axis=1)) - A
+    p = xnys.return_probability(L, [0.0, 200.0])
+    assert abs(p[0] - 1.0) < 1e-15
+    assert abs(p[1] - 2.0 / 7.0) < 1e-12
+
+
+def _cycle_csr(n):
+    rp = np.arange(0, 2 * n + 1, 2, dtype=np.int64)
+    col = np.empty(2 * n, dtype=np.int32)
+    for i in range(n):
+        a, b = (i - 1) % n, (i + 1) % n
+        col[2 * i], col[2 * i + 1] = min(a, b), max(a, b)
+    return rp, col
