@@ -32,6 +32,14 @@ constexpr int kPhaseBlock = 256;   // threads per CTA of the phase kernels
 #define WL_PHASE_MINB 5
 #endif
 constexpr int kPhaseMinBlocks = WL_PHASE_MINB;  // CTAs per SM the S kernel's registers are sized for
+// FP32 CG kernels: 6 CTAs per SM (40 registers) keep more gathers in flight;
+// measured 251 vs 265 us per K = 16 iteration on the Chung-Lu 1e6 graph
+#ifndef WL_PHASE_MINB_F32
+#define WL_PHASE_MINB_F32 6
+#endif
+constexpr int kPhaseMinBlocksF32 = WL_PHASE_MINB_F32;
+template <typename T>
+constexpr int phase_min_blocks() { return sizeof(T) == 4 ? kPhaseMinBlocksF32 : kPhaseMinBlocks; }
 
 // Per-solve device state (written by the last CTA of each kernel).
 struct CgState {
@@ -160,7 +168,7 @@ __device__ __forceinline__ void sum_partials(const double* part, int nblk, doubl
 
 // ---------------------------------------------------------------- S phase
 template <typename T, int K>
-__global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) cg_s_phase(PhaseArgs<T> a) {
+__global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks<T>()) cg_s_phase(PhaseArgs<T> a) {
   using C = Cfg<T, K>;
   constexpr int VW = C::VW, G = C::G, RPB = kPhaseBlock / G;  // rows per CTA pass
   __shared__ __align__(16) T s_red[kPhaseBlock * VW];
@@ -171,12 +179,12 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) cg_s_phase(Phase
   const int tid = threadIdx.x, sl = tid % G, lane_off = sl * VW;
   const bool first = (st->iters == 0);
   const T ca = (T)a.ca, cA = (T)a.cA, cD = (T)a.cD;
-  T al[VW], be[VW];
-#pragma unroll
-  for (int v = 0; v < VW; ++v) {
-    al[v] = (T)st->alpha[lane_off + v];
-    be[v] = (T)st->beta[lane_off + v];
+  __shared__ T s_ab[2][K];
+  if (tid < K) {
+    s_ab[0][tid] = (T)st->alpha[tid];
+    s_ab[1][tid] = (T)st->beta[tid];
   }
+  __syncthreads();
   T dacc[VW];  // per-thread partials in the working precision (FP64 adds are scarce on this GPU)
 #pragma unroll
   for (int v = 0; v < VW; ++v) dacc[v] = T(0);
@@ -193,15 +201,16 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) cg_s_phase(Phase
     Own o;
     const size_t off = (size_t)row * K + lane_off;
     o.r = ld_plain<T, VW>(pr + off);
-    if (!first) {
-      o.x = ld_plain<T, VW>(px + off);
-      o.p = ld_plain<T, VW>(pp_ + off);
-      o.q = ld_plain<T, VW>(pq + off);
-    }
     return o;
   };
-  auto fin = [&](int64_t row, int deg, const T (&nb)[VW], const Own& w) {
+  auto fin = [&](int64_t row, int deg, const T (&nb)[VW], const Own& w0) {
     const size_t o = (size_t)row * K + lane_off;
+    Own w = w0;
+    if (!first) {
+      w.x = ld_plain<T, VW>(px + o);
+      w.p = ld_plain<T, VW>(pp_ + o);
+      w.q = ld_plain<T, VW>(pq + o);
+    }
     const Pack<T, VW>& rr = w.r;
     Pack<T, VW> pp, qq;
     const T dg = (T)deg;
@@ -216,9 +225,10 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) cg_s_phase(Phase
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
         const T s = ca * rr.v[v] + cA * nb[v] + cD * dg * rr.v[v];
-        xx.v[v] += al[v] * w.p.v[v];
-        pp.v[v] = rr.v[v] + be[v] * w.p.v[v];
-        qq.v[v] = s + be[v] * w.q.v[v];
+        const T al = s_ab[0][lane_off + v], be = s_ab[1][lane_off + v];
+        xx.v[v] += al * w.p.v[v];
+        pp.v[v] = rr.v[v] + be * w.p.v[v];
+        qq.v[v] = s + be * w.q.v[v];
       }
       stp<T, VW>(px + o, xx);
     }
@@ -310,7 +320,7 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) cg_s_phase(Phase
 // ---------------------------------------------------------------- U phase (and init)
 // init = 1: gamma_0 = (r, r), convergence reference and flags, no update.
 template <typename T, int K>
-__global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) cg_u_phase(PhaseArgs<T> a, int init) {
+__global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks<T>()) cg_u_phase(PhaseArgs<T> a, int init) {
   using C = Cfg<T, K>;
   constexpr int VW = C::VW, G = C::G;
   __shared__ double s_tmp[kPhaseBlock];
