@@ -137,11 +137,27 @@ def recorded_traffic(kernel_tag):
     return d.get("dram_bytes_per_iteration")
 
 
-def make_workload(rank):
+def make_workload(rank, n=N_NODES):
+    """The graph (the same on every rank) and this rank's point sources (each
+    rank draws its own: replicas with weak scaling)."""
     import wlgen
-    g = wlgen.chung_lu(N_NODES, seed=SEED_GRAPH)
+    g = wlgen.chung_lu(n, seed=SEED_GRAPH)
     nodes = wlgen.point_sources(g, K_SRC, SEED_SRC + rank)
     return g, nodes
+
+
+def reduce_over_ranks(ms, units, device=None):
+    """Whole-job timing of the replicas: the slowest rank's time and the sum of
+    all ranks' units (no collective on the data path; this is the only one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(units)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 # ------------------------------------------------------------------ our arm
@@ -223,13 +239,7 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms, units], dtype=torch.float64, device=dev)
-    if ws > 1:
-        tm = t.clone()
-        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
-        t = tm
-    ms_max, units_all = float(t[0]), float(t[1])
+    ms_max, units_all = reduce_over_ranks(ms, units, dev)
     value = units_all / (ms_max / 1000.0)
     if rank != 0:
         dist.destroy_process_group()
