@@ -42,7 +42,7 @@ TAUS = [0.1, 1.0, 10.0]
 K_SRC = 16
 METRIC = "nnz*RHS*iters/s (exp(-tau L)u0, NBT resolvent, refined form)"
 UNIT = "nnz*RHS*iters/s"
-TIME_TO_RULE = {"tol": 1e-10, "outer_tol": 1e-9}  # stopping rule shared by both forms (time-to-1e-8)
+TIME_TO_RULE = {"tol": 3e-10, "outer_tol": 3e-9}  # stopping rule shared by both forms (time-to-1e-8): the loosest measured rule under which the FP64 form reaches 1e-8
 
 
 def log(*a):
