@@ -72,3 +72,23 @@ def test_exp_on_a_tree_with_nbt_walks():
     phi = walks.phi_series(A, 1.0, walks.exp_coeffs(0.9))
     assert relerr(w.degrees().cpu().numpy(), walks.walk_degrees(phi)) <= TOL
     w.close()
+
+
+def test_exp_edge_cases():
+    """No edges: phi = I (only c_0 q_0 survives), D_f = 1, L = 0. An overflowing
+    scale is reported as non-finite, not returned as garbage."""
+    from paper_2601_11338_gb300 import wl
+    from paper_2601_11338_gb300.api import WalkLaplacian
+    n = 7
+    w = WalkLaplacian(np.zeros(n + 1, np.int32), np.zeros(0, np.int32), n, f="exp", beta=0.7)
+    np.testing.assert_allclose(w.degrees().cpu().numpy(), np.ones(n), rtol=0, atol=1e-15)
+    V = torch.randn(n, 3, dtype=torch.float64, device="cuda")
+    # phi V is V carried through the double-float series (48-bit significand)
+    assert float(w.apply(V).abs().max()) <= 1e-14 * float(V.abs().max())
+    w.close()
+    g = wlgen.erdos_renyi(200, 12, 9)
+    w = WL(g, beta=200.0)
+    with pytest.raises(wl.WLError) as e:
+        w.degrees()
+    assert e.value.status == wl.WL_ERR_NONFINITE
+    w.close()

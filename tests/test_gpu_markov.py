@@ -107,3 +107,25 @@ def test_argument_checks():
         with pytest.raises(wl.WLError):
             wl.wl_markov(w.h, P0, 2, 2, steps, out, 2)
     w.close()
+
+
+def test_edge_cases():
+    """Zero steps return the start; k = 0 is a no-op; a graph without edges
+    keeps every distribution where it is (phi = I, D_f = 1)."""
+    g = wlgen.erdos_renyi(120, 5, 8)
+    w = WL(g, variant="nbt", alpha_rel=0.5)
+    P0 = point_masses(g.n, [5, 9])
+    got = w.markov(torch.as_tensor(P0, device="cuda"), [0, 0]).cpu().numpy()
+    np.testing.assert_array_equal(got[0], P0)
+    np.testing.assert_array_equal(got[1], P0)
+    out = torch.empty((1, g.n, 0), dtype=torch.float64, device="cuda")
+    from paper_2601_11338_gb300 import wl
+    assert wl.wl_markov(w.h, torch.empty((g.n, 0), dtype=torch.float64, device="cuda"), 0, 0, [3], out, 0) == wl.WL_OK
+    w.close()
+    n = 9
+    from paper_2601_11338_gb300.api import WalkLaplacian
+    w0 = WalkLaplacian(np.zeros(n + 1, np.int32), np.zeros(0, np.int32), n, alpha=0.3)
+    P0 = point_masses(n, [1, 4])
+    got = w0.markov(torch.as_tensor(P0, device="cuda"), [3]).cpu().numpy()[0]
+    np.testing.assert_allclose(got, P0, rtol=0, atol=1e-15)
+    w0.close()

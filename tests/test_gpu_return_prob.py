@@ -66,3 +66,15 @@ def test_argument_checks():
         with pytest.raises(wl.WLError):
             w.return_prob(M, 1, ts)
     w.close()
+
+
+def test_graph_without_edges():
+    """L = 0: exp(-t L) = I at every t, so the estimate is XNysTrace of the
+    identity (unbiased for n; its spread is the error estimate)."""
+    from paper_2601_11338_gb300.api import WalkLaplacian
+    n = 2000
+    w = WalkLaplacian(np.zeros(n + 1, np.int32), np.zeros(0, np.int32), n, alpha=0.3)
+    p, e = w.return_prob(16, 3, [0.0, 1.0, 50.0])
+    assert np.all(np.abs(p - 1.0) <= 6 * e + 1e-12)
+    assert abs(p[0] - p[2]) < 1e-12
+    w.close()
