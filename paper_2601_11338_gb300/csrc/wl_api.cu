@@ -1058,7 +1058,7 @@ int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& inf
       TridiagArgs ta{Ta, Tb, mcol, dtaus, (double*)h->ybuf.p, (double*)h->yprev.p, mprev, errd, ldT, ntau, 1,
                      kChebMax};
       counted(h);
-      e = launch_tridiag_exp(ta, K, S(h));
+      e = launch_tridiag_exp(ta, K, m, S(h));
       if (e != cudaSuccess) return set_cuda_error(e, "tridiag_exp");
       WL_CU(cudaMemcpyAsync(mprev, mcol, K * 4, cudaMemcpyDeviceToDevice, S(h)));
       WL_CU(cudaMemcpyAsync(h->h_pin, errd, (size_t)K * ntau * 8, cudaMemcpyDeviceToHost, S(h)));
@@ -1095,7 +1095,7 @@ int outer_combine(wl_handle* h, const OuterRun& o, int t0, int nt, double* out, 
   TridiagArgs ta{Ta, Tb, mcol, o.dtaus + t0, (double*)h->ybuf.p, (double*)h->yprev.p, mzero, errd, ldT, nt, 1,
                  kChebMax};
   counted(h);
-  cudaError_t e = launch_tridiag_exp(ta, K, S(h));
+  cudaError_t e = launch_tridiag_exp(ta, K, o.m, S(h));
   if (e != cudaSuccess) return set_cuda_error(e, "tridiag_exp");
   if (o.dfp) {
     const size_t ny = (size_t)K * nt * ldT;

@@ -120,7 +120,8 @@ cudaError_t launch_list_entries(const int32_t* row_ptr, const int32_t* rows, int
 // ---- wl_k_lanczos.cu
 int lanczos_step_grid(int K);
 cudaError_t launch_lanczos_step(int K, const LanczosStepArgs& a, int G, cudaStream_t s);
-cudaError_t launch_tridiag_exp(const TridiagArgs& a, int K, cudaStream_t s);
+// y = exp(-tau T_m) e_1 per (column, tau); mmax bounds the steps of every column
+cudaError_t launch_tridiag_exp(const TridiagArgs& a, int K, int mmax, cudaStream_t s);
 cudaError_t launch_combine(int K, const CombineArgs& a, cudaStream_t s);
 
 // ---- wl_k_spec.cu: spectral-scale Lanczos (double-float basis, k = 1)

@@ -29,8 +29,15 @@ cudaError_t launch_lanczos_step(int K, const LanczosStepArgs& a, int G, cudaStre
   return coop_launch(f, G, a, s);
 }
 
-cudaError_t launch_tridiag_exp(const TridiagArgs& a, int K, cudaStream_t s) {
-  tridiag_exp<<<dim3(K, a.ntau), kBlock, 0, s>>>(a);
+// a warp per (column, tau) when every column has at most kWarpRows steps
+// (mmax is the host's bound on the steps), else a CTA per pair
+cudaError_t launch_tridiag_exp(const TridiagArgs& a, int K, int mmax, cudaStream_t s) {
+  if (mmax <= kWarpRows) {
+    const int pairs = K * a.ntau;
+    tridiag_exp_warp<<<(pairs + 3) / 4, 128, 0, s>>>(a, K);
+  } else {
+    tridiag_exp<<<dim3(K, a.ntau), kBlock, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -307,6 +307,153 @@ __global__ void __launch_bounds__(kBlock) tridiag_exp(TridiagArgs a) {
   }
 }
 
+// One warp per (column, tau), for m <= kWarpRows: the same Chebyshev
+// expansion summed by Clenshaw's backward recurrence, which runs in the same
+// direction as Miller's recurrence for the Bessel coefficients, so neither
+// the coefficients nor a block barrier is needed: every lane carries the
+// scalar recurrence and kRowsPerLane consecutive rows of the vectors, and
+// the tridiagonal product takes its two off-lane neighbours by shuffles.
+// With B_{N+1} = B_{N+2} = 0 and B_k = c_k e_1 + 2 X B_{k+1} - B_{k+2}
+// (X = (T - mid) / half), sum_{k<=N} c_k T_k(X) e_1 = c_0 e_1 + X B_1 - B_2.
+constexpr int kRowsPerLane = 4;
+constexpr int kWarpRows = 32 * kRowsPerLane;
+
+__global__ void __launch_bounds__(128) tridiag_exp_warp(TridiagArgs a, int K) {
+  const int lane = threadIdx.x & 31;
+  const int pair = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int c = pair / a.ntau, t = pair % a.ntau;
+  if (c >= K) return;  // whole warp
+  const int m = a.mcol[c];
+  const double tau = a.taus[t];
+  const double* Ta = a.Ta + (size_t)c * a.ldT;
+  const double* Tb = a.Tb + (size_t)c * a.ldT;
+  // rows i = lane * R + q of this lane
+  constexpr int R = kRowsPerLane;
+  double al[R], bl[R], bm;  // diagonal, coupling to row i+1, coupling of the lane's first row to row i-1
+  double lo = 1e300, hi = -1e300;
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int i = lane * R + q;
+    al[q] = (i < m) ? Ta[i] : 0.0;
+    bl[q] = (i + 1 < m) ? Tb[i] : 0.0;
+  }
+  bm = (lane * R > 0 && lane * R < m) ? Tb[lane * R - 1] : 0.0;
+  // Gershgorin bounds
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int i = lane * R + q;
+    if (i < m) {
+      const double left = (q == 0) ? fabs(bm) : fabs(bl[q - 1]);
+      const double r = left + fabs(bl[q]);
+      lo = fmin(lo, al[q] - r);
+      hi = fmax(hi, al[q] + r);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+  }
+  if (a.psd) lo = fmax(lo, 0.0);
+  if (hi < lo) hi = lo;
+  const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+  const double zz = fabs(tau) * half;
+  const double pref = exp(-tau * mid + zz);
+  const double ih = (half > 0.0) ? 1.0 / half : 0.0;
+  int N = (int)ceil(sqrt(90.0 * zz) + 30.0);
+  if (N > a.max_terms - 1) N = a.max_terms - 1;
+  if (N > kChebMax - 1) N = kChebMax - 1;
+  double yv[R];
+  if (zz < 1e-30) {  // exp(-z x) = 1 + O(1e-30) on [-1, 1]
+#pragma unroll
+    for (int q = 0; q < R; ++q) yv[q] = (lane * R + q == 0) ? pref : 0.0;
+  } else {
+    // X v for the lane's rows (shuffles for the neighbours across lanes)
+    auto xmul = [&](const double (&v)[R], double (&out)[R]) {
+      const double prev = __shfl_up_sync(0xffffffffu, v[R - 1], 1);
+      const double next = __shfl_down_sync(0xffffffffu, v[0], 1);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const double vm = (q == 0) ? (lane > 0 ? prev : 0.0) : v[q - 1];
+        const double vp = (q == R - 1) ? (lane < 31 ? next : 0.0) : v[q + 1];
+        const double bmq = (q == 0) ? bm : bl[q - 1];
+        out[q] = ((al[q] - mid) * v[q] + bmq * vm + bl[q] * vp) * ih;
+      }
+    };
+    const double sgn = (tau >= 0.0) ? -1.0 : 1.0;
+    const int M0 = 2 * N + 60;
+    const double tz = 2.0 / zz;
+    double ikp1 = 0.0, ik = 1e-280;  // Miller: I_{k-1} = (2k / z) I_k + I_{k+1}
+    double b1[R], b2[R];             // B_{k+1}, B_{k+2}
+#pragma unroll
+    for (int q = 0; q < R; ++q) b1[q] = b2[q] = 0.0;
+    double S = 0.0;                  // I_0 + 2 sum_{k=1}^{N} I_k (unnormalised)
+    double c0 = 0.0;
+    for (int k = M0; k >= 1; --k) {
+      const double ikm1 = (tz * k) * ik + ikp1;
+      ikp1 = ik;
+      ik = ikm1;  // I_{k-1}
+      const int kk = k - 1;
+      if (kk <= N) {
+        const double ck = (kk == 0 ? 1.0 : 2.0) * ((kk & 1) ? sgn : 1.0) * ik;
+        S += (kk == 0 ? 1.0 : 2.0) * ik;
+        if (kk >= 1) {
+          double xb[R];
+          xmul(b1, xb);
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const double bk = ((lane * R + q == 0) ? ck : 0.0) + 2.0 * xb[q] - b2[q];
+            b2[q] = b1[q];
+            b1[q] = bk;
+          }
+        } else {
+          c0 = ck;
+        }
+      }
+      if (fabs(ik) > 1e250) {  // rescale everything linear in the I_k
+        ik *= 1e-250;
+        ikp1 *= 1e-250;
+        S *= 1e-250;
+        c0 *= 1e-250;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          b1[q] *= 1e-250;
+          b2[q] *= 1e-250;
+        }
+      }
+    }
+    // sum = c0 e_1 + X B_1 - B_2, normalised by S
+    double xb[R];
+    xmul(b1, xb);
+    const double sc = pref / S;
+#pragma unroll
+    for (int q = 0; q < R; ++q) yv[q] = sc * (((lane * R + q == 0) ? c0 : 0.0) + xb[q] - b2[q]);
+  }
+  // write y and the change against the previous result
+  double* yo = a.y + ((size_t)c * a.ntau + t) * a.ldT;
+  double* yp = a.yprev + ((size_t)c * a.ntau + t) * a.ldT;
+  const int mp = a.mprev[c];
+  double e2 = 0.0;
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int i = lane * R + q;
+    if (i < m) {
+      yo[i] = yv[q];
+      const double d = yv[q] - (i < mp ? yp[i] : 0.0);
+      e2 += d * d;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
+  if (lane == 0) a.err[c * a.ntau + t] = sqrt(e2);
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int i = lane * R + q;
+    if (i < m) yp[i] = yv[q];
+  }
+}
+
 #endif  // WL_LANCZOS_KERNELS
 
 // ------------------------------------------------------------------ U = |u0| V y
