@@ -5,7 +5,8 @@ Chung-Lu power-law graph (n = 1e6, degree exponent 2.5, mean degree 12,
 minimum degree 1), alpha = 0.5 / rho(Z_1), and the diffusion
 exp(-tau L) U0 for 16 point sources at tau in {0.1, 1, 10}: graph build
 (validation + spectral radius), walk degrees, then the Lanczos/CG diffusion,
-in the refined form (FP32 inner CG, FP64 residual, FP64 Lanczos). Inputs are
+in the refined form (FP32 inner CG; residual, iterate and Lanczos basis in
+double-float, i.e. FP32 pairs). Inputs are
 resident on the GPU when the timed region starts.
 
 Metric: nnz * RHS * iterations per second over all operator SpMM
@@ -308,7 +309,7 @@ def run_ours(args):
         "config": {"workload": "chung_lu_1e6_nbt_expmv_16src_3tau", "graph": "Chung-Lu power law",
                    "n": g.n, "nnz": g.nnz, "gamma": 2.5, "mean_degree": 12, "min_degree": 1,
                    "variant": "nbt", "f": "resolvent", "alpha": "0.5/rho(Z_1)", "rhs": K_SRC, "taus": TAUS,
-                   "form": "refined (FP32 CG + FP64 residual/update, FP64 Lanczos)",
+                   "form": "refined (FP32 CG + double-float residual/update and Lanczos)",
                    "stopping_rule": dict(TIME_TO_RULE), "parallelism": f"replicas{ws}",
                    "l2": "flushed between steps (256 MB write inside the timed region); per-step working set > 10 GB",
                    "seeds": {"graph": SEED_GRAPH, "sources": SEED_SRC}},
@@ -492,7 +493,7 @@ def run_batch(args):
         "config": {"workload": "batch64_er_ba_grid_5mu_k32", "graphs": len(gs), "n": n, "nnz": nnz,
                    "sizes": "log-uniform [1e3, 2e5]", "generators": "ER(mean deg 10) / BA(m=3) / 2D grid",
                    "mus": BATCH_MUS, "rhs": BATCH_K, "alpha": "0.5/rho(Z_mu) per problem", "tol": 1e-10,
-                   "form": "refined (FP32 CG + FP64 residual/update)", "tile_rows": tile,
+                   "form": "refined (FP32 CG + double-float residual, FP64 iterate)", "tile_rows": tile,
                    "l2": "per-step working set > 3 GB (> L2)", "seed": SEED_BATCH},
         "build_ms": build_ms,
         "iters": {"df_max": max(i["iters_df"] for i in iters), "v_max": max(i["iters_v"] for i in iters),

@@ -79,7 +79,7 @@ typedef enum {
 
 typedef enum {
   WL_FP64    = 0, /* every vector operation in FP64 ("plain FP64 Krylov") */
-  WL_REFINED = 1  /* inner CG in FP32, FP64 residual and update (iterative refinement) */
+  WL_REFINED = 1  /* inner CG in FP32; residual and update in double-float (FP32 pairs), FP64-level accuracy */
 } wl_precision;
 
 /* ------------------------------------------------------------ structs */
@@ -114,7 +114,7 @@ typedef struct {
   int status;         /* status of the call */
   int iters;          /* operator SpMM applications (lockstep blocks) in the call */
   int outer_iters;    /* Lanczos steps (wl_expmv) */
-  int refinements;    /* FP64 residual evaluations (WL_REFINED) */
+  int refinements;    /* residual evaluations of the refinement (WL_REFINED) */
   double rel_res;     /* largest final relative residual over the call's solves */
   double time_ms;     /* device time of the call (CUDA events on the handle's stream) */
   double nnz_rhs_iters; /* sum over SpMM applications of nnz * columns */
@@ -127,7 +127,7 @@ typedef struct {
   int k_cg_iters;     /* CG iterations executed by those launches */
   double k_cg_ms;
   double k_cg_bytes;  /* algorithmic bytes of those iterations */
-  int k_res_launches; /* FP64 residual kernels */
+  int k_res_launches; /* refinement residual kernels (double-float) */
   double k_res_ms;
   int k_lan_launches; /* Lanczos step kernels */
   double k_lan_ms;

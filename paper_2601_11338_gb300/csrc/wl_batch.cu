@@ -89,6 +89,7 @@ struct SolveBufs {
   int K = 0;
   DBuf x, r, p, q;      // FP64 form: doubles; refined: x = d32, r/p/q FP32
   DBuf x64;             // refined form: FP64 iterate
+  DBuf rdf;             // refined form: double-float residual (rh then rl, FP32 each)
   DBuf part;            // [nslab][ntile][2K] doubles
   DBuf colstate;        // gamma, alpha, beta, b2, rn2, bn2 (doubles) per problem-column
   DBuf colint;          // done, status, skip, ostatus (ints) per problem-column
@@ -172,6 +173,7 @@ int alloc_solve(wl_batch* b, SolveBufs& s, int K) {
   BT_CU(dalloc(s.p, elems * 8));
   BT_CU(dalloc(s.q, elems * 8));
   BT_CU(dalloc(s.x64, elems * 8));
+  if (b->prm.prec == WL_REFINED) BT_CU(dalloc(s.rdf, elems * 8));
   BT_CU(dalloc(s.part, (size_t)b->nslab * std::max(max_tiles(b), 1) * 2 * K * 8));
   BT_CU(dalloc(s.colstate, nc * 6 * 8));
   BT_CU(dalloc(s.colint, nc * 4 * 4));
@@ -368,17 +370,6 @@ int emit_red_res(int K, const BatchGraph& g, const BatchOuter& o, const double* 
   return WL_OK;
 }
 
-int emit_acc(int K, const BatchGraph& g, double* x64, const float* d32, const int* oact, int nslab, cudaStream_t s) {
-  switch (K) {
-#define C(k) case k: bacc<k><<<grid1(g.n * k * nslab), kPhaseBlock, 0, s>>>(g, x64, d32, oact, nslab); break;
-    BT_FOR_K(C)
-#undef C
-    default: return WL_ERR_INVALID_ARG;
-  }
-  BT_CU(cudaGetLastError());
-  return WL_OK;
-}
-
 // one batched solve M_{s,g} X = bscale b for all problems: X ends in
 // sb.x (FP64 form) or sb.x64 (refined form)
 int emit_solve(wl_batch* b, Emitter& em, SolveBufs& sb, const TileSet& ts, const double* rhs, const double* bscale) {
@@ -397,8 +388,8 @@ int emit_solve(wl_batch* b, Emitter& em, SolveBufs& sb, const TileSet& ts, const
     BT_TRY(emit_red_init(K, g, st, a.part, nullptr, nullptr, nullptr, tol2, nslab, s));
     return em.loop(sb, st.any, b->prm.max_iter + 2, [&]() { return emit_iteration<double>(K, a, nslab, em.s()); });
   }
-  // refined: FP64 residual / update around an FP32 CG whose target is the
-  // inner tolerance relative to the current residual
+  // refined: double-float residual / FP64 iterate around an FP32 CG whose
+  // target is the inner tolerance relative to the current residual
   const BatchOuter o = bouter(b, sb);
   const double tin = std::min(1e-3, std::max(4e-6, 0.5 * std::sqrt(b->prm.tol)));
   BT_CU(cudaMemsetAsync(sb.x64.p, 0, (size_t)nslab * b->n * K * 8, s));
@@ -407,9 +398,10 @@ int emit_solve(wl_batch* b, Emitter& em, SolveBufs& sb, const TileSet& ts, const
   BT_CU(cudaMemsetAsync(o.outer_iters, 0, sizeof(int) * np, s));
   bfill_int<<<1, 1, 0, s>>>(o.any, 1, 1);
   BT_CU(cudaGetLastError());
-  BatchResArgs ra{g, (const double*)sb.x64.p, rhs, bscale, (const double*)b->ca.p, (const double*)b->cA.p,
-                  (const double*)b->cD.p, (float*)sb.r.p, (float*)sb.x.p, (double*)sb.part.p, o.outer_active,
-                  o.outer_iters};
+  const size_t elems = (size_t)nslab * b->n * K;
+  BatchResArgs ra{g, (const float*)sb.x.p, rhs, bscale, (const double*)b->ca.p, (const double*)b->cA.p,
+                  (const double*)b->cD.p, (float*)sb.rdf.p, (float*)sb.rdf.p + elems, (float*)sb.r.p,
+                  (double*)sb.x64.p, (double*)sb.part.p, o.outer_active, o.outer_iters};
   BatchArgs<float> ia{g, (float*)sb.x.p, (float*)sb.r.p, (float*)sb.p.p, (float*)sb.q.p, (const double*)b->ca.p,
                       (const double*)b->cA.p, (const double*)b->cD.p, nullptr, nullptr, o.rn2, o.skip,
                       (double*)sb.part.p, st, b->prm.max_iter, tin * tin};
@@ -419,8 +411,8 @@ int emit_solve(wl_batch* b, Emitter& em, SolveBufs& sb, const TileSet& ts, const
     BT_TRY(emit_red_res(K, g, o, ra.part, tol2, b->prm.max_outer, nslab, so));
     BT_TRY(emit_init<float>(K, ia, o.outer_active, nslab, so));
     BT_TRY(emit_red_init(K, g, st, ia.part, o.rn2, o.skip, o.outer_active, tin * tin, nslab, so));
-    BT_TRY(em.loop(sb, st.any, b->prm.max_iter + 2, [&]() { return emit_iteration<float>(K, ia, nslab, em.s()); }));
-    return emit_acc(K, g, (double*)sb.x64.p, (const float*)sb.x.p, o.outer_active, nslab, em.s());
+    // the correction d ends in sb.x; the next residual pass adds it to x64
+    return em.loop(sb, st.any, b->prm.max_iter + 2, [&]() { return emit_iteration<float>(K, ia, nslab, em.s()); });
   });
 }
 
@@ -517,7 +509,7 @@ void free_batch(wl_batch* b) {
   }
   SolveBufs* sbs[] = {&b->sb1, &b->sbk};
   for (SolveBufs* s : sbs) {
-    DBuf* bufs[] = {&s->x, &s->r, &s->p, &s->q, &s->x64, &s->part, &s->colstate, &s->colint, &s->probint, &s->flags};
+    DBuf* bufs[] = {&s->x, &s->r, &s->p, &s->q, &s->x64, &s->rdf, &s->part, &s->colstate, &s->colint, &s->probint, &s->flags};
     for (DBuf* d : bufs) dfree(*d);
   }
   DBuf* bufs[] = {&b->rp, &b->col, &b->goff, &b->ca, &b->cA, &b->cD, &b->phis, &b->ones, &b->Vin, &b->Df, &b->W};
@@ -723,7 +715,7 @@ int wl_batch_run(wl_batch* b, const double* V, int k, double* Df, double* W, int
     b->execs.clear();
     SolveBufs fresh;
     std::swap(b->sbk, fresh);
-    DBuf* bufs[] = {&fresh.x, &fresh.r, &fresh.p, &fresh.q, &fresh.x64, &fresh.part, &fresh.colstate, &fresh.colint,
+    DBuf* bufs[] = {&fresh.x, &fresh.r, &fresh.p, &fresh.q, &fresh.x64, &fresh.rdf, &fresh.part, &fresh.colstate, &fresh.colint,
                     &fresh.probint, &fresh.flags};
     for (DBuf* d : bufs) dfree(*d);
     BT_TRY(alloc_solve(b, b->sbk, k));

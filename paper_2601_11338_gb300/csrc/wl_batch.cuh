@@ -20,6 +20,7 @@
 // A problem that has converged is skipped by every later launch.
 #pragma once
 #include "wl_cg2.cuh"
+#include "wl_res.cuh"
 
 namespace wl {
 
@@ -390,98 +391,135 @@ __global__ void __launch_bounds__(kPhaseBlock) bred_u(BatchGraph g, BatchState s
 }
 
 // ---------------------------------------------------------------- refined form
-// r64 = bscale b - M x64 (FP64 gather), r32 = (float) r64 into the inner
-// CG's r, d32 = 0; partials of (r64, r64) and (bscale b, bscale b).
+// Residual of the refinement in double-float arithmetic (FP32 instructions
+// only), carried recursively as in the single-graph refined solve:
+//   first pass (x = 0):  r = bscale b
+//   later passes:        r <- r - M d,  x64 <- x64 + d
+// with d the FP32 correction of the previous inner solve (gathered: 4 bytes
+// per neighbour entry) and r = rh + rl a double-float vector. The neighbour
+// sum A d is accumulated with the error-free two-sum, M d and the subtraction
+// in double-float, so r stays equal to bscale b - M x64 up to about 2^-46 of
+// |r| + |M d| per pass. r32 = rh is the next inner solve's right-hand side
+// (the inner init zeroes d). Partials per column: (r, r) from the leading
+// terms, and on the first pass (bscale b, bscale b).
 struct BatchResArgs {
   BatchGraph g;
-  const double* x64;    // [nslab][n][K]
+  const float* d32;     // [nslab][n][K] correction of the last inner solve
   const double* b;      // [n][K]
   const double* bscale; // per problem or NULL
   const double* ca;
   const double* cA;
   const double* cD;
-  float* r32;           // [nslab][n][K]
-  float* d32;           // [nslab][n][K]
+  float* rh;            // [nslab][n][K] residual, leading term
+  float* rl;            // [nslab][n][K] residual, trailing term
+  float* r32;           // [nslab][n][K] inner right-hand side
+  double* x64;          // [nslab][n][K] iterate
   double* part;         // [nslab][ntile][2K]
   const int* outer_active;  // per problem (NULL: all)
-  const int* outer_iters;   // per problem: 0 means x64 = 0 (no gather)
+  const int* outer_iters;   // per problem: 0 means x64 = 0 and r = bscale b
 };
 
 template <int K>
 __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) bres(BatchResArgs a) {
-  using C = Cfg<double, K>;
+  using C = Cfg<float, K>;
   constexpr int VW = C::VW, G = C::G, RPB = kPhaseBlock / G;
-  __shared__ __align__(16) double s_red[kPhaseBlock * VW];
+  __shared__ __align__(16) float s_red[2][kPhaseBlock * VW];
   const BTile tl = a.g.tiles[blockIdx.x];
   const int s = blockIdx.y, pr = s * a.g.ngraph + tl.graph;
   if (a.outer_active && !a.outer_active[pr]) return;
   const bool first = a.outer_iters[pr] == 0;
   const int tid = threadIdx.x, sl = tid % G, lane_off = sl * VW;
   const size_t slab = (size_t)s * a.g.n * K;
-  const double ca = a.ca[pr], cA = a.cA[pr], cD = a.cD[pr];
+  const df ca = df_from_double(a.ca[pr]), cA = df_from_double(a.cA[pr]), cD = df_from_double(a.cD[pr]);
   const double sc = a.bscale ? a.bscale[pr] : 1.0;
-  const double* X = a.x64 + slab;
-  double acc_r[VW], acc_b[VW];
+  const float* D = a.d32 + slab;
+  float acc_r[VW], acc_b[VW];
 #pragma unroll
-  for (int v = 0; v < VW; ++v) acc_r[v] = acc_b[v] = 0.0;
-  auto fin = [&](int64_t row, int deg, const double (&nb)[VW]) {
+  for (int v = 0; v < VW; ++v) acc_r[v] = acc_b[v] = 0.f;
+  auto fin = [&](int64_t row, int deg, const float (&sm)[VW], const float (&cm)[VW]) {
     const size_t o = (size_t)row * K + lane_off;
-    const Pack<double, VW> bb = ld_plain<double, VW>(a.b + o);
-    Pack<double, VW> xx;
+    Pack<float, VW> rh, rl;
     if (first) {
+      const Pack<double, VW> bb = ld_plain<double, VW>(a.b + o);
 #pragma unroll
-      for (int v = 0; v < VW; ++v) xx.v[v] = 0.0;
+      for (int v = 0; v < VW; ++v) {
+        const df r = df_from_double(sc * bb.v[v]);
+        rh.v[v] = r.hi;
+        rl.v[v] = r.lo;
+        acc_b[v] = __fmaf_rn(r.hi, r.hi, acc_b[v]);
+      }
     } else {
-      xx = ld_plain<double, VW>(X + o);
-    }
-    Pack<float, VW> r32, z;
+      const df crow = df_add(ca, df_mul_f(cD, (float)deg));
+      const Pack<float, VW> dd = ld_plain<float, VW>(D + o);
+      const Pack<float, VW> ph = ld_plain<float, VW>(a.rh + slab + o);
+      const Pack<float, VW> pl = ld_plain<float, VW>(a.rl + slab + o);
+      Pack<double, VW> xx = ld_plain<double, VW>(a.x64 + slab + o);
 #pragma unroll
-    for (int v = 0; v < VW; ++v) {
-      const double bv = sc * bb.v[v];
-      const double rv = bv - (ca * xx.v[v] + cA * nb[v] + cD * (double)deg * xx.v[v]);
-      acc_r[v] += rv * rv;
-      acc_b[v] += bv * bv;
-      r32.v[v] = (float)rv;
-      z.v[v] = 0.0f;
+      for (int v = 0; v < VW; ++v) {
+        const df nb = two_sum(sm[v], cm[v]);
+        const df Md = df_add(df_mul_f(crow, dd.v[v]), df_mul(cA, nb));
+        const df r = df_sub(df{ph.v[v], pl.v[v]}, Md);
+        rh.v[v] = r.hi;
+        rl.v[v] = r.lo;
+        xx.v[v] += (double)dd.v[v];
+      }
+      stp<double, VW>(a.x64 + slab + o, xx);
     }
-    *reinterpret_cast<Pack<float, VW>*>(a.r32 + slab + o) = r32;
-    *reinterpret_cast<Pack<float, VW>*>(a.d32 + slab + o) = z;
+#pragma unroll
+    for (int v = 0; v < VW; ++v) acc_r[v] = __fmaf_rn(rh.v[v], rh.v[v], acc_r[v]);
+    stp<float, VW>(a.rh + slab + o, rh);
+    stp<float, VW>(a.rl + slab + o, rl);
+    stp<float, VW>(a.r32 + slab + o, rh);
   };
   if (tl.hub) {
     const int64_t row = tl.row_beg;
     const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
-    double acc[VW];
+    float sm[VW], cm[VW], lm[VW];
 #pragma unroll
-    for (int v = 0; v < VW; ++v) acc[v] = 0.0;
-    if (!first) row_gather<double, K, VW>(a.g.col, beg + tid / G, end, RPB, X, lane_off, acc);
+    for (int v = 0; v < VW; ++v) sm[v] = cm[v] = lm[v] = 0.f;
+    if (!first) df_row_gather<K, VW, false>(a.g.col, beg + tid / G, end, RPB, D, nullptr, lane_off, sm, cm, lm);
 #pragma unroll
-    for (int v = 0; v < VW; ++v) s_red[tid * VW + v] = acc[v];
+    for (int v = 0; v < VW; ++v) {
+      s_red[0][tid * VW + v] = sm[v];
+      s_red[1][tid * VW + v] = cm[v];
+    }
     __syncthreads();
     if (tid < G) {
       for (int gr = 1; gr < RPB; ++gr)
 #pragma unroll
-        for (int v = 0; v < VW; ++v) acc[v] += s_red[(gr * G + sl) * VW + v];
-      fin(row, end - beg, acc);
+        for (int v = 0; v < VW; ++v) {
+          const int k = (gr * G + sl) * VW + v;
+          const df t = two_sum(sm[v], s_red[0][k]);
+          sm[v] = t.hi;
+          cm[v] += t.lo + s_red[1][k];
+        }
+      fin(row, end - beg, sm, cm);
     }
   } else {
     for (int64_t row = tl.row_beg + tid / G; row < tl.row_end; row += RPB) {
       const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
       if (end - beg > kHubDeg) continue;
-      double acc[VW];
+      float sm[VW], cm[VW], lm[VW];
 #pragma unroll
-      for (int v = 0; v < VW; ++v) acc[v] = 0.0;
-      if (!first) row_gather<double, K, VW>(a.g.col, beg, end, 1, X, lane_off, acc);
-      fin(row, end - beg, acc);
+      for (int v = 0; v < VW; ++v) sm[v] = cm[v] = lm[v] = 0.f;
+      if (!first) df_row_gather<K, VW, false>(a.g.col, beg, end, 1, D, nullptr, lane_off, sm, cm, lm);
+      fin(row, end - beg, sm, cm);
     }
   }
+  double pr_r[VW], pr_b[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) {
+    pr_r[v] = (double)acc_r[v];
+    pr_b[v] = (double)acc_b[v];
+  }
   double* out = a.part + ((size_t)s * a.g.ntile + blockIdx.x) * 2 * K;
-  block_colsum_store<double, K>(acc_r, out);
+  block_colsum_store<float, K>(pr_r, out);
   __syncthreads();
-  block_colsum_store<double, K>(acc_b, out + K);
+  block_colsum_store<float, K>(pr_b, out + K);
 }
 
-// outer (refinement) control per problem: the relative FP64 residual
-// decides convergence; the inner solve's reference norm is ||r64||^2 and
+// outer (refinement) control per problem: the relative double-float residual
+// decides convergence; the inner solve's reference norm is ||r||^2 and
 // columns already converged are skipped. grid (ngraph, nslab)
 struct BatchOuter {
   double* rn2;         // per problem-column ||r64||^2 (inner reference)
@@ -525,9 +563,10 @@ __global__ void __launch_bounds__(kPhaseBlock) bred_res(BatchGraph g, BatchOuter
   const int it = o.outer_iters[pr];
   if (tid < K) {
     const int i = pr * K + tid;
-    const double rn = s_out[tid], bn = s_out[K + tid];
+    const double rn = s_out[tid];
+    const double bn = it == 0 ? s_out[K + tid] : o.bn2[i];  // ||bscale b||^2 from the first pass
     o.rn2[i] = rn;
-    o.bn2[i] = bn;
+    if (it == 0) o.bn2[i] = bn;
     int conv = (bn <= 0.0) || (rn <= tol2 * bn);
     if (!isfinite(rn)) {
       conv = 1;
@@ -555,19 +594,6 @@ __device__ __forceinline__ int graph_of(const BatchGraph& g, int64_t row) {
     if (g.goff[mid] <= row) lo = mid; else hi = mid - 1;
   }
   return lo;
-}
-
-// x64 += d32 for problems still refining
-template <int K>
-__global__ void __launch_bounds__(kPhaseBlock) bacc(BatchGraph g, double* x64, const float* d32, const int* outer_active,
-                                                     int nslab) {
-  const int64_t per = g.n * K;
-  const int64_t total = per * nslab;
-  for (int64_t e = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; e < total; e += (int64_t)gridDim.x * kPhaseBlock) {
-    const int s = (int)(e / per);
-    const int64_t row = (e - (int64_t)s * per) / K;
-    if (outer_active[s * g.ngraph + graph_of(g, row)]) x64[e] += (double)d32[e];
-  }
 }
 
 // ---------------------------------------------------------------- outputs
