@@ -43,7 +43,7 @@ TAUS = [0.1, 1.0, 10.0]
 K_SRC = 16
 METRIC = "nnz*RHS*iters/s (exp(-tau L)u0, NBT resolvent, refined form)"
 UNIT = "nnz*RHS*iters/s"
-TIME_TO_RULE = {"tol": 3e-10, "outer_tol": 3e-9}  # stopping rule shared by both forms (time-to-1e-8): the loosest measured rule under which the FP64 form reaches 1e-8
+TIME_TO_RULE = {"tol": 3e-10, "outer_tol": 1e-7}  # stopping rule shared by both forms (time-to-1e-8): the loosest measured rule under which the FP64 form reaches 1e-8
 
 
 def log(*a):
@@ -59,7 +59,11 @@ def dist_env():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed
+    region. start() launches the sampler and waits for its first sample, so
+    that nvidia-smi's own start-up happens before the timed region; begin()
+    and stop() bracket the timed region, and only the samples taken inside it
+    are reported."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -69,6 +73,8 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.t_begin = None
+        self.first = threading.Event()
 
     def start(self):
         try:
@@ -77,24 +83,34 @@ class ClockSampler:
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            self.first.wait(timeout=15.0)
         except OSError:
             self.proc = None
+        return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+            self.first.set()
+
+    def begin(self):
+        self.t_begin = time.monotonic()
 
     def stop(self):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t_end = time.monotonic()
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        t0 = self.t_begin if self.t_begin is not None else 0.0
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for t, ln in self.lines:
+            if not (t0 <= t <= t_end + 0.25):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -111,6 +127,24 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
+ALPHA_RULES = {"half": "0.5/rho(Z_mu)", "paper": "1/(1+rho(Z_mu))"}
+
+
+def pinned_empty(shape, dtype=np.float64):
+    """Page-locked host array (numpy view of a pinned torch tensor): the
+    end-to-end legs copy their inputs and results through pinned memory."""
+    import torch
+    tdt = torch.from_numpy(np.empty(0, dtype=dtype)).dtype
+    return torch.empty(shape, dtype=tdt, pin_memory=True).numpy()
+
+
+def pinned(a):
+    """Pinned host copy of the numpy array a."""
+    out = pinned_empty(a.shape, a.dtype)
+    out[...] = a
+    return out
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -184,8 +218,20 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     taus = np.array(TAUS)
 
+    # alpha: 0.5 / rho(Z_1) (alpha_rel, found by every build), or the paper's
+    # harder-conditioned 1 / (1 + rho(Z_1)) from rho measured once up front
+    alpha_abs = 0.0
+    if args.alpha_rule == "paper":
+        h0 = wl.wl_build(rp, ci, g.n, g.nnz, wl.WL_NBT, wl.make_params(alpha_rel=0.5, prec=wl.WL_REFINED,
+                                                                        stream=stream.cuda_stream))
+        alpha_abs = 1.0 / (1.0 + wl.wl_get_info(h0).rho)
+        h0.destroy()
+
     def params(prec, tol, outer_tol):
-        return wl.make_params(f=wl.WL_F_RESOLVENT, alpha_rel=0.5, prec=prec, tol=tol, outer_tol=outer_tol,
+        # near the pole the walk degrees (and |L|) grow by two orders of
+        # magnitude and tau = 10 needs more Lanczos steps than the default cap
+        return wl.make_params(f=wl.WL_F_RESOLVENT, alpha=alpha_abs, alpha_rel=0.0 if alpha_abs else 0.5, prec=prec,
+                              tol=tol, outer_tol=outer_tol, max_outer=1000 if alpha_abs else 0,
                               stream=stream.cuda_stream)
 
     def step(prec=wl.WL_REFINED, tol=TIME_TO_RULE["tol"], outer_tol=TIME_TO_RULE["outer_tol"], out=U):
@@ -215,10 +261,14 @@ def run_ours(args):
     phase_launches = {"build": 0.0, "degrees": 0.0, "expmv": 0.0}
     kcg_ms = kcg_bytes = kres_ms = klan_ms = 0.0
     kcg_launches = kcg_iters = 0
+    wall_ms = []
+    clocks.begin()
     ev0.record(stream)
     for _ in range(args.steps):
+        tw = time.perf_counter()
         flush.zero_()
         sb, sd, se = step()
+        wall_ms.append((time.perf_counter() - tw) * 1000.0)
         units += sd.nnz_rhs_iters + se.nnz_rhs_iters
         launches += sb.launches + sd.launches + se.launches
         phase_ms["build"] += sb.time_ms / args.steps
@@ -248,7 +298,7 @@ def run_ours(args):
     if args.timed_only:  # profiling runs: the timed steps alone
         print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "steps": args.steps,
                           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "timed_only": True,
-                          "phase_ms_per_step": phase_ms, "phase_launches_per_step": phase_launches,
+                          "phase_ms_per_step": phase_ms, "host_wall_ms_per_step": wall_ms, "phase_launches_per_step": phase_launches,
                           "gpu_launches": launches}), flush=True)
         return
     # ---- time to 1e-8: reference u* (FP64, tight), then both forms under one rule
@@ -270,11 +320,11 @@ def run_ours(args):
     tt["speedup_refined_vs_fp64"] = tt["fp64"]["ms"] / tt["refined"]["ms"]
     tt["rule"] = dict(TIME_TO_RULE)
     # ---- end to end through the C ABI with host buffers
-    rp_h = g.row_ptr.astype(np.int32)
-    ci_h = np.ascontiguousarray(g.col_idx)
-    U0_h = wlgen.unit_block(g.n, nodes)
-    Df_h = np.empty(g.n)
-    U_h = np.empty((len(TAUS), g.n, K_SRC))
+    rp_h = pinned(g.row_ptr.astype(np.int32))
+    ci_h = pinned(g.col_idx)
+    U0_h = pinned(wlgen.unit_block(g.n, nodes))
+    Df_h = pinned_empty((g.n,))
+    U_h = pinned_empty((len(TAUS), g.n, K_SRC))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sb, sd, se = wl.wl_stats(), wl.wl_stats(), wl.wl_stats()
@@ -308,12 +358,14 @@ def run_ours(args):
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "chung_lu_1e6_nbt_expmv_16src_3tau", "graph": "Chung-Lu power law",
                    "n": g.n, "nnz": g.nnz, "gamma": 2.5, "mean_degree": 12, "min_degree": 1,
-                   "variant": "nbt", "f": "resolvent", "alpha": "0.5/rho(Z_1)", "rhs": K_SRC, "taus": TAUS,
+                   "variant": "nbt", "f": "resolvent", "alpha": ALPHA_RULES[args.alpha_rule],
+                   "alpha_value": alpha_abs or None, "rhs": K_SRC, "taus": TAUS,
                    "form": "refined (FP32 CG + double-float residual/update and Lanczos)",
                    "stopping_rule": dict(TIME_TO_RULE), "parallelism": f"replicas{ws}",
                    "l2": "flushed between steps (256 MB write inside the timed region); per-step working set > 10 GB",
                    "seeds": {"graph": SEED_GRAPH, "sources": SEED_SRC}},
-        "phase_ms_per_step": phase_ms, "phase_launches_per_step": phase_launches, "time_to_1e-8": tt, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "phase_ms_per_step": phase_ms, "host_wall_ms_per_step": wall_ms, "phase_launches_per_step": phase_launches,
+        "time_to_1e-8": tt, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -425,6 +477,7 @@ def run_batch(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     units = 0.0
+    clocks.begin()
     e0.record(stream)
     for _ in range(args.steps):
         wl.wl_batch_run(b, V, BATCH_K, Df, W, 0, st)
@@ -448,13 +501,14 @@ def run_batch(args):
     peak, peak_kind = peaks()
     achieved = alg / (ms / 1000.0) / 1e9
     # e2e: host V in, host D_f and W out, through the same call
-    Dh = np.empty((nmu, n))
-    Wh = np.empty((nmu, n, BATCH_K))
+    Vp = pinned(Vh)
+    Dh = pinned_empty((nmu, n))
+    Wh = pinned_empty((nmu, n, BATCH_K))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    wl.wl_batch_run(b, Vh, BATCH_K, Dh, Wh, 0, st)
+    wl.wl_batch_run(b, Vp, BATCH_K, Dh, Wh, 0, st)
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": st.nnz_rhs_iters / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(Vh.nbytes),
+    e2e = {"value": st.nnz_rhs_iters / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(Vp.nbytes),
            "d2h_bytes_per_step": int(Dh.nbytes + Wh.nbytes), "ms": e2e_s * 1000.0}
     # same batch in the FP64 form (one graph launch)
     b64, _ = build(wl.WL_FP64)
@@ -526,8 +580,12 @@ def run_trace(args):
     g = wlgen.rmat(scale, 16, 0.57, 0.19, 0.19, seed=20260300 + scale)
     gen_s = time.perf_counter() - t0
     log(f"trace: R-MAT scale {scale}: n={g.n} nnz={g.nnz} (generated in {gen_s:.1f} s)")
-    w = WalkLaplacian(g.row_ptr.astype(np.int32), g.col_idx, g.n, variant="allwalk", alpha_rel=0.5, prec="refined",
-                      tol=1e-7)
+    rp_np = g.row_ptr.astype(np.int32)
+    w = WalkLaplacian(rp_np, g.col_idx, g.n, variant="allwalk", alpha_rel=0.5, prec="refined", tol=1e-7)
+    if args.alpha_rule == "paper":  # 1 / (1 + lambda_max(A)) instead of 0.5 / lambda_max(A)
+        a_paper = 1.0 / (1.0 + w.info["rho"])
+        w.close()
+        w = WalkLaplacian(rp_np, g.col_idx, g.n, variant="allwalk", alpha=a_paper, prec="refined", tol=1e-7)
     build_ms = w.build_stats.time_ms
     for i in range(args.warmup):
         w.trace(64, 1000 + i)
@@ -537,6 +595,7 @@ def run_trace(args):
     ms, units, res = [], 0.0, []
     kcg_ms = kcg_bytes = 0.0
     kcg_iters = 0
+    clocks.begin()
     for i in range(args.steps):
         est, err = w.trace(64, 1 + i)
         st = w.last
@@ -556,7 +615,9 @@ def run_trace(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32+f64",
         "data": "synthetic",
         "config": {"workload": f"rmat{scale}_xnystrace_m64", "n": g.n, "nnz": g.nnz, "a": 0.57, "b": 0.19,
-                   "c": 0.19, "edge_factor": 16, "alpha": "0.5/lambda_max(A)", "cg_tol": 1e-7,
+                   "c": 0.19, "edge_factor": 16,
+                   "alpha": "0.5/lambda_max(A)" if args.alpha_rule == "half" else "1/(1+lambda_max(A))",
+                   "cg_tol": 1e-7,
                    "l2": "per-step working set > 2 GB (> L2)"},
         "build_ms": build_ms, "estimates": res,
         "roofline": {"bound": "hbm", "kernel": "block CG iteration kernels (FP32, k = 64)", "achieved": achieved,
@@ -656,6 +717,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--workload", default="chung_lu_1e6", choices=["chung_lu_1e6", "batch64", "trace_rmat", "warmstart_rmat"],
                     help="chung_lu_1e6: the headline diffusion step; batch64: the batched executor")
+    ap.add_argument("--alpha-rule", default="half", choices=sorted(ALPHA_RULES),
+                    help="chung_lu_1e6 / trace_rmat: alpha = 0.5/rho (default) or the paper's 1/(1+rho)")
     ap.add_argument("--no-loop", action="store_true", help="batch64: skip the per-problem FP64 loop baseline")
     ap.add_argument("--scale", type=int, default=0, help="trace_rmat / warmstart_rmat: R-MAT scale (22 / 24)")
     ap.add_argument("--timed-only", action="store_true",

@@ -102,7 +102,7 @@ typedef struct {
   wl_precision prec;
   double tol;        /* relative residual target of each solve (<= 0: 1e-12) */
   int max_iter;      /* CG iteration cap per solve (<= 0: 2000) */
-  int max_outer;     /* Lanczos step cap of wl_expmv (<= 0: 400) */
+  int max_outer;     /* Lanczos step cap of wl_expmv (<= 0: 400; at most 1000) */
   double outer_tol;  /* wl_expmv relative accuracy target (<= 0: 1e-10) */
   void* stream;      /* cudaStream_t the handle works on; NULL: legacy default stream */
   int reorder;       /* 0: keep the caller's node order internally; 1: relabel nodes by

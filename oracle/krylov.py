@@ -101,7 +101,11 @@ def lanczos_expmv(apply_L, u0, taus, tol=1e-10, m_max=400, check=4):
                 prev = ys
                 break
             if prev is not None:
-                ok = all(np.linalg.norm(y - np.concatenate([p, np.zeros(len(y) - len(p))])) <= tol * np.linalg.norm(y)
+                # an approximation that underflowed to zero is not converged:
+                # exp(-tau L) conserves the mass of u0 (L 1 = 0), the Krylov
+                # space just has not reached the slow modes yet
+                ok = all(np.linalg.norm(y) > 0 and
+                         np.linalg.norm(y - np.concatenate([p, np.zeros(len(y) - len(p))])) <= tol * np.linalg.norm(y)
                          for y, p in zip(ys, prev))
                 if ok:
                     prev = ys

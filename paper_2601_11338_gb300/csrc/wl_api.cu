@@ -909,7 +909,8 @@ int stage_taus(wl_handle* h, const double* taus, int ntau, const double** dtaus)
 // (n x K FP64, internal order) in h->packX starts K lockstep Lanczos
 // recurrences on L, one apply of L per step; every `check` steps y(tau) =
 // exp(-tau T_m) e_1 is recomputed for all tau and the run stops when no
-// (column, tau) changed by more than outer_tol since the last check. The
+// (column, tau) changed by more than outer_tol |y| since the last check
+// (an underflowed y = 0 never counts as converged). The
 // basis, T, the column norms and m stay in the handle for outer_combine.
 struct OuterRun {
   int K = 0, m = 0, ntau = 0;
@@ -918,7 +919,7 @@ struct OuterRun {
   const double* dtaus = nullptr;
 };
 
-constexpr int kLdT = 512;  // T and y leading dimension (Lanczos steps per column at most kLdT - 1)
+constexpr int kLdT = 1024;  // T and y leading dimension (Lanczos steps per column at most kLdT - 1)
 constexpr int kMaxReturnT = 256;  // time points per wl_return_prob call
 
 int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& info, OuterRun& o, int& outer_total) {
@@ -1162,7 +1163,7 @@ void default_params(wl_params* p) {
   if (p->tol <= 0) p->tol = 1e-12;
   if (p->max_iter <= 0) p->max_iter = 2000;
   if (p->max_outer <= 0) p->max_outer = 400;
-  if (p->max_outer > 500) p->max_outer = 500;
+  if (p->max_outer > 1000) p->max_outer = 1000;
   if (p->outer_tol <= 0) p->outer_tol = 1e-10;
 }
 

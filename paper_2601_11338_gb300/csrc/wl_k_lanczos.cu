@@ -36,7 +36,9 @@ cudaError_t launch_tridiag_exp(const TridiagArgs& a, int K, int mmax, cudaStream
     const int pairs = K * a.ntau;
     tridiag_exp_warp<<<(pairs + 3) / 4, 128, 0, s>>>(a, K);
   } else {
-    tridiag_exp<<<dim3(K, a.ntau), kBlock, 0, s>>>(a);
+    const cudaError_t e = cudaFuncSetAttribute(tridiag_exp, cudaFuncAttributeMaxDynamicSharedMemorySize, kTridiagSmem);
+    if (e != cudaSuccess) return e;
+    tridiag_exp<<<dim3(K, a.ntau), kBlock, kTridiagSmem, s>>>(a);
   }
   return cudaGetLastError();
 }

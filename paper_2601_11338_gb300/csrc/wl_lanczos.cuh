@@ -148,21 +148,29 @@ struct TridiagArgs {
   double* y;          // K x ntau x ldT (out)
   double* yprev;      // K x ntau x ldT (previous result, updated in place after err)
   const int* mprev;   // K: length of yprev (0: none)
-  double* err;        // K x ntau: |y - [yprev; 0]|_2
+  double* err;        // K x ntau: |y - [yprev; 0]|_2 / |y|_2, or kErrVanished when y = 0
   int ldT;
   int ntau;
   int psd;            // 1: operator is PSD, use 0 as lower spectral bound
   int max_terms;      // cap of the expansion length
 };
 
-constexpr int kTridiagMax = 512;    // max Lanczos steps handled per column
+constexpr int kTridiagMax = 1024;   // max Lanczos steps handled per column
+// err of a (column, tau) whose y underflowed to zero: the Krylov space does
+// not yet reach the slow modes (exp(-tau L) conserves the mass 1^T u0, so the
+// exact result of a start vector with mass never vanishes); never converged
+constexpr double kErrVanished = 1e300;
 constexpr int kChebMax = 2048;      // max Chebyshev terms (|tau| (hi - lo) / 2 up to ~4e4)
+// dynamic shared memory of tridiag_exp: T (2 vectors), 3 recurrence vectors, coefficients
+constexpr int kTridiagSmem = (5 * kTridiagMax + kChebMax) * (int)sizeof(double);
 
 #ifdef WL_LANCZOS_KERNELS
 __global__ void __launch_bounds__(kBlock) tridiag_exp(TridiagArgs a) {
-  __shared__ double s_a[kTridiagMax], s_b[kTridiagMax];
-  __shared__ double s_v[3][kTridiagMax];
-  __shared__ double s_c[kChebMax];
+  extern __shared__ __align__(16) double s_tri[];  // kTridiagSmem bytes
+  double* const s_a = s_tri;                      // diagonal
+  double* const s_b = s_tri + kTridiagMax;        // off-diagonal
+  double* const s_v = s_tri + 2 * kTridiagMax;    // three Chebyshev vectors
+  double* const s_c = s_tri + 5 * kTridiagMax;    // Chebyshev coefficients
   __shared__ double s_lohi[2];
   __shared__ int s_N;
   const int c = blockIdx.x, t = blockIdx.y, tid = threadIdx.x;
@@ -240,8 +248,8 @@ __global__ void __launch_bounds__(kBlock) tridiag_exp(TridiagArgs a) {
     const int i = tid + q * kBlock;
     yacc[q] = 0.0;
     if (i < m) {
-      s_v[0][i] = (i == 0) ? 1.0 : 0.0;
-      yacc[q] = s_c[0] * s_v[0][i];
+      s_v[i] = (i == 0) ? 1.0 : 0.0;
+      yacc[q] = s_c[0] * s_v[i];
     }
   }
   __syncthreads();
@@ -251,11 +259,11 @@ __global__ void __launch_bounds__(kBlock) tridiag_exp(TridiagArgs a) {
     for (int q = 0; q < RPT; ++q) {
       const int i = tid + q * kBlock;
       if (i < m) {
-        double s = (s_a[i] - mid) * s_v[0][i];
-        if (i > 0) s += s_b[i - 1] * s_v[0][i - 1];
-        if (i + 1 < m) s += s_b[i] * s_v[0][i + 1];
-        s_v[1][i] = s * ih;
-        yacc[q] += s_c[1] * s_v[1][i];
+        double s = (s_a[i] - mid) * s_v[i];
+        if (i > 0) s += s_b[i - 1] * s_v[i - 1];
+        if (i + 1 < m) s += s_b[i] * s_v[i + 1];
+        s_v[kTridiagMax + i] = s * ih;
+        yacc[q] += s_c[1] * s_v[kTridiagMax + i];
       }
     }
     __syncthreads();
@@ -265,11 +273,11 @@ __global__ void __launch_bounds__(kBlock) tridiag_exp(TridiagArgs a) {
       for (int q = 0; q < RPT; ++q) {
         const int i = tid + q * kBlock;
         if (i < m) {
-          double s = (s_a[i] - mid) * s_v[cv][i];
-          if (i > 0) s += s_b[i - 1] * s_v[cv][i - 1];
-          if (i + 1 < m) s += s_b[i] * s_v[cv][i + 1];
-          const double nxt = 2.0 * s * ih - s_v[pv][i];
-          s_v[nv][i] = nxt;
+          double s = (s_a[i] - mid) * s_v[cv * kTridiagMax + i];
+          if (i > 0) s += s_b[i - 1] * s_v[cv * kTridiagMax + i - 1];
+          if (i + 1 < m) s += s_b[i] * s_v[cv * kTridiagMax + i + 1];
+          const double nxt = 2.0 * s * ih - s_v[pv * kTridiagMax + i];
+          s_v[nv * kTridiagMax + i] = nxt;
           yacc[q] += s_c[k] * nxt;
         }
       }
@@ -281,7 +289,7 @@ __global__ void __launch_bounds__(kBlock) tridiag_exp(TridiagArgs a) {
   double* yo = a.y + ((size_t)c * a.ntau + t) * a.ldT;
   double* yp = a.yprev + ((size_t)c * a.ntau + t) * a.ldT;
   const int mp = a.mprev[c];
-  double e2 = 0.0;
+  double e2 = 0.0, y2 = 0.0;
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int i = tid + q * kBlock;
@@ -290,14 +298,19 @@ __global__ void __launch_bounds__(kBlock) tridiag_exp(TridiagArgs a) {
       yo[i] = yi;
       const double d = yi - (i < mp ? yp[i] : 0.0);
       e2 += d * d;
+      y2 += yi * yi;
     }
   }
-  s_v[0][tid] = e2;  // reuse (m may be < kBlock, slots are free after the loop)
+  s_v[tid] = e2;  // reuse (m may be < kBlock, slots are free after the loop)
+  s_v[kBlock + tid] = y2;
   __syncthreads();
   if (tid == 0) {
-    double s = 0.0;
-    for (int i = 0; i < kBlock; ++i) s += s_v[0][i];
-    a.err[c * a.ntau + t] = sqrt(s);
+    double s = 0.0, sy = 0.0;
+    for (int i = 0; i < kBlock; ++i) {
+      s += s_v[i];
+      sy += s_v[kBlock + i];
+    }
+    a.err[c * a.ntau + t] = sy > 0.0 ? sqrt(s / sy) : kErrVanished;
   }
   __syncthreads();
 #pragma unroll
@@ -433,7 +446,7 @@ __global__ void __launch_bounds__(128) tridiag_exp_warp(TridiagArgs a, int K) {
   double* yo = a.y + ((size_t)c * a.ntau + t) * a.ldT;
   double* yp = a.yprev + ((size_t)c * a.ntau + t) * a.ldT;
   const int mp = a.mprev[c];
-  double e2 = 0.0;
+  double e2 = 0.0, y2 = 0.0;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     const int i = lane * R + q;
@@ -441,11 +454,15 @@ __global__ void __launch_bounds__(128) tridiag_exp_warp(TridiagArgs a, int K) {
       yo[i] = yv[q];
       const double d = yv[q] - (i < mp ? yp[i] : 0.0);
       e2 += d * d;
+      y2 += yv[q] * yv[q];
     }
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
-  if (lane == 0) a.err[c * a.ntau + t] = sqrt(e2);
+  for (int off = 16; off > 0; off >>= 1) {
+    e2 += __shfl_xor_sync(0xffffffffu, e2, off);
+    y2 += __shfl_xor_sync(0xffffffffu, y2, off);
+  }
+  if (lane == 0) a.err[c * a.ntau + t] = y2 > 0.0 ? sqrt(e2 / y2) : kErrVanished;
   __syncwarp();
 #pragma unroll
   for (int q = 0; q < R; ++q) {

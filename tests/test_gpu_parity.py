@@ -103,6 +103,32 @@ def test_variants_apply_and_degrees(variant, mu, prec, reorder):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "refined"])
+def test_long_lanczos_run_near_the_pole(prec):
+    """alpha = 0.998 / rho(Z_1) on a Chung-Lu graph (n = 4000): the hub's walk
+    degree reaches about 3.4e3, so exp(-10 L) e_hub takes about 500 Lanczos
+    steps (the oracle's own run needs 512): the long basis and the block
+    evaluation of exp(-tau T_m) e_1 (more than 128 steps). Relative error
+    1e-9 (FP64) / 1e-8 (refined): without reorthogonalisation the
+    check-to-check stopping rule bounds the error less tightly here."""
+    g = wlgen.chung_lu(4000, seed=7)
+    A = dense(g)
+    w = WL(g, variant="nbt", alpha_rel=0.998, prec=prec, tol=1e-13 if prec == "fp64" else 1e-12,
+           outer_tol=1e-12, max_outer=1000)
+    phi, Df, L = oracle_for(A, 1.0, w.info["alpha"])
+    hub = int(np.argmax(A.sum(axis=1)))
+    U0 = np.zeros((g.n, 1))
+    U0[hub, 0] = 1.0
+    U = cpu(w.expmv(torch.as_tensor(U0, device="cuda"), [10.0]))
+    steps = w.last.outer_iters
+    w.close()
+    assert Df.max() > 2e3
+    assert steps > 256, steps
+    want = walks.diffusion(L, U0, [10.0])[0]
+    assert relerr(U[0], want) <= (1e-9 if prec == "fp64" else 1e-8)
+    np.testing.assert_allclose(U[0].sum(0), 1.0, rtol=1e-9)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "refined"])
 def test_nbt_diffusion_several_taus(prec):
     g = wlgen.barabasi_albert(700, 3, 11)
     A = dense(g)

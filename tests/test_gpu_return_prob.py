@@ -58,6 +58,35 @@ def test_many_time_points_and_identity_function():
     w.close()
 
 
+def test_btdw_exponential_mu_sweep():
+    """L_mu(exp) on a 20 x 30 grid for mu in {0, .25, .5, .75, 1} at the
+    same beta = 1 / lambda_max(A) and the same Omega: each estimate matches
+    the oracle's Alg. 1 (1e-5 relative), and, as in Sec. 4.4's figure on
+    varying mu, both the exact values and the estimates rise with mu at every
+    t (the common Omega correlates the estimates)."""
+    from oracle import spectral
+    g = wlgen.grid2d(20, 30)
+    A = graph.dense_adjacency(g.row_ptr, g.col_idx, g.n)
+    beta = 1.0 / spectral.lambda_max(A)
+    ts = [0.5, 1.0, 2.0, 4.0]
+    M, seed = 32, 4242
+    Om, _ = philox.gaussian_sketch(g.n, M, seed)
+    got, exact = [], []
+    for mu in (0.0, 0.25, 0.5, 0.75, 1.0):
+        w = WL(g, variant="btdw", f="exp", beta=beta, mu=mu, prec="refined", tol=1e-12, outer_tol=1e-11)
+        p, e = w.return_prob(M, seed, ts)
+        w.close()
+        L = walks.walk_laplacian(walks.phi_series(A, mu, walks.exp_coeffs(beta)))
+        want = xnys.xnys_return_probability(L, Om, ts)
+        for i, (pe, ee) in enumerate(want):
+            assert abs(p[i] - pe) <= 1e-5 * abs(pe), (mu, ts[i], p[i], pe)
+            assert abs(e[i] - ee) <= 1e-2 * ee + 1e-12, (mu, ts[i], e[i], ee)
+        got.append(p)
+        exact.append(xnys.return_probability(L, ts))
+    assert np.all(np.diff(np.array(exact), axis=0) > 0)
+    assert np.all(np.diff(np.array(got), axis=0) > 0)
+
+
 def test_argument_checks():
     from paper_2601_11338_gb300 import wl
     g = wlgen.erdos_renyi(50, 4, 3)

@@ -175,6 +175,31 @@ def test_return_probability_limits():
     assert abs(p[1] - 2.0 / 7.0) < 1e-12
 
 
+@pytest.mark.parametrize("which", ["grid", "er"])
+def test_return_probability_grows_with_mu_for_exp(which):
+    """Sec. 4.4 (figure on varying mu): for the BTDW exponential Laplacian
+    L_mu(exp) the average return probability rises as mu grows from 0 (all
+    walks) to 1 (nonbacktracking), since suppressing backtracks slows the
+    spreading. Checked on a grid (a road-network-like stand-in) and an ER
+    graph at beta = 1 / lambda_max(A), t in (0, 5]; the mu = 0 end equals the
+    all-walk exponential by eigendecomposition."""
+    if which == "grid":
+        g = wlgen.grid2d(8, 10)
+    else:
+        g = wlgen.erdos_renyi(60, 5, 1)
+    A = graph.dense_adjacency(g.row_ptr, g.col_idx, g.n)
+    beta = 1.0 / spectral.lambda_max(A)
+    ts = np.linspace(0.0, 5.0, 11)[1:]
+    ps = []
+    for mu in (0.0, 0.25, 0.5, 0.75, 1.0):
+        phi = walks.phi_series(A, mu, walks.exp_coeffs(beta))
+        ps.append(xnys.return_probability(walks.walk_laplacian(phi), ts))
+    ps = np.array(ps)
+    assert np.all(np.diff(ps, axis=0) > 0), np.diff(ps, axis=0).min()
+    p0 = xnys.return_probability(walks.walk_laplacian(walks.phi_allwalk_exp_eig(A, beta)), ts)
+    np.testing.assert_allclose(ps[0], p0, rtol=1e-12)
+
+
 def _cycle_csr(n):
     rp = np.arange(0, 2 * n + 1, 2, dtype=np.int64)
     col = np.empty(2 * n, dtype=np.int32)

@@ -265,6 +265,27 @@ def test_cpu_krylov_matches_dense_definitions(mu):
     assert 0 < m <= 300
 
 
+def test_cpu_lanczos_does_not_stop_on_a_vanished_approximation():
+    """Near the pole (alpha = 0.998 / rho(Z_1)) the hub of a Chung-Lu graph has
+    a walk degree in the hundreds, so for tau = 100 the first Ritz values all
+    exceed 745 / tau and exp(-tau T_m) e_1 underflows to zero for the first
+    few steps. Two zero approximations agree, but the exact result keeps the
+    mass of u0 (L 1 = 0, Sec. 4.1): the run must go on until the slow modes
+    enter the Krylov space, and then match the dense definition."""
+    from oracle import krylov
+    g = wlgen.chung_lu(1500, seed=7)
+    A = dense(g)
+    Asp = krylov.adjacency(g.row_ptr, g.col_idx, g.n)
+    L = walks.walk_laplacian(walks.phi_resolvent_closed(A, 1.0, 0.998 / krylov.rho_companion_sparse(Asp, 1.0)))
+    u0 = np.zeros(g.n)
+    u0[int(np.argmax(A.sum(axis=1)))] = 1.0
+    U, m = krylov.lanczos_expmv(lambda v: L @ v, u0, [100.0], tol=1e-10, m_max=1000)
+    want = walks.diffusion(L, u0[:, None], [100.0])[0][:, 0]
+    assert m > 100, m
+    assert abs(U[0].sum() - 1.0) <= 1e-9
+    assert np.linalg.norm(U[0] - want) <= 1e-9 * np.linalg.norm(want)
+
+
 @pytest.mark.parametrize("mu", [0.0, 0.5, 1.0])
 def test_sparse_companion_radius_matches_dense(mu):
     from oracle import krylov
