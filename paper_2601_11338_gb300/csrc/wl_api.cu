@@ -137,7 +137,7 @@ struct wl_handle {
   std::map<std::tuple<int, int, int, int>, PartDev> parts;
   Buf csr_rp, csr_col;
   Buf x, r, p, q;         // CG vectors (FP64 or FP32), n * 64 doubles each at most
-  Buf x64, b64, r64;      // refinement
+  Buf b64;                // FP64 right-hand sides (walk degrees, apply)
   Buf d32, d32b, r32;     // refined form: FP32 corrections (two, alternating) and inner right-hand side
   Buf xh, xl;             // refined form: the iterate as two FP32 terms (x = xh + xl)
   Buf bh, bl, rh, rl;     // refined form: right-hand side and residual as two FP32 terms
@@ -387,11 +387,10 @@ int solve_fp64(wl_handle* h, const double* b, double* x, int K, double tol, bool
     WL_CU(cudaMemcpyAsync(h->r.p, b, nk * 8, cudaMemcpyDeviceToDevice, S(h)));
   } else {
     const int gr = res_blocks(K) + h->nhub;
-    ResPhaseArgs ra{phase_graph(h), x, nullptr, b, (double*)h->r.p, nullptr, h->ca, h->cA, h->cD,
-                    (double*)h->part.p, st};
+    ResPhaseArgs ra{phase_graph(h), x, b, (double*)h->r.p, h->ca, h->cA, h->cD, (double*)h->part.p, st};
     const int pi = prof_begin(h, kCatRes);
     counted(h);
-    WL_CU(launch_res_phases(K, ra, gr, 0, S(h)));
+    WL_CU(launch_res_phases(K, ra, gr, S(h)));
     prof_end(h, pi);
     bn2 = st->b2;
     info.nnz_rhs += (double)h->nnz * K;
@@ -1144,7 +1143,7 @@ void free_handle(wl_handle* h) {
     pool_free(kv.second.seg);
     pool_free(kv.second.meta);
   }
-  Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->x64, &h->b64, &h->r64, &h->d32,
+  Buf* bufs[] = {&h->csr_rp, &h->csr_col, &h->x, &h->r, &h->p, &h->q, &h->b64, &h->d32,
                  &h->r32, &h->xh, &h->xl, &h->d32b, &h->bh, &h->bl, &h->rh, &h->rl, &h->dfdf, &h->ydf, &h->ew, &h->taus, &h->ybig, &h->part, &h->small, &h->Df, &h->warm, &h->basis, &h->Tab, &h->ybuf, &h->yprev,
                  &h->errb, &h->stage_a, &h->stage_b, &h->packV, &h->packX, &h->spV, &h->spW, &h->spstate, &h->mid, &h->omega, &h->gram,
                  &h->omega_int, &h->ptmp, &h->perm_b, &h->iperm_b, &h->hubs, &h->cgstate};

@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) bres(BatchResArg
 // decides convergence; the inner solve's reference norm is ||r||^2 and
 // columns already converged are skipped. grid (ngraph, nslab)
 struct BatchOuter {
-  double* rn2;         // per problem-column ||r64||^2 (inner reference)
+  double* rn2;         // per problem-column ||r||^2 of the refinement residual (inner reference)
   double* bn2;         // per problem-column ||b||^2
   int* skip;           // per problem-column
   int* outer_active;   // per problem

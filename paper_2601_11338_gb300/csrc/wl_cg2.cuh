@@ -409,56 +409,18 @@ __global__ void __launch_bounds__(kPhaseBlock) cg_f_phase(PhaseArgs<T> a) {
   }
 }
 
-// ---------------------------------------------------------------- FP64 residual (refinement)
-// pass 0: x64 += d32 (elementwise); pass 1: r64 = b - M x64, r32 = (float) r64,
-// d32 = 0, column norms ||r64||^2 -> st->gamma, ||b||^2 -> st->b2 (last CTA).
+// ---------------------------------------------------------------- FP64 residual
+// Start of an FP64-form solve from a warm start x: r = b - M x, column norms
+// ||r||^2 -> st->gamma and ||b||^2 -> st->b2 (last CTA).
 struct ResPhaseArgs {
   PhaseGraph g;
-  double* x;
-  float* d;
+  const double* x;
   const double* b;
-  double* r;     // FP64 residual out, or NULL
-  float* r32;
+  double* r;
   double ca, cA, cD;
   double* part;  // 2 * gridDim.x * K
   CgState* st;
 };
-
-// x64 = 0: r64 = b needs no SpMM; r32 = (float) b, d32 = 0, ||b||^2 -> gamma and b2
-template <int K>
-__global__ void __launch_bounds__(kPhaseBlock) res_zero_phase(ResPhaseArgs a) {
-  using C = Cfg<double, K>;
-  constexpr int VW = C::VW;
-  __shared__ double s_tmp[kPhaseBlock];
-  __shared__ double s_out[K];
-  const int tid = threadIdx.x;
-  double acc[VW];
-#pragma unroll
-  for (int v = 0; v < VW; ++v) acc[v] = 0.0;
-  const size_t nv = (size_t)a.g.n * K / VW;
-  for (size_t e = (size_t)blockIdx.x * kPhaseBlock + tid; e < nv; e += (size_t)gridDim.x * kPhaseBlock) {
-    const Pack<double, VW> bb = ld_plain<double, VW>(a.b + e * VW);
-#pragma unroll
-    for (int v = 0; v < VW; ++v) {
-      acc[v] += bb.v[v] * bb.v[v];
-      if (a.r32) a.r32[e * VW + v] = (float)bb.v[v];
-      if (a.d) a.d[e * VW + v] = 0.0f;
-    }
-  }
-  if (!block_partials_last<double, K>(acc, a.part, &a.st->ticket)) return;
-  sum_partials<K>(a.part, gridDim.x, s_tmp, s_out);
-  if (tid < K) {
-    a.st->gamma[tid] = s_out[tid];
-    a.st->b2[tid] = s_out[tid];
-  }
-  if (tid == 0) a.st->ticket = 0;
-}
-
-template <int K>
-__global__ void __launch_bounds__(kPhaseBlock) res_acc_phase(double* x, const float* d, int64_t total) {
-  for (int64_t e = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; e < total; e += (int64_t)gridDim.x * kPhaseBlock)
-    x[e] += (double)d[e];
-}
 
 template <int K>
 __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) res_phase(ResPhaseArgs a) {
@@ -482,10 +444,8 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) res_phase(ResPha
       rr.v[v] = bb.v[v] - (ca * xx.v[v] + cA * nb[v] + cD * (double)deg * xx.v[v]);
       racc[v] += rr.v[v] * rr.v[v];
       racc[VW + v] += bb.v[v] * bb.v[v];
-      if (a.r32) a.r32[o + v] = (float)rr.v[v];
-      if (a.d) a.d[o + v] = 0.0f;
     }
-    if (a.r) stp<double, VW>(a.r + o, rr);
+    stp<double, VW>(a.r + o, rr);
   };
   if ((int)blockIdx.x < a.g.nhub) {
     const int64_t row = a.g.hubs[blockIdx.x];

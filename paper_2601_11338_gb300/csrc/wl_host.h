@@ -77,9 +77,8 @@ cudaError_t launch_cg_phases_f32(int K, const PhaseArgs<float>& a, int grid_s, i
                                  cudaStream_t s);
 cudaError_t launch_cg_phases_f64(int K, const PhaseArgs<double>& a, int grid_s, int grid_u, int mode, int chunk,
                                  cudaStream_t s);
-// FP64 residual r = b - M x (after x += d when accumulate > 0; accumulate < 0: x = 0, so r = b),
-// norms into st->gamma / st->b2
-cudaError_t launch_res_phases(int K, const ResPhaseArgs& a, int grid, int accumulate, cudaStream_t s);
+// FP64 residual r = b - M x of a warm start, norms into st->gamma / st->b2
+cudaError_t launch_res_phases(int K, const ResPhaseArgs& a, int grid, cudaStream_t s);
 // x (n K doubles) -> (xh, xl) FP32 terms, or (join) xh + xl -> xout
 cudaError_t launch_split_x(const double* x, int64_t total, float* xh, float* xl, bool join, double* xout,
                            cudaStream_t s);

@@ -1,5 +1,5 @@
-// FP64 instances of the CG phase kernels and the FP64 residual of the
-// iterative refinement, K = 1, 2, 4, ..., 64 columns.
+// FP64 instances of the CG phase kernels, the FP64 residual of a warm start
+// and the FP64 <-> double-float split of an iterate, K = 1, 2, 4, ..., 64 columns.
 #include "wl_cg2.cuh"
 #include "wl_host.h"
 
@@ -36,18 +36,12 @@ cudaError_t launch_cg_phases_f64(int K, const PhaseArgs<double>& a, int grid_s, 
 }
 
 template <int K>
-static cudaError_t run_res(const ResPhaseArgs& a, int grid, int accumulate, cudaStream_t s) {
-  if (accumulate < 0) {  // x = 0
-    res_zero_phase<K><<<grid, kPhaseBlock, 0, s>>>(a);
-    return cudaGetLastError();
-  }
-  const int64_t total = a.g.n * K;
-  if (accumulate) res_acc_phase<K><<<grid, kPhaseBlock, 0, s>>>(a.x, a.d, total);
+static cudaError_t run_res(const ResPhaseArgs& a, int grid, cudaStream_t s) {
   res_phase<K><<<grid, kPhaseBlock, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-// x64 <-> (xh, xl)
+// FP64 iterate <-> double-float terms (xh, xl)
 __global__ void __launch_bounds__(kPhaseBlock) split_x(const double* x, int64_t total, float* xh, float* xl) {
   for (int64_t e = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; e < total; e += (int64_t)gridDim.x * kPhaseBlock) {
     const float h = (float)x[e];
@@ -71,11 +65,11 @@ cudaError_t launch_split_x(const double* x, int64_t total, float* xh, float* xl,
   return cudaGetLastError();
 }
 
-cudaError_t launch_res_phases(int K, const ResPhaseArgs& a, int grid, int accumulate, cudaStream_t s) {
+cudaError_t launch_res_phases(int K, const ResPhaseArgs& a, int grid, cudaStream_t s) {
   switch (K) {
 #define R64(k) \
   case k:      \
-    return run_res<k>(a, grid, accumulate, s);
+    return run_res<k>(a, grid, s);
     WL_FOR_K(R64)
 #undef R64
   }

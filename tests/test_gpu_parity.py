@@ -2,7 +2,7 @@
 
 Tolerances (relative 2-norm per output column and per tau):
   FP64 form   1e-10     (inner CG tol 1e-13, Lanczos target 1e-12)
-  refined     1e-8      (FP32 inner CG with FP64 residual and update)
+  refined     1e-8      (FP32 inner CG with double-float residual and update)
 """
 import numpy as np
 import pytest
