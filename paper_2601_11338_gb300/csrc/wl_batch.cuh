@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kPhaseBlock) bcg_init(BatchArgs<T> a, const in
   constexpr int VW = C::VW, G = C::G, RPB = kPhaseBlock / G;
   const BTile tl = a.g.tiles[blockIdx.x];
   const int s = blockIdx.y, pr = s * a.g.ngraph + tl.graph;
-  if (pmask && !pmask[pr]) {  // problem not solved this round: zero partials only
+  if (pmask && !pmask[pr]) {  // problem not refining any more: zero partials only
     double z[Cfg<T, K>::VW];
 #pragma unroll
     for (int v = 0; v < Cfg<T, K>::VW; ++v) z[v] = 0.0;
