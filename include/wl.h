@@ -354,6 +354,17 @@ int wl_batch_tile_rows(const wl_batch* b, int k);
 
 void wl_batch_destroy(wl_batch* b);
 
+/* ---------------------------------------------------------------- self-test
+ * Failure detection of the device-side waits. One CTA enters the grid barrier
+ * that the cooperative kernels use (Lanczos step, spectral search), told to
+ * expect 1 + missing CTAs. missing = 0: the barrier completes; WL_OK.
+ * missing > 0: no other CTA ever arrives, the wait gives up after its limit
+ * (2 s of GPU time), records WL_ERR_TIMEOUT and the kernel returns normally,
+ * so the context stays usable; the call returns WL_ERR_TIMEOUT. stream: a
+ * cudaStream_t or NULL (default stream). Synchronous. WL_ERR_INVALID_ARG for
+ * missing < 0 or missing > 1024. */
+int wl_selftest_bounded_wait(int missing, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

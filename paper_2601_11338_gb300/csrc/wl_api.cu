@@ -1879,6 +1879,27 @@ void wl_destroy(wl_handle* h) {
   free_handle(h);
 }
 
+int wl_selftest_bounded_wait(int missing, void* stream) {
+  if (missing < 0 || missing > 1024) return WL_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  GridBar* bar = nullptr;
+  if (cudaMalloc(&bar, sizeof(GridBar)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return WL_ERR_OOM;
+  }
+  int err = 0;
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBar), s);
+  if (e == cudaSuccess) e = launch_selftest_wait(bar, 1u + (unsigned)missing, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &bar->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(bar);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return WL_ERR_CUDA;
+  }
+  return err != 0 ? err : WL_OK;
+}
+
 }  // extern "C"
 
 namespace wl {

@@ -77,6 +77,8 @@ cudaError_t launch_cg_phases_f32(int K, const PhaseArgs<float>& a, int grid_s, i
                                  cudaStream_t s);
 cudaError_t launch_cg_phases_f64(int K, const PhaseArgs<double>& a, int grid_s, int grid_u, int mode, int chunk,
                                  cudaStream_t s);
+// one CTA waiting in the bounded grid barrier for nblocks CTAs (failure-detection self-test)
+cudaError_t launch_selftest_wait(GridBar* bar, unsigned nblocks, cudaStream_t s);
 // FP64 residual r = b - M x of a warm start, norms into st->gamma / st->b2
 cudaError_t launch_res_phases(int K, const ResPhaseArgs& a, int grid, cudaStream_t s);
 // x (n K doubles) -> (xh, xl) FP32 terms, or (join) xh + xl -> xout

@@ -8,6 +8,14 @@
 
 namespace wl {
 
+// One CTA in the bounded grid barrier, expecting `nblocks` CTAs
+__global__ void k_selftest_wait(GridBar* bar, unsigned nblocks) { (void)grid_sync(bar, nblocks); }
+
+cudaError_t launch_selftest_wait(GridBar* bar, unsigned nblocks, cudaStream_t s) {
+  k_selftest_wait<<<1, 32, 0, s>>>(bar, nblocks);
+  return cudaGetLastError();
+}
+
 // rb[g] = first row i with row_ptr[i] + kRowCost * i >= g * total / G
 __global__ void k_partition_bounds(const int32_t* row_ptr, int64_t n, int G, int32_t* rb) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;

@@ -96,6 +96,8 @@ def lib():
         L.wl_degrees_noalloc.argtypes = [ctypes.POINTER(wl_csr), c_int, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, c_int, vp, vp, ctypes.POINTER(wl_stats)]
         L.wl_degrees_noalloc.restype = c_int
+        L.wl_selftest_bounded_wait.argtypes = [c_int, vp]
+        L.wl_selftest_bounded_wait.restype = c_int
         L.wl_batch_build.argtypes = [vp, c_int, vp, c_int, ctypes.POINTER(wl_params), ctypes.POINTER(vp),
                                      ctypes.POINTER(wl_stats)]
         L.wl_batch_build.restype = c_int
@@ -247,6 +249,13 @@ def wl_degrees_noalloc(row_ptr, col_idx, n, nnz, variant, mu, alpha, Df, tol=0.0
     st = stats if stats is not None else wl_stats()
     return _check(lib().wl_degrees_noalloc(ctypes.byref(A), variant, mu, alpha, tol, max_iter, _ptr(Df), stream,
                                            ctypes.byref(st)), "wl_degrees_noalloc", allow)
+
+
+def wl_selftest_bounded_wait(missing, stream=None):
+    """Status of one CTA in the bounded grid barrier expecting 1 + missing CTAs:
+    WL_OK when missing = 0, WL_ERR_TIMEOUT after the wait limit otherwise
+    (the kernel returns; the context stays usable). See include/wl.h."""
+    return lib().wl_selftest_bounded_wait(int(missing), stream)
 
 
 def wl_set_warm_start(h, x0):

@@ -63,3 +63,8 @@ def test_null_handle_calls_are_rejected():
     assert L.wl_apply(None, None, 0, 0, None, 0, None) == wl.WL_ERR_INVALID_ARG
     assert L.wl_expmv(None, None, 0, 0, None, 0, None, 0, None) == wl.WL_ERR_INVALID_ARG
     L.wl_destroy(None)
+
+
+def test_wait_selftest_rejects_bad_counts_before_touching_the_gpu():
+    assert wl.wl_selftest_bounded_wait(-1) == wl.WL_ERR_INVALID_ARG
+    assert wl.wl_selftest_bounded_wait(5000) == wl.WL_ERR_INVALID_ARG
