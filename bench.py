@@ -382,7 +382,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(g, nodes, budget_cols=1, max_steps=12):
+def cpu_baseline(g, nodes, budget_cols=2, max_steps=12):
     """Time the oracle's CPU FP64 Krylov restatement on a sample of the workload:
     the same graph and operator, `budget_cols` of the point sources, all taus,
     the Lanczos process capped at `max_steps` steps (units are counted exactly,
@@ -418,8 +418,8 @@ def run_reference(args):
     if rank != 0:
         return
     g, nodes = make_workload(0)
-    for _ in range(args.warmup if args.warmup < 1 else 0):
-        pass
+    for _ in range(args.warmup):  # untimed: imports, page cache, allocator
+        cpu_baseline(g, nodes)
     vals = []
     for _ in range(max(1, args.steps)):
         c = cpu_baseline(g, nodes)
