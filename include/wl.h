@@ -103,7 +103,7 @@ typedef struct {
   double tol;        /* relative residual target of each solve (<= 0: 1e-12) */
   int max_iter;      /* CG iteration cap per solve (<= 0: 2000) */
   int max_outer;     /* Lanczos step cap of wl_expmv (<= 0: 400; at most 1000) */
-  double outer_tol;  /* wl_expmv relative accuracy target (<= 0: 1e-10) */
+  double outer_tol;  /* wl_expmv: relative change of exp(-tau T_m) e_1 between checks (<= 0: 1e-10) */
   void* stream;      /* cudaStream_t the handle works on; NULL: legacy default stream */
   int reorder;       /* 0: keep the caller's node order internally; 1: relabel nodes by
                         decreasing degree inside the handle (better gather locality).
@@ -163,7 +163,12 @@ int wl_apply(wl_handle* h, const double* V, int64_t ldv, int k, double* W, int64
  * column form; L = L^T), by Lanczos on L with one apply per step
  * (Sec. 4.1, Krylov evaluation of f(A)v). U0 is n x k (ld ldu); U holds
  * ntau blocks, block t at U + t * n * ldo, each n x k with leading dimension
- * ldo. taus is a host array of ntau values >= 0. */
+ * ldo. taus is a host array of ntau values >= 0. Every 4 steps y(tau) =
+ * exp(-tau T_m) e_1 is evaluated; a column stops when, for every tau, y
+ * changed by at most outer_tol |y| since the previous evaluation (a y that
+ * underflowed to zero does not count as converged: the exact result keeps
+ * the mass of U0). WL_ERR_NO_CONVERGENCE when max_outer steps do not
+ * suffice (U then holds the last approximation). */
 int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* taus, int ntau,
              double* U, int64_t ldo, wl_stats* st);
 

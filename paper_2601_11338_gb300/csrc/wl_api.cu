@@ -1606,6 +1606,7 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
     const double* dtaus = nullptr;
     if ((rc = stage_taus(h, taus, ntau, &dtaus)) != WL_OK) break;
     int c0 = 0;
+    bool capped = false;  // a column block reached max_outer: every block is still evaluated
     for (int K : column_blocks(k)) {
       if ((rc = ensure(h->packX, (size_t)n * K * 8)) != WL_OK) break;
       counted(h);
@@ -1616,10 +1617,11 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
       if ((rc = outer_run(h, K, dtaus, ntau, info, o, outer_total)) != WL_OK) break;
       if (info.status != WL_OK) break;
       if ((rc = outer_combine(h, o, 0, ntau, Ud, ldo, n * ldo, c0, h->perm)) != WL_OK) break;
-      if (!o.converged) info.status = WL_ERR_NO_CONVERGENCE;
+      if (!o.converged) capped = true;
       c0 += K;
     }
     if (rc != WL_OK) break;
+    if (capped && info.status == WL_OK) info.status = WL_ERR_NO_CONVERGENCE;
     if (!u_dev) {
       cudaError_t e = cudaMemcpyAsync(U, Ud, (size_t)ntau * n * ldo * 8, cudaMemcpyDeviceToHost, S(h));
       if (e != cudaSuccess) { rc = set_cuda_error(e, "copy U"); break; }
