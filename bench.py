@@ -438,6 +438,82 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ NEXT rows
+def run_next(args):
+    """The rows built after the headline path, each timed on GB300 (CUDA events
+    of the library's own calls, after a warm-up call):
+      * exponential NBT walk Laplacian (beta = 1/lambda_max(A), q_k series in
+        double-float) on the headline graph: D_f, then L V for 16 Gaussian columns;
+      * discrete-time chain P = D_f^{-1} phi (NBT resolvent, alpha = 0.5/rho) from
+        the 16 point sources, distributions after 1, 2, 4 and 8 steps;
+      * average return probability tr(exp(-t L))/n by XNysTrace on a 1000 x 1000
+        grid (stand-in for the paper's road networks), NBT resolvent with the
+        paper's alpha = 1/(1 + rho(Z_1)), M = 32, 90 time points in [0, 100]."""
+    import torch
+
+    import wlgen
+    from paper_2601_11338_gb300.api import WalkLaplacian
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    g, nodes = make_workload(0)
+    rp, ci = g.row_ptr.astype(np.int32), g.col_idx
+    out = {}
+    clocks = ClockSampler(0).start()
+    clocks.begin()
+    # exponential walk function
+    w = WalkLaplacian(rp, ci, g.n, variant="nbt", f="exp", prec="refined")
+    V = torch.as_tensor(wlgen.gaussian_block(g.n, K_SRC, SEED_SRC + 7), device=dev)
+    for rep in range(2):  # the first pass warms up; wl_degrees sums its series on every call
+        Df = w.degrees()
+        sd = w.last
+        d_ms, d_units = sd.time_ms, sd.nnz_rhs_iters
+        w.apply(V)
+        sa = w.last
+    out["exp_nbt"] = {"beta": w.info["beta"], "degrees_ms": d_ms, "degrees_terms": sd.iters,
+                      "apply16_ms": sa.time_ms, "apply16_terms": sa.iters,
+                      "value": (d_units + sa.nnz_rhs_iters) / ((d_ms + sa.time_ms) / 1000.0),
+                      "unit": UNIT, "Df_max": float(Df.max())}
+    w.close()
+    # discrete-time chain
+    w = WalkLaplacian(rp, ci, g.n, variant="nbt", alpha_rel=0.5, prec="refined", tol=1e-10)
+    P0 = torch.as_tensor(wlgen.unit_block(g.n, nodes), device=dev)
+    for rep in range(2):
+        P = w.markov(P0, [1, 2, 4, 8])
+    sm = w.last
+    mass = float((P[-1].sum(dim=0) - 1.0).abs().max())
+    out["markov_nbt"] = {"steps": [1, 2, 4, 8], "sources": K_SRC, "ms": sm.time_ms,
+                         "value": sm.nnz_rhs_iters / (sm.time_ms / 1000.0), "unit": UNIT,
+                         "cg_iters": sm.k_cg_iters, "max_mass_error": mass}
+    w.close()
+    # average return probability
+    gg = wlgen.grid2d(1000, 1000)
+    w = WalkLaplacian(gg.row_ptr.astype(np.int32), gg.col_idx, gg.n, variant="nbt", alpha_rel=0.5,
+                      prec="refined", tol=1e-8, outer_tol=1e-8)
+    a_paper = 1.0 / (1.0 + w.info["rho"])
+    w.close()
+    w = WalkLaplacian(gg.row_ptr.astype(np.int32), gg.col_idx, gg.n, variant="nbt", alpha=a_paper,
+                      prec="refined", tol=1e-8, outer_tol=1e-8)
+    ts = np.linspace(0.0, 100.0, 90)
+    for rep in range(2):
+        p, e = w.return_prob(32, 1234 + rep, ts)
+    sr = w.last
+    out["return_prob_nbt_grid"] = {"n": gg.n, "nnz": gg.nnz, "alpha": a_paper, "M": 32, "times": len(ts),
+                                   "t_max": float(ts[-1]), "ms": sr.time_ms, "lanczos_steps": sr.outer_iters,
+                                   "value": sr.nnz_rhs_iters / (sr.time_ms / 1000.0), "unit": UNIT,
+                                   "p": {f"{t:g}": [float(p[i]), float(e[i])] for i, t in enumerate(ts)
+                                         if i in (1, 9, 45, 89)}}
+    w.close()
+    clk = clocks.stop()
+    line = {"metric": "NEXT rows on GB300 (exponential walk function, chain, return probability)",
+            "value": out["exp_nbt"]["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "next_rows_chunglu1e6_grid1000", "n": g.n, "nnz": g.nnz, "rhs": K_SRC},
+            "rows": out, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ batched workload
 BATCH_MUS = [1.0, 0.75, 0.5, 0.25, 0.0]  # theta = 1 - mu in {0, .25, .5, .75, 1}
 BATCH_K = 32
@@ -724,7 +800,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
-    ap.add_argument("--workload", default="chung_lu_1e6", choices=["chung_lu_1e6", "batch64", "trace_rmat", "warmstart_rmat"],
+    ap.add_argument("--workload", default="chung_lu_1e6",
+                    choices=["chung_lu_1e6", "batch64", "trace_rmat", "warmstart_rmat", "next_rows"],
                     help="chung_lu_1e6: the headline diffusion step; batch64: the batched executor")
     ap.add_argument("--alpha-rule", default="half", choices=sorted(ALPHA_RULES),
                     help="chung_lu_1e6 / trace_rmat: alpha = 0.5/rho (default) or the paper's 1/(1+rho)")
@@ -741,6 +818,8 @@ def main():
         run_trace(args)
     elif args.workload == "warmstart_rmat":
         run_warmstart(args)
+    elif args.workload == "next_rows":
+        run_next(args)
     else:
         run_ours(args)
 

@@ -566,21 +566,22 @@ int exp_series(wl_handle* h, const double* V, double* X, int K, SolveInfo& info)
   const int one = 1;
   WL_CU(cudaMemcpyAsync(&st->active, &one, sizeof(int), cudaMemcpyHostToDevice, S(h)));
   counted(h);
-  WL_CU(launch_df_split(V, nk, W[0][0], W[0][1], S(h)));  // w_0 = V
-  WL_CU(cudaMemcpyAsync(Ah, W[0][0], nk * 4, cudaMemcpyDeviceToDevice, S(h)));  // acc = c_0 w_0
+  WL_CU(launch_df_split(V, nk, W[0][0], W[0][1], S(h)));  // s_0 = c_0 w_0 = V
+  WL_CU(cudaMemcpyAsync(Ah, W[0][0], nk * 4, cudaMemcpyDeviceToDevice, S(h)));  // acc = s_0
   WL_CU(cudaMemcpyAsync(Al, W[0][1], nk * 4, cudaMemcpyDeviceToDevice, S(h)));
   const PhaseGraph pg = phase_graph_mid(h, gu);
   const int max_terms = std::max(h->prm.max_iter, 8);
   const int pc = prof_begin(h, kCatCG);
-  double ck = 1.0;
   int k = 0;
   int* hp = (int*)h->h_pin;
   for (;;) {
     for (int i = 0; i < kChunk && k < max_terms; ++i, ++k) {
-      ck *= h->beta / (double)(k + 1);  // c_{k+1}
+      // s_{k+1} = ak A s_k + bk (diagonal) s_{k-1} with s_k = c_k w_k (bounded terms)
+      const double ak = h->beta / (double)(k + 1);
+      const double bk = k >= 1 ? h->beta * h->beta / ((double)k * (double)(k + 1)) : 0.0;
       ExpArgs a{pg, W[k % 3][0], W[k % 3][1], W[(k + 2) % 3][0], W[(k + 2) % 3][1], W[(k + 1) % 3][0],
-                W[(k + 1) % 3][1], Ah, Al, df_from_double(h->mu), df_from_double(ck), k, max_terms,
-                (double*)h->part.p, st};
+                W[(k + 1) % 3][1], Ah, Al, df_from_double(h->mu), df_from_double(ak), df_from_double(bk), k,
+                max_terms, (double*)h->part.p, st};
       counted(h);
       WL_CU(launch_exp_term(K, a, gs, S(h)));
     }

@@ -3,13 +3,17 @@
 // walk counts of Eq. qrec act on the block V through
 //   w_0 = V, w_1 = A w_0, w_2 = A w_1 - mu D w_0,
 //   w_{k+1} = A w_k + mu (mu I - D) w_{k-1}   (k >= 2),
-// one gather per term, and acc = sum_k c_k w_k. Every vector is a
-// double-float pair (FP32 instructions only; GB300 runs FP64 at 1/64 of the
-// FP32 rate). The term coefficients c_k w_k are nonnegative combinations of
-// walk counts, so for mu in [0, 1] nothing cancels in the counts
-// themselves.
+// one gather per term, and acc = sum_k c_k w_k. The kernels carry the terms
+// s_k = c_k w_k themselves, not the counts: w_k grows like rho(Z_mu)^k and
+// leaves the FP32 exponent range after about 17 terms when rho is near 160,
+// while the terms of the convergent series stay bounded. With c_{k+1} / c_k =
+// beta / (k+1) and c_{k+1} / c_{k-1} = beta^2 / (k (k+1)) the recurrence reads
+//   s_{k+1} = (beta / (k+1)) A s_k + (beta^2 / (k (k+1))) mu (mu I - D) s_{k-1}
+// (k = 1: the diagonal factor is -mu D), and acc = sum_k s_k. Every vector is
+// a double-float pair (FP32 instructions only; GB300 runs FP64 at 1/64 of the
+// FP32 rate).
 //
-// The last CTA of each term reduces |c_{k+1} w_{k+1}|^2 and |acc|^2 per
+// The last CTA of each term reduces |s_{k+1}|^2 and |acc|^2 per
 // column; a column is finished after kExpQuiet consecutive terms below
 // kExpRel |acc|, and the kernel of a finished series returns at once (the
 // host launches terms in chunks and reads one flag between chunks).
@@ -24,16 +28,17 @@ constexpr int kExpQuiet = 3;       // consecutive small terms that end a column'
 
 struct ExpArgs {
   PhaseGraph g;
-  const float* wh;  // w_k (gathered)
+  const float* wh;  // s_k (gathered)
   const float* wl;
-  const float* mh;  // w_{k-1} (own row; unused at k = 0)
+  const float* mh;  // s_{k-1} (own row; unused at k = 0)
   const float* ml;
-  float* oh;        // w_{k+1} out
+  float* oh;        // s_{k+1} out
   float* ol;
-  float* ah;        // acc += c_{k+1} w_{k+1} (in place)
+  float* ah;        // acc += s_{k+1} (in place)
   float* al;
   df mu;
-  df ck;            // c_{k+1}
+  df ak;            // beta / (k + 1): factor of A s_k
+  df bk;            // beta^2 / (k (k + 1)) for k >= 1: factor of the diagonal term
   int k;
   int max_terms;
   double* part;     // 2 gridDim.x K partials
@@ -86,10 +91,10 @@ __global__ void __launch_bounds__(kPhaseBlock, 4) exp_term(ExpArgs a) {
   for (int v = 0; v < VW; ++v) tn[v] = an[v] = 0.f;
   auto fin = [&](int64_t row, int deg, const float (&s)[VW], const float (&c)[VW], const float (&l)[VW]) {
     const size_t o = (size_t)row * K + lane_off;
-    // diagonal coefficient of w_{k-1}: none at k = 0, -mu d at k = 1, mu (mu - d) after
+    // diagonal coefficient of s_{k-1}: none at k = 0, bk (-mu d) at k = 1, bk mu (mu - d) after
     df corr{0.f, 0.f};
-    if (a.k == 1) corr = df_mul_f(a.mu, -(float)deg);
-    else if (a.k >= 2) corr = df_mul(a.mu, df_add_f(a.mu, -(float)deg));
+    if (a.k == 1) corr = df_mul(a.bk, df_mul_f(a.mu, -(float)deg));
+    else if (a.k >= 2) corr = df_mul(a.bk, df_mul(a.mu, df_add_f(a.mu, -(float)deg)));
     Pack<float, VW> mh, ml;
     if (a.k >= 1) {
       mh = ld_plain<float, VW>(a.mh + o);
@@ -99,11 +104,11 @@ __global__ void __launch_bounds__(kPhaseBlock, 4) exp_term(ExpArgs a) {
     Pack<float, VW> oh, ol;
 #pragma unroll
     for (int v = 0; v < VW; ++v) {
-      df w = two_sum(s[v], c[v] + l[v]);
+      df w = df_mul(a.ak, two_sum(s[v], c[v] + l[v]));
       if (a.k >= 1) w = df_add(w, df_mul(corr, df{mh.v[v], ml.v[v]}));
       oh.v[v] = w.hi;
       ol.v[v] = w.lo;
-      const df t = df_mul(a.ck, w);
+      const df t = w;
       const df acc = df_add(df{ah.v[v], al.v[v]}, t);
       ah.v[v] = acc.hi;
       al.v[v] = acc.lo;

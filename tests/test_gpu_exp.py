@@ -74,6 +74,37 @@ def test_exp_on_a_tree_with_nbt_walks():
     w.close()
 
 
+@pytest.mark.parametrize("mu", [0.0, 1.0])
+def test_exp_walk_degrees_of_a_large_star_closed_form(mu):
+    """Star with m = 40000 leaves, beta = 1 / lambda_max(A) = 1 / sqrt(m), beyond
+    the dense oracle's sizes. mu = 0: exp(beta A) acts on span{e_hub, leaves / sqrt(m)}
+    as cosh(c) I + sinh(c) J with c = beta sqrt(m) = 1, so D_f(hub) = cosh c +
+    sqrt(m) sinh c and D_f(leaf) = cosh c + sinh c / sqrt(m). The raw walk counts
+    A^k 1 reach 200^k at the hub and leave the FP32 exponent range after 17
+    terms; the series must carry the bounded terms c_k A^k 1 instead. mu = 1: a
+    tree has no nonbacktracking walks of length 3 or more, so phi = I + beta A +
+    (beta^2 / 2)(A^2 - D): D_f(hub) = 1 + beta m, D_f(leaf) = 1 + beta + (beta^2 / 2)(m - 1)."""
+    from paper_2601_11338_gb300.api import WalkLaplacian
+    m = 40000
+    g = wlgen.star(m)
+    variant = "allwalk" if mu == 0.0 else "nbt"
+    w = WalkLaplacian(g.row_ptr.astype(np.int32), g.col_idx, g.n, variant=variant, f="exp", prec="refined")
+    beta = w.info["beta"]
+    assert abs(beta * np.sqrt(m) - 1.0) <= 1e-9
+    Df = w.degrees().cpu().numpy()
+    w.close()
+    deg = np.diff(g.row_ptr)
+    hub = int(np.argmax(deg))
+    leaves = np.arange(g.n) != hub
+    if mu == 0.0:
+        c = beta * np.sqrt(m)
+        want_hub, want_leaf = np.cosh(c) + np.sqrt(m) * np.sinh(c), np.cosh(c) + np.sinh(c) / np.sqrt(m)
+    else:
+        want_hub, want_leaf = 1.0 + beta * m, 1.0 + beta + 0.5 * beta * beta * (m - 1)
+    assert abs(Df[hub] - want_hub) <= 1e-12 * want_hub, (Df[hub], want_hub)
+    assert np.abs(Df[leaves] - want_leaf).max() <= 1e-12 * want_leaf
+
+
 def test_exp_edge_cases():
     """No edges: phi = I (only c_0 q_0 survives), D_f = 1, L = 0. An overflowing
     scale is reported as non-finite, not returned as garbage."""
