@@ -777,11 +777,14 @@ int rho_companion(wl_handle* h, double mu, double lmaxA, double* rho) {
     r.c0 = mu * mu / lam;
     r.cD = -mu / lam;
     double rtol = 1e-6;
-    for (;;) {
+    // a run that cannot resolve the sign (bound stuck above kTight) is taken as
+    // |h| below the attainable accuracy after kMaxPasses passes: lambda is then the root
+    constexpr int kMaxPasses = 32;
+    for (int pass = 0;; ++pass) {
       WL_TRY(sp_run(h, &r, rtol, false));
       *val = r.theta - lam;
       certain = std::fabs(*val) > 10.0 * r.bound;
-      if (certain || r.exact || r.bound <= kTight * std::fabs(r.theta)) break;
+      if (certain || r.exact || r.bound <= kTight * std::fabs(r.theta) || pass + 1 >= kMaxPasses) break;
       rtol = std::max(kTight, 1e-3 * std::fabs(*val) / std::fabs(r.theta));
     }
     return sp_ritz_q(h, &q, &uAu);
