@@ -106,8 +106,11 @@ typedef struct {
   double outer_tol;  /* wl_expmv: relative change of exp(-tau T_m) e_1 between checks (<= 0: 1e-10) */
   void* stream;      /* cudaStream_t the handle works on; NULL: legacy default stream */
   int reorder;       /* 0: keep the caller's node order internally; 1: relabel nodes by
-                        decreasing degree inside the handle (better gather locality).
-                        Results are always returned in the caller's node order. */
+                        decreasing degree inside the handle (better gather locality);
+                        2: reverse Cuthill-McKee order (wl_rcm_order, computed on the host
+                        at build time; for graphs with geometric locality such as road
+                        networks and grids). Results are always returned in the caller's
+                        node order. Other values: WL_ERR_INVALID_ARG. */
 } wl_params;
 
 typedef struct {
@@ -358,6 +361,15 @@ int wl_batch_info(const wl_batch* b, int graph, int mu_index, double* alpha, dou
 int wl_batch_tile_rows(const wl_batch* b, int k);
 
 void wl_batch_destroy(wl_batch* b);
+
+/* Reverse Cuthill-McKee order of a simple graph (host arrays, the CSR of
+ * wl_csr; the relabelling of reorder = 2): perm[new] = old, a permutation of
+ * 0..n-1. Each connected component is numbered breadth-first from a
+ * pseudo-peripheral node with neighbours by increasing degree (ties by id),
+ * components in order of their lowest-degree node, and the numbering is then
+ * reversed. Deterministic. The CSR is not validated here (wl_build does);
+ * indices must be in range. WL_ERR_INVALID_ARG for n < 0 or NULL arrays. */
+int wl_rcm_order(const int32_t* row_ptr, const int32_t* col_idx, int64_t n, int32_t* perm);
 
 /* ---------------------------------------------------------------- self-test
  * Failure detection of the device-side waits. One CTA enters the grid barrier

@@ -1257,8 +1257,29 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
   if (flags & 4) return fail(WL_ERR_SELF_LOOP);
   if (flags & 8) return fail(WL_ERR_NOT_SYMMETRIC);
 
-  // optional relabelling by decreasing degree (internal only)
-  if (p->reorder == 1 && h->n > 1) {
+  // optional relabelling (internal only): by decreasing degree (1) or reverse
+  // Cuthill-McKee (2, ordered on the host from the validated graph)
+  if ((p->reorder == 1 || p->reorder == 2) && h->n > 1) {
+    std::vector<int32_t> hperm;
+    if (p->reorder == 2) {
+      std::vector<int32_t> hrp, hcol;
+      const int32_t* rp_h = A->row_ptr;
+      const int32_t* col_h = A->col_idx;
+      if (is_device_ptr(A->row_ptr) || (A->nnz > 0 && is_device_ptr(A->col_idx))) {
+        hrp.resize((size_t)h->n + 1);
+        hcol.resize((size_t)std::max<int64_t>(h->nnz, 1));
+        cudaError_t e = cudaMemcpyAsync(hrp.data(), h->csr_rp.p, sizeof(int32_t) * (h->n + 1), cudaMemcpyDeviceToHost,
+                                        S(h));
+        if (e == cudaSuccess && h->nnz > 0)
+          e = cudaMemcpyAsync(hcol.data(), h->csr_col.p, sizeof(int32_t) * h->nnz, cudaMemcpyDeviceToHost, S(h));
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S(h));
+        if (e != cudaSuccess) return fail(set_cuda_error(e, "CSR to host for RCM"));
+        rp_h = hrp.data();
+        col_h = hcol.data();
+      }
+      hperm.resize((size_t)h->n);
+      if ((rc = rcm_order(rp_h, col_h, h->n, hperm.data())) != WL_OK) return fail(rc);
+    }
     Buf rp2, col2;
     if ((rc = ensure(h->perm_b, sizeof(int32_t) * h->n)) != WL_OK) return fail(rc);
     if ((rc = ensure(h->iperm_b, sizeof(int32_t) * h->n)) != WL_OK) return fail(rc);
@@ -1274,10 +1295,18 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
     }
     h->perm = (int32_t*)h->perm_b.p;
     h->iperm = (int32_t*)h->iperm_b.p;
-    counted(h, 9);
-    cudaError_t e = launch_relabel(h->g, h->perm, h->iperm, (int32_t*)rp2.p, (int32_t*)col2.p,
-                                   (int64_t*)h->ptmp.p, S(h));
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S(h));
+    cudaError_t e;
+    if (p->reorder == 1) {
+      counted(h, 9);
+      e = launch_relabel(h->g, h->perm, h->iperm, (int32_t*)rp2.p, (int32_t*)col2.p, (int64_t*)h->ptmp.p, S(h));
+    } else {
+      counted(h, 7);
+      e = cudaMemcpyAsync(h->perm, hperm.data(), sizeof(int32_t) * h->n, cudaMemcpyHostToDevice, S(h));
+      if (e == cudaSuccess)
+        e = launch_relabel_apply(h->g, h->perm, h->iperm, (int32_t*)rp2.p, (int32_t*)col2.p, (int64_t*)h->ptmp.p,
+                                 S(h));
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S(h));  // hperm stays alive until the copy is done
     if (e != cudaSuccess) {
       release(rp2);
       release(col2);
@@ -1288,7 +1317,7 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
     h->csr_rp = rp2;
     h->csr_col = col2;
     h->g = Graph{(const int32_t*)h->csr_rp.p, (const int32_t*)h->csr_col.p, h->n, h->nnz};
-  } else if (p->reorder != 0 && p->reorder != 1) {
+  } else if (p->reorder < 0 || p->reorder > 2) {
     return fail(WL_ERR_INVALID_ARG);
   }
 

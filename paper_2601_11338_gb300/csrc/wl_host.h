@@ -61,6 +61,12 @@ cudaError_t launch_laplacian_apply(const Graph& g, const PartDev& p, const doubl
 cudaError_t launch_relabel(const Graph& g, int32_t* perm, int32_t* iperm, int32_t* new_rp, int32_t* new_col,
                            int64_t* tmp, cudaStream_t s);
 size_t relabel_tmp_i64(int64_t n);
+// the relabelled CSR for a given device perm[new] = old (iperm, new_rp, new_col);
+// tmp holds at least 2 (n + 1) + n / 1024 + 4 int64 (relabel_tmp_i64(n) suffices)
+cudaError_t launch_relabel_apply(const Graph& g, const int32_t* perm, int32_t* iperm, int32_t* new_rp,
+                                 int32_t* new_col, int64_t* tmp, cudaStream_t s);
+// reverse Cuthill-McKee order of a host CSR: perm[new] = old (host arrays)
+int rcm_order(const int32_t* rp, const int32_t* col, int64_t n, int32_t* perm);
 cudaError_t launch_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* tmp, cudaStream_t s);
 // partition by prefix of cost(row) = deg + kRowCost (hub rows weighted x3); tmp: 2 (n + 1) + n / 1024 + 4 int64
 cudaError_t launch_partition_weighted(const Graph& g, PartDev& p, int64_t* tmp, cudaStream_t s);

@@ -489,13 +489,25 @@ cudaError_t launch_relabel(const Graph& g, int32_t* perm, int32_t* iperm, int32_
   cudaError_t e = launch_scan(hist, (int64_t)kKeys * nch, off, sc, s);
   if (e != cudaSuccess) return e;
   k_key_scatter<<<nch, 32, 0, s>>>(g.row_ptr, n, off, nch, perm);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_relabel_apply(g, perm, iperm, new_rp, new_col, sc + (n / kScanBlock + 2), s);
+}
+
+// the relabelled CSR for a given perm[new] = old: iperm, new row pointers
+// (prefix sum of the permuted degrees) and new column labels
+cudaError_t launch_relabel_apply(const Graph& g, const int32_t* perm, int32_t* iperm, int32_t* new_rp,
+                                 int32_t* new_col, int64_t* tmp_i64 /* 2 (n + 1) + n / kScanBlock + 4 */,
+                                 cudaStream_t s) {
+  const int64_t n = g.n;
+  if (n == 0) return cudaMemsetAsync(new_rp, 0, sizeof(int32_t), s);
   const unsigned gb = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32);
   k_inverse_perm<<<gb, 256, 0, s>>>(perm, n, iperm);
-  int64_t* deg = sc + (n / kScanBlock + 2);   // n
+  int64_t* deg = tmp_i64;                     // n
   int64_t* rp64 = deg + n;                    // n + 1
   int64_t* sc2 = rp64 + n + 1;
   k_perm_degrees<<<gb, 256, 0, s>>>(g.row_ptr, perm, n, deg);
-  e = launch_scan(deg, n, rp64, sc2, s);
+  cudaError_t e = launch_scan(deg, n, rp64, sc2, s);
   if (e != cudaSuccess) return e;
   k_i64_to_i32<<<gb, 256, 0, s>>>(rp64, n, new_rp);
   const int64_t warps = std::min<int64_t>(n, 152 * 64);

@@ -96,6 +96,8 @@ def lib():
         L.wl_degrees_noalloc.argtypes = [ctypes.POINTER(wl_csr), c_int, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, c_int, vp, vp, ctypes.POINTER(wl_stats)]
         L.wl_degrees_noalloc.restype = c_int
+        L.wl_rcm_order.argtypes = [vp, vp, i64, vp]
+        L.wl_rcm_order.restype = c_int
         L.wl_selftest_bounded_wait.argtypes = [c_int, vp]
         L.wl_selftest_bounded_wait.restype = c_int
         L.wl_batch_build.argtypes = [vp, c_int, vp, c_int, ctypes.POINTER(wl_params), ctypes.POINTER(vp),
@@ -249,6 +251,16 @@ def wl_degrees_noalloc(row_ptr, col_idx, n, nnz, variant, mu, alpha, Df, tol=0.0
     st = stats if stats is not None else wl_stats()
     return _check(lib().wl_degrees_noalloc(ctypes.byref(A), variant, mu, alpha, tol, max_iter, _ptr(Df), stream,
                                            ctypes.byref(st)), "wl_degrees_noalloc", allow)
+
+
+def wl_rcm_order(row_ptr, col_idx, n):
+    """Reverse Cuthill-McKee order perm[new] = old of a host CSR (int32 arrays).
+    See include/wl.h."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    perm = np.empty(max(int(n), 0), dtype=np.int32)
+    _check(lib().wl_rcm_order(_ptr(rp), _ptr(ci) if ci.size else None, int(n), _ptr(perm)), "wl_rcm_order")
+    return perm
 
 
 def wl_selftest_bounded_wait(missing, stream=None):

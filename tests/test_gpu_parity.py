@@ -43,7 +43,7 @@ def oracle_for(A, mu, alpha):
 
 
 # ------------------------------------------------------------ the small workload
-@pytest.mark.parametrize("reorder", [0, 1])
+@pytest.mark.parametrize("reorder", [0, 1, 2])
 @pytest.mark.parametrize("prec", ["fp64", "refined"])
 def test_erdos_renyi_allwalk_resolvent(prec, reorder):
     """ER n = 2000, mean degree 8, all-walk resolvent, alpha = 0.5 / lambda_max(A):
@@ -83,7 +83,7 @@ def hub_graph():
     return wlgen.csr_from_edges(n, s, d, "hub")
 
 
-@pytest.mark.parametrize("reorder", [0, 1])
+@pytest.mark.parametrize("reorder", [0, 1, 2])
 @pytest.mark.parametrize("variant,mu", [("nbt", 1.0), ("btdw", 0.5), ("btdw", 0.25), ("allwalk", 0.0)])
 @pytest.mark.parametrize("prec", ["fp64", "refined"])
 def test_variants_apply_and_degrees(variant, mu, prec, reorder):
@@ -146,7 +146,7 @@ def test_nbt_diffusion_several_taus(prec):
         assert U[t].min() >= -1e-12
 
 
-@pytest.mark.parametrize("reorder", [0, 1])
+@pytest.mark.parametrize("reorder", [0, 1, 2])
 def test_identity_function_is_combinatorial_laplacian(reorder):
     g = hub_graph()
     A = dense(g)
@@ -242,7 +242,7 @@ def test_iteration_cap_reports_no_convergence():
     assert rc == wl.WL_ERR_NO_CONVERGENCE and w.last.iters == 2
 
 
-@pytest.mark.parametrize("reorder", [0, 1])
+@pytest.mark.parametrize("reorder", [0, 1, 2])
 def test_host_pointers_match_device_pointers(reorder):
     g = wlgen.erdos_renyi(800, 8, 9)
     w = WL(g, alpha_rel=0.5, tol=1e-13, reorder=reorder)
@@ -267,13 +267,15 @@ def test_reruns_are_bit_identical():
 
 
 # ------------------------------------------------------------ full size: properties and closed forms
-def test_torus_closed_form_large():
+@pytest.mark.parametrize("reorder", [1, 2])
+def test_torus_closed_form_large(reorder):
     """4-regular torus 600 x 500 (n = 3e5): D_f and exp(-tau L) e_1 against the
     closed forms of a d-regular graph (eigenvalues of A are
-    2 cos(2 pi j / r) + 2 cos(2 pi k / c))."""
+    2 cos(2 pi j / r) + 2 cos(2 pi k / c)); degree relabelling and reverse
+    Cuthill-McKee relabelling inside the handle."""
     r, c, d, mu = 600, 500, 4, 1.0
     g = wlgen.torus2d(r, c)
-    w = WL(g, variant="nbt", alpha_rel=0.5, tol=1e-13, outer_tol=1e-12)
+    w = WL(g, variant="nbt", alpha_rel=0.5, tol=1e-13, outer_tol=1e-12, reorder=reorder)
     info = w.info
     assert abs(info["rho"] - (d - mu)) <= 1e-8 * (d - mu)
     alpha = info["alpha"]
