@@ -374,6 +374,7 @@ int ensure_phase_buffers(wl_handle* h, int grid) {
 // FP64 lockstep CG on M x = b for K columns (b, x contiguous n x K doubles).
 // x holds the starting guess on entry (zero unless a warm start is given).
 int solve_fp64(wl_handle* h, const double* b, double* x, int K, double tol, bool x_is_zero, SolveInfo& info) {
+  NvtxRange nvtx__("fp64 solve");
   const int grid_u = phase_blocks_f64(K), grid_s = grid_u + h->nhub;
   const size_t nk = (size_t)h->n * K;
   WL_TRY(ensure(h->r, nk * 8));
@@ -410,6 +411,7 @@ int solve_fp64(wl_handle* h, const double* b, double* x, int K, double tol, bool
 // On return (xh, xl) holds X. x0 (FP64, or NULL for X0 = 0) is a warm start.
 int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const double* bn2, float* xh, float* xl,
                      const double* x0, int K, double tol, SolveInfo& info) {
+  NvtxRange nvtx__("refined solve");
   const int grid_u = phase_blocks_f32(K), grid_s = grid_u + h->nhub;
   const int grid_r = df_res_blocks(K) + h->nhub;
   const size_t nk = (size_t)h->n * K;
@@ -553,6 +555,7 @@ int solve(wl_handle* h, const double* b, double* x, int K, bool x_is_zero, Solve
 // series sum_k c_k q_k V with the q_k of Eq. qrec applied term by term
 // (exp_term kernels, double-float), V and X n x K FP64 in the internal order.
 int exp_series(wl_handle* h, const double* V, double* X, int K, SolveInfo& info) {
+  NvtxRange nvtx__("exponential series");
   const size_t nk = (size_t)h->n * K;
   const int gu = exp_blocks(K), gs = gu + h->nhub;
   WL_TRY(ensure(h->ew, nk * 4 * 8));
@@ -757,6 +760,7 @@ int lambda_max_adaptive(wl_handle* h, double rtol, double* lmax) {
 // current one, quadratically convergent), kept inside the bracket of signs
 // seen so far; outside it, regula falsi (Illinois) or halving.
 int rho_companion(wl_handle* h, double mu, double lmaxA, double* rho) {
+  NvtxRange nvtx__("rho(Z_mu)");
   if (mu == 0.0 || lmaxA <= 0.0) {
     *rho = lmaxA;
     return WL_OK;
@@ -926,6 +930,7 @@ constexpr int kLdT = 1024;  // T and y leading dimension (Lanczos steps per colu
 constexpr int kMaxReturnT = 256;  // time points per wl_return_prob call
 
 int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& info, OuterRun& o, int& outer_total) {
+  NvtxRange nvtx__("outer Lanczos on L");
   const int64_t n = h->n;
   const int ldT = kLdT;
   const int maxm = std::min(h->prm.max_outer, ldT - 1);
@@ -1197,6 +1202,7 @@ const char* wl_status_string(int s) {
 const char* wl_last_error(void) { return g_last_error.c_str(); }
 
 int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out, wl_stats* st) {
+  NvtxRange nvtx__("wl_build");
   if (!out) return WL_ERR_INVALID_ARG;
   *out = nullptr;
   if (!A || !p || A->n < 0 || A->nnz < 0 || A->nnz >= (int64_t)INT32_MAX || A->n >= (int64_t)INT32_MAX)
@@ -1466,6 +1472,7 @@ int wl_set_warm_start(wl_handle* h, const double* x0) {
 // Node features of the warm-start network and the analytic guess x_an,
 // in the caller's node order.
 int wl_mlp_features(wl_handle* h, float* feats, double* xan, wl_stats* st) {
+  NvtxRange nvtx__("wl_mlp_features");
   CallScope cs__(h ? &h->retired : nullptr);
   if (st) memset(st, 0, sizeof(*st));
   if (!h || (!feats && !xan)) return WL_ERR_INVALID_ARG;
@@ -1499,6 +1506,7 @@ int wl_mlp_features(wl_handle* h, float* feats, double* xan, wl_stats* st) {
 // Warm start of the walk-degree solve from the network: features, x_an and
 // x0 = x_an * exp(y) on the device, kept as the handle's starting guess.
 int wl_mlp_warm_start(wl_handle* h, const float* params, wl_stats* st) {
+  NvtxRange nvtx__("wl_mlp_warm_start");
   CallScope cs__(h ? &h->retired : nullptr);
   if (st) memset(st, 0, sizeof(*st));
   if (!h || !params) return WL_ERR_INVALID_ARG;
@@ -1531,6 +1539,7 @@ int wl_mlp_warm_start(wl_handle* h, const float* params, wl_stats* st) {
 }
 
 int wl_degrees(wl_handle* h, double* Df, wl_stats* st) {
+  NvtxRange nvtx__("wl_degrees");
   CallScope cs__(h ? &h->retired : nullptr);
   if (!h || (!Df && h->n > 0)) return WL_ERR_INVALID_ARG;
   SolveInfo info;
@@ -1549,6 +1558,7 @@ int wl_degrees(wl_handle* h, double* Df, wl_stats* st) {
 }
 
 int wl_apply(wl_handle* h, const double* V, int64_t ldv, int k, double* W, int64_t ldw, wl_stats* st) {
+  NvtxRange nvtx__("wl_apply");
   CallScope cs__(h ? &h->retired : nullptr);
   if (!h || k < 0 || (k > 0 && h->n > 0 && (!V || !W || ldv < k || ldw < k))) return WL_ERR_INVALID_ARG;
   SolveInfo info;
@@ -1612,6 +1622,7 @@ int wl_apply(wl_handle* h, const double* V, int64_t ldv, int k, double* W, int64
 
 int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* taus, int ntau, double* U,
              int64_t ldo, wl_stats* st) {
+  NvtxRange nvtx__("wl_expmv");
   CallScope cs__(h ? &h->retired : nullptr);
   if (!h || k < 0 || ntau < 0 || ntau > kMaxTau) return WL_ERR_INVALID_ARG;
   if (k > 0 && h->n > 0 && (!U0 || !U || !taus || ldu < k || ldo < k)) return WL_ERR_INVALID_ARG;
@@ -1668,6 +1679,7 @@ int wl_expmv(wl_handle* h, const double* U0, int64_t ldu, int k, const double* t
 
 int wl_markov(wl_handle* h, const double* P0, int64_t ldp, int k, const int* steps, int nsteps, double* out,
               int64_t ldo, wl_stats* st) {
+  NvtxRange nvtx__("wl_markov");
   CallScope cs__(h ? &h->retired : nullptr);
   if (!h || k < 0 || nsteps < 1 || nsteps > 64 || !steps) return WL_ERR_INVALID_ARG;
   if (k > 0 && h->n > 0 && (!P0 || !out || ldp < k || ldo < k)) return WL_ERR_INVALID_ARG;
@@ -1747,6 +1759,7 @@ int wl_markov(wl_handle* h, const double* P0, int64_t ldp, int k, const int* ste
 }
 
 int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, uint16_t* omega_out, wl_stats* st) {
+  NvtxRange nvtx__("wl_trace");
   CallScope cs__(h ? &h->retired : nullptr);
   if (!h || !est || !err_est || M < 2 || M > kMaxSketch) return WL_ERR_INVALID_ARG;
   if (h->prm.f != WL_F_RESOLVENT) return WL_ERR_UNSUPPORTED;
@@ -1830,6 +1843,7 @@ int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, u
 
 int wl_return_prob(wl_handle* h, int M, uint64_t seed, const double* ts, int nt, double* p_est, double* p_err,
                    wl_stats* st) {
+  NvtxRange nvtx__("wl_return_prob");
   CallScope cs__(h ? &h->retired : nullptr);
   if (!h || !ts || !p_est || !p_err || M < 2 || M > kMaxSketch || nt < 1 || nt > kMaxReturnT) return WL_ERR_INVALID_ARG;
   for (int t = 0; t < nt; ++t)

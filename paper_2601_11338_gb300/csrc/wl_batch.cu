@@ -535,6 +535,7 @@ extern "C" {
 
 int wl_batch_build(const wl_csr* graphs, int ngraph, const double* mus, int nmu, const wl_params* p, wl_batch** out,
                    wl_stats* st) {
+  NvtxRange nvtx__("wl_batch_build");
   if (st) memset(st, 0, sizeof(*st));
   if (!out) return WL_ERR_INVALID_ARG;
   *out = nullptr;
@@ -705,6 +706,7 @@ int wl_batch_build(const wl_csr* graphs, int ngraph, const double* mus, int nmu,
 }
 
 int wl_batch_run(wl_batch* b, const double* V, int k, double* Df, double* W, int stepped, wl_stats* st) {
+  NvtxRange nvtx__("wl_batch_run");
   if (st) memset(st, 0, sizeof(*st));
   if (!b || !V || !Df || !W || !valid_k(k)) return WL_ERR_INVALID_ARG;
   const int nslab = b->nslab, np = nprob(b);

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 
 #include "wl_cg2.cuh"
@@ -16,6 +18,15 @@
 #include "wl_spec.cuh"
 
 namespace wl {
+
+// An NVTX range for the lifetime of a scope: API calls and solver phases show
+// up by name on a profiler timeline (a no-op when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct PartDev {
   int G = 0;
