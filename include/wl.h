@@ -79,7 +79,11 @@ typedef enum {
 
 typedef enum {
   WL_FP64    = 0, /* every vector operation in FP64 ("plain FP64 Krylov") */
-  WL_REFINED = 1  /* inner CG in FP32; residual and update in double-float (FP32 pairs), FP64-level accuracy */
+  WL_REFINED = 1, /* inner CG in FP32; residual and update in double-float (FP32 pairs), FP64-level accuracy */
+  WL_SKETCH  = 2  /* the fast form of the randomized estimators (wl_trace, wl_return_prob): Y enters the Gram
+                     in FP32 on the tensor cores, and wl_trace solves Y = phi Omega by FP32 CG alone (relative
+                     residual max(tol, 1e-7)); about 1e-5 relative agreement with the exact-Y estimate. Every
+                     other call treats it as WL_REFINED. */
 } wl_precision;
 
 /* ------------------------------------------------------------ structs */
@@ -111,6 +115,22 @@ typedef struct {
                         at build time; for graphs with geometric locality such as road
                         networks and grids). Results are always returned in the caller's
                         node order. Other values: WL_ERR_INVALID_ARG. */
+  int reorth;        /* outer Lanczos of wl_expmv and wl_return_prob (Sec. 4.1): 0 none (the plain
+                        three-term recurrence); 1 full: every new basis block is made orthogonal
+                        to all earlier blocks of its column by two classical Gram-Schmidt passes
+                        (cost of step j: four reads of j basis blocks). A basis kept orthogonal
+                        needs fewer steps for the same change of exp(-tau T_m) e_1 between checks;
+                        without it the steps still converge (more slowly) to the same result.
+                        Other values: WL_ERR_INVALID_ARG. */
+  double shift;      /* outer Krylov space of wl_expmv and wl_return_prob (Sec. 4.4, rational
+                        Krylov): 0 the polynomial Lanczos process on L (one apply of L per step);
+                        sigma > 0 the shift-and-invert Lanczos process on (L + sigma I)^{-1}
+                        (resolvent only): each step is one CG solve with the sparse positive
+                        definite M - a (D_f + sigma I)^{-1} and one product with M, and
+                        exp(-tau L) u0 ~ |u0| V_m exp(-tau (T_m^{-1} - sigma I)) e_1 with the
+                        eigendecomposition of the small T_m. Its step count does not grow with
+                        |L| (walk degrees near the pole, large tau). Negative or non-finite:
+                        WL_ERR_INVALID_ARG. */
 } wl_params;
 
 typedef struct {
@@ -132,8 +152,9 @@ typedef struct {
   double k_cg_bytes;  /* algorithmic bytes of those iterations */
   int k_res_launches; /* refinement residual kernels (double-float) */
   double k_res_ms;
-  int k_lan_launches; /* Lanczos step kernels */
+  int k_lan_launches; /* Lanczos step (and basis reorthogonalisation) kernels */
   double k_lan_ms;
+  int reorth_blocks;  /* outer Lanczos basis blocks reorthogonalised (wl_params.reorth) */
 } wl_stats;
 
 typedef struct wl_handle wl_handle;
@@ -149,7 +170,8 @@ typedef struct wl_handle wl_handle;
 int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out, wl_stats* st);
 
 /* Updates the per-call settings of a handle: prec, tol, max_iter,
- * max_outer, outer_tol and stream (the operator parameters stay fixed). */
+ * max_outer, outer_tol, reorth, shift and stream (the operator parameters
+ * stay fixed). */
 int wl_set_params(wl_handle* h, const wl_params* p);
 
 /* Walk degrees D_f = phi 1 (total communicability, Sec. 3.1), n FP64
@@ -193,12 +215,15 @@ int wl_markov(wl_handle* h, const double* P0, int64_t ldp, int k, const int* ste
 /* XNysTrace estimate of tr(phi) with M Gaussian test vectors (Alg. 1,
  * "XNysTrace(Y, Omega)"). Omega (n x M) is drawn on the device by
  * Philox4x32-10 from `seed` (element e = i M + j uses block e / 4, see the
- * library documentation), rounded to bfloat16; Y = phi Omega is solved in
- * FP32 CG; the Gram matrices [Omega Y]^T Y are accumulated in FP32 from
- * exact bf16 products; the leave-one-out core runs in FP64. Writes the
- * estimate and the error estimate std(t_i)/sqrt(M) to the host scalars.
- * omega_out (optional, n x M uint16 bf16 bits, host or device) receives
- * Omega. 2 <= M <= 64. */
+ * library documentation), rounded to bfloat16. Y = phi Omega and the Gram
+ * matrices [Omega Y]^T Y depend on the handle's prec:
+ *   WL_FP64, WL_REFINED: Y by the CG solve of that form (to tol), the Gram
+ *     in FP64 on CUDA cores (estimate as accurate as Y);
+ *   WL_SKETCH: Y by FP32 CG, the Gram in TF32 on the tensor cores with Y
+ *     split in two terms and FP32 sums per node chunk.
+ * The leave-one-out core runs in FP64. Writes the estimate and the error
+ * estimate std(t_i)/sqrt(M) to the host scalars. omega_out (optional,
+ * n x M uint16 bf16 bits, host or device) receives Omega. 2 <= M <= 64. */
 int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, uint16_t* omega_out,
              wl_stats* st);
 
@@ -209,7 +234,9 @@ int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, u
  * exp(-t L) Omega comes from one lockstep Lanczos run on L per column
  * (Sec. 4.1) evaluated at every t; XNysTrace(Y(t), Omega) / n gives
  * p_est[t] and the error estimate p_err[t] (host arrays of nt values).
- * ts: host array of nt time points >= 0, 1 <= nt <= 256; 2 <= M <= 64.
+ * The Gram takes Y(t) in FP64 (WL_FP64, WL_REFINED) or rounded to FP32 on
+ * the tensor cores (WL_SKETCH). ts: host array of nt time points >= 0,
+ * 1 <= nt <= 256; 2 <= M <= 64.
  * A polynomial Krylov basis replaces the paper's block rational one (one
  * apply of L per step instead of shifted solves with L). */
 int wl_return_prob(wl_handle* h, int M, uint64_t seed, const double* ts, int nt, double* p_est, double* p_err,
@@ -253,8 +280,12 @@ size_t wl_pool_cached_bytes(void);
  *    WL_ERR_INVALID_ARG because the fixed array cannot hold their vectors.
  *  - A (row_ptr, col_idx) and Df are DEVICE pointers owned by the caller; Df
  *    receives n FP64 values. mu is used only with WL_BTDW. alpha is taken
- *    as given (alpha * rho(Z_mu) >= 1 shows up as WL_ERR_NOT_SPD); tol <= 0
- *    means 1e-12, max_iter <= 0 means 2000.
+ *    as given and the call does not estimate rho(Z_mu): the caller must keep
+ *    alpha < 1 / rho(Z_mu), the range where M is positive definite.
+ *    WL_ERR_NOT_SPD is returned only when CG meets a non-positive curvature
+ *    (p, M p); for an indefinite M it may instead stop on max_iter or return
+ *    a finite vector that is not the walk series. tol <= 0 means 1e-12,
+ *    max_iter <= 0 means 2000.
  *  - The first call on each device looks up the array's device address with
  *    cudaGetSymbolAddress (that device must be current) and caches it; make
  *    that first call before any stream capture begins.
@@ -262,7 +293,10 @@ size_t wl_pool_cached_bytes(void);
  *    zero. Calls that overlap on the GPU (different streams or host threads
  *    at the same time) race on the array and corrupt each other's results;
  *    serialise them.
- *  - Returns after the device work has completed. `st` may be NULL. */
+ *  - Every call synchronises `stream` before it returns (it reads the
+ *    validation flags and the CG state back into host memory), so its device
+ *    work has completed on return. st->status equals the return code on every
+ *    exit. `st` may be NULL. */
 int wl_degrees_noalloc(const wl_csr* A, wl_variant v, double mu, double alpha, double tol, int max_iter,
                        double* Df, void* stream, wl_stats* st);
 

@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwl.so")
 
-UNITS = ["wl_api.cu", "wl_k_misc.cu", "wl_k_cg64.cu", "wl_k_cg32.cu", "wl_k_lanczos.cu", "wl_k_trace.cu", "wl_k_df.cu", "wl_k_spec.cu", "wl_noalloc.cu",
+UNITS = ["wl_api.cu", "wl_k_misc.cu", "wl_k_cg64.cu", "wl_k_cg32.cu", "wl_k_lanczos.cu", "wl_k_trace.cu", "wl_k_df.cu", "wl_k_spec.cu", "wl_k_reorth.cu", "wl_k_si.cu", "wl_noalloc.cu",
          "wl_batch.cu", "wl_mlp.cu", "wl_pool.cu", "wl_order.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

@@ -120,6 +120,7 @@ struct SolveInfo {
   int status = WL_OK;
   double nnz_rhs = 0.0;
   double bytes = 0.0;
+  int reorth_blocks = 0;  // basis blocks reorthogonalised (outer Lanczos)
 };
 
 }  // namespace
@@ -155,6 +156,13 @@ struct wl_handle {
   Buf basis;
   size_t basis_blocks = 0;
   Buf Tab, ybuf, yprev, errb;
+  Buf robuf, romask;      // basis reorthogonalisation: partial sums / coefficients, per-column mask
+  Buf sibuf;              // shift-and-invert: -a / (D_f + sigma) and 1 / (D_f + sigma), FP64 and double-float
+  double si_sigma = 0.0;  // the shift sibuf was computed for (0: none)
+  // per-row diagonal added to M by the solves while a shift-and-invert step runs (else NULL)
+  const double* si_dsh64 = nullptr;
+  const float* si_dsh_h = nullptr;
+  const float* si_dsh_l = nullptr;
   Buf stage_a, stage_b;   // host <-> device staging
   Buf packV, packX;
   Buf omega, gram;        // sketch and Gram workspace
@@ -398,6 +406,7 @@ int solve_fp64(wl_handle* h, const double* b, double* x, int K, double tol, bool
   }
   PhaseArgs<double> a{phase_graph_mid(h, grid_u), x, (double*)h->r.p, (double*)h->p.p, (double*)h->q.p, h->ca, h->cA, h->cD,
                       bn2, nullptr, (double*)h->part.p, st, h->prm.max_iter, tol * tol};
+  a.dshift = h->si_dsh64;  // shifted solve of the shift-and-invert Lanczos (else NULL)
   WL_TRY(run_cg<double>(h, K, a, grid_s, grid_u, info, 8));
   info.max_rel = std::max(info.max_rel, info.last_rel);
   return WL_OK;
@@ -446,6 +455,8 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
     WL_CU(launch_split_x(x0, (int64_t)nk, xh, xl, false, nullptr, S(h)));
     DfResArgs ra{phase_graph_mid(h, grid_r - h->nhub), xh, xl, bh, bl, rh, rl, (float*)h->r32.p, nullptr, nullptr, nullptr,
                  ca, cA, cD, (double*)h->part.p, st, 0};
+    ra.dsh_h = h->si_dsh_h;
+    ra.dsh_l = h->si_dsh_l;
     const int pi = prof_begin(h, kCatRes);
     WL_CU(launch_df_res(K, ra, grid_r, true, S(h)));
     prof_end(h, pi);
@@ -489,6 +500,7 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
     PhaseArgs<float> a{phase_graph_mid(h, grid_u), dcur, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
                        h->ca, h->cA, h->cD, nullptr, dskip, (double*)h->part.p, st, h->prm.max_iter,
                        inner_tol * inner_tol};
+    a.dshift = h->si_dsh_h;
     SolveInfo inner;
     WL_TRY(run_cg<float>(h, K, a, grid_s, grid_u, inner, 4));
     if (inner.status == WL_ERR_NOT_SPD || inner.status == WL_ERR_NONFINITE) {
@@ -503,6 +515,8 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
     WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
     DfResArgs ra{phase_graph_mid(h, grid_r - h->nhub), dcur, nullptr, rch, rcl, rh, rl, (float*)h->r32.p, xh, xl, dnext,
                  ca, cA, cD, (double*)h->part.p, st, x_zero ? 1 : 0};
+    ra.dsh_h = h->si_dsh_h;
+    ra.dsh_l = h->si_dsh_l;
     const int pi = prof_begin(h, kCatRes);
     counted(h);
     WL_CU(launch_df_res(K, ra, grid_r, false, S(h)));
@@ -546,7 +560,7 @@ int solve_refined(wl_handle* h, const double* b, double* x, int K, double tol, b
 
 int solve(wl_handle* h, const double* b, double* x, int K, bool x_is_zero, SolveInfo& info) {
   const double tol = h->prm.tol;
-  if (h->prm.prec == WL_REFINED) return solve_refined(h, b, x, K, tol, x_is_zero, info);
+  if (h->prm.prec != WL_FP64) return solve_refined(h, b, x, K, tol, x_is_zero, info);
   if (x_is_zero) WL_CU(cudaMemsetAsync(x, 0, (size_t)h->n * K * 8, S(h)));
   return solve_fp64(h, b, x, K, tol, x_is_zero, info);
 }
@@ -900,6 +914,7 @@ void fill_stats(wl_handle* h, wl_stats* st, const SolveInfo& in, int status, dou
   st->mu = h->mu;
   st->rho = h->rho;
   st->lambda_max = h->lmax;
+  st->reorth_blocks = in.reorth_blocks;
 }
 
 // internal-order n-vector -> caller's array (host or device), undoing the relabelling
@@ -924,9 +939,212 @@ struct OuterRun {
   bool converged = false, dfp = false;
   size_t blk = 0;
   const double* dtaus = nullptr;
+  // shift-and-invert run: the shift, the time points and T_m per column (host)
+  bool si = false;
+  double sigma = 0.0;
+  std::vector<double> taus, Ta, Tb;  // Ta, Tb: K x m
 };
 
 constexpr int kLdT = 1024;  // T and y leading dimension (Lanczos steps per column at most kLdT - 1)
+
+// ------------------------------------------------------------------ shift-and-invert Lanczos (Sec. 4.4)
+// Eigenvalues th[0..m) and eigenvectors (column k: Z[i * m + k]) of the
+// symmetric tridiagonal matrix with diagonal a[0..m) and off-diagonal
+// b[0..m-1), by implicit QR sweeps with the Wilkinson shift on each
+// unreduced block (Golub and Van Loan, Sec. 8.3), the rotations accumulated
+// into Z. False if a block needs more than 30 m sweeps.
+bool tridiag_eig_host(int m, const double* a, const double* b, std::vector<double>& th, std::vector<double>& Z) {
+  th.assign(a, a + m);
+  std::vector<double> e(std::max(m, 1), 0.0);
+  for (int i = 0; i + 1 < m; ++i) e[i] = b[i];
+  Z.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) Z[(size_t)i * m + i] = 1.0;
+  const double eps = 2.220446049250313e-16;
+  int hi = m - 1, sweeps = 0;
+  while (hi > 0) {
+    if (std::fabs(e[hi - 1]) <= eps * (std::fabs(th[hi - 1]) + std::fabs(th[hi]))) {
+      e[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && std::fabs(e[lo - 1]) > eps * (std::fabs(th[lo - 1]) + std::fabs(th[lo]))) --lo;
+    if (lo > 0) e[lo - 1] = 0.0;
+    if (++sweeps > 30 * m) return false;
+    const double t = 0.5 * (th[hi - 1] - th[hi]), bb = e[hi - 1];
+    const double mu = th[hi] - bb * bb / (t + std::copysign(std::hypot(t, bb), t));
+    double x = th[lo] - mu, z = e[lo];
+    for (int k = lo; k < hi; ++k) {
+      const double r = std::hypot(x, z);
+      const double c = r > 0.0 ? x / r : 1.0, sn = r > 0.0 ? z / r : 0.0;
+      if (k > lo) e[k - 1] = r;
+      const double dk = th[k], dk1 = th[k + 1], ek = e[k];
+      th[k] = c * c * dk + 2.0 * c * sn * ek + sn * sn * dk1;
+      th[k + 1] = sn * sn * dk - 2.0 * c * sn * ek + c * c * dk1;
+      e[k] = c * sn * (dk1 - dk) + (c * c - sn * sn) * ek;
+      if (k + 1 < hi) {
+        z = sn * e[k + 1];
+        e[k + 1] *= c;
+        x = e[k];
+      }
+      for (int i = 0; i < m; ++i) {
+        double* zr = &Z[(size_t)i * m];
+        const double zk = zr[k], zk1 = zr[k + 1];
+        zr[k] = c * zk + sn * zk1;
+        zr[k + 1] = -sn * zk + c * zk1;
+      }
+    }
+  }
+  return true;
+}
+
+// y(tau) = exp(-tau (T^{-1} - sigma I)) e_1 for every tau from the
+// eigendecomposition of one column's T (m steps): y[t * ld + i]. An
+// eigenvalue theta <= 0 (a direction that the shifted inverse maps to 0, or
+// rounding of one) contributes nothing.
+bool si_eval(int m, const double* a, const double* b, double sigma, const std::vector<double>& taus, double* y,
+             int ld) {
+  std::vector<double> th, Z;
+  if (!tridiag_eig_host(m, a, b, th, Z)) return false;
+  for (size_t t = 0; t < taus.size(); ++t) {
+    double* yt = y + t * ld;
+    for (int i = 0; i < m; ++i) yt[i] = 0.0;
+    for (int k = 0; k < m; ++k) {
+      if (!(th[k] > 0.0)) continue;
+      const double f = std::exp(-taus[t] * (1.0 / th[k] - sigma)) * Z[k];
+      if (f == 0.0) continue;
+      for (int i = 0; i < m; ++i) yt[i] += Z[(size_t)i * m + k] * f;
+    }
+  }
+  return true;
+}
+
+// the per-row diagonal and scaling of the shifted solves for the handle's
+// D_f and shift sigma (sibuf: dsh64, inv64 (n doubles each), then dsh_h,
+// dsh_l, inv_h, inv_l (n floats each))
+int si_setup(wl_handle* h, double sigma) {
+  const int64_t n = h->n;
+  WL_TRY(ensure(h->sibuf, (size_t)n * 32 + 256));
+  double* d64 = (double*)h->sibuf.p;
+  float* f32 = (float*)(d64 + 2 * n);
+  counted(h);
+  WL_CU(launch_si_prep((const double*)h->Df.p, n, h->a_scale, sigma, d64, f32, f32 + n, d64 + n, f32 + 2 * n,
+                       f32 + 3 * n, S(h)));
+  h->si_sigma = sigma;
+  return WL_OK;
+}
+
+// While alive, the solves of the handle add the diagonal -a / (D_f + sigma) to M.
+struct SiScope {
+  wl_handle* h;
+  SiScope(wl_handle* hh, bool dfp) : h(hh) {
+    const int64_t n = h->n;
+    double* d64 = (double*)h->sibuf.p;
+    float* f32 = (float*)(d64 + 2 * n);
+    if (dfp) {
+      h->si_dsh_h = f32;
+      h->si_dsh_l = f32 + n;
+    } else {
+      h->si_dsh64 = d64;
+    }
+  }
+  ~SiScope() {
+    h->si_dsh64 = nullptr;
+    h->si_dsh_h = h->si_dsh_l = nullptr;
+  }
+};
+
+// One application of R = (L + sigma I)^{-1} to the basis block j, leaving
+// -R v_j where the Lanczos step kernels read it: the double-float form in
+// (h->rh, h->rl), the FP64 form in h->packX.
+int si_apply(wl_handle* h, bool dfp, int K, int j, size_t blk, SolveInfo& info) {
+  const int64_t n = h->n;
+  double* d64 = (double*)h->sibuf.p;
+  float* f32 = (float*)(d64 + 2 * n);
+  if (dfp) {
+    float* vjh = (float*)h->basis.p + (size_t)2 * j * blk;
+    WL_TRY(ensure(h->bh, blk * 4));
+    WL_TRY(ensure(h->bl, blk * 4));
+    WL_TRY(ensure(h->part, (size_t)std::max(si_rhs_blocks(n, K), 1) * 64 * 8 + 1024));
+    double* bn2si = (double*)h->small.p + 744;
+    counted(h, 2);
+    WL_CU(launch_si_rhs_df(vjh, vjh + blk, f32 + 2 * n, f32 + 3 * n, n, K, (float*)h->bh.p, (float*)h->bl.p,
+                           (double*)h->part.p, bn2si, S(h)));
+    {
+      SiScope sc(h, true);
+      WL_TRY(solve_refined_df(h, (const float*)h->bh.p, (const float*)h->bl.p, bn2si, (float*)h->xh.p,
+                              (float*)h->xl.p, nullptr, K, h->prm.tol, info));
+    }
+    if (info.status != WL_OK) return WL_OK;
+    // (rh, rl) = 0 - M z
+    const int grid_r = df_res_blocks(K) + h->nhub;
+    const df ca = df_from_double(h->ca), cA = df_from_double(h->cA), cD = df_from_double(h->cD);
+    DfResArgs ra{phase_graph_mid(h, grid_r - h->nhub), (const float*)h->xh.p, (const float*)h->xl.p, nullptr, nullptr,
+                 (float*)h->rh.p, (float*)h->rl.p, nullptr, nullptr, nullptr, nullptr, ca, cA, cD,
+                 (double*)h->part.p, h->cgst(), 0};
+    const int pi = prof_begin(h, kCatRes);
+    counted(h);
+    WL_CU(launch_df_res(K, ra, grid_r, true, S(h)));
+    prof_end(h, pi);
+  } else {
+    const double* vj = (const double*)h->basis.p + (size_t)j * blk;
+    WL_TRY(ensure(h->b64, blk * 8));
+    WL_TRY(ensure(h->x, blk * 8));
+    counted(h);
+    WL_CU(launch_si_rhs64(vj, d64 + n, n, K, (double*)h->b64.p, S(h)));
+    WL_CU(cudaMemsetAsync(h->x.p, 0, blk * 8, S(h)));
+    {
+      SiScope sc(h, false);
+      WL_TRY(solve_fp64(h, (const double*)h->b64.p, (double*)h->x.p, K, h->prm.tol, true, info));
+    }
+    if (info.status != WL_OK) return WL_OK;
+    // packX = 0 - M z
+    const int gr = res_blocks(K) + h->nhub;
+    ResPhaseArgs ra{phase_graph(h), (const double*)h->x.p, nullptr, (double*)h->packX.p, h->ca, h->cA, h->cD,
+                    (double*)h->part.p, h->cgst()};
+    const int pi = prof_begin(h, kCatRes);
+    counted(h);
+    WL_CU(launch_res_phases(K, ra, gr, S(h)));
+    prof_end(h, pi);
+  }
+  info.nnz_rhs += (double)h->nnz * K;
+  info.iters += 1;
+  return WL_OK;
+}
+
+// Reorthogonalises basis block j + 1 (columns with mask 1) against blocks
+// 0..j; beta_j of those columns is rescaled on the device.
+int reorth_block(wl_handle* h, bool dfp, int K, int j, size_t blk, double* Tb, int* done, const int* hmask) {
+  const int nb = j + 1;
+  WL_TRY(ensure(h->robuf, reorth_part_doubles(nb, K, blk) * 8));
+  WL_TRY(ensure(h->romask, 64 * sizeof(int)));
+  WL_CU(cudaMemcpyAsync(h->romask.p, hmask, K * sizeof(int), cudaMemcpyHostToDevice, S(h)));
+  ReorthArgs ra{};
+  ra.basis = h->basis.p;
+  if (dfp) {
+    ra.v = (float*)h->basis.p + (size_t)2 * (j + 1) * blk;
+    ra.vlo = (float*)h->basis.p + (size_t)(2 * (j + 1) + 1) * blk;
+  } else {
+    ra.v = (double*)h->basis.p + (size_t)(j + 1) * blk;
+    ra.vlo = nullptr;
+  }
+  ra.n = h->n;
+  ra.K = K;
+  ra.nb = nb;
+  ra.blk = blk;
+  ra.part = (double*)h->robuf.p;
+  ra.mask = (const int*)h->romask.p;
+  ra.Tb = Tb;
+  ra.done = done;
+  ra.j = j;
+  ra.ldT = kLdT;
+  const int pl = prof_begin(h, kCatLan);
+  counted(h, 8);
+  const cudaError_t e = launch_reorth(ra, dfp, S(h));
+  prof_end(h, pl);
+  if (e != cudaSuccess) return set_cuda_error(e, "reorth");
+  return WL_OK;
+}
 constexpr int kMaxReturnT = 256;  // time points per wl_return_prob call
 
 int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& info, OuterRun& o, int& outer_total) {
@@ -936,14 +1154,25 @@ int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& inf
   const int maxm = std::min(h->prm.max_outer, ldT - 1);
   const int check = 4;
   // refined resolvent form: double-float outer recurrence (FP32 instructions only)
-  const bool dfp = h->prm.prec == WL_REFINED && h->prm.f == WL_F_RESOLVENT;
+  const bool dfp = h->prm.prec != WL_FP64 && h->prm.f == WL_F_RESOLVENT;
   o = OuterRun{};
   o.K = K;
   o.ntau = ntau;
   o.dfp = dfp;
   o.dtaus = dtaus;
+  const bool si = h->prm.shift > 0.0;  // shift-and-invert Lanczos on (L + sigma I)^{-1}
+  if (si && h->prm.f != WL_F_RESOLVENT) return WL_ERR_UNSUPPORTED;
   if (h->prm.f != WL_F_IDENTITY && !h->have_Df) WL_TRY(compute_Df(h, info));
   if (info.status != WL_OK) return WL_OK;
+  if (si) {
+    WL_TRY(si_setup(h, h->prm.shift));
+    o.si = true;
+    o.sigma = h->prm.shift;
+    o.taus.resize(ntau);
+    WL_CU(cudaMemcpyAsync(h->h_pin, dtaus, (size_t)ntau * 8, cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaStreamSynchronize(S(h)));
+    for (int t = 0; t < ntau; ++t) o.taus[t] = h->h_pin[t];
+  }
   if (dfp && !h->have_dfdf) {  // D_f as two FP32 terms for the double-float outer recurrence
     WL_TRY(ensure(h->dfdf, (size_t)n * 8));
     counted(h);
@@ -1002,6 +1231,9 @@ int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& inf
   WL_TRY(ensure(h->part, (size_t)std::max(Gs, 1) * 64 * 2 * 8 + 1024));
   int m = 0;
   bool converged = false;
+  const bool reorth = h->prm.reorth == 1;
+  const std::vector<int> rmask(K, 1);
+  std::vector<std::vector<double>> si_prev(si ? (size_t)K * ntau : 0);  // y(tau) of the last check
   for (int j = 0; j < maxm; ++j) {
     if ((size_t)(j + 2) > cap_blocks) {
       // grow the basis (double), keeping the blocks computed so far
@@ -1021,13 +1253,24 @@ int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& inf
       float* vjh = (float*)basis + (size_t)2 * j * blk;
       float* vmh = j > 0 ? (float*)basis + (size_t)2 * (j - 1) * blk : nullptr;
       float* vph = (float*)basis + (size_t)2 * (j + 1) * blk;
-      WL_TRY(solve_refined_df(h, vjh, vjh + blk, bn2, (float*)h->xh.p, (float*)h->xl.p, nullptr, K, h->prm.tol, info));
+      if (si) {  // Y = -R v_j in (rh, rl); w = 0 v_j - 1 Y
+        WL_TRY(si_apply(h, true, K, j, blk, info));
+      } else {
+        WL_TRY(solve_refined_df(h, vjh, vjh + blk, bn2, (float*)h->xh.p, (float*)h->xl.p, nullptr, K, h->prm.tol,
+                                info));
+      }
       if (info.status != WL_OK) return WL_OK;
       WL_TRY(ensure(h->part, (size_t)std::max(Gs, 1) * 64 * 2 * 8 + 1024));
       DfLanczosArgs la{vjh, vjh + blk, vmh, vmh ? vmh + blk : nullptr, (const float*)h->xh.p,
                        (const float*)h->xl.p, (const float*)h->dfdf.p, (const float*)h->dfdf.p + n,
                        df_from_double(h->a_scale), vph, vph + blk, Ta, Tb, done, bn2, (double*)h->part.p,
                        h->bar, n, j, ldT};
+      if (si) {
+        la.yh = (const float*)h->rh.p;
+        la.yl = (const float*)h->rl.p;
+        la.dfh = la.dfl = nullptr;
+        la.ascale = df_from_double(1.0);
+      }
       WL_TRY(reset_bar(h));
       const int pl = prof_begin(h, kCatLan);
       counted(h);
@@ -1040,7 +1283,13 @@ int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& inf
       double* vjp1 = basis + (size_t)(j + 1) * blk;
       LanczosStepArgs la{h->g, pd->view(), vj, vjm1, nullptr, (const double*)h->Df.p, 0, 0, 0, vjp1,
                          Ta, Tb, done, (double*)h->part.p, h->bar, j, ldT, 0};
-      if (h->prm.f == WL_F_IDENTITY) {
+      if (si) {  // X = -R v_j in packX; w = 0 v_j - X
+        WL_TRY(si_apply(h, false, K, j, blk, info));
+        if (info.status != WL_OK) return WL_OK;
+        la.X = (const double*)h->packX.p;
+        la.Df = nullptr;
+        la.part = (double*)h->part.p;
+      } else if (h->prm.f == WL_F_IDENTITY) {
         la.mode = 1;
         la.c0 = 0.0;
         la.cA = -1.0;
@@ -1061,7 +1310,39 @@ int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& inf
     }
     m = j + 1;
     ++outer_total;
-    if (m % check == 0 || m == maxm) {
+    if (si && (m % check == 0 || m == maxm)) {
+      // y(tau) = exp(-tau (T_m^{-1} - sigma I)) e_1 per column on the host,
+      // compared with the previous check's (the rule of the polynomial run)
+      std::vector<double> hT((size_t)2 * K * m);
+      WL_CU(cudaMemcpy2DAsync(hT.data(), (size_t)m * 8, Ta, (size_t)ldT * 8, (size_t)m * 8, K,
+                              cudaMemcpyDeviceToHost, S(h)));
+      WL_CU(cudaMemcpy2DAsync(hT.data() + (size_t)K * m, (size_t)m * 8, Tb, (size_t)ldT * 8, (size_t)m * 8, K,
+                              cudaMemcpyDeviceToHost, S(h)));
+      WL_CU(cudaStreamSynchronize(S(h)));
+      const int berr = check_bar(h);
+      if (berr) return berr;
+      bool all = true;
+      std::vector<double> y((size_t)ntau * m);
+      for (int c = 0; c < K; ++c) {
+        if (!si_eval(m, hT.data() + (size_t)c * m, hT.data() + (size_t)(K + c) * m, o.sigma, o.taus, y.data(), m)) {
+          all = false;
+          continue;
+        }
+        for (int t = 0; t < ntau; ++t) {
+          const double* yt = y.data() + (size_t)t * m;
+          double ny = 0.0, dy = 0.0;
+          const std::vector<double>& yp = si_prev[(size_t)c * ntau + t];
+          for (int i = 0; i < m; ++i) {
+            const double d = yt[i] - (i < (int)yp.size() ? yp[i] : 0.0);
+            ny += yt[i] * yt[i];
+            dy += d * d;
+          }
+          if (!(ny > 0.0) || yp.empty() || !(std::sqrt(dy) <= h->prm.outer_tol * std::sqrt(ny))) all = false;
+          si_prev[(size_t)c * ntau + t].assign(yt, yt + m);
+        }
+      }
+      if (all) { converged = true; break; }
+    } else if (m % check == 0 || m == maxm) {
       std::vector<int> hm(K, m);
       WL_CU(cudaMemcpyAsync(mcol, hm.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
       TridiagArgs ta{Ta, Tb, mcol, dtaus, (double*)h->ybuf.p, (double*)h->yprev.p, mprev, errd, ldT, ntau, 1,
@@ -1079,9 +1360,22 @@ int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& inf
           if (!(h->h_pin[c * ntau + t] <= h->prm.outer_tol)) { all = false; break; }
       if (all) { converged = true; break; }
     }
+    if (reorth && m < maxm) {  // the run goes on: make v_{j+1} orthogonal to v_0 .. v_j
+      WL_TRY(reorth_block(h, dfp, K, j, blk, Tb, done, rmask.data()));
+      info.reorth_blocks += 1;
+    }
   }
   o.m = m;
   o.converged = converged;
+  if (si && m > 0) {  // T_m per column for outer_combine
+    o.Ta.resize((size_t)K * m);
+    o.Tb.resize((size_t)K * m);
+    WL_CU(cudaMemcpy2DAsync(o.Ta.data(), (size_t)m * 8, Ta, (size_t)ldT * 8, (size_t)m * 8, K,
+                            cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaMemcpy2DAsync(o.Tb.data(), (size_t)m * 8, Tb, (size_t)ldT * 8, (size_t)m * 8, K,
+                            cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaStreamSynchronize(S(h)));
+  }
   return WL_OK;
 }
 
@@ -1101,11 +1395,23 @@ int outer_combine(wl_handle* h, const OuterRun& o, int t0, int nt, double* out, 
   std::vector<int> hm(K, o.m), hz(K, 0);
   WL_CU(cudaMemcpyAsync(mcol, hm.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
   WL_CU(cudaMemcpyAsync(mzero, hz.data(), K * 4, cudaMemcpyHostToDevice, S(h)));
-  TridiagArgs ta{Ta, Tb, mcol, o.dtaus + t0, (double*)h->ybuf.p, (double*)h->yprev.p, mzero, errd, ldT, nt, 1,
-                 kChebMax};
-  counted(h);
-  cudaError_t e = launch_tridiag_exp(ta, K, o.m, S(h));
-  if (e != cudaSuccess) return set_cuda_error(e, "tridiag_exp");
+  cudaError_t e = cudaSuccess;
+  if (o.si) {  // y(tau) from the eigendecomposition of each column's T_m (host)
+    std::vector<double> hy((size_t)K * nt * ldT, 0.0);
+    const std::vector<double> tt(o.taus.begin() + t0, o.taus.begin() + t0 + nt);
+    for (int c = 0; c < K; ++c)
+      if (o.m > 0 && !si_eval(o.m, o.Ta.data() + (size_t)c * o.m, o.Tb.data() + (size_t)c * o.m, o.sigma, tt,
+                              hy.data() + (size_t)c * nt * ldT, ldT))
+        return WL_ERR_NO_CONVERGENCE;
+    WL_CU(cudaMemcpyAsync(h->ybuf.p, hy.data(), hy.size() * 8, cudaMemcpyHostToDevice, S(h)));
+    WL_CU(cudaStreamSynchronize(S(h)));
+  } else {
+    TridiagArgs ta{Ta, Tb, mcol, o.dtaus + t0, (double*)h->ybuf.p, (double*)h->yprev.p, mzero, errd, ldT, nt, 1,
+                   kChebMax};
+    counted(h);
+    e = launch_tridiag_exp(ta, K, o.m, S(h));
+    if (e != cudaSuccess) return set_cuda_error(e, "tridiag_exp");
+  }
   if (o.dfp) {
     const size_t ny = (size_t)K * nt * ldT;
     WL_TRY(ensure(h->ydf, ny * 8));
@@ -1210,7 +1516,9 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
   if ((A->n > 0 && !A->row_ptr) || (A->nnz > 0 && !A->col_idx)) return WL_ERR_INVALID_ARG;
   if (v != WL_ALLWALK && v != WL_NBT && v != WL_BTDW) return WL_ERR_INVALID_ARG;
   if (p->f != WL_F_RESOLVENT && p->f != WL_F_EXP && p->f != WL_F_IDENTITY) return WL_ERR_INVALID_ARG;
-  if (p->prec != WL_FP64 && p->prec != WL_REFINED) return WL_ERR_INVALID_ARG;
+  if (p->prec != WL_FP64 && p->prec != WL_REFINED && p->prec != WL_SKETCH) return WL_ERR_INVALID_ARG;
+  if (p->reorth < 0 || p->reorth > 1) return WL_ERR_INVALID_ARG;
+  if (!(p->shift >= 0.0) || !std::isfinite(p->shift)) return WL_ERR_INVALID_ARG;
   double mu = (v == WL_ALLWALK) ? 0.0 : (v == WL_NBT ? 1.0 : p->mu);
   if (!(mu >= 0.0 && mu <= 1.0)) return WL_ERR_INVALID_ARG;
 
@@ -1421,8 +1729,12 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
 
 int wl_set_params(wl_handle* h, const wl_params* p) {
   if (!h || !p) return WL_ERR_INVALID_ARG;
-  if (p->prec != WL_FP64 && p->prec != WL_REFINED) return WL_ERR_INVALID_ARG;
+  if (p->prec != WL_FP64 && p->prec != WL_REFINED && p->prec != WL_SKETCH) return WL_ERR_INVALID_ARG;
+  if (p->reorth < 0 || p->reorth > 1) return WL_ERR_INVALID_ARG;
+  if (!(p->shift >= 0.0) || !std::isfinite(p->shift)) return WL_ERR_INVALID_ARG;
   h->prm.prec = p->prec;
+  h->prm.reorth = p->reorth;
+  h->prm.shift = p->shift;
   h->prm.tol = p->tol;
   h->prm.max_iter = p->max_iter;
   h->prm.max_outer = p->max_outer;
@@ -1798,6 +2110,36 @@ int wl_trace(wl_handle* h, int M, uint64_t seed, double* est, double* err_est, u
       counted(h);
       e = launch_permute_rows_u16(omega, n, M, h->perm, om_int, S(h));
     }
+    if (h->prm.prec != WL_SKETCH) {
+      // Y = phi Omega by the solve of the handle's form (FP64 n x K), Gram in FP64
+      if (e == cudaSuccess && (rc = ensure(h->packV, nk * 8)) != WL_OK) break;
+      if (e == cudaSuccess && (rc = ensure(h->packX, nk * 8)) != WL_OK) break;
+      if (e == cudaSuccess && (rc = ensure(h->gram, (size_t)Gg * 2 * kMaxSketch * kMaxSketch * 8 +
+                                                     2 * kMaxSketch * kMaxSketch * 8 + 128 * 8)) != WL_OK) break;
+      counted(h);
+      if (e == cudaSuccess) e = launch_sketch_block_f64(om_int, n, M, K, (double*)h->packV.p, S(h));
+      if (e != cudaSuccess) { rc = set_cuda_error(e, "sketch"); break; }
+      if ((rc = phi_apply(h, (const double*)h->packV.p, (double*)h->packX.p, K, info)) != WL_OK) break;
+      if (info.status != WL_OK) break;
+      double* part64 = (double*)h->gram.p;
+      gout = part64 + (size_t)Gg * 2 * kMaxSketch * kMaxSketch;
+      core = gout + 2 * kMaxSketch * kMaxSketch;
+      counted(h, 3);
+      e = launch_gram_f64(om_int, (const double*)h->packX.p, n, M, K, part64, Gg, gout, S(h));
+      if (e == cudaSuccess) e = launch_nys_core(gout, M, core, S(h));
+      if (e != cudaSuccess) { rc = set_cuda_error(e, "gram/core"); break; }
+      double* hp = h->h_pin;
+      WL_CU(cudaMemcpyAsync(hp, core, 8 * 8, cudaMemcpyDeviceToHost, S(h)));
+      WL_CU(cudaStreamSynchronize(S(h)));
+      if (hp[2] != 0.0) { rc = WL_ERR_NOT_SPD; break; }
+      *est = hp[0];
+      *err_est = hp[1];
+      if (omega_out) {
+        e = cudaMemcpyAsync(omega_out, omega, (size_t)n * M * sizeof(uint16_t), cudaMemcpyDefault, S(h));
+        if (e != cudaSuccess) { rc = set_cuda_error(e, "copy omega"); break; }
+      }
+      break;
+    }
     if (e == cudaSuccess) e = launch_sketch_rhs(om_int, n, M, K, h->a_scale, (float*)h->r32.p, S(h));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->x.p, 0, nk * 4, S(h));
     if (e != cudaSuccess) { rc = set_cuda_error(e, "sketch"); break; }
@@ -1867,11 +2209,12 @@ int wl_return_prob(wl_handle* h, int M, uint64_t seed, const double* ts, int nt,
     if ((rc = ensure(h->packX, nk * 8)) != WL_OK) break;  // Omega as the FP64 start block
     if ((rc = ensure(h->ybig, (size_t)kMaxTau * nk * 8)) != WL_OK) break;
     const int Gg = gram_grid(n);
-    if ((rc = ensure(h->gram, (size_t)Gg * 2 * kMaxSketch * kMaxSketch * 4 + 2 * kMaxSketch * kMaxSketch * 8 +
-                                 128 * 8)) != WL_OK) break;
+    const bool sketch = h->prm.prec == WL_SKETCH;  // FP32 Gram on the tensor cores; else FP64
+    const size_t pbytes = (size_t)Gg * 2 * kMaxSketch * kMaxSketch * (sketch ? 4 : 8);
+    if ((rc = ensure(h->gram, pbytes + 2 * kMaxSketch * kMaxSketch * 8 + 128 * 8)) != WL_OK) break;
     uint16_t* omega = (uint16_t*)h->omega.p;
     float* partial = (float*)h->gram.p;
-    double* gout = (double*)((char*)h->gram.p + (size_t)Gg * 2 * kMaxSketch * kMaxSketch * 4);
+    double* gout = (double*)((char*)h->gram.p + pbytes);
     double* core = gout + 2 * kMaxSketch * kMaxSketch;
     counted(h, 2);
     cudaError_t e = launch_philox_sketch(omega, n, M, seed, S(h));
@@ -1900,16 +2243,21 @@ int wl_return_prob(wl_handle* h, int M, uint64_t seed, const double* ts, int nt,
       for (int i = 0; i < nb; ++i) {
         // XNysTrace of exp(-t L) from Y(t) and Omega (Alg. 1, last step)
         counted(h, 3);
-        e = launch_to_f32(Y + (size_t)i * nk, (int64_t)nk, (float*)h->x.p, S(h));
-        if (e == cudaSuccess) e = cudaMemsetAsync(gerr, 0, sizeof(int), S(h));
-        if (e == cudaSuccess)
-          e = launch_gram(om_int, (const float*)h->x.p, n, M, K, partial, Gg, gout, h->gram_tc, gerr, S(h));
+        e = cudaMemsetAsync(gerr, 0, sizeof(int), S(h));
+        if (!sketch) {
+          if (e == cudaSuccess)
+            e = launch_gram_f64(om_int, Y + (size_t)i * nk, n, M, K, (double*)h->gram.p, Gg, gout, S(h));
+        } else {
+          if (e == cudaSuccess) e = launch_to_f32(Y + (size_t)i * nk, (int64_t)nk, (float*)h->x.p, S(h));
+          if (e == cudaSuccess)
+            e = launch_gram(om_int, (const float*)h->x.p, n, M, K, partial, Gg, gout, h->gram_tc, gerr, S(h));
+        }
         if (e == cudaSuccess) e = launch_nys_core(gout, M, core, S(h));
         if (e != cudaSuccess) { rc = set_cuda_error(e, "return probability gram/core"); break; }
         WL_CU(cudaMemcpyAsync(hp, core, 8 * 8, cudaMemcpyDeviceToHost, S(h)));
         WL_CU(cudaMemcpyAsync(hp + 8, gerr, sizeof(int), cudaMemcpyDeviceToHost, S(h)));
         WL_CU(cudaStreamSynchronize(S(h)));
-        if (h->gram_tc && *(int*)(hp + 8) != 0) { rc = *(int*)(hp + 8); break; }
+        if (sketch && h->gram_tc && *(int*)(hp + 8) != 0) { rc = *(int*)(hp + 8); break; }
         if (hp[2] != 0.0 && info.status == WL_OK) info.status = WL_ERR_NOT_SPD;
         p_est[t0 + i] = hp[0] / (double)n;
         p_err[t0 + i] = hp[1] / (double)n;

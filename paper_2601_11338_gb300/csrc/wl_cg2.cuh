@@ -32,10 +32,11 @@ constexpr int kPhaseBlock = 256;   // threads per CTA of the phase kernels
 #define WL_PHASE_MINB 5
 #endif
 constexpr int kPhaseMinBlocks = WL_PHASE_MINB;  // CTAs per SM the S kernel's registers are sized for
-// FP32 CG kernels: 6 CTAs per SM (40 registers) keep more gathers in flight;
-// measured 251 vs 265 us per K = 16 iteration on the Chung-Lu 1e6 graph
+// FP32 CG kernels: 5 CTAs per SM (48 registers) hold the eight predicated
+// gathers per lane; measured 236 us per K = 16 iteration on the Chung-Lu 1e6
+// graph (6 CTAs: 240 us; 4 CTAs: 248 us)
 #ifndef WL_PHASE_MINB_F32
-#define WL_PHASE_MINB_F32 6
+#define WL_PHASE_MINB_F32 5
 #endif
 constexpr int kPhaseMinBlocksF32 = WL_PHASE_MINB_F32;
 template <typename T>
@@ -76,6 +77,9 @@ struct PhaseArgs {
   CgState* st;
   int max_iter;
   double tol2;
+  // optional per-row diagonal added to M (the shifted solves of the
+  // shift-and-invert Lanczos: M - a (D_f + sigma I)^{-1}); NULL: none
+  const T* dshift = nullptr;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -84,10 +88,49 @@ __device__ __forceinline__ Pack<T, VW> ld_plain(const T* p) {
   return *reinterpret_cast<const Pack<T, VW>*>(p);
 }
 
-// Sum of X over entries [beg, end) with stride `step`, 4 gathers in flight.
+// Gathers per lane in flight in row_gather: predicated batches of 8 (1)
+// measured 240 vs 252 us per K = 16 FP32 CG iteration against the unrolled
+// loop with a serial tail (0), and 236 us with the FP32 kernels at 5 CTAs per
+// SM (48 registers)
+#ifndef WL_GATHER_PRED
+#define WL_GATHER_PRED 1
+#endif
+#ifndef WL_GATHER_U
+#define WL_GATHER_U 8
+#endif
+
+// Sum of X over entries [beg, end) with stride `step`.
+// WL_GATHER_PRED = 1: every batch of WL_GATHER_U entries, the last one too,
+// issues its index loads and then its gathers together (predicated on the
+// row end), so a short row costs one index latency and one gather latency
+// per batch instead of a dependent pair per entry of its tail. (0: batches of
+// four with the tail walked entry by entry.)
 template <typename T, int K, int VW>
 __device__ __forceinline__ void row_gather(const int32_t* __restrict__ col, int beg, int end, int step,
                                            const T* X, int lane_off, T (&acc)[VW]) {
+#if WL_GATHER_PRED
+  constexpr int U = WL_GATHER_U;
+  for (int e = beg; e < end; e += U * step) {
+    int j[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) j[u] = (e + u * step < end) ? __ldg(col + e + u * step) : -1;
+    Pack<T, VW> a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (j[u] >= 0) {
+        a[u] = ld_plain<T, VW>(X + (size_t)j[u] * K + lane_off);
+      } else {
+#pragma unroll
+        for (int v = 0; v < VW; ++v) a[u].v[v] = T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int v = 0; v < VW; ++v) acc[v] += a[u].v[v];
+  }
+  return;
+#endif
   int e = beg;
   for (; e + 3 * step < end; e += 4 * step) {
     const int j0 = __ldg(col + e), j1 = __ldg(col + e + step);
@@ -214,17 +257,20 @@ __global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks<T>()) cg_s_phase
     const Pack<T, VW>& rr = w.r;
     Pack<T, VW> pp, qq;
     const T dg = (T)deg;
+    const T dx = a.dshift ? a.dshift[row] : T(0);
     if (first) {
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
         pp.v[v] = rr.v[v];
         qq.v[v] = ca * rr.v[v] + cA * nb[v] + cD * dg * rr.v[v];
+        if (a.dshift) qq.v[v] += dx * rr.v[v];
       }
     } else {
       Pack<T, VW> xx = w.x;
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
-        const T s = ca * rr.v[v] + cA * nb[v] + cD * dg * rr.v[v];
+        T s = ca * rr.v[v] + cA * nb[v] + cD * dg * rr.v[v];
+        if (a.dshift) s += dx * rr.v[v];
         const T al = s_ab[0][lane_off + v], be = s_ab[1][lane_off + v];
         xx.v[v] += al * w.p.v[v];
         pp.v[v] = rr.v[v] + be * w.p.v[v];
@@ -415,7 +461,7 @@ __global__ void __launch_bounds__(kPhaseBlock) cg_f_phase(PhaseArgs<T> a) {
 struct ResPhaseArgs {
   PhaseGraph g;
   const double* x;
-  const double* b;
+  const double* b;  // NULL: b = 0 (then r = -M x)
   double* r;
   double ca, cA, cD;
   double* part;  // 2 * gridDim.x * K
@@ -437,7 +483,13 @@ __global__ void __launch_bounds__(kPhaseBlock, kPhaseMinBlocks) res_phase(ResPha
   auto fin = [&](int64_t row, int deg, const double (&nb)[VW]) {
     const size_t o = (size_t)row * K + lane_off;
     const Pack<double, VW> xx = ld_plain<double, VW>(a.x + o);
-    const Pack<double, VW> bb = ld_plain<double, VW>(a.b + o);
+    Pack<double, VW> bb;
+    if (a.b) {
+      bb = ld_plain<double, VW>(a.b + o);
+    } else {
+#pragma unroll
+      for (int v = 0; v < VW; ++v) bb.v[v] = 0.0;
+    }
     Pack<double, VW> rr;
 #pragma unroll
     for (int v = 0; v < VW; ++v) {

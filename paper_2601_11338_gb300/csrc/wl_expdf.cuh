@@ -21,7 +21,7 @@ struct DfLanczosArgs {
   const float* vml;
   const float* yh;    // Y = M^{-1} v_j
   const float* yl;
-  const float* dfh;   // D_f (n)
+  const float* dfh;   // D_f (n); NULL: zero (shift-and-invert: w = -a Y with Y = -R v_j)
   const float* dfl;
   df ascale;          // phi = a M^{-1}: w = D_f v_j - a Y
   float* wh;          // v_{j+1} out
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kBlock) df_lanczos_step(DfLanczosArgs a) {
   for (int v = 0; v < VW; ++v) S[v] = Cc[v] = 0.f;
   for (size_t e = (size_t)cta * kBlock + tid; e < nv; e += stride) {
     const size_t row = e * VW / K;
-    const df d{__ldg(a.dfh + row), __ldg(a.dfl + row)};
+    const df d = a.dfh ? df{__ldg(a.dfh + row), __ldg(a.dfl + row)} : df{0.f, 0.f};
     const Pack<float, VW> vh = ldp<float, VW>(a.vjh + e * VW), vl = ldp<float, VW>(a.vjl + e * VW);
     const Pack<float, VW> yh = ldp<float, VW>(a.yh + e * VW), yl = ldp<float, VW>(a.yl + e * VW);
     Pack<float, VW> wh, wl;

@@ -16,6 +16,7 @@
 #include "wl_res.cuh"
 #include "wl_exps.cuh"
 #include "wl_spec.cuh"
+#include "wl_reorth.cuh"
 
 namespace wl {
 
@@ -135,6 +136,20 @@ cudaError_t launch_row_list(const int32_t* row_ptr, int64_t n, int lo, int hi, i
 cudaError_t launch_list_entries(const int32_t* row_ptr, const int32_t* rows, int64_t count, unsigned long long* out,
                                 cudaStream_t s);
 
+// ---- wl_k_si.cu: shift-and-invert Lanczos (shifted solves with M - a (D_f + sigma)^{-1})
+cudaError_t launch_si_prep(const double* Df, int64_t n, double a, double sigma, double* dsh64, float* dsh_h,
+                           float* dsh_l, double* inv64, float* inv_h, float* inv_l, cudaStream_t s);
+cudaError_t launch_si_rhs64(const double* V, const double* inv, int64_t n, int K, double* B, cudaStream_t s);
+int si_rhs_blocks(int64_t n, int K);
+// (bh, bl) = (vh, vl) / (D_f + sigma) row-wise; |B|^2 per column -> bn2; part: si_rhs_blocks * K doubles
+cudaError_t launch_si_rhs_df(const float* vh, const float* vl, const float* inv_h, const float* inv_l, int64_t n,
+                             int K, float* bh, float* bl, double* part, double* bn2, cudaStream_t s);
+
+// ---- wl_k_reorth.cu: basis reorthogonalisation of the outer Lanczos
+int reorth_chunks(int nb, size_t blk);
+size_t reorth_part_doubles(int nb, int K, size_t blk);
+cudaError_t launch_reorth(ReorthArgs a, bool df, cudaStream_t s);
+
 // ---- wl_k_lanczos.cu
 int lanczos_step_grid(int K);
 cudaError_t launch_lanczos_step(int K, const LanczosStepArgs& a, int G, cudaStream_t s);
@@ -169,6 +184,9 @@ cudaError_t launch_gram(const uint16_t* omega, const float* Y, int64_t n, int M,
                         double* out, bool tensor_cores, int* err, cudaStream_t s);
 // out[0] estimate, out[1] error estimate, out[2] status, out[8 + i] = t_i
 cudaError_t launch_nys_core(const double* gram, int M, double* out, cudaStream_t s);
+// [Omega Y]^T Y from an FP64 Y (n x K, first M columns), FP64 throughout; partial: G x 2 x 64 x 64 doubles
+cudaError_t launch_gram_f64(const uint16_t* omega, const double* Y, int64_t n, int M, int K, double* partial, int G,
+                            double* out, cudaStream_t s);
 
 // cooperative launch helper (all CTAs co-resident; required by grid_sync)
 template <typename Args>

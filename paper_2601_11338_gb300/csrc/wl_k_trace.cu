@@ -77,6 +77,14 @@ cudaError_t launch_gram(const uint16_t* omega, const float* Y, int64_t n, int M,
   return cudaGetLastError();
 }
 
+cudaError_t launch_gram_f64(const uint16_t* omega, const double* Y, int64_t n, int M, int K, double* partial, int G,
+                            double* out, cudaStream_t s) {
+  const int64_t chunk = (n + G - 1) / G;
+  gram_f64<<<G, 256, 0, s>>>(omega, Y, n, M, K, chunk, partial);
+  gram_reduce_f64<<<(2 * kMaxSketch * kMaxSketch + 255) / 256, 256, 0, s>>>(partial, G, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_nys_core(const double* gram, int M, double* out, cudaStream_t s) {
   const int smem = 4 * kMaxSketch * kMaxSketch * (int)sizeof(double);
   static bool attr = false;

@@ -21,7 +21,7 @@ struct LanczosStepArgs {
   const double* vj;     // n x K
   const double* vjm1;   // n x K (ignored when first)
   const double* X;      // n x K: phi v_j from the inner solve (mode 0)
-  const double* Df;     // n walk degrees (mode 0)
+  const double* Df;     // n walk degrees (mode 0; NULL: zero)
   double c0, cA, cD;    // mode 1: w = Op v_j
   double* vjp1;         // n x K out
   double* Ta;           // K x ldT alphas
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) lanczos_step(LanczosStepAr
 #pragma unroll 2
     for (size_t e = v0 + tid; e < v1; e += kBlock) {
       const size_t row = e * VW / K;
-      const double d = __ldg(a.Df + row);
+      const double d = a.Df ? __ldg(a.Df + row) : 0.0;  // NULL: w = -X (shift-and-invert: X = -R v_j)
       const Pack<double, VW> vv = ldp<double, VW>(a.vj + e * VW);
       const Pack<double, VW> xx = ldp<double, VW>(a.X + e * VW);
       Pack<double, VW> ww;

@@ -119,34 +119,39 @@ int na_blocks() {
 
 using namespace wl;
 
-#define NA_CU(call)               \
-  do {                            \
-    if ((call) != cudaSuccess) {  \
-      (void)cudaGetLastError();   \
-      return WL_ERR_CUDA;         \
-    }                             \
+// Records the status in st (when given) and returns it: every exit of the
+// entry point goes through here, so st->status always matches the return code.
+static int na_done(wl_stats* st, int status) {
+  if (st) st->status = status;
+  return status;
+}
+
+#define NA_CU(call)                          \
+  do {                                       \
+    if ((call) != cudaSuccess) {             \
+      (void)cudaGetLastError();              \
+      return na_done(st, WL_ERR_CUDA);       \
+    }                                        \
   } while (0)
 
 extern "C" int wl_degrees_noalloc(const wl_csr* A, wl_variant v, double mu, double alpha, double tol, int max_iter,
                                   double* Df, void* stream, wl_stats* st) {
   if (st) memset(st, 0, sizeof(*st));
   if (!A || A->n < 0 || A->nnz < 0 || (A->n > 0 && (!A->row_ptr || !Df)) || (A->nnz > 0 && !A->col_idx))
-    return WL_ERR_INVALID_ARG;
-  if (A->n > kNaMaxN) {  // the fixed scratch array holds vectors of at most kNaMaxN nodes
-    if (st) st->status = WL_ERR_INVALID_ARG;
-    return WL_ERR_INVALID_ARG;
-  }
-  if (v != WL_ALLWALK && v != WL_NBT && v != WL_BTDW) return WL_ERR_INVALID_ARG;
+    return na_done(st, WL_ERR_INVALID_ARG);
+  if (A->n > kNaMaxN)  // the fixed scratch array holds vectors of at most kNaMaxN nodes
+    return na_done(st, WL_ERR_INVALID_ARG);
+  if (v != WL_ALLWALK && v != WL_NBT && v != WL_BTDW) return na_done(st, WL_ERR_INVALID_ARG);
   const double m = (v == WL_ALLWALK) ? 0.0 : (v == WL_NBT ? 1.0 : mu);
-  if (!(m >= 0.0 && m <= 1.0) || !(alpha >= 0.0) || !std::isfinite(alpha)) return WL_ERR_INVALID_ARG;
-  if (A->n == 0) return WL_OK;
+  if (!(m >= 0.0 && m <= 1.0) || !(alpha >= 0.0) || !std::isfinite(alpha)) return na_done(st, WL_ERR_INVALID_ARG);
+  if (A->n == 0) return na_done(st, WL_OK);
   if (tol <= 0) tol = 1e-12;
   if (max_iter <= 0) max_iter = 2000;
   cudaStream_t s = (cudaStream_t)stream;
 
   unsigned char* base = nullptr;
   int rc = scratch_address(&base);
-  if (rc != WL_OK) return rc;
+  if (rc != WL_OK) return na_done(st, rc);
   const int64_t n = A->n;
   double* r = (double*)base;
   double* p = r + kNaMaxN;
@@ -166,12 +171,12 @@ extern "C" int wl_degrees_noalloc(const wl_csr* A, wl_variant v, double mu, doub
   int hostv[2] = {0, 0};
   NA_CU(cudaMemcpyAsync(hostv, misc, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   NA_CU(cudaStreamSynchronize(s));
-  if (hostv[0] & 3) return WL_ERR_UNSORTED;
-  if (hostv[0] & 4) return WL_ERR_SELF_LOOP;
-  if (hostv[0] & 8) return WL_ERR_NOT_SYMMETRIC;
+  if (hostv[0] & 3) return na_done(st, WL_ERR_UNSORTED);
+  if (hostv[0] & 4) return na_done(st, WL_ERR_SELF_LOOP);
+  if (hostv[0] & 8) return na_done(st, WL_ERR_NOT_SYMMETRIC);
   const int nhub = hostv[1];
   const int grid_u = na_blocks(), grid_s = grid_u + nhub;
-  if (grid_s > kNaMaxGrid + kNaMaxN) return WL_ERR_INVALID_ARG;
+  if (grid_s > kNaMaxGrid + kNaMaxN) return na_done(st, WL_ERR_INVALID_ARG);
 
   // M x = a 1, M = a I - alpha A + alpha^2 mu D (FP64 CG from x = 0)
   const double a = 1.0 - m * m * alpha * alpha;
@@ -206,12 +211,11 @@ extern "C" int wl_degrees_noalloc(const wl_csr* A, wl_variant v, double mu, doub
   NA_CU(cudaStreamSynchronize(s));
   if (status == 0 && !done) status = WL_ERR_NO_CONVERGENCE;
   if (st) {
-    st->status = status;
     st->iters = iters;
     st->rel_res = b2 > 0 ? std::sqrt(gam / b2) : 0.0;
     st->alpha = alpha;
     st->mu = m;
     st->nnz_rhs_iters = (double)iters * (double)A->nnz;
   }
-  return status;
+  return na_done(st, status);
 }

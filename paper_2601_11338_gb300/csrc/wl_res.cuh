@@ -37,6 +37,10 @@ struct DfResArgs {
   double* part;     // gridDim.x * K partials
   CgState* st;      // st->gamma[c] = |r_out[:, c]|^2
   int x_zero;       // the iterate is zero on entry: x = d
+  // optional per-row diagonal added to M as a double-float pair (shifted
+  // solves); NULL: none. bh == NULL (FULL only): b = 0, r_out = -M x
+  const float* dsh_h = nullptr;
+  const float* dsh_l = nullptr;
 };
 
 // (s, c, l): neighbour sum of the leading terms with its rounding errors,
@@ -45,6 +49,38 @@ template <int K, int VW, bool FULL>
 __device__ __forceinline__ void df_row_gather(const int32_t* __restrict__ col, int beg, int end, int step,
                                               const float* YH, const float* YL, int lane_off, float (&s)[VW],
                                               float (&c)[VW], float (&l)[VW]) {
+#if WL_GATHER_PRED
+  constexpr int U = WL_GATHER_U;  // predicated batches, as in row_gather
+  for (int e = beg; e < end; e += U * step) {
+    int j[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) j[u] = (e + u * step < end) ? __ldg(col + e + u * step) : -1;
+    Pack<float, VW> hh[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (j[u] >= 0) {
+        hh[u] = ld_plain<float, VW>(YH + (size_t)j[u] * K + lane_off);
+      } else {
+#pragma unroll
+        for (int v = 0; v < VW; ++v) hh[u].v[v] = 0.f;
+      }
+    }
+    if constexpr (FULL) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (j[u] >= 0) {
+          const Pack<float, VW> l0 = ld_plain<float, VW>(YL + (size_t)j[u] * K + lane_off);
+#pragma unroll
+          for (int v = 0; v < VW; ++v) l[v] += l0.v[v];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int v = 0; v < VW; ++v) df_acc(s[v], c[v], hh[u].v[v]);
+  }
+  return;
+#endif
   int e = beg;
   for (; e + 3 * step < end; e += 4 * step) {
     const int j0 = __ldg(col + e), j1 = __ldg(col + e + step);
@@ -96,12 +132,19 @@ __global__ void __launch_bounds__(kPhaseBlock, 4) df_res(DfResArgs a) {
 
   auto fin = [&](int64_t row, int deg, const float (&s)[VW], const float (&c)[VW], const float (&l)[VW]) {
     const size_t o = (size_t)row * K + lane_off;
-    const df crow = df_add(a.ca, df_mul_f(a.cD, (float)deg));
+    df crow = df_add(a.ca, df_mul_f(a.cD, (float)deg));
+    if (a.dsh_h) crow = df_add(crow, df{a.dsh_h[row], a.dsh_l[row]});
     const Pack<float, VW> yh = ld_plain<float, VW>(a.yh + o);
     Pack<float, VW> yl;
     if constexpr (FULL) yl = ld_plain<float, VW>(a.yl + o);
-    const Pack<float, VW> bh = ld_plain<float, VW>(a.bh + o);
-    const Pack<float, VW> bl = ld_plain<float, VW>(a.bl + o);
+    Pack<float, VW> bh, bl;
+    if (a.bh) {
+      bh = ld_plain<float, VW>(a.bh + o);
+      bl = ld_plain<float, VW>(a.bl + o);
+    } else {
+#pragma unroll
+      for (int v = 0; v < VW; ++v) bh.v[v] = bl.v[v] = 0.f;
+    }
     Pack<float, VW> xh, xl;
     if constexpr (!FULL) {
       if (!a.x_zero) {

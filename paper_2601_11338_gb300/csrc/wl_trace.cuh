@@ -179,6 +179,65 @@ __global__ void gram_reduce(const float* partial, int G, double* out) {
   out[e] = s;
 }
 
+// ---------------------------------------------------------------- Gram in FP64 (CUDA cores)
+// The same block [Omega Y]^T Y from an FP64 Y (the FP64 and refined forms of
+// the estimators): FP64 products and sums throughout, partial per CTA in
+// the layout of gram_cc (doubles), summed by gram_reduce_f64.
+constexpr int kGramRows64 = 16;  // rows staged per tile
+
+__global__ void __launch_bounds__(256) gram_f64(const uint16_t* omega, const double* Y, int64_t n, int M, int K,
+                                                int64_t chunk, double* partial /* G x 2M x M */) {
+  __shared__ double sX[kGramRows64][2 * kMaxSketch];  // [Omega_i, Y_i]
+  const int tid = threadIdx.x;
+  const int rt = tid / 16, ct = tid % 16;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk;
+  const int64_t r1 = min(n, r0 + chunk);
+  double acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int64_t base = r0; base < r1; base += kGramRows64) {
+    const int rows = (int)min((int64_t)kGramRows64, r1 - base);
+    __syncthreads();
+    for (int e = tid; e < kGramRows64 * kMaxSketch; e += 256) {
+      const int i = e / kMaxSketch, j = e % kMaxSketch;
+      double om = 0.0, y = 0.0;
+      if (i < rows && j < M) {
+        om = (double)bf16_to_f32(omega[(base + i) * M + j]);
+        y = Y[(base + i) * K + j];
+      }
+      sX[i][j] = om;
+      sX[i][kMaxSketch + j] = y;
+    }
+    __syncthreads();
+    for (int i = 0; i < rows; ++i) {
+      double xv[8], yv[4];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) xv[a] = sX[i][rt + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) yv[b] = sX[i][kMaxSketch + ct + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(xv[a], yv[b], acc[a][b]);
+    }
+  }
+  double* out = partial + (size_t)blockIdx.x * (2 * kMaxSketch) * kMaxSketch;
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) out[(rt + 16 * a) * kMaxSketch + (ct + 16 * b)] = acc[a][b];
+}
+
+__global__ void gram_reduce_f64(const double* partial, int G, double* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * kMaxSketch * kMaxSketch) return;
+  double s = 0.0;
+  for (int g = 0; g < G; ++g) s += partial[(size_t)g * 2 * kMaxSketch * kMaxSketch + e];
+  out[e] = s;
+}
+
 // ---------------------------------------------------------------- FP64 leave-one-out core
 // gram: 128 x 64 doubles, rows 0..63 = Omega^T Y (H), rows 64..127 = Y^T Y (G).
 // out[0] = estimate, out[1] = error estimate, out[2] = status (0 ok, 1 not PD), out[8 + i] = t_i

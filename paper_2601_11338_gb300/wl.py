@@ -30,7 +30,7 @@ WL_ERR_UNSUPPORTED = -12
 
 WL_ALLWALK, WL_NBT, WL_BTDW = 0, 1, 2
 WL_F_RESOLVENT, WL_F_EXP, WL_F_IDENTITY = 0, 1, 2
-WL_FP64, WL_REFINED = 0, 1
+WL_FP64, WL_REFINED, WL_SKETCH = 0, 1, 2
 
 
 class wl_csr(ctypes.Structure):
@@ -42,7 +42,8 @@ class wl_params(ctypes.Structure):
     _fields_ = [("f", ctypes.c_int), ("alpha", ctypes.c_double), ("alpha_rel", ctypes.c_double),
                 ("beta", ctypes.c_double), ("mu", ctypes.c_double), ("prec", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
-                ("outer_tol", ctypes.c_double), ("stream", ctypes.c_void_p), ("reorder", ctypes.c_int)]
+                ("outer_tol", ctypes.c_double), ("stream", ctypes.c_void_p), ("reorder", ctypes.c_int),
+                ("reorth", ctypes.c_int), ("shift", ctypes.c_double)]
 
 
 class wl_stats(ctypes.Structure):
@@ -53,7 +54,7 @@ class wl_stats(ctypes.Structure):
                 ("rho", ctypes.c_double), ("lambda_max", ctypes.c_double), ("launches", ctypes.c_int),
                 ("k_cg_launches", ctypes.c_int), ("k_cg_iters", ctypes.c_int), ("k_cg_ms", ctypes.c_double),
                 ("k_cg_bytes", ctypes.c_double), ("k_res_launches", ctypes.c_int), ("k_res_ms", ctypes.c_double),
-                ("k_lan_launches", ctypes.c_int), ("k_lan_ms", ctypes.c_double)]
+                ("k_lan_launches", ctypes.c_int), ("k_lan_ms", ctypes.c_double), ("reorth_blocks", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -161,8 +162,9 @@ def _ptr(a):
 
 
 def make_params(f=WL_F_RESOLVENT, alpha=0.0, alpha_rel=0.0, beta=0.0, mu=0.0, prec=WL_FP64, tol=0.0,
-                max_iter=0, max_outer=0, outer_tol=0.0, stream=None, reorder=1):
-    return wl_params(f, alpha, alpha_rel, beta, mu, prec, tol, max_iter, max_outer, outer_tol, stream, reorder)
+                max_iter=0, max_outer=0, outer_tol=0.0, stream=None, reorder=1, reorth=0, shift=0.0):
+    return wl_params(f, alpha, alpha_rel, beta, mu, prec, tol, max_iter, max_outer, outer_tol, stream, reorder,
+                     reorth, shift)
 
 
 class Handle:

@@ -11,6 +11,7 @@ import pytest
 
 import wlgen
 from oracle import graph, spectral, walks
+from parity_metrics import relerr  # max of norm-wise and element-wise error per column
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -25,13 +26,6 @@ def dense(g):
 def WL(g, **kw):
     from paper_2601_11338_gb300.api import WalkLaplacian
     return WalkLaplacian(g.row_ptr[:].astype(np.int32), g.col_idx, g.n, f="exp", **kw)
-
-
-def relerr(got, want):
-    got, want = np.asarray(got), np.asarray(want)
-    if want.ndim == 1:
-        return np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-300)
-    return (np.linalg.norm(got - want, axis=0) / np.maximum(np.linalg.norm(want, axis=0), 1e-300)).max()
 
 
 @pytest.mark.parametrize("variant,mu", [("allwalk", 0.0), ("btdw", 0.5), ("nbt", 1.0)])

@@ -1,7 +1,7 @@
 """Discrete-time diffusion (Sec. 3.3, Eq. let_there_be_markov with D = the
 walk degrees): the CUDA chain through the C ABI against the CPU FP64 oracle.
 
-Tolerances as for the other single-graph paths: relative 2-norm per column,
+Tolerances as for the other single-graph paths: relative 2-norm and largest element-wise error (relative to the column's largest entry) per column,
 1e-10 for the FP64 form and 1e-8 for the refined form.
 """
 import numpy as np
@@ -9,6 +9,7 @@ import pytest
 
 import wlgen
 from oracle import graph, walks
+from parity_metrics import relerr  # max of norm-wise and element-wise error per column
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -24,10 +25,6 @@ def dense(g):
 def WL(g, **kw):
     from paper_2601_11338_gb300.api import WalkLaplacian
     return WalkLaplacian(g.row_ptr[:].astype(np.int32), g.col_idx, g.n, **kw)
-
-
-def relerr(got, want):
-    return (np.linalg.norm(got - want, axis=0) / np.maximum(np.linalg.norm(want, axis=0), 1e-300)).max()
 
 
 def point_masses(n, nodes):
