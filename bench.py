@@ -6,12 +6,14 @@ minimum degree 1), alpha = 0.5 / rho(Z_1), and the diffusion
 exp(-tau L) U0 for 16 point sources at tau in {0.1, 1, 10}: graph build
 (validation + spectral radius), walk degrees, then the Lanczos/CG diffusion,
 in the refined form (FP32 inner CG; residual, iterate and Lanczos basis in
-double-float, i.e. FP32 pairs). Inputs are
-resident on the GPU when the timed region starts.
+double-float, i.e. FP32 pairs), by the shift-and-invert Lanczos process on
+(L + sigma I)^{-1} (sigma = 1; --shift 0 selects the polynomial Lanczos
+process on L). Inputs are resident on the GPU when the timed region starts.
 
 Metric: nnz * RHS * iterations per second over all operator SpMM
 applications of the step, plus time-to-1e-8 relative error of
-exp(-tau L) U0 for the refined and the plain FP64 form.
+exp(-tau L) U0 for the refined and the plain FP64 form, each by the
+polynomial and by the shift-and-invert Lanczos process.
 
 Multi-GPU: replicas only - each rank runs its own 16 sources on its own
 copy of the graph (weak scaling, no collective on the data path).
@@ -44,7 +46,8 @@ K_SRC = 16
 METRIC = "nnz*RHS*iters/s (exp(-tau L)u0, NBT resolvent, refined form)"
 UNIT = "nnz*RHS*iters/s"
 TIME_TO_RULE = {"tol": 3e-10, "outer_tol": 1e-7}  # stopping rule shared by both forms (time-to-1e-8): the loosest measured rule under which the FP64 form reaches 1e-8
-SI_SHIFT = 1.0  # shift sigma of the shift-and-invert Lanczos legs of the time-to-1e-8 comparison
+SI_SHIFT = 2.0  # shift sigma of the shift-and-invert Lanczos (headline step and its time-to-1e-8 rows); measured
+# per step on the headline workload: sigma = 1: 128.8 ms, 2: 115.2 ms, 3: 129.7 ms (polynomial Lanczos: 231.6 ms)
 
 
 def log(*a):
@@ -282,6 +285,7 @@ def run_ours(args):
         wall_ms.append((time.perf_counter() - tw) * 1000.0)
         units += sd.nnz_rhs_iters + se.nnz_rhs_iters
         launches += sb.launches + sd.launches + se.launches
+        lanczos_steps = se.outer_iters
         phase_ms["build"] += sb.time_ms / args.steps
         phase_launches["build"] += sb.launches / args.steps
         phase_launches["degrees"] += sd.launches / args.steps
@@ -310,13 +314,14 @@ def run_ours(args):
         print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "steps": args.steps,
                           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "timed_only": True,
                           "phase_ms_per_step": phase_ms, "host_wall_ms_per_step": wall_ms, "phase_launches_per_step": phase_launches,
-                          "gpu_launches": launches}), flush=True)
+                          "gpu_launches": launches, "shift": args.shift, "lanczos_steps": lanczos_steps,
+                          "cg_iters_per_step": kcg_iters / args.steps}), flush=True)
         return
     # ---- time to 1e-8: reference u* (FP64, tight), then both forms under one rule
     Ustar = torch.empty_like(U)
     step(prec=wl.WL_FP64, tol=1e-13, outer_tol=1e-12, out=Ustar)
     tt = {}
-    si_shift = args.shift or SI_SHIFT
+    si_shift = args.shift if args.shift > 0 else SI_SHIFT
     for name, prec, shift in (("refined", wl.WL_REFINED, 0.0), ("fp64", wl.WL_FP64, 0.0),
                               ("refined_si", wl.WL_REFINED, si_shift), ("fp64_si", wl.WL_FP64, si_shift)):
         Ux = torch.empty_like(U)
@@ -379,7 +384,7 @@ def run_ours(args):
     if not args.no_legs:
         legs = {}
         for name, fn in (("batch64", lambda: leg_batch(args)), ("trace_rmat22", lambda: leg_trace(args)),
-                         ("warmstart_rmat24", lambda: leg_warmstart(args))):
+                         ("warmstart_rmat24", lambda: leg_warmstart(args)), ("next_rows", lambda: leg_next(args))):
             t0 = time.perf_counter()
             try:
                 legs[name] = fn()
@@ -515,7 +520,11 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ NEXT rows
-def run_next(args):
+RP_SHIFT = 0.0  # return-probability row: the polynomial Lanczos (a single repeated shift of 1 or 3 did not
+# converge within 250 steps over t in [1.1, 100] on the grid; the polynomial run converges in 100)
+
+
+def leg_next(args, shift=None):
     """The rows built after the headline path, each timed on GB300 (CUDA events
     of the library's own calls, after a warm-up call):
       * exponential NBT walk Laplacian (beta = 1/lambda_max(A), q_k series in
@@ -524,14 +533,16 @@ def run_next(args):
         the 16 point sources, distributions after 1, 2, 4 and 8 steps;
       * average return probability tr(exp(-t L))/n by XNysTrace on a 1000 x 1000
         grid (stand-in for the paper's road networks), NBT resolvent with the
-        paper's alpha = 1/(1 + rho(Z_1)), M = 32, 90 time points in [0, 100]."""
+        paper's alpha = 1/(1 + rho(Z_1)), M = 30, 90 time points in [0, 100]
+        (the paper's XNysTrace-exp settings), by the polynomial Lanczos (with
+        shift > 0 also by the shift-and-invert one, for comparison)."""
     import torch
 
     import wlgen
     from paper_2601_11338_gb300.api import WalkLaplacian
 
-    torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
+    shift = RP_SHIFT if shift is None else shift
     g, nodes = make_workload(0)
     rp, ci = g.row_ptr.astype(np.int32), g.col_idx
     out = {}
@@ -543,10 +554,10 @@ def run_next(args):
     for rep in range(2):  # the first pass warms up; wl_degrees sums its series on every call
         Df = w.degrees()
         sd = w.last
-        d_ms, d_units = sd.time_ms, sd.nnz_rhs_iters
+        d_ms, d_units, d_terms = sd.time_ms, sd.nnz_rhs_iters, sd.iters
         w.apply(V)
         sa = w.last
-    out["exp_nbt"] = {"beta": w.info["beta"], "degrees_ms": d_ms, "degrees_terms": sd.iters,
+    out["exp_nbt"] = {"beta": w.info["beta"], "degrees_ms": d_ms, "degrees_terms": d_terms,
                       "apply16_ms": sa.time_ms, "apply16_terms": sa.iters,
                       "value": (d_units + sa.nnz_rhs_iters) / ((d_ms + sa.time_ms) / 1000.0),
                       "unit": UNIT, "Df_max": float(Df.max())}
@@ -568,25 +579,35 @@ def run_next(args):
                       prec="refined", tol=1e-8, outer_tol=1e-8)
     a_paper = 1.0 / (1.0 + w.info["rho"])
     w.close()
-    w = WalkLaplacian(gg.row_ptr.astype(np.int32), gg.col_idx, gg.n, variant="nbt", alpha=a_paper,
-                      prec="refined", tol=1e-8, outer_tol=1e-8)
     ts = np.linspace(0.0, 100.0, 90)
-    for rep in range(2):
-        p, e = w.return_prob(32, 1234 + rep, ts)
-    sr = w.last
-    out["return_prob_nbt_grid"] = {"n": gg.n, "nnz": gg.nnz, "alpha": a_paper, "M": 32, "times": len(ts),
-                                   "t_max": float(ts[-1]), "ms": sr.time_ms, "lanczos_steps": sr.outer_iters,
-                                   "value": sr.nnz_rhs_iters / (sr.time_ms / 1000.0), "unit": UNIT,
-                                   "p": {f"{t:g}": [float(p[i]), float(e[i])] for i, t in enumerate(ts)
-                                         if i in (1, 9, 45, 89)}}
-    w.close()
+    rows = {}
+    runs = (("polynomial", 0.0),) if not shift else (("shift_invert", shift), ("polynomial", 0.0))
+    for name, sh in runs:
+        # the polynomial basis of 32 columns on 1e6 nodes takes 256 MB per step: capped at 200 steps
+        w = WalkLaplacian(gg.row_ptr.astype(np.int32), gg.col_idx, gg.n, variant="nbt", alpha=a_paper,
+                          prec="refined", tol=1e-8, outer_tol=1e-8, shift=sh, max_outer=250 if sh else 200)
+        for rep in range(2):
+            p, e = w.return_prob(30, 1234 + rep, ts, allow=(-8,))
+        sr = w.last
+        rows[name] = {"shift": sh, "ms": sr.time_ms, "lanczos_steps": sr.outer_iters, "status": sr.status,
+                      "cg_iters": sr.k_cg_iters, "value": sr.nnz_rhs_iters / (sr.time_ms / 1000.0), "unit": UNIT,
+                      "p": {f"{t:g}": [float(p[i]), float(e[i])] for i, t in enumerate(ts) if i in (1, 9, 45, 89)}}
+        w.close()
+    out["return_prob_nbt_grid"] = {"n": gg.n, "nnz": gg.nnz, "alpha": a_paper, "M": 30, "times": len(ts),
+                                   "t_max": float(ts[-1]), **rows}
     clk = clocks.stop()
-    line = {"metric": "NEXT rows on GB300 (exponential walk function, chain, return probability)",
-            "value": out["exp_nbt"]["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-            "data": "synthetic",
+    return {"metric": "NEXT rows on GB300 (exponential walk function, chain, return probability)",
+            "value": out["exp_nbt"]["value"], "unit": UNIT,
             "config": {"workload": "next_rows_chunglu1e6_grid1000", "n": g.n, "nnz": g.nnz, "rhs": K_SRC},
             "rows": out, "clocks": clk}
+
+
+def run_next(args):
+    import torch
+    torch.cuda.set_device(0)
+    leg = leg_next(args)
+    line = {"n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic", **leg}
     print(json.dumps(line), flush=True)
 
 
@@ -973,6 +994,8 @@ def run_profile(args):
       apply : walk degrees, then L V twice for K Gaussian columns on the
               Chung-Lu graph (NBT resolvent, alpha = 0.5 / rho(Z_1));
               --n, --k, --prec-name, --reorder
+      si    : four shift-and-invert Lanczos steps of the headline diffusion
+              (16 point sources, refined form), twice
       batch : 16 graphs x 5 mu, k = 32, refined form, two graph launches
       trace : XNysTrace on R-MAT scale 18, M = 64
       mlp   : warm-start features and 20 training steps on 2e5 rows"""
@@ -998,6 +1021,21 @@ def run_profile(args):
                     "cg_us_per_iteration": 1000.0 * s.k_cg_ms / max(s.k_cg_iters, 1), "cg_iterations": s.k_cg_iters,
                     "residual_ms_per_launch": s.k_res_ms / max(s.k_res_launches, 1),
                     "residual_launches": s.k_res_launches, "apply_ms": s.time_ms})
+        w.close()
+    elif args.profile == "si":
+        # four shift-and-invert Lanczos steps of the headline diffusion (the shifted CG kernels)
+        g, nodes = make_workload(0)
+        w = WalkLaplacian(g.row_ptr.astype(np.int32), g.col_idx, g.n, variant="nbt", alpha_rel=0.5, prec="refined",
+                          tol=TIME_TO_RULE["tol"], outer_tol=TIME_TO_RULE["outer_tol"], shift=SI_SHIFT, max_outer=4)
+        w.degrees()
+        U0 = torch.as_tensor(wlgen.unit_block(g.n, nodes), device="cuda")
+        for _ in range(2):
+            w.expmv(U0, TAUS, allow=(-8,))
+        torch.cuda.synchronize()
+        s = w.last
+        out.update({"n": g.n, "nnz": g.nnz, "shift": SI_SHIFT, "lanczos_steps": s.outer_iters,
+                    "cg_us_per_iteration": 1000.0 * s.k_cg_ms / max(s.k_cg_iters, 1), "cg_iterations": s.k_cg_iters,
+                    "residual_ms_per_launch": s.k_res_ms / max(s.k_res_launches, 1), "expmv_ms": s.time_ms})
         w.close()
     elif args.profile == "batch":
         gs = wlgen.batch_graphs(16, 1e3, 1e5, seed=SEED_BATCH)
@@ -1053,15 +1091,16 @@ def main():
     ap.add_argument("--alpha-rule", default="half", choices=sorted(ALPHA_RULES),
                     help="chung_lu_1e6 / trace_rmat: alpha = 0.5/rho (default) or the paper's 1/(1+rho)")
     ap.add_argument("--no-loop", action="store_true", help="batch64: skip the per-problem FP64 loop baseline")
-    ap.add_argument("--shift", type=float, default=0.0,
-                    help="chung_lu_1e6: shift of the shift-and-invert Lanczos for the timed steps (0: polynomial); "
-                         "the time-to-1e-8 legs use it (or the default shift) for their shift-and-invert rows")
+    ap.add_argument("--shift", type=float, default=SI_SHIFT,
+                    help="chung_lu_1e6: shift sigma of the shift-and-invert Lanczos of the timed steps (0: the "
+                         "polynomial Lanczos); the time-to-1e-8 rows use it (or the default) for their "
+                         "shift-and-invert rows")
     ap.add_argument("--no-legs", action="store_true",
                     help="chung_lu_1e6: skip the batched, trace and warm-start legs added to the headline line")
     ap.add_argument("--scale", type=int, default=0, help="trace_rmat / warmstart_rmat: R-MAT scale (22 / 24)")
     ap.add_argument("--timed-only", action="store_true",
                     help="profiling aid: run the warm-up and timed steps only (no time-to-1e-8, e2e or CPU legs)")
-    ap.add_argument("--profile", default="", choices=["", "apply", "batch", "trace", "mlp"],
+    ap.add_argument("--profile", default="", choices=["", "apply", "si", "batch", "trace", "mlp"],
                     help="profiling drivers: small runs of one workload's kernels (see run_profile)")
     ap.add_argument("--n", type=int, default=N_NODES, help="--profile apply: nodes of the Chung-Lu graph")
     ap.add_argument("--k", type=int, default=K_SRC, help="--profile apply: columns")

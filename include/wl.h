@@ -323,6 +323,16 @@ int wl_sketch_gram(const uint16_t* omega, const float* Y, int64_t n, int M, int 
  * W1[64][4], b1[64], W2[64][64], b2[64], W3[64], b3. */
 int wl_mlp_param_count(void);
 
+/* Checkpoint of the network (host arrays of wl_mlp_param_count() floats):
+ * a 32-byte header (magic "WLMLP001", inputs, hidden width, outputs,
+ * parameter count, FNV-1a hash of the parameter bytes) and the parameters as
+ * little-endian FP32. wl_mlp_load rejects a file of another shape, length or
+ * magic (WL_ERR_INVALID_ARG) and one whose hash does not match its
+ * parameters (WL_ERR_NONFINITE); params is left untouched then. The paper has
+ * no counterpart (its method has no learned part). */
+int wl_mlp_save(const char* path, const float* params);
+int wl_mlp_load(const char* path, float* params);
+
 /* Features (n x 4 FP32, row-major) and x_an (n FP64) of the handle's graph
  * and parameters (f = WL_F_RESOLVENT), in the caller's node order; either
  * output may be NULL; host or device pointers. Synchronous. */

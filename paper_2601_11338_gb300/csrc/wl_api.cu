@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <string>
 #include <tuple>
@@ -68,9 +69,36 @@ void retire(void* p) {
     pool_free(p);
 }
 
+// ------------------------------------------------------------------ host-side fault injection
+// The environment variable WL_FAULT (read at each use) makes one kind of
+// failure happen on the host, for tests of the error paths:
+//   alloc    every device allocation of a buffer fails (WL_ERR_OOM)
+//   nan      every CG solve starts from a residual with a NaN entry
+//            (WL_ERR_NONFINITE)
+//   timeout  every grid barrier starts in the gave-up state, so the
+//            cooperative kernels leave at their first barrier (WL_ERR_TIMEOUT)
+//   noconv   every CG solve is capped at one iteration (WL_ERR_NO_CONVERGENCE)
+// Nothing here faults, traps or hangs the GPU; each failure goes through the
+// library's normal status paths.
+enum FaultMode { kFaultNone = 0, kFaultAlloc, kFaultNan, kFaultTimeout, kFaultNoconv };
+
+int fault_mode() {
+  const char* s = getenv("WL_FAULT");
+  if (!s || !*s) return kFaultNone;
+  if (!strcmp(s, "alloc")) return kFaultAlloc;
+  if (!strcmp(s, "nan")) return kFaultNan;
+  if (!strcmp(s, "timeout")) return kFaultTimeout;
+  if (!strcmp(s, "noconv")) return kFaultNoconv;
+  return kFaultNone;
+}
+
 int ensure(Buf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return WL_OK;
+  if (fault_mode() == kFaultAlloc) {
+    g_last_error = "WL_FAULT=alloc: device allocation refused";
+    return WL_ERR_OOM;
+  }
   retire(b.p);
   b.p = nullptr;
   b.bytes = 0;
@@ -183,6 +211,7 @@ struct wl_handle {
   double sp_c0 = 0.0, sp_cD = 0.0, sp_theta = 0.0;  // operator and Ritz value of the basis held in spV
   bool sp_ritz_ready = false;                        // W[1] holds that run's Ritz vector
   double inner_tol = 4e-6;  // floor of the FP32 correction target of the refined form
+  int cg_hint = 7;          // CG iterations of the handle's last solve (sizes the first launch chunk)
   bool gram_tc = true;      // XNysTrace Gram on the tensor cores (tcgen05); false: CUDA cores
   CgState* cgst() { return (CgState*)cgstate.p; }
   double* h_pin = nullptr;  // pinned host scratch (4096 doubles)
@@ -264,6 +293,10 @@ int get_part(wl_handle* h, int G, int Tw, int Tc, PartDev** out, int K = 16, int
 
 int reset_bar(wl_handle* h) {
   WL_CU(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), S(h)));
+  if (fault_mode() == kFaultTimeout) {
+    static const int gave_up = WL_ERR_TIMEOUT;
+    WL_CU(cudaMemcpyAsync(&h->bar->err, &gave_up, sizeof(int), cudaMemcpyHostToDevice, S(h)));
+  }
   return WL_OK;
 }
 
@@ -321,12 +354,20 @@ PhaseGraph phase_graph_mid(wl_handle* h, int grid_u) {
   return g;
 }
 
-constexpr int kChunk = 8;  // CG iterations launched between two reads of the device flag
+constexpr int kChunk = 8;      // CG iterations launched between two reads of the device flag (cap: 2 kChunk)
+constexpr int kChunkMore = 4;  // iterations of every chunk after the first
 
 // Runs the CG iterations of an initialised solve state to completion (or the
 // iteration cap), reading back one flag per chunk, then the final x update.
 template <typename T>
-int run_cg(wl_handle* h, int K, const PhaseArgs<T>& a, int grid_s, int grid_u, SolveInfo& info, int cat_bytes) {
+int run_cg(wl_handle* h, int K, const PhaseArgs<T>& a_in, int grid_s, int grid_u, SolveInfo& info, int cat_bytes) {
+  PhaseArgs<T> a = a_in;
+  const int fault = fault_mode();
+  if (fault == kFaultNoconv) a.max_iter = 1;
+  if (fault == kFaultNan) {
+    static const T nan_v = (T)NAN;
+    WL_CU(cudaMemcpyAsync(a.r, &nan_v, sizeof(T), cudaMemcpyHostToDevice, S(h)));
+  }
   auto launch = [&](int mode, int chunk) -> cudaError_t {
     if constexpr (sizeof(T) == 4)
       return launch_cg_phases_f32(K, a, grid_s, grid_u, mode, chunk, S(h));
@@ -337,12 +378,17 @@ int run_cg(wl_handle* h, int K, const PhaseArgs<T>& a, int grid_s, int grid_u, S
   counted(h, 1);
   WL_CU(launch(0, 0));
   int* hp = (int*)h->h_pin;
+  // first chunk: one more iteration than the handle's previous solve took (a
+  // launch that finds the solve finished returns at once, but still costs a
+  // grid); later chunks of kChunkMore iterations
+  int chunk = std::min(std::max(h->cg_hint + 1, 2), 2 * kChunk);
   for (;;) {
-    counted(h, 2 * kChunk);
-    WL_CU(launch(1, kChunk));
+    counted(h, 2 * chunk);
+    WL_CU(launch(1, chunk));
     WL_CU(cudaMemcpyAsync(hp, &h->cgst()->active, 2 * sizeof(int), cudaMemcpyDeviceToHost, S(h)));
     WL_CU(cudaStreamSynchronize(S(h)));
     if (!hp[0]) break;
+    chunk = kChunkMore;
   }
   counted(h, 1);
   WL_CU(launch(2, 0));
@@ -357,6 +403,7 @@ int run_cg(wl_handle* h, int K, const PhaseArgs<T>& a, int grid_s, int grid_u, S
   WL_CU(cudaMemcpyAsync(hd + 192, st->done, 64 * 4, cudaMemcpyDeviceToHost, S(h)));
   WL_CU(cudaStreamSynchronize(S(h)));
   const int it = *(const int*)(hd + 160);
+  h->cg_hint = it;
   int* cs = (int*)(hd + 128);
   const int* dn = (const int*)(hd + 192);
   for (int c = 0; c < K; ++c)  // iteration cap reached with this column still iterating
@@ -773,13 +820,20 @@ int lambda_max_adaptive(wl_handle* h, double rtol, double* lmax) {
 // root of lambda^2 - lambda u^T A u + mu u^T (D - mu I) u = 0 nearest the
 // current one, quadratically convergent), kept inside the bracket of signs
 // seen so far; outside it, regula falsi (Illinois) or halving.
+// Relative accuracy of the spectral searches of wl_build on the calling
+// thread: 0 keeps the defaults (lambda_max(A) to a bound of 1e-12, rho(Z_mu)
+// to 1e-11 / a bracket of 1e-12); the batched build sets a looser value for
+// its many small graphs, whose alpha = alpha_rel / rho needs no more.
+thread_local double t_spec_rtol = 0.0;
+
 int rho_companion(wl_handle* h, double mu, double lmaxA, double* rho) {
   NvtxRange nvtx__("rho(Z_mu)");
   if (mu == 0.0 || lmaxA <= 0.0) {
     *rho = lmaxA;
     return WL_OK;
   }
-  constexpr double kTight = 1e-11;
+  const double kTight = t_spec_rtol > 0.0 ? t_spec_rtol : 1e-11;
+  const double kBracket = t_spec_rtol > 0.0 ? t_spec_rtol : 1e-12;
   double q = 0.0, uAu = 0.0;
   WL_TRY(sp_ritz_q(h, &q, &uAu));
   auto rf = [&](double near) {
@@ -814,12 +868,20 @@ int rho_companion(wl_handle* h, double mu, double lmaxA, double* rho) {
   double lam = rf(lmaxA);
   if (!(lam > 0.0 && lam < hi)) lam = 0.5 * hi;
   int side = 0;
+  // the evaluation with the largest h: a double root (h touches zero from
+  // below, as for mu = 1 on a cycle, where rho(Z_1) = 1 = d - mu = mu) shows
+  // no sign change, and is taken where h came closest to zero
+  double best_l = 0.0, best_h = -HUGE_VAL;
   for (int it = 0; it < 60; ++it) {
     double fx;
     WL_TRY(hfun(lam, &fx));
     if (!certain) {  // |h| is below what the Lanczos run resolves: lam is the root
       *rho = lam;
       return WL_OK;
+    }
+    if (fx > best_h) {
+      best_h = fx;
+      best_l = lam;
     }
     if (fx > 0) {
       lo = lam;
@@ -834,9 +896,9 @@ int rho_companion(wl_handle* h, double mu, double lmaxA, double* rho) {
       if (side == -1 && have_lo) flo *= 0.5;
       side = -1;
     }
-    if (hi - lo <= 1e-12 * hi) break;
-    if (!have_lo && hi < 1e-12 * lmaxA) {  // no positive side found: rho is 0
-      *rho = 0.0;
+    if (hi - lo <= kBracket * hi) break;
+    if (!have_lo && hi < 1e-12 * lmaxA) {  // no positive side found: a double root, or rho is 0
+      *rho = (best_h > -1e-6 * lmaxA) ? best_l : 0.0;
       return WL_OK;
     }
     double nxt = rf(lam);
@@ -852,7 +914,7 @@ int rho_companion(wl_handle* h, double mu, double lmaxA, double* rho) {
     }
     lam = nxt;
   }
-  *rho = have_lo ? 0.5 * (lo + hi) : lam;
+  *rho = have_lo ? 0.5 * (lo + hi) : ((best_h > -1e-6 * lmaxA) ? best_l : lam);
   return WL_OK;
 }
 
@@ -1056,7 +1118,9 @@ struct SiScope {
 
 // One application of R = (L + sigma I)^{-1} to the basis block j, leaving
 // -R v_j where the Lanczos step kernels read it: the double-float form in
-// (h->rh, h->rl), the FP64 form in h->packX.
+// (h->rh, h->rl), the FP64 form in h->packX. x = R v_j = M z with z the
+// solution of (M - a Dt^{-1}) z = Dt^{-1} v_j, and M z follows without a
+// product with M from the solve's final residual r: M z = (B - r) + a Dt^{-1} z.
 int si_apply(wl_handle* h, bool dfp, int K, int j, size_t blk, SolveInfo& info) {
   const int64_t n = h->n;
   double* d64 = (double*)h->sibuf.p;
@@ -1076,16 +1140,11 @@ int si_apply(wl_handle* h, bool dfp, int K, int j, size_t blk, SolveInfo& info) 
                               (float*)h->xl.p, nullptr, K, h->prm.tol, info));
     }
     if (info.status != WL_OK) return WL_OK;
-    // (rh, rl) = 0 - M z
-    const int grid_r = df_res_blocks(K) + h->nhub;
-    const df ca = df_from_double(h->ca), cA = df_from_double(h->cA), cD = df_from_double(h->cD);
-    DfResArgs ra{phase_graph_mid(h, grid_r - h->nhub), (const float*)h->xh.p, (const float*)h->xl.p, nullptr, nullptr,
-                 (float*)h->rh.p, (float*)h->rl.p, nullptr, nullptr, nullptr, nullptr, ca, cA, cD,
-                 (double*)h->part.p, h->cgst(), 0};
-    const int pi = prof_begin(h, kCatRes);
+    // (rh, rl) = -M z = -((B - r) + a Dt^{-1} z), r the solve's final residual in (rh, rl)
     counted(h);
-    WL_CU(launch_df_res(K, ra, grid_r, true, S(h)));
-    prof_end(h, pi);
+    WL_CU(launch_si_mz_df((const float*)h->bh.p, (const float*)h->bl.p, (const float*)h->rh.p,
+                          (const float*)h->rl.p, (const float*)h->xh.p, (const float*)h->xl.p, f32 + 2 * n,
+                          f32 + 3 * n, h->a_scale, n, K, (float*)h->rh.p, (float*)h->rl.p, S(h)));
   } else {
     const double* vj = (const double*)h->basis.p + (size_t)j * blk;
     WL_TRY(ensure(h->b64, blk * 8));
@@ -1098,17 +1157,11 @@ int si_apply(wl_handle* h, bool dfp, int K, int j, size_t blk, SolveInfo& info) 
       WL_TRY(solve_fp64(h, (const double*)h->b64.p, (double*)h->x.p, K, h->prm.tol, true, info));
     }
     if (info.status != WL_OK) return WL_OK;
-    // packX = 0 - M z
-    const int gr = res_blocks(K) + h->nhub;
-    ResPhaseArgs ra{phase_graph(h), (const double*)h->x.p, nullptr, (double*)h->packX.p, h->ca, h->cA, h->cD,
-                    (double*)h->part.p, h->cgst()};
-    const int pi = prof_begin(h, kCatRes);
+    // packX = -M z = -((B - r) + a Dt^{-1} z), r the CG's final residual in h->r
     counted(h);
-    WL_CU(launch_res_phases(K, ra, gr, S(h)));
-    prof_end(h, pi);
+    WL_CU(launch_si_mz64((const double*)h->b64.p, (const double*)h->r.p, (const double*)h->x.p, d64 + n,
+                         h->a_scale, n, K, (double*)h->packX.p, S(h)));
   }
-  info.nnz_rhs += (double)h->nnz * K;
-  info.iters += 1;
   return WL_OK;
 }
 
@@ -1686,7 +1739,7 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
   h->lmax = 0.0;
   h->rho = 0.0;
   if (h->n > 0 && h->nnz > 0) {
-    if ((rc = lambda_max_adaptive(h, 1e-12, &h->lmax)) != WL_OK) return fail(rc);
+    if ((rc = lambda_max_adaptive(h, t_spec_rtol > 0.0 ? t_spec_rtol : 1e-12, &h->lmax)) != WL_OK) return fail(rc);
     if (p->f == WL_F_RESOLVENT) {
       if ((rc = rho_companion(h, mu, h->lmax, &h->rho)) != WL_OK) return fail(rc);
     } else {
@@ -2308,7 +2361,13 @@ std::string last_error_copy() { return g_last_error; }
 // Spectral scale of one graph for several mu values (Sec. 4.1): validates
 // the CSR as wl_build does, then lambda_max(A) and rho(Z_mu) for each mu
 // (rho(Z_0) = lambda_max(A)).
-int graph_spectral(const wl_csr* A, const double* mus, int nmu, void* stream, double* lmax, double* rho) {
+int graph_spectral(const wl_csr* A, const double* mus, int nmu, void* stream, double* lmax, double* rho,
+                   double rtol) {
+  struct RtolScope {
+    double old;
+    explicit RtolScope(double r) : old(t_spec_rtol) { t_spec_rtol = r; }
+    ~RtolScope() { t_spec_rtol = old; }
+  } rs(rtol);
   wl_params p;
   memset(&p, 0, sizeof(p));
   p.f = WL_F_IDENTITY;

@@ -38,6 +38,11 @@ using namespace wl;
 
 namespace {
 
+// spectral scales of the batch: lambda_max(A) and rho(Z_mu) to 1e-10
+// relative (alpha = alpha_rel / rho needs no more), searches on 16 threads
+constexpr double kSpecRtol = 1e-10;
+constexpr int kSpecThreads = 16;
+
 constexpr int kLoopHardCap = 1 << 20;  // body executions of one while node, whatever the flags say
 
 struct DBuf {
@@ -584,7 +589,9 @@ int wl_batch_build(const wl_csr* graphs, int ngraph, const double* mus, int nmu,
     std::string msg;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int nth = std::min(ngraph, 8);
+    // host threads each with its own stream: the searches on graphs of 1e3 - 2e5
+    // nodes are chains of small latency-bound launches, so more of them overlap
+    const int nth = std::min(ngraph, kSpecThreads);
     std::vector<std::thread> th;
     for (int t = 0; t < nth; ++t)
       th.emplace_back([&]() {
@@ -597,7 +604,7 @@ int wl_batch_build(const wl_csr* graphs, int ngraph, const double* mus, int nmu,
         std::vector<double> r(nmu);
         for (int g; (g = next++) < ngraph && err == WL_OK;) {
           double lm = 0.0;
-          const int rc = graph_spectral(&graphs[g], mus, nmu, s, &lm, r.data());
+          const int rc = graph_spectral(&graphs[g], mus, nmu, s, &lm, r.data(), kSpecRtol);
           if (rc != WL_OK) {
             std::lock_guard<std::mutex> lk(mtx);
             if (err == WL_OK) {

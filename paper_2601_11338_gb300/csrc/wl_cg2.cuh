@@ -98,6 +98,10 @@ __device__ __forceinline__ Pack<T, VW> ld_plain(const T* p) {
 #ifndef WL_GATHER_U
 #define WL_GATHER_U 8
 #endif
+// the same choice for the FP64 kernels (the plain FP64 form), measured on its own
+#ifndef WL_GATHER_PRED_F64
+#define WL_GATHER_PRED_F64 0
+#endif
 
 // Sum of X over entries [beg, end) with stride `step`.
 // WL_GATHER_PRED = 1: every batch of WL_GATHER_U entries, the last one too,
@@ -108,7 +112,7 @@ __device__ __forceinline__ Pack<T, VW> ld_plain(const T* p) {
 template <typename T, int K, int VW>
 __device__ __forceinline__ void row_gather(const int32_t* __restrict__ col, int beg, int end, int step,
                                            const T* X, int lane_off, T (&acc)[VW]) {
-#if WL_GATHER_PRED
+  if constexpr (sizeof(T) == 4 ? WL_GATHER_PRED : WL_GATHER_PRED_F64) {
   constexpr int U = WL_GATHER_U;
   for (int e = beg; e < end; e += U * step) {
     int j[U];
@@ -130,7 +134,7 @@ __device__ __forceinline__ void row_gather(const int32_t* __restrict__ col, int 
       for (int v = 0; v < VW; ++v) acc[v] += a[u].v[v];
   }
   return;
-#endif
+  }
   int e = beg;
   for (; e + 3 * step < end; e += 4 * step) {
     const int j0 = __ldg(col + e), j1 = __ldg(col + e + step);
@@ -210,7 +214,9 @@ __device__ __forceinline__ void sum_partials(const double* part, int nblk, doubl
 }
 
 // ---------------------------------------------------------------- S phase
-template <typename T, int K>
+// SH: the solve carries the per-row diagonal a.dshift (a separate instance,
+// so that the unshifted kernel carries no trace of it)
+template <typename T, int K, bool SH = false>
 __global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks<T>()) cg_s_phase(PhaseArgs<T> a) {
   using C = Cfg<T, K>;
   constexpr int VW = C::VW, G = C::G, RPB = kPhaseBlock / G;  // rows per CTA pass
@@ -257,20 +263,21 @@ __global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks<T>()) cg_s_phase
     const Pack<T, VW>& rr = w.r;
     Pack<T, VW> pp, qq;
     const T dg = (T)deg;
-    const T dx = a.dshift ? a.dshift[row] : T(0);
+    T dx = T(0);
+    if constexpr (SH) dx = a.dshift[row];
     if (first) {
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
         pp.v[v] = rr.v[v];
         qq.v[v] = ca * rr.v[v] + cA * nb[v] + cD * dg * rr.v[v];
-        if (a.dshift) qq.v[v] += dx * rr.v[v];
+        if constexpr (SH) qq.v[v] += dx * rr.v[v];
       }
     } else {
       Pack<T, VW> xx = w.x;
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
         T s = ca * rr.v[v] + cA * nb[v] + cD * dg * rr.v[v];
-        if (a.dshift) s += dx * rr.v[v];
+        if constexpr (SH) s += dx * rr.v[v];
         const T al = s_ab[0][lane_off + v], be = s_ab[1][lane_off + v];
         xx.v[v] += al * w.p.v[v];
         pp.v[v] = rr.v[v] + be * w.p.v[v];

@@ -144,6 +144,12 @@ int si_rhs_blocks(int64_t n, int K);
 // (bh, bl) = (vh, vl) / (D_f + sigma) row-wise; |B|^2 per column -> bn2; part: si_rhs_blocks * K doubles
 cudaError_t launch_si_rhs_df(const float* vh, const float* vl, const float* inv_h, const float* inv_l, int64_t n,
                              int K, float* bh, float* bl, double* part, double* bn2, cudaStream_t s);
+// -M z = -((B - r) + a (D_f + sigma)^{-1} z) from the shifted solve's residual r (no gather); y may alias r
+cudaError_t launch_si_mz_df(const float* bh, const float* bl, const float* rh, const float* rl, const float* zh,
+                            const float* zl, const float* inv_h, const float* inv_l, double a, int64_t n, int K,
+                            float* yh, float* yl, cudaStream_t s);
+cudaError_t launch_si_mz64(const double* B, const double* R, const double* Z, const double* inv, double a, int64_t n,
+                           int K, double* X, cudaStream_t s);
 
 // ---- wl_k_reorth.cu: basis reorthogonalisation of the outer Lanczos
 int reorth_chunks(int nb, size_t blk);
@@ -229,6 +235,8 @@ cudaError_t launch_mlp_predict(const float* P, const float* F, int64_t rows, con
 int report_cuda_error(cudaError_t e, const char* where);
 void report_error(const std::string& msg);
 std::string last_error_copy();
-int graph_spectral(const wl_csr* A, const double* mus, int nmu, void* stream, double* lmax, double* rho);
+// rtol: relative accuracy of lambda_max(A) and rho(Z_mu) (0: wl_build's defaults)
+int graph_spectral(const wl_csr* A, const double* mus, int nmu, void* stream, double* lmax, double* rho,
+                   double rtol);
 
 }  // namespace wl

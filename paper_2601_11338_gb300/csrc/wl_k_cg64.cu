@@ -14,7 +14,10 @@ static cudaError_t run_cg64(const PhaseArgs<double>& a, int grid_s, int grid_u, 
     cg_u_phase<double, K><<<grid_u, kPhaseBlock, 0, s>>>(a, 1);
   } else if (mode == 1) {
     for (int i = 0; i < chunk; ++i) {
-      cg_s_phase<double, K><<<grid_s, kPhaseBlock, 0, s>>>(a);
+      if (a.dshift)
+        cg_s_phase<double, K, true><<<grid_s, kPhaseBlock, 0, s>>>(a);
+      else
+        cg_s_phase<double, K><<<grid_s, kPhaseBlock, 0, s>>>(a);
       cg_u_phase<double, K><<<grid_u, kPhaseBlock, 0, s>>>(a, 0);
     }
   } else {

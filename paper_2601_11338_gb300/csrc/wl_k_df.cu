@@ -17,8 +17,12 @@ cudaError_t launch_df_res(int K, const DfResArgs& a, int grid, bool full, cudaSt
   switch (K) {
 #define DR(k)                                                      \
   case k:                                                          \
-    if (full)                                                      \
+    if (full && a.dsh_h)                                           \
+      df_res<k, true, true><<<grid, kPhaseBlock, 0, s>>>(a);       \
+    else if (full)                                                 \
       df_res<k, true><<<grid, kPhaseBlock, 0, s>>>(a);             \
+    else if (a.dsh_h)                                              \
+      df_res<k, false, true><<<grid, kPhaseBlock, 0, s>>>(a);      \
     else                                                           \
       df_res<k, false><<<grid, kPhaseBlock, 0, s>>>(a);            \
     return cudaGetLastError();

@@ -17,6 +17,7 @@
 // W2[64][64], b2[64], W3[64], b3 (4553 values).
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -634,6 +635,76 @@ int wl_mlp_predict(const float* params, const float* feats, int64_t rows, const 
 }
 
 int wl_mlp_param_count(void) { return kParams; }
+
+// Checkpoint file of the network: a 32-byte header (magic "WLMLP001",
+// uint32 inputs, hidden width, output width, parameter count, FNV-1a hash of
+// the parameter bytes, uint32 zero) followed by the parameter vector as
+// little-endian FP32 in the order of the parameter layout above.
+namespace {
+constexpr char kMlpMagic[8] = {'W', 'L', 'M', 'L', 'P', '0', '0', '1'};
+
+uint32_t fnv1a(const unsigned char* p, size_t n) {
+  uint32_t h = 2166136261u;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 16777619u;
+  }
+  return h;
+}
+
+void put_u32(unsigned char* p, uint32_t v) {
+  for (int i = 0; i < 4; ++i) p[i] = (unsigned char)(v >> (8 * i));
+}
+
+uint32_t get_u32(const unsigned char* p) {
+  uint32_t v = 0;
+  for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i);
+  return v;
+}
+}  // namespace
+
+int wl_mlp_save(const char* path, const float* params) {
+  if (!path || !params) return WL_ERR_INVALID_ARG;
+  std::vector<unsigned char> buf(32 + (size_t)kParams * 4);
+  memcpy(buf.data(), kMlpMagic, 8);
+  for (int i = 0; i < kParams; ++i) {
+    uint32_t bits;
+    memcpy(&bits, params + i, 4);
+    put_u32(buf.data() + 32 + (size_t)i * 4, bits);
+  }
+  put_u32(buf.data() + 8, kIn);
+  put_u32(buf.data() + 12, kH);
+  put_u32(buf.data() + 16, 1);
+  put_u32(buf.data() + 20, kParams);
+  put_u32(buf.data() + 24, fnv1a(buf.data() + 32, (size_t)kParams * 4));
+  put_u32(buf.data() + 28, 0);
+  FILE* f = fopen(path, "wb");
+  if (!f) return WL_ERR_INVALID_ARG;
+  const size_t w = fwrite(buf.data(), 1, buf.size(), f);
+  const int rc = fclose(f);
+  return (w == buf.size() && rc == 0) ? WL_OK : WL_ERR_INVALID_ARG;
+}
+
+int wl_mlp_load(const char* path, float* params) {
+  if (!path || !params) return WL_ERR_INVALID_ARG;
+  FILE* f = fopen(path, "rb");
+  if (!f) return WL_ERR_INVALID_ARG;
+  std::vector<unsigned char> buf(32 + (size_t)kParams * 4);
+  const size_t r = fread(buf.data(), 1, buf.size(), f);
+  unsigned char extra;
+  const bool trailing = fread(&extra, 1, 1, f) == 1;
+  fclose(f);
+  if (r != buf.size() || trailing || memcmp(buf.data(), kMlpMagic, 8) != 0) return WL_ERR_INVALID_ARG;
+  if (get_u32(buf.data() + 8) != (uint32_t)kIn || get_u32(buf.data() + 12) != (uint32_t)kH ||
+      get_u32(buf.data() + 16) != 1u || get_u32(buf.data() + 20) != (uint32_t)kParams)
+    return WL_ERR_INVALID_ARG;
+  if (get_u32(buf.data() + 24) != fnv1a(buf.data() + 32, (size_t)kParams * 4)) return WL_ERR_NONFINITE;
+  for (int i = 0; i < kParams; ++i) {
+    const uint32_t bits = get_u32(buf.data() + 32 + (size_t)i * 4);
+    memcpy(params + i, &bits, 4);
+  }
+  return WL_OK;
+}
 
 int wl_mlp_targets(const double* Df, const double* xan, int64_t rows, float* target, void* stream) {
   if (!Df || !xan || !target || rows < 0) return WL_ERR_INVALID_ARG;

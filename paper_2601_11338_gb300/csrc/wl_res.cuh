@@ -118,7 +118,9 @@ __device__ __forceinline__ void df_row_gather(const int32_t* __restrict__ col, i
   }
 }
 
-template <int K, bool FULL>
+// SH: the solve's M carries the per-row diagonal (dsh_h, dsh_l); a separate
+// instance, so that the unshifted kernel carries no trace of it
+template <int K, bool FULL, bool SH = false>
 __global__ void __launch_bounds__(kPhaseBlock, 4) df_res(DfResArgs a) {
   using C = Cfg<float, K>;
   constexpr int VW = C::VW, G = C::G, RPB = kPhaseBlock / G;
@@ -133,12 +135,12 @@ __global__ void __launch_bounds__(kPhaseBlock, 4) df_res(DfResArgs a) {
   auto fin = [&](int64_t row, int deg, const float (&s)[VW], const float (&c)[VW], const float (&l)[VW]) {
     const size_t o = (size_t)row * K + lane_off;
     df crow = df_add(a.ca, df_mul_f(a.cD, (float)deg));
-    if (a.dsh_h) crow = df_add(crow, df{a.dsh_h[row], a.dsh_l[row]});
+    if constexpr (SH) crow = df_add(crow, df{a.dsh_h[row], a.dsh_l[row]});
     const Pack<float, VW> yh = ld_plain<float, VW>(a.yh + o);
     Pack<float, VW> yl;
     if constexpr (FULL) yl = ld_plain<float, VW>(a.yl + o);
     Pack<float, VW> bh, bl;
-    if (a.bh) {
+    if (!FULL || a.bh) {
       bh = ld_plain<float, VW>(a.bh + o);
       bl = ld_plain<float, VW>(a.bl + o);
     } else {

@@ -111,6 +111,10 @@ def lib():
         L.wl_batch_info.restype = c_int
         L.wl_batch_tile_rows.argtypes = [vp, c_int]
         L.wl_batch_tile_rows.restype = c_int
+        L.wl_mlp_save.argtypes = [ctypes.c_char_p, vp]
+        L.wl_mlp_save.restype = c_int
+        L.wl_mlp_load.argtypes = [ctypes.c_char_p, vp]
+        L.wl_mlp_load.restype = c_int
         L.wl_mlp_param_count.restype = c_int
         L.wl_mlp_param_count.argtypes = []
         L.wl_mlp_features.argtypes = [vp, vp, vp, ctypes.POINTER(wl_stats)]
@@ -380,3 +384,17 @@ def wl_pool_release():
 def wl_pool_cached_bytes():
     return int(lib().wl_pool_cached_bytes())
 
+
+
+def wl_mlp_save(path, params):
+    """Write the network's parameter vector (host float32 array) to a checkpoint file."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    return _check(lib().wl_mlp_save(os.fsencode(path), p.ctypes.data), "wl_mlp_save")
+
+
+def wl_mlp_load(path, allow=()):
+    """Parameter vector (float32) read from a checkpoint file. A rejected file
+    raises WLError, or returns None when its status is in `allow`."""
+    p = np.empty(wl_mlp_param_count(), dtype=np.float32)
+    rc = _check(lib().wl_mlp_load(os.fsencode(path), p.ctypes.data), "wl_mlp_load", allow)
+    return p if rc == WL_OK else None

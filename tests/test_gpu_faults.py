@@ -36,3 +36,80 @@ def test_barrier_wait_expires_with_timeout_status_and_context_survives():
     want = walks.walk_degrees(walks.phi_resolvent_closed(A, 1.0, w.info["alpha"]))
     w.close()
     assert np.linalg.norm(Df - want) <= 1e-10 * np.linalg.norm(want)
+
+
+# ---------------------------------------------------------------- host-side fault injection (WL_FAULT)
+def _small():
+    g = wlgen.erdos_renyi(300, 6, 4)
+    A = graph.dense_adjacency(g.row_ptr, g.col_idx, g.n)
+    return g, A
+
+
+@pytest.fixture
+def fault(monkeypatch):
+    def set_mode(mode):
+        monkeypatch.setenv("WL_FAULT", mode)
+    yield set_mode
+    monkeypatch.delenv("WL_FAULT", raising=False)
+
+
+def _clean_solve_matches_oracle(g, A):
+    from paper_2601_11338_gb300.api import WalkLaplacian
+    w = WalkLaplacian(g.row_ptr.astype(np.int32), g.col_idx, g.n, variant="nbt", alpha_rel=0.5, tol=1e-13)
+    Df = w.degrees().cpu().numpy()
+    want = walks.walk_degrees(walks.phi_resolvent_closed(A, 1.0, w.info["alpha"]))
+    w.close()
+    return np.linalg.norm(Df - want) <= 1e-10 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "refined"])
+@pytest.mark.parametrize("mode,status", [("nan", "WL_ERR_NONFINITE"), ("noconv", "WL_ERR_NO_CONVERGENCE")])
+def test_injected_solver_faults_surface_as_status(fault, mode, status, prec):
+    """A NaN in the starting residual and a one-iteration cap, made on the
+    host, come back as the documented statuses; the next clean call on the
+    same context is correct."""
+    from paper_2601_11338_gb300 import wl
+    from paper_2601_11338_gb300.api import WalkLaplacian
+    g, A = _small()
+    w = WalkLaplacian(g.row_ptr.astype(np.int32), g.col_idx, g.n, variant="nbt", alpha_rel=0.5, tol=1e-12, prec=prec)
+    code = getattr(wl, status)
+    fault(mode)
+    w.degrees(allow=(code,))
+    assert w.last.status == code
+    fault("")
+    w.close()
+    assert _clean_solve_matches_oracle(g, A)
+
+
+def test_injected_allocation_failure(fault):
+    from paper_2601_11338_gb300 import wl
+    g, A = _small()
+    fault("alloc")
+    rp = torch.as_tensor(g.row_ptr.astype(np.int32), device="cuda")
+    ci = torch.as_tensor(g.col_idx, device="cuda")
+    with pytest.raises(wl.WLError) as e:
+        wl.wl_build(rp, ci, g.n, g.nnz, wl.WL_NBT, wl.make_params(alpha_rel=0.5))
+    assert e.value.status == wl.WL_ERR_OOM
+    fault("")
+    assert _clean_solve_matches_oracle(g, A)
+
+
+def test_injected_barrier_timeout(fault):
+    """Every grid barrier starts in the gave-up state: the cooperative Lanczos
+    step leaves at its first barrier and wl_expmv reports WL_ERR_TIMEOUT
+    without waiting."""
+    from paper_2601_11338_gb300 import wl
+    from paper_2601_11338_gb300.api import WalkLaplacian
+    g, A = _small()
+    w = WalkLaplacian(g.row_ptr.astype(np.int32), g.col_idx, g.n, variant="nbt", alpha_rel=0.5, tol=1e-12)
+    U0 = torch.zeros((g.n, 1), dtype=torch.float64, device="cuda")
+    U0[0, 0] = 1.0
+    w.degrees()
+    fault("timeout")
+    t0 = time.perf_counter()
+    w.expmv(U0, [1.0], allow=(wl.WL_ERR_TIMEOUT,))
+    assert w.last.status == wl.WL_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 1.5  # no 2 s wait: the barrier had already given up
+    fault("")
+    w.close()
+    assert _clean_solve_matches_oracle(g, A)

@@ -168,6 +168,19 @@ def test_spectral_radius_of_companion(mu):
     assert abs(w.info["rho"] - rho) <= 1e-8 * rho
 
 
+@pytest.mark.parametrize("n", [12, 3000])
+def test_spectral_radius_double_root_on_a_cycle(n):
+    """mu = 1 on a cycle: d = 2 and h(lambda) = 2 - 1/lambda - lambda touches
+    zero at lambda = 1 without changing sign (a double root), and rho(Z_1) = 1
+    (the dense eigenvalues of Z agree)."""
+    g = wlgen.cycle(n)
+    if n <= 12:
+        assert abs(spectral.rho_companion(dense(g), 1.0) - 1.0) <= 1e-6
+    w = WL(g, variant="nbt", alpha_rel=0.5)
+    assert abs(w.info["rho"] - 1.0) <= 1e-6, w.info["rho"]
+    w.close()
+
+
 # ------------------------------------------------------------ edge cases
 def test_graph_without_edges():
     n = 10
