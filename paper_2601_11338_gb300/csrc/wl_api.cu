@@ -212,6 +212,7 @@ struct wl_handle {
   bool sp_ritz_ready = false;                        // W[1] holds that run's Ritz vector
   double inner_tol = 4e-6;  // floor of the FP32 correction target of the refined form
   int cg_hint = 7;          // CG iterations of the handle's last solve (sizes the first launch chunk)
+  int cg_hint_ref[2] = {7, 7};  // the same for the first and the later corrections of a refined solve
   bool gram_tc = true;      // XNysTrace Gram on the tensor cores (tcgen05); false: CUDA cores
   CgState* cgst() { return (CgState*)cgstate.p; }
   double* h_pin = nullptr;  // pinned host scratch (4096 doubles)
@@ -549,7 +550,12 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
                        inner_tol * inner_tol};
     a.dshift = h->si_dsh_h;
     SolveInfo inner;
+    // the first correction and the later ones go to different depths: each
+    // sizes its first launch chunk from the previous solve of its kind
+    int& hint = h->cg_hint_ref[ref == 0 ? 0 : 1];
+    h->cg_hint = hint;
     WL_TRY(run_cg<float>(h, K, a, grid_s, grid_u, inner, 4));
+    hint = h->cg_hint;
     if (inner.status == WL_ERR_NOT_SPD || inner.status == WL_ERR_NONFINITE) {
       info.status = inner.status;
       break;
@@ -746,8 +752,17 @@ int sp_buffers(wl_handle* h, int gs) {
 
 // Extend the run of r (or start one: seeded, or from the vector in W[1]
 // when r->m == 0) until its bound is below rtol |theta| or it is exact.
+// CTAs of the spectral kernels' row loops: all SMs' worth for large graphs,
+// but no more than one pass of rows, so that the searches of small graphs (the
+// batched build runs many side by side on separate streams) leave the GPU to
+// the others
+int sp_grid(wl_handle* h) {
+  const int64_t need = std::max<int64_t>(1, (h->n + kPhaseBlock - 1) / kPhaseBlock);
+  return (int)std::min<int64_t>(sp_blocks(), need);
+}
+
 int sp_run(wl_handle* h, SpRun* r, double rtol, bool seeded) {
-  const int cap = sp_cap(h), gu = sp_blocks(), gs = gu + h->nhub + h->nmid_blk;
+  const int cap = sp_cap(h), gu = sp_grid(h), gs = gu + h->nhub + h->nmid_blk;
   WL_TRY(sp_buffers(h, gs));
   const SpArgs a = sp_args(h, r->c0, r->cD);
   SpState* st = (SpState*)h->spstate.p;
@@ -789,7 +804,7 @@ int sp_run(wl_handle* h, SpRun* r, double rtol, bool seeded) {
 // Ritz vector of the last run into W[1]; q = u^T D u / |u|^2 and
 // u^T A u / |u|^2 from the run's Ritz value.
 int sp_ritz_q(wl_handle* h, double* q, double* uAu) {
-  const int gu = sp_blocks();
+  const int gu = sp_grid(h);
   const SpArgs a = sp_args(h, h->sp_c0, h->sp_cD);
   SpState* st = (SpState*)h->spstate.p;
   if (!h->sp_ritz_ready) {
@@ -2373,7 +2388,7 @@ int graph_spectral(const wl_csr* A, const double* mus, int nmu, void* stream, do
   p.f = WL_F_IDENTITY;
   p.prec = WL_FP64;
   p.stream = stream;
-  p.reorder = 1;
+  p.reorder = 0;  // the searches need no node relabelling
   wl_handle* h = nullptr;
   int rc = wl_build(A, WL_ALLWALK, &p, &h, nullptr);
   if (rc != WL_OK) return rc;

@@ -39,9 +39,9 @@ using namespace wl;
 namespace {
 
 // spectral scales of the batch: lambda_max(A) and rho(Z_mu) to 1e-10
-// relative (alpha = alpha_rel / rho needs no more), searches on 16 threads
+// relative (alpha = alpha_rel / rho needs no more), searches on 32 threads
 constexpr double kSpecRtol = 1e-10;
-constexpr int kSpecThreads = 16;
+constexpr int kSpecThreads = 32;
 
 constexpr int kLoopHardCap = 1 << 20;  // body executions of one while node, whatever the flags say
 

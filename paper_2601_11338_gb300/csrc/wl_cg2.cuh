@@ -98,6 +98,10 @@ __device__ __forceinline__ Pack<T, VW> ld_plain(const T* p) {
 #ifndef WL_GATHER_U
 #define WL_GATHER_U 8
 #endif
+// short rows of the S kernel: the next row's bounds loaded one row ahead (1)
+#ifndef WL_ROW_PREFETCH
+#define WL_ROW_PREFETCH 0
+#endif
 // the same choice for the FP64 kernels (the plain FP64 form), measured on its own
 #ifndef WL_GATHER_PRED_F64
 #define WL_GATHER_PRED_F64 0
@@ -244,12 +248,15 @@ __global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks<T>()) cg_s_phase
   const T* __restrict__ pr = a.r;
   struct Own {
     Pack<T, VW> r, x, p, q;
+    T dx;  // the row's shift diagonal (SH)
   };
-  // own-row vectors, loaded before the row's gathers so the two overlap
+  // own-row vectors (and the shift diagonal), loaded before the row's gathers
+  // so the two overlap
   auto own = [&](int64_t row) {
     Own o;
     const size_t off = (size_t)row * K + lane_off;
     o.r = ld_plain<T, VW>(pr + off);
+    if constexpr (SH) o.dx = __ldg(a.dshift + row);
     return o;
   };
   auto fin = [&](int64_t row, int deg, const T (&nb)[VW], const Own& w0) {
@@ -264,7 +271,7 @@ __global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks<T>()) cg_s_phase
     Pack<T, VW> pp, qq;
     const T dg = (T)deg;
     T dx = T(0);
-    if constexpr (SH) dx = a.dshift[row];
+    if constexpr (SH) dx = w.dx;
     if (first) {
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
@@ -333,6 +340,30 @@ __global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks<T>()) cg_s_phase
     const int nlist = a.g.nhub + a.g.nmid_blk;
     const int lim = a.g.nmid_blk > 0 ? kMidDeg : kHubDeg;  // longer rows: hub CTAs or mid warps
     const int64_t nblk = (int64_t)gridDim.x - nlist;
+#if WL_ROW_PREFETCH
+    // the next row's bounds are loaded while this row's gathers are in flight
+    int64_t row = ((int64_t)blockIdx.x - nlist) * RPB + tid / G;
+    int nbeg = 0, nend = 0;
+    if (row < a.g.n) {
+      nbeg = a.g.row_ptr[row];
+      nend = a.g.row_ptr[row + 1];
+    }
+    for (; row < a.g.n; row += nblk * RPB) {
+      const int beg = nbeg, end = nend;
+      const int64_t nxt = row + nblk * RPB;
+      if (nxt < a.g.n) {
+        nbeg = a.g.row_ptr[nxt];
+        nend = a.g.row_ptr[nxt + 1];
+      }
+      if (end - beg > lim) continue;
+      const Own w = own(row);
+      T acc[VW];
+#pragma unroll
+      for (int v = 0; v < VW; ++v) acc[v] = T(0);
+      row_gather<T, K, VW>(a.g.col, beg, end, 1, a.r, lane_off, acc);
+      fin(row, end - beg, acc, w);
+    }
+#else
     for (int64_t row = ((int64_t)blockIdx.x - nlist) * RPB + tid / G; row < a.g.n; row += nblk * RPB) {
       const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
       if (end - beg > lim) continue;
@@ -343,6 +374,7 @@ __global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks<T>()) cg_s_phase
       row_gather<T, K, VW>(a.g.col, beg, end, 1, a.r, lane_off, acc);
       fin(row, end - beg, acc, w);
     }
+#endif
   }
   double dd[VW];
 #pragma unroll

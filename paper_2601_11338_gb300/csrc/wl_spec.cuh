@@ -254,12 +254,14 @@ __global__ void __launch_bounds__(kPhaseBlock) sp_u(SpArgs a, int last) {
 // principal minors p_i(x) (Sturm sequence), with no division: p_{i+1} =
 // (alpha_i - x) p_i - beta_{i-1}^2 p_{i-1}, rescaled by powers of two to
 // stay in range; a zero minor takes the sign opposite to its predecessor.
-__device__ inline int sturm_count_poly(const double* a, const double* b, int m, double x) {
+// Sturm count (eigenvalues below x) of the tridiagonal with diagonal a and
+// squared off-diagonal b2, by the scaled three-term determinant recurrence
+__device__ inline int sturm_count_poly(const double* a, const double* b2, int m, double x) {
   double pm = 1.0, p = a[0] - x;
   int cnt = (p < 0.0) ? 1 : 0;
   double sprev = (p == 0.0) ? -1.0 : p;
   for (int i = 1; i < m; ++i) {
-    const double pn = (a[i] - x) * p - (b[i - 1] * b[i - 1]) * pm;
+    const double pn = (a[i] - x) * p - b2[i - 1] * pm;
     pm = p;
     p = pn;
     const double ap = fabs(p);
@@ -280,31 +282,45 @@ __device__ inline int sturm_count_poly(const double* a, const double* b, int m, 
 // Two largest eigenvalues of T_m by multisection (a group of kSpEigT threads
 // per eigenvalue, kSpEigRounds rounds of kSpEigT Sturm counts: 129^7 > 1e14),
 // then the top eigenvector by inverse iteration and the error bound; stops
-// the run when the bound is below rtol |theta_1| (or after a breakdown).
+// the run when the bound is below rtol |theta_1|. T_m, its squared
+// off-diagonal and the inverse-iteration vectors are staged in shared memory
+// (the serial sweeps of one thread would otherwise wait on global memory at
+// every row).
 constexpr int kSpEigT = 128;
 constexpr int kSpEigRounds = 7;
 
 __global__ void __launch_bounds__(2 * kSpEigT) sp_eig(SpState* st, double rtol) {
   __shared__ double s_lo[2], s_hi[2];
   __shared__ int s_cnt[2][kSpEigT];
+  __shared__ double s_a[kSpMax], s_b[kSpMax], s_b2[kSpMax], s_y[kSpMax], s_cp[kSpMax];
+  __shared__ double s_tn;
   const int m = st->m_eff;
   if (m <= 0 || m > kSpMax) return;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double a = st->alpha[i], b = (i + 1 < m) ? st->beta[i] : 0.0;
+    s_a[i] = a;
+    s_b[i] = b;
+    s_b2[i] = b * b;
+  }
+  __syncthreads();
   const int grp = threadIdx.x / kSpEigT, t = threadIdx.x % kSpEigT;
   const int idx = grp == 0 ? m - 1 : (m >= 2 ? m - 2 : m - 1);
-  if (t == 0) {
-    double lo = 1e300, hi = -1e300;
+  if (threadIdx.x == 0) {
+    double lo = 1e300, hi = -1e300, tn = 0.0;
     for (int i = 0; i < m; ++i) {
-      const double r = (i > 0 ? fabs(st->beta[i - 1]) : 0.0) + (i + 1 < m ? fabs(st->beta[i]) : 0.0);
-      lo = fmin(lo, st->alpha[i] - r);
-      hi = fmax(hi, st->alpha[i] + r);
+      const double r = (i > 0 ? fabs(s_b[i - 1]) : 0.0) + fabs(s_b[i]);
+      lo = fmin(lo, s_a[i] - r);
+      hi = fmax(hi, s_a[i] + r);
+      tn = fmax(tn, fabs(s_a[i]) + r);
     }
-    s_lo[grp] = lo;
-    s_hi[grp] = hi;
+    s_lo[0] = s_lo[1] = lo;
+    s_hi[0] = s_hi[1] = hi;
+    s_tn = tn;
   }
   __syncthreads();
   for (int round = 0; round < kSpEigRounds; ++round) {
     const double lo = s_lo[grp], w = s_hi[grp] - lo;
-    s_cnt[grp][t] = sturm_count_poly(st->alpha, st->beta, m, lo + w * (double)(t + 1) / (double)(kSpEigT + 1));
+    s_cnt[grp][t] = sturm_count_poly(s_a, s_b2, m, lo + w * (double)(t + 1) / (double)(kSpEigT + 1));
     __syncthreads();
     if (t == 0) {
       int k = 0;
@@ -314,51 +330,52 @@ __global__ void __launch_bounds__(2 * kSpEigT) sp_eig(SpState* st, double rtol) 
     }
     __syncthreads();
   }
-  if (threadIdx.x != 0) return;
-  const double th1 = 0.5 * (s_lo[0] + s_hi[0]);
-  const double th2 = 0.5 * (s_lo[1] + s_hi[1]);
-  // inverse iteration on T_m - sigma I (Thomas algorithm, tiny pivots
-  // replaced), sigma just above theta_1
-  double* y = st->y;
-  double tn = 0.0;
-  for (int i = 0; i < m; ++i) tn = fmax(tn, fabs(st->alpha[i]) + (i > 0 ? fabs(st->beta[i - 1]) : 0.0) +
-                                             (i + 1 < m ? fabs(st->beta[i]) : 0.0));
-  const double sigma = th1 + 1e-13 * (tn + 1e-300);
-  const double tiny = 1e-300 + 1e-15 * tn;
-  for (int i = 0; i < m; ++i) y[i] = 1.0 + 0.01 * (double)(i % 7);
-  double cp[kSpMax];
-  for (int it = 0; it < 2; ++it) {
-    // forward sweep: T - sigma I = L U, solve in place (one division a row)
-    double piv = st->alpha[0] - sigma;
-    if (fabs(piv) < tiny) piv = tiny;
-    double rp = 1.0 / piv;
-    cp[0] = (m > 1 ? st->beta[0] : 0.0) * rp;
-    y[0] = y[0] * rp;
-    for (int i = 1; i < m; ++i) {
-      const double bl = st->beta[i - 1];
-      piv = (st->alpha[i] - sigma) - bl * cp[i - 1];
+  if (threadIdx.x == 0) {
+    const double th1 = 0.5 * (s_lo[0] + s_hi[0]);
+    const double th2 = 0.5 * (s_lo[1] + s_hi[1]);
+    // inverse iteration on T_m - sigma I (Thomas algorithm, tiny pivots
+    // replaced), sigma just above theta_1
+    const double tn = s_tn;
+    const double sigma = th1 + 1e-13 * (tn + 1e-300);
+    const double tiny = 1e-300 + 1e-15 * tn;
+    double* y = s_y;
+    double* cp = s_cp;
+    for (int i = 0; i < m; ++i) y[i] = 1.0 + 0.01 * (double)(i % 7);
+    for (int it = 0; it < 2; ++it) {
+      // forward sweep: T - sigma I = L U, solve in place (one division a row)
+      double piv = s_a[0] - sigma;
       if (fabs(piv) < tiny) piv = tiny;
-      rp = 1.0 / piv;
-      cp[i] = (i + 1 < m ? st->beta[i] : 0.0) * rp;
-      y[i] = (y[i] - bl * y[i - 1]) * rp;
+      double rp = 1.0 / piv;
+      cp[0] = s_b[0] * rp;
+      y[0] = y[0] * rp;
+      for (int i = 1; i < m; ++i) {
+        const double bl = s_b[i - 1];
+        piv = (s_a[i] - sigma) - bl * cp[i - 1];
+        if (fabs(piv) < tiny) piv = tiny;
+        rp = 1.0 / piv;
+        cp[i] = s_b[i] * rp;
+        y[i] = (y[i] - bl * y[i - 1]) * rp;
+      }
+      for (int i = m - 2; i >= 0; --i) y[i] -= cp[i] * y[i + 1];
+      double nn = 0.0;
+      for (int i = 0; i < m; ++i) nn += y[i] * y[i];
+      const double sc = 1.0 / sqrt(nn);
+      for (int i = 0; i < m; ++i) y[i] *= sc;
     }
-    for (int i = m - 2; i >= 0; --i) y[i] -= cp[i] * y[i + 1];
-    double nn = 0.0;
-    for (int i = 0; i < m; ++i) nn += y[i] * y[i];
-    const double s = 1.0 / sqrt(nn);
-    for (int i = 0; i < m; ++i) y[i] *= s;
+    const double r = fabs(st->beta[m - 1] * y[m - 1]);
+    const double gap = th1 - th2;
+    double bound = r;
+    if (gap > 0.0) bound = fmin(r, r * r / gap);
+    if (st->brk) bound = 0.0;
+    st->out[0] = th1;
+    st->out[1] = th2;
+    st->out[2] = r;
+    st->out[3] = bound;
+    st->out[4] = (double)m;
+    if (bound <= rtol * fabs(th1)) st->stop = 1;
   }
-  const double r = fabs(st->beta[m - 1] * y[m - 1]);
-  const double gap = th1 - th2;
-  double bound = r;
-  if (gap > 0.0) bound = fmin(r, r * r / gap);
-  if (st->brk) bound = 0.0;
-  st->out[0] = th1;
-  st->out[1] = th2;
-  st->out[2] = r;
-  st->out[3] = bound;
-  st->out[4] = (double)m;
-  if (bound <= rtol * fabs(th1)) st->stop = 1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) st->y[i] = s_y[i];
 }
 
 // Ritz vector u = V_m y into W[1] (the start of the next run), |u|^2 and
