@@ -361,7 +361,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     sb, sd, se = wl.wl_stats(), wl.wl_stats(), wl.wl_stats()
     h = wl.wl_build(rp_h, ci_h, g.n, g.nnz, wl.WL_NBT, params(wl.WL_REFINED, TIME_TO_RULE["tol"],
-                                                             TIME_TO_RULE["outer_tol"]), sb)
+                                                             TIME_TO_RULE["outer_tol"], args.shift), sb)
     wl.wl_degrees(h, Df_h, sd)
     wl.wl_expmv(h, U0_h, K_SRC, K_SRC, taus, U_h, K_SRC, se)
     h.destroy()

@@ -355,6 +355,10 @@ PhaseGraph phase_graph_mid(wl_handle* h, int grid_u) {
   return g;
 }
 
+// first FP32 correction target of a refined solve: kInner0C sqrt(tol), at
+// least the handle's inner_tol floor (a deeper first target, 0.1 sqrt(tol),
+// measured no fewer CG iterations in all)
+constexpr double kInner0C = 0.5;
 constexpr int kChunk = 8;      // CG iterations launched between two reads of the device flag (cap: 2 kChunk)
 constexpr int kChunkMore = 4;  // iterations of every chunk after the first
 
@@ -516,7 +520,7 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
   // reliably gets (the inner_tol floor) unless tol is loose; a later one only
   // as deep as the current relative residual rel needs to reach tol (0.5 tol /
   // rel, with the same floor)
-  const double inner0 = std::min(1e-3, std::max(h->inner_tol, 0.5 * std::sqrt(tol)));
+  const double inner0 = std::min(1e-3, std::max(h->inner_tol, kInner0C * std::sqrt(tol)));
   const int max_ref = 12;
   int ndf = 0;
   for (int ref = 0;; ++ref) {
@@ -756,8 +760,12 @@ int sp_buffers(wl_handle* h, int gs) {
 // but no more than one pass of rows, so that the searches of small graphs (the
 // batched build runs many side by side on separate streams) leave the GPU to
 // the others
+#ifndef WL_SP_ROWS
+#define WL_SP_ROWS 1
+#endif
 int sp_grid(wl_handle* h) {
-  const int64_t need = std::max<int64_t>(1, (h->n + kPhaseBlock - 1) / kPhaseBlock);
+  const int64_t per = (int64_t)kPhaseBlock * WL_SP_ROWS;  // rows per CTA and pass of the row loop
+  const int64_t need = std::max<int64_t>(1, (h->n + per - 1) / per);
   return (int)std::min<int64_t>(sp_blocks(), need);
 }
 

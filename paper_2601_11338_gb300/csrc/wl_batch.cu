@@ -40,8 +40,11 @@ namespace {
 
 // spectral scales of the batch: lambda_max(A) and rho(Z_mu) to 1e-10
 // relative (alpha = alpha_rel / rho needs no more), searches on 32 threads
+#ifndef WL_SPEC_THREADS
+#define WL_SPEC_THREADS 32
+#endif
 constexpr double kSpecRtol = 1e-10;
-constexpr int kSpecThreads = 32;
+constexpr int kSpecThreads = WL_SPEC_THREADS;
 
 constexpr int kLoopHardCap = 1 << 20;  // body executions of one while node, whatever the flags say
 

@@ -42,6 +42,7 @@ constexpr int kPhaseMinBlocksF32 = WL_PHASE_MINB_F32;
 template <typename T>
 constexpr int phase_min_blocks() { return sizeof(T) == 4 ? kPhaseMinBlocksF32 : kPhaseMinBlocks; }
 
+
 // Per-solve device state (written by the last CTA of each kernel).
 struct CgState {
   double gamma[64], alpha[64], beta[64], b2[64];
@@ -97,10 +98,6 @@ __device__ __forceinline__ Pack<T, VW> ld_plain(const T* p) {
 #endif
 #ifndef WL_GATHER_U
 #define WL_GATHER_U 8
-#endif
-// short rows of the S kernel: the next row's bounds loaded one row ahead (1)
-#ifndef WL_ROW_PREFETCH
-#define WL_ROW_PREFETCH 0
 #endif
 // the same choice for the FP64 kernels (the plain FP64 form), measured on its own
 #ifndef WL_GATHER_PRED_F64
@@ -340,30 +337,6 @@ __global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks<T>()) cg_s_phase
     const int nlist = a.g.nhub + a.g.nmid_blk;
     const int lim = a.g.nmid_blk > 0 ? kMidDeg : kHubDeg;  // longer rows: hub CTAs or mid warps
     const int64_t nblk = (int64_t)gridDim.x - nlist;
-#if WL_ROW_PREFETCH
-    // the next row's bounds are loaded while this row's gathers are in flight
-    int64_t row = ((int64_t)blockIdx.x - nlist) * RPB + tid / G;
-    int nbeg = 0, nend = 0;
-    if (row < a.g.n) {
-      nbeg = a.g.row_ptr[row];
-      nend = a.g.row_ptr[row + 1];
-    }
-    for (; row < a.g.n; row += nblk * RPB) {
-      const int beg = nbeg, end = nend;
-      const int64_t nxt = row + nblk * RPB;
-      if (nxt < a.g.n) {
-        nbeg = a.g.row_ptr[nxt];
-        nend = a.g.row_ptr[nxt + 1];
-      }
-      if (end - beg > lim) continue;
-      const Own w = own(row);
-      T acc[VW];
-#pragma unroll
-      for (int v = 0; v < VW; ++v) acc[v] = T(0);
-      row_gather<T, K, VW>(a.g.col, beg, end, 1, a.r, lane_off, acc);
-      fin(row, end - beg, acc, w);
-    }
-#else
     for (int64_t row = ((int64_t)blockIdx.x - nlist) * RPB + tid / G; row < a.g.n; row += nblk * RPB) {
       const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
       if (end - beg > lim) continue;
@@ -374,7 +347,6 @@ __global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks<T>()) cg_s_phase
       row_gather<T, K, VW>(a.g.col, beg, end, 1, a.r, lane_off, acc);
       fin(row, end - beg, acc, w);
     }
-#endif
   }
   double dd[VW];
 #pragma unroll

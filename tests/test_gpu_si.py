@@ -125,3 +125,24 @@ def test_si_needs_the_resolvent():
     w.expmv(U0, [1.0], allow=(wl.WL_ERR_UNSUPPORTED,))
     assert w.last.status == wl.WL_ERR_UNSUPPORTED
     w.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "refined"])
+def test_si_with_reorthogonalisation(prec):
+    """The shift-and-invert basis kept orthogonal (reorth = 1) gives the same
+    diffusion within the tolerances, in no more steps."""
+    g = wlgen.barabasi_albert(1500, 3, 21)
+    L = oracle_L(g, 1.0, WL(g, variant="nbt", alpha_rel=0.9).info["alpha"])
+    U0 = wlgen.unit_block(g.n, wlgen.point_sources(g, 2, 3))
+    steps = {}
+    for reorth in (0, 1):
+        w = WL(g, variant="nbt", alpha_rel=0.9, prec=prec, tol=1e-13 if prec == "fp64" else 1e-12, outer_tol=1e-12,
+               shift=1.0, reorth=reorth)
+        U = w.expmv(torch.as_tensor(U0, device="cuda"), [0.5, 5.0]).cpu().numpy()
+        steps[reorth] = w.last.outer_iters
+        assert w.last.reorth_blocks == (steps[reorth] - 1 if reorth else 0)
+        w.close()
+        want = walks.diffusion(L, U0, [0.5, 5.0])
+        for t in range(2):
+            assert relerr(U[t], want[t]) <= TOL[prec], (reorth, t, relerr(U[t], want[t]))
+    assert steps[1] <= steps[0], steps
