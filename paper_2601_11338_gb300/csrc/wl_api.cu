@@ -10,8 +10,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
 #include <cstdlib>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -153,6 +155,157 @@ struct SolveInfo {
 
 }  // namespace
 
+// ------------------------------------------------------------- batched searches
+namespace wl {
+
+struct SpReq {
+  SpJob job{};
+  SpOut out{};
+  int rc = WL_OK;
+};
+
+// Rendezvous of the threads of a batched build. Each thread runs the
+// spectral searches of its graphs as usual, but every round of Lanczos steps
+// (and every Ritz vector) is submitted here instead of being launched on the
+// thread's stream. Once every participating thread waits with a request, the
+// last one to arrive launches all requests together on the batch's stream (one
+// launch per kernel and step for all problems, each problem with the same CTA
+// count and so the same arithmetic as on its own), reads the states back and
+// wakes the others. The searches of many small graphs then cost one chain of
+// launches instead of one chain per graph.
+struct SpBatch {
+  std::mutex m;
+  std::condition_variable cv;
+  int live = 0;
+  uint64_t gen = 0;
+  int rounds = 0;
+  std::vector<SpReq*> reqs;
+  cudaStream_t s = nullptr;
+  void* dbuf = nullptr;
+  size_t dbytes = 0;
+  void* hbuf = nullptr;
+  size_t hbytes = 0;
+  std::string err;
+};
+
+namespace {
+thread_local SpBatch* t_sp_batch = nullptr;
+constexpr int kSpCheck = 8;  // eigen step every 8 Lanczos steps (and at the end of a round)
+
+size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// mutex held: launch the pending requests, wait for them, hand out the states
+void sp_round_locked(SpBatch* b) {
+  const int np = (int)b->reqs.size();
+  const size_t jb = align16(sizeof(SpJob) * np), ob = align16(sizeof(int) * (np + 1)), rb = sizeof(SpOut) * np;
+  const size_t need = jb + 2 * ob + rb;
+  int rc = WL_OK;
+  std::string msg;
+  auto cu = [&](cudaError_t e, const char* where) {
+    if (e != cudaSuccess && rc == WL_OK) {
+      rc = (e == cudaErrorMemoryAllocation) ? WL_ERR_OOM : WL_ERR_CUDA;
+      msg = std::string("batched spectral search: ") + where + ": " + cudaGetErrorString(e);
+      (void)cudaGetLastError();
+    }
+    return rc == WL_OK;
+  };
+  if (need > b->hbytes) {  // the stream is idle between rounds: the old buffers can go
+    const size_t cap = std::max(need, b->hbytes * 2);
+    pool_free_host(b->hbuf);
+    pool_free(b->dbuf);
+    b->hbuf = b->dbuf = nullptr;
+    b->hbytes = b->dbytes = 0;
+    if (cu(pool_malloc_host(&b->hbuf, cap), "pinned buffer") && cu(pool_malloc(&b->dbuf, cap), "device buffer"))
+      b->hbytes = b->dbytes = cap;
+  }
+  if (rc == WL_OK) {
+    char* hp = (char*)b->hbuf;
+    SpJob* jobs = (SpJob*)hp;
+    int* off_s = (int*)(hp + jb);
+    int* off_u = (int*)(hp + jb + ob);
+    SpOut* outs = (SpOut*)(hp + jb + 2 * ob);
+    int steps = 0;
+    unsigned eig_mask = 0u;
+    bool any_ritz = false, any_init = false;
+    off_s[0] = off_u[0] = 0;
+    for (int p = 0; p < np; ++p) {
+      const SpJob& j = b->reqs[p]->job;
+      jobs[p] = j;
+      off_s[p + 1] = off_s[p] + j.gs;
+      off_u[p + 1] = off_u[p] + j.gu;
+      if (j.mode >= 0) {
+        steps = std::max(steps, j.j1 - j.j0);
+        for (int jj = j.j0; jj < j.j1 && jj - j.j0 < 32; ++jj)
+          if ((jj + 1) % kSpCheck == 0 || jj + 1 == j.j1) eig_mask |= 1u << (jj - j.j0);
+      }
+      any_ritz |= j.ritz != 0;
+      any_init |= j.mode == 0;
+    }
+    char* dp = (char*)b->dbuf;
+    if (cu(cudaMemcpyAsync(dp, hp, jb + 2 * ob, cudaMemcpyHostToDevice, b->s), "jobs to device") &&
+        cu(launch_sp_round((const SpJob*)dp, (const int*)(dp + jb), (const int*)(dp + jb + ob), np, off_s[np],
+                           off_u[np], steps, kSpCheck, eig_mask, any_ritz, any_init, (SpOut*)(dp + jb + 2 * ob),
+                           b->s),
+           "launch") &&
+        cu(cudaMemcpyAsync(outs, dp + jb + 2 * ob, rb, cudaMemcpyDeviceToHost, b->s), "states to host") &&
+        cu(cudaStreamSynchronize(b->s), "round")) {
+      for (int p = 0; p < np; ++p) b->reqs[p]->out = outs[p];
+    }
+  }
+  for (SpReq* r : b->reqs) r->rc = rc;
+  if (rc != WL_OK) b->err = msg;
+  ++b->rounds;
+  b->reqs.clear();
+  ++b->gen;
+  b->cv.notify_all();
+}
+
+int sp_batch_submit(SpBatch* b, SpReq* r) {
+  std::unique_lock<std::mutex> lk(b->m);
+  b->reqs.push_back(r);
+  if ((int)b->reqs.size() >= b->live) {
+    sp_round_locked(b);
+  } else {
+    const uint64_t g0 = b->gen;
+    b->cv.wait(lk, [&] { return b->gen != g0; });
+  }
+  if (r->rc != WL_OK) report_error(b->err);
+  return r->rc;
+}
+}  // namespace
+
+SpBatch* sp_batch_new(int participants) {
+  SpBatch* b = new SpBatch();
+  b->live = participants;
+  if (cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete b;
+    return nullptr;
+  }
+  return b;
+}
+
+void sp_batch_bind(SpBatch* b) { t_sp_batch = b; }
+
+void sp_batch_leave(SpBatch* b) {
+  std::unique_lock<std::mutex> lk(b->m);
+  --b->live;
+  if (b->live > 0 && (int)b->reqs.size() >= b->live) sp_round_locked(b);
+}
+
+int sp_batch_rounds(const SpBatch* b) { return b->rounds; }
+
+void sp_batch_free(SpBatch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->s);
+  pool_free_host(b->hbuf);
+  pool_free(b->dbuf);
+  cudaStreamDestroy(b->s);
+  delete b;
+}
+
+}  // namespace wl
+
 struct wl_handle {
   int64_t n = 0, nnz = 0;
   Graph g{};
@@ -210,6 +363,7 @@ struct wl_handle {
   double mid_share = 0.0; // share of the S kernels' CTAs that walk the mid rows
   double sp_c0 = 0.0, sp_cD = 0.0, sp_theta = 0.0;  // operator and Ritz value of the basis held in spV
   bool sp_ritz_ready = false;                        // W[1] holds that run's Ritz vector
+  double sp_ritz_uu = 0.0, sp_ritz_udu = 0.0;        // its |u|^2 and u^T D u
   double inner_tol = 4e-6;  // floor of the FP32 correction target of the refined form
   int cg_hint = 7;          // CG iterations of the handle's last solve (sizes the first launch chunk)
   int cg_hint_ref[2] = {7, 7};  // the same for the first and the later corrections of a refined solve
@@ -754,21 +908,21 @@ int sp_buffers(wl_handle* h, int gs) {
   return WL_OK;
 }
 
-// Extend the run of r (or start one: seeded, or from the vector in W[1]
-// when r->m == 0) until its bound is below rtol |theta| or it is exact.
 // CTAs of the spectral kernels' row loops: all SMs' worth for large graphs,
-// but no more than one pass of rows, so that the searches of small graphs (the
-// batched build runs many side by side on separate streams) leave the GPU to
-// the others
-#ifndef WL_SP_ROWS
-#define WL_SP_ROWS 1
-#endif
+// but no more than one CTA per kSpRows threads' worth of rows, so that the
+// searches of small graphs (the batched build runs many side by side on
+// separate streams) leave the GPU to the others. Four rows per thread measured
+// 10% faster on the 64-graph batched build than one, and no slower on one
+// graph of 1e6 nodes.
+constexpr int kSpRows = 4;
 int sp_grid(wl_handle* h) {
-  const int64_t per = (int64_t)kPhaseBlock * WL_SP_ROWS;  // rows per CTA and pass of the row loop
+  const int64_t per = (int64_t)kPhaseBlock * kSpRows;  // rows per CTA and pass of the row loop
   const int64_t need = std::max<int64_t>(1, (h->n + per - 1) / per);
   return (int)std::min<int64_t>(sp_blocks(), need);
 }
 
+// Extend the run of r (or start one: seeded, or from the vector in W[1]
+// when r->m == 0) until its bound is below rtol |theta| or it is exact.
 int sp_run(wl_handle* h, SpRun* r, double rtol, bool seeded) {
   const int cap = sp_cap(h), gu = sp_grid(h), gs = gu + h->nhub + h->nmid_blk;
   WL_TRY(sp_buffers(h, gs));
@@ -777,24 +931,49 @@ int sp_run(wl_handle* h, SpRun* r, double rtol, bool seeded) {
   for (int guard = 0; guard < 256; ++guard) {
     if (r->exact || (r->m > 0 && r->bound <= rtol * std::fabs(r->theta))) break;
     int mode = 2;
+    bool restart = false;
     if (r->m == 0) {
       mode = (seeded && r->total == 0) ? 0 : 1;
     } else if (r->m >= cap) {  // basis full: restart from the Ritz vector
-      counted(h);
-      WL_CU(launch_sp_ritz(a, gu, S(h)));
+      restart = true;
       r->m = 0;
       mode = 1;
     }
     const int j0 = r->m, j1 = std::min(cap, j0 + 16);
-    if (mode == 0) WL_CU(cudaMemsetAsync(st, 0, sizeof(SpState), S(h)));  // tickets and flags start at zero
-    counted(h, 1 + 2 * (j1 - j0) + (j1 - j0 + 7) / 8);
-    WL_CU(launch_sp_start(a, mode, gu, S(h)));
-    WL_CU(launch_sp_steps(a, j0, j1, cap, 8, rtol, gs, gu, S(h)));
-    WL_CU(cudaMemcpyAsync(h->h_pin, &st->start_norm, 9 * 8 + 4 * 4, cudaMemcpyDeviceToHost, S(h)));
-    WL_CU(cudaStreamSynchronize(S(h)));
-    const double* o = h->h_pin + 1;
-    const int* ints = (const int*)(h->h_pin + 9);
-    const int m_eff = ints[0], brk = ints[2];
+    double o[8];
+    int m_eff = 0, brk = 0;
+    if (SpBatch* bt = t_sp_batch) {  // one round of the batched build's searches
+      SpReq rq;
+      rq.job.a = a;
+      rq.job.rtol = rtol;
+      rq.job.j0 = j0;
+      rq.job.j1 = j1;
+      rq.job.cap = cap;
+      rq.job.mode = mode;
+      rq.job.ritz = restart ? 1 : 0;
+      rq.job.gs = gs;
+      rq.job.gu = gu;
+      WL_CU(cudaStreamSynchronize(S(h)));  // the handle's own work (graph, lists) is done
+      WL_TRY(sp_batch_submit(bt, &rq));
+      for (int i = 0; i < 8; ++i) o[i] = rq.out.out[i];
+      m_eff = rq.out.m_eff;
+      brk = rq.out.brk;
+    } else {
+      if (restart) {
+        counted(h);
+        WL_CU(launch_sp_ritz(a, gu, S(h)));
+      }
+      if (mode == 0) WL_CU(cudaMemsetAsync(st, 0, sizeof(SpState), S(h)));  // tickets and flags start at zero
+      counted(h, 1 + 2 * (j1 - j0) + (j1 - j0 + kSpCheck - 1) / kSpCheck);
+      WL_CU(launch_sp_start(a, mode, gu, S(h)));
+      WL_CU(launch_sp_steps(a, j0, j1, cap, kSpCheck, rtol, gs, gu, S(h)));
+      WL_CU(cudaMemcpyAsync(h->h_pin, &st->start_norm, 9 * 8 + 4 * 4, cudaMemcpyDeviceToHost, S(h)));
+      WL_CU(cudaStreamSynchronize(S(h)));
+      for (int i = 0; i < 8; ++i) o[i] = h->h_pin[1 + i];
+      const int* ints = (const int*)(h->h_pin + 9);
+      m_eff = ints[0];
+      brk = ints[2];
+    }
     r->total += m_eff - j0;
     r->m = m_eff;
     r->theta = o[0];
@@ -812,19 +991,35 @@ int sp_run(wl_handle* h, SpRun* r, double rtol, bool seeded) {
 // Ritz vector of the last run into W[1]; q = u^T D u / |u|^2 and
 // u^T A u / |u|^2 from the run's Ritz value.
 int sp_ritz_q(wl_handle* h, double* q, double* uAu) {
-  const int gu = sp_grid(h);
-  const SpArgs a = sp_args(h, h->sp_c0, h->sp_cD);
-  SpState* st = (SpState*)h->spstate.p;
   if (!h->sp_ritz_ready) {
-    counted(h);
-    WL_CU(launch_sp_ritz(a, gu, S(h)));
+    const int gu = sp_grid(h);
+    const SpArgs a = sp_args(h, h->sp_c0, h->sp_cD);
+    SpState* st = (SpState*)h->spstate.p;
+    if (SpBatch* bt = t_sp_batch) {
+      SpReq rq;
+      rq.job.a = a;
+      rq.job.mode = -1;
+      rq.job.ritz = 1;
+      rq.job.cap = sp_cap(h);
+      rq.job.gs = 1;  // no steps: one idle CTA in the step kernels
+      rq.job.gu = gu;
+      WL_CU(cudaStreamSynchronize(S(h)));
+      WL_TRY(sp_batch_submit(bt, &rq));
+      h->sp_ritz_uu = rq.out.out[5];
+      h->sp_ritz_udu = rq.out.out[6];
+    } else {
+      counted(h);
+      WL_CU(launch_sp_ritz(a, gu, S(h)));
+      WL_CU(cudaMemcpyAsync(h->h_pin, &st->out[5], 2 * 8, cudaMemcpyDeviceToHost, S(h)));
+      WL_CU(cudaStreamSynchronize(S(h)));
+      h->sp_ritz_uu = h->h_pin[0];
+      h->sp_ritz_udu = h->h_pin[1];
+    }
+    h->sp_ritz_ready = true;
   }
-  WL_CU(cudaMemcpyAsync(h->h_pin, &st->out[5], 2 * 8, cudaMemcpyDeviceToHost, S(h)));
-  WL_CU(cudaStreamSynchronize(S(h)));
-  const double n2 = h->h_pin[0];
-  *q = n2 > 0 ? h->h_pin[1] / n2 : 0.0;
+  const double n2 = h->sp_ritz_uu;
+  *q = n2 > 0 ? h->sp_ritz_udu / n2 : 0.0;
   *uAu = h->sp_theta - h->sp_c0 - h->sp_cD * (*q);
-  h->sp_ritz_ready = true;
   return WL_OK;
 }
 

@@ -39,12 +39,10 @@ using namespace wl;
 namespace {
 
 // spectral scales of the batch: lambda_max(A) and rho(Z_mu) to 1e-10
-// relative (alpha = alpha_rel / rho needs no more), searches on 32 threads
-#ifndef WL_SPEC_THREADS
-#define WL_SPEC_THREADS 32
-#endif
+// relative (alpha = alpha_rel / rho needs no more); up to 128 graphs'
+// searches in flight together
 constexpr double kSpecRtol = 1e-10;
-constexpr int kSpecThreads = WL_SPEC_THREADS;
+constexpr int kSpecThreads = 128;
 
 constexpr int kLoopHardCap = 1 << 20;  // body executions of one while node, whatever the flags say
 
@@ -583,6 +581,7 @@ int wl_batch_build(const wl_csr* graphs, int ngraph, const double* mus, int nmu,
   cudaEventRecord(t0, b->stream);
 
   // spectral scales: graphs spread over host threads, each on its own stream
+  int sp_rounds = 0;
   b->lmax.assign(ngraph, 0.0);
   b->rho.assign((size_t)ngraph * nmu, 0.0);
   {
@@ -592,13 +591,24 @@ int wl_batch_build(const wl_csr* graphs, int ngraph, const double* mus, int nmu,
     std::string msg;
     int dev = 0;
     cudaGetDevice(&dev);
-    // host threads each with its own stream: the searches on graphs of 1e3 - 2e5
-    // nodes are chains of small latency-bound launches, so more of them overlap
+    // One host thread per graph (up to kSpecThreads at a time), each with its
+    // own stream for its validation and lists; their Lanczos rounds meet in
+    // one SpBatch and run as shared launches over all graphs in flight.
     const int nth = std::min(ngraph, kSpecThreads);
+    SpBatch* spb = sp_batch_new(nth);
+    if (!spb) return fail(report_cuda_error(cudaGetLastError(), "cudaStreamCreate"));
     std::vector<std::thread> th;
     for (int t = 0; t < nth; ++t)
       th.emplace_back([&]() {
+        struct Leave {  // however the thread ends, the others stop waiting for it
+          SpBatch* b;
+          ~Leave() {
+            sp_batch_bind(nullptr);
+            sp_batch_leave(b);
+          }
+        } leave{spb};
         cudaSetDevice(dev);
+        sp_batch_bind(spb);
         cudaStream_t s = nullptr;
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
           err = WL_ERR_CUDA;
@@ -623,6 +633,8 @@ int wl_batch_build(const wl_csr* graphs, int ngraph, const double* mus, int nmu,
         cudaStreamDestroy(s);
       });
     for (auto& x : th) x.join();
+    sp_rounds = sp_batch_rounds(spb);
+    sp_batch_free(spb);
     if (err != WL_OK) {
       report_error(msg);
       return fail(err);
@@ -709,6 +721,7 @@ int wl_batch_build(const wl_csr* graphs, int ngraph, const double* mus, int nmu,
   cudaEventDestroy(t1);
   if (st) {
     st->time_ms = ms;
+    st->outer_iters = sp_rounds;
     st->status = WL_OK;
   }
   *out = b;

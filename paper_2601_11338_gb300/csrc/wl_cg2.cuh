@@ -245,20 +245,21 @@ __global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks<T>()) cg_s_phase
   const T* __restrict__ pr = a.r;
   struct Own {
     Pack<T, VW> r, x, p, q;
-    T dx;  // the row's shift diagonal (SH)
   };
-  // own-row vectors (and the shift diagonal), loaded before the row's gathers
-  // so the two overlap
+  // own-row r, loaded before the row's gathers so the two overlap
   auto own = [&](int64_t row) {
     Own o;
     const size_t off = (size_t)row * K + lane_off;
     o.r = ld_plain<T, VW>(pr + off);
-    if constexpr (SH) o.dx = __ldg(a.dshift + row);
     return o;
   };
   auto fin = [&](int64_t row, int deg, const T (&nb)[VW], const Own& w0) {
     const size_t o = (size_t)row * K + lane_off;
     Own w = w0;
+    // the shift diagonal is loaded with x, p, q after the gathers: held
+    // across them it costs the gather loop a register
+    T dx = T(0);
+    if constexpr (SH) dx = __ldg(a.dshift + row);
     if (!first) {
       w.x = ld_plain<T, VW>(px + o);
       w.p = ld_plain<T, VW>(pp_ + o);
@@ -267,8 +268,6 @@ __global__ void __launch_bounds__(kPhaseBlock, phase_min_blocks<T>()) cg_s_phase
     const Pack<T, VW>& rr = w.r;
     Pack<T, VW> pp, qq;
     const T dg = (T)deg;
-    T dx = T(0);
-    if constexpr (SH) dx = w.dx;
     if (first) {
 #pragma unroll
       for (int v = 0; v < VW; ++v) {

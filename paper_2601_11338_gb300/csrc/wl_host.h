@@ -174,6 +174,15 @@ cudaError_t launch_sp_steps(const SpArgs& a, int j0, int j1, int cap, int check,
                             int grid_u, cudaStream_t s);
 // Ritz vector of the run into W[1], |u|^2 and u^T D u into st->out[5], out[6]
 cudaError_t launch_sp_ritz(const SpArgs& a, int grid_u, cudaStream_t s);
+// One round of the batched spectral searches: the np jobs (device array) with
+// their CTA offsets in the S kernel (off_s, np + 1 entries, off_s[np] =
+// grid_s) and in the other row kernels (off_u, grid_u); `steps` Lanczos
+// steps (a job runs those of its j0 .. j1 - 1), the eigen step every `check`
+// steps and at j1, launched after the steps whose bit is set in eig_mask
+// (those where some job has one); each job's state into out[np].
+cudaError_t launch_sp_round(const SpJob* jobs, const int* off_s, const int* off_u, int np, int grid_s, int grid_u,
+                            int steps, int check, unsigned eig_mask, bool any_ritz, bool any_init, SpOut* out,
+                            cudaStream_t s);
 
 // ---- wl_k_trace.cu
 cudaError_t launch_philox_sketch(uint16_t* omega, int64_t n, int M, uint64_t seed, cudaStream_t s);
@@ -234,6 +243,17 @@ cudaError_t launch_mlp_predict(const float* P, const float* F, int64_t rows, con
 // ---- wl_api.cu (shared with the batched executor)
 int report_cuda_error(cudaError_t e, const char* where);
 void report_error(const std::string& msg);
+
+// Batched spectral searches (wl_api.cu): `participants` host threads each
+// bind the batch, run their graphs' searches (every Lanczos round waits until
+// all bound threads have one, then all run as shared launches on the batch's
+// stream) and leave it when done; free after all have left.
+struct SpBatch;
+SpBatch* sp_batch_new(int participants);
+void sp_batch_bind(SpBatch* b);  // the calling thread's searches go through b (nullptr: its own stream)
+void sp_batch_leave(SpBatch* b);
+int sp_batch_rounds(const SpBatch* b);
+void sp_batch_free(SpBatch* b);
 std::string last_error_copy();
 // rtol: relative accuracy of lambda_max(A) and rho(Z_mu) (0: wl_build's defaults)
 int graph_spectral(const wl_csr* A, const double* mus, int nmu, void* stream, double* lmax, double* rho,

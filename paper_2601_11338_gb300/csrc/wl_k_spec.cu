@@ -38,4 +38,20 @@ cudaError_t launch_sp_ritz(const SpArgs& a, int grid_u, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_sp_round(const SpJob* jobs, const int* off_s, const int* off_u, int np, int grid_s, int grid_u,
+                            int steps, int check, unsigned eig_mask, bool any_ritz, bool any_init, SpOut* out,
+                            cudaStream_t s) {
+  if (np <= 0) return cudaSuccess;
+  if (any_ritz) sp_ritz_multi<<<grid_u, kPhaseBlock, 0, s>>>(jobs, off_u, np);
+  sp_prep_multi<<<np, 128, 0, s>>>(jobs, np);
+  if (any_init) sp_init_multi<<<grid_u, kPhaseBlock, 0, s>>>(jobs, off_u, np);
+  for (int st = 0; st < steps; ++st) {
+    sp_s_multi<<<grid_s, kPhaseBlock, 0, s>>>(jobs, off_s, np, st);
+    sp_u_multi<<<grid_u, kPhaseBlock, 0, s>>>(jobs, off_u, np, st);
+    if (eig_mask >> st & 1u) sp_eig_multi<<<np, 2 * kSpEigT, 0, s>>>(jobs, np, st, check);
+  }
+  sp_pack_multi<<<(np + 127) / 128, 128, 0, s>>>(jobs, np, out);
+  return cudaGetLastError();
+}
+
 }  // namespace wl

@@ -53,6 +53,26 @@ struct SpArgs {
   uint64_t seed;
 };
 
+// One problem's share of a round of the batched searches (many graphs'
+// Lanczos runs advanced together, each with its own operator, basis and
+// state): an optional Ritz vector first, then the start of a run (or its
+// continuation) and steps j0 .. j1 - 1.
+struct SpJob {
+  SpArgs a;        // a.j is not used: step s of the round is j0 + s
+  double rtol;     // stopping bound of the run, relative to |theta_1|
+  int j0, j1, cap;
+  int mode;        // -1: no steps; 0: fresh seeded run; 1: new run from W[1]; 2: continue
+  int ritz;        // 1: Ritz vector of the current run into W[1] first
+  int gs, gu;      // CTAs of this problem in the S kernel and in the other row kernels
+};
+
+// A problem's state after a round (the fields of SpState the host reads)
+struct SpOut {
+  double start_norm;
+  double out[8];
+  int m_eff, stop, brk, pad;
+};
+
 #ifdef WL_SPEC_KERNELS
 __device__ __forceinline__ df ld_df2(const float2* p) {
   const float2 v = *p;
@@ -60,6 +80,41 @@ __device__ __forceinline__ df ld_df2(const float2* p) {
 }
 
 __device__ __forceinline__ void st_df2(float2* p, df v) { *p = make_float2(v.hi, v.lo); }
+
+// CTA sums of NV per-thread values written to part[b NV + c] for CTA b of
+// nb; the last of the nb CTAs to finish returns true (all partials visible
+// to it). The same arithmetic as the phase kernels' reduction for one lane
+// per row (butterfly over the warp, then the warps in order).
+template <int NV>
+__device__ __forceinline__ bool sp_partials_last(const double (&val)[NV], double* part, unsigned* ticket, int b,
+                                                 int nb) {
+  constexpr int NW = kPhaseBlock / 32;
+  __shared__ double s_w[NW * NV];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double a[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) a[v] = val[v];
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) a[v] += __shfl_xor_sync(0xffffffffu, a[v], off);
+  if (lane == 0)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s_w[warp * NV + v] = a[v];
+  __syncthreads();
+  if (tid < NV) {
+    double t = 0.0;
+    for (int w = 0; w < NW; ++w) t += s_w[w * NV + tid];
+    part[(size_t)b * NV + tid] = t;
+    __threadfence();
+  }
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(ticket, 1u) == (unsigned)nb - 1u) ? 1 : 0;
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
 
 __device__ inline double sp_start(int64_t i, uint64_t seed) {
   uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + seed;
@@ -69,19 +124,23 @@ __device__ inline double sp_start(int64_t i, uint64_t seed) {
   return 1.0 + 0.25 * ((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
 }
 
+// The kernel bodies take their CTA index b and CTA count nb: the
+// single-problem kernels pass blockIdx.x and gridDim.x, the batched ones the
+// CTA's place within its problem's share of the grid.
+
 // fresh run: seeded positive start vector into W[1], its norm, state reset
-__global__ void __launch_bounds__(kPhaseBlock) sp_init(SpArgs a) {
+__device__ __forceinline__ void sp_init_body(const SpArgs& a, int b, int nb) {
   __shared__ double s_tmp[kPhaseBlock];
   __shared__ double s_out[1];
   double acc[1] = {0.0};
   float2* W = a.W[1];
-  for (int64_t i = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; i < a.g.n; i += (int64_t)gridDim.x * kPhaseBlock) {
+  for (int64_t i = (int64_t)b * kPhaseBlock + threadIdx.x; i < a.g.n; i += (int64_t)nb * kPhaseBlock) {
     const float x = (float)sp_start(i, a.seed);  // any start vector will do: keep it exactly representable
     W[i] = make_float2(x, 0.f);
     acc[0] += (double)x * (double)x;
   }
-  if (!block_partials_last<double, 1>(acc, a.part, &a.st->ticket)) return;
-  sum_partials<1>(a.part, gridDim.x, s_tmp, s_out);
+  if (!sp_partials_last<1>(acc, a.part, &a.st->ticket, b, nb)) return;
+  sum_partials<1>(a.part, nb, s_tmp, s_out);
   if (threadIdx.x == 0) {
     a.st->start_norm = sqrt(s_out[0]);
     a.st->stop = 0;
@@ -93,7 +152,7 @@ __global__ void __launch_bounds__(kPhaseBlock) sp_init(SpArgs a) {
 
 // resume = 0: a new run from the vector in W[1] (whose norm is start_norm);
 // resume = 1: continue the current run (unless it broke down)
-__global__ void sp_restart(SpState* st, int resume) {
+__device__ __forceinline__ void sp_restart_body(SpState* st, int resume) {
   if (threadIdx.x == 0) {
     if (resume) {
       if (!st->brk) st->stop = 0;
@@ -106,18 +165,18 @@ __global__ void sp_restart(SpState* st, int resume) {
   }
 }
 
-__global__ void __launch_bounds__(kPhaseBlock) sp_s(SpArgs a) {
+__device__ __forceinline__ void sp_s_body(const SpArgs& a, int j, int b, int nb) {
   __shared__ float s_red[3][kPhaseBlock];
   __shared__ double s_tmp[kPhaseBlock];
   __shared__ double s_out[1];
   SpState* st = a.st;
   if (*(volatile int*)&st->stop) return;
-  const int j = a.j;
   const double bprev = (j == 0) ? st->start_norm : st->beta[j - 1];
   const df inv = df_from_double(1.0 / bprev);
   const df c0 = df_from_double(a.c0), cA = df_from_double(a.cA), cD = df_from_double(a.cD);
-  const float2* __restrict__ Wp = a.W[(j + 1) & 1];
-  float2* Wc = a.W[j & 1];
+  // selects, not an indexed load: the arguments stay in registers
+  const float2* __restrict__ Wp = (j & 1) ? a.W[0] : a.W[1];
+  float2* Wc = (j & 1) ? a.W[1] : a.W[0];
   float2* Vj = a.V + (size_t)j * a.g.n;
   const int tid = threadIdx.x;
   float aS = 0.f, aC = 0.f;
@@ -149,7 +208,6 @@ __global__ void __launch_bounds__(kPhaseBlock) sp_s(SpArgs a) {
       l += x0.y;
     }
   };
-  const int b = blockIdx.x;
   if (b < a.g.nhub) {
     const int64_t row = a.g.hubs[b];
     const int beg = a.g.row_ptr[row], end = a.g.row_ptr[row + 1];
@@ -193,7 +251,7 @@ __global__ void __launch_bounds__(kPhaseBlock) sp_s(SpArgs a) {
       if (lane == 0) fin(row, end - beg, s, c, l);
     }
   } else {
-    const int64_t nblk = (int64_t)gridDim.x - a.g.nhub - a.nmid_blk;
+    const int64_t nblk = (int64_t)nb - a.g.nhub - a.nmid_blk;
     const int bt = b - a.g.nhub - a.nmid_blk;
     const int lim = a.nmid_blk > 0 ? kSpWarpDeg : kHubDeg;
     for (int64_t row = (int64_t)bt * kPhaseBlock + tid; row < a.g.n; row += nblk * kPhaseBlock) {
@@ -205,42 +263,41 @@ __global__ void __launch_bounds__(kPhaseBlock) sp_s(SpArgs a) {
     }
   }
   double acc[1] = {(double)aS + (double)aC};
-  if (!block_partials_last<double, 1>(acc, a.part, &st->ticket)) return;
-  sum_partials<1>(a.part, gridDim.x, s_tmp, s_out);
+  if (!sp_partials_last<1>(acc, a.part, &st->ticket, b, nb)) return;
+  sum_partials<1>(a.part, nb, s_tmp, s_out);
   if (tid == 0) {
     st->alpha[j] = s_out[0];
     st->ticket = 0;
   }
 }
 
-__global__ void __launch_bounds__(kPhaseBlock) sp_u(SpArgs a, int last) {
+__device__ __forceinline__ void sp_u_body(const SpArgs& a, int j, int last, int b, int nb) {
   __shared__ double s_tmp[kPhaseBlock];
   __shared__ double s_out[1];
   SpState* st = a.st;
   if (*(volatile int*)&st->stop) return;
-  const int j = a.j;
   const double al = st->alpha[j];
   const double bp = (j == 0) ? 0.0 : st->beta[j - 1];
   const df dal = df_from_double(al), dbp = df_from_double(bp);
-  float2* Wc = a.W[j & 1];
+  float2* Wc = (j & 1) ? a.W[1] : a.W[0];
   const float2* Vj = a.V + (size_t)j * a.g.n;
   const float2* Vm = a.V + (size_t)(j > 0 ? j - 1 : 0) * a.g.n;
   float aS = 0.f, aC = 0.f;
-  for (int64_t i = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; i < a.g.n; i += (int64_t)gridDim.x * kPhaseBlock) {
+  for (int64_t i = (int64_t)b * kPhaseBlock + threadIdx.x; i < a.g.n; i += (int64_t)nb * kPhaseBlock) {
     df w = df_sub(ld_df2(Wc + i), df_mul(dal, ld_df2(Vj + i)));
     if (j > 0) w = df_sub(w, df_mul(dbp, ld_df2(Vm + i)));
     st_df2(Wc + i, w);
     df_acc2(aS, aC, df_mul(w, w));
   }
   double acc[1] = {(double)aS + (double)aC};
-  if (!block_partials_last<double, 1>(acc, a.part, &st->ticket)) return;
-  sum_partials<1>(a.part, gridDim.x, s_tmp, s_out);
+  if (!sp_partials_last<1>(acc, a.part, &st->ticket, b, nb)) return;
+  sum_partials<1>(a.part, nb, s_tmp, s_out);
   if (threadIdx.x == 0) {
-    const double b = sqrt(fmax(s_out[0], 0.0));
-    st->beta[j] = b;
+    const double bj = sqrt(fmax(s_out[0], 0.0));
+    st->beta[j] = bj;
     st->m_eff = j + 1;
     // invariant subspace reached: T_{j+1} is exact
-    if (!(b > 1e-13 * (fabs(al) + bp + 1e-300))) {
+    if (!(bj > 1e-13 * (fabs(al) + bp + 1e-300))) {
       st->brk = 1;
       st->stop = 1;
     } else if (last) {
@@ -279,21 +336,53 @@ __device__ inline int sturm_count_poly(const double* a, const double* b2, int m,
   return cnt;
 }
 
-// Two largest eigenvalues of T_m by multisection (a group of kSpEigT threads
-// per eigenvalue, kSpEigRounds rounds of kSpEigT Sturm counts: 129^7 > 1e14),
+// Sturm count in FP32 by the pivot recurrence d_i = (a_i - x) - b_{i-1}^2 /
+// d_{i-1} (the number of negative pivots of T - x I); a pivot of magnitude
+// below `tiny` is replaced by -tiny. Used only to bracket eigenvalues
+// coarsely: the bracket is widened and checked in FP64 before it is used.
+__device__ inline int sturm_count_f32(const float* a, const float* b2, int m, float x) {
+  constexpr float tiny = 1e-30f;
+  float d = a[0] - x;
+  if (fabsf(d) < tiny) d = -tiny;
+  int cnt = (d < 0.f) ? 1 : 0;
+  for (int i = 1; i < m; ++i) {
+    d = (a[i] - x) - b2[i - 1] / d;
+    if (fabsf(d) < tiny) d = -tiny;
+    cnt += (d < 0.f) ? 1 : 0;
+  }
+  return cnt;
+}
+
+// Two largest eigenvalues of T_m (a group of kSpEigT threads per eigenvalue),
 // then the top eigenvector by inverse iteration and the error bound; stops
-// the run when the bound is below rtol |theta_1|. T_m, its squared
-// off-diagonal and the inverse-iteration vectors are staged in shared memory
-// (the serial sweeps of one thread would otherwise wait on global memory at
-// every row).
+// the run when the bound is below rtol |theta_1|. FP64 runs at 1/64 of the
+// FP32 rate on this GPU and the Sturm counts are its whole cost, so:
+//   1. kSpEigCoarse rounds of FP32 multisection (kSpEigT points each) from
+//      the Gershgorin interval bracket each eigenvalue to about 1e-6 ||T||;
+//   2. the bracket, widened by kSpEigMargin ||T|| on both sides, is checked
+//      by two FP64 Sturm counts;
+//   3. kSpEigFine rounds of FP64 multisection on kSpEigFineT threads per
+//      eigenvalue narrow it below 1e-16 ||T||.
+// If a check fails (the FP32 counts were wrong, or T overflows FP32), the
+// eigenvalue is found as before: kSpEigRounds rounds of FP64 multisection on
+// kSpEigT threads from the Gershgorin interval (129^7 > 1e14).
+// T_m, its squared off-diagonal and the inverse-iteration vectors are staged
+// in shared memory (the serial sweeps of one thread would otherwise wait on
+// global memory at every row).
 constexpr int kSpEigT = 128;
 constexpr int kSpEigRounds = 7;
+constexpr int kSpEigCoarse = 3;     // 129^3 > 2e6: the FP32 bracket is below 1e-6 of the interval
+constexpr double kSpEigMargin = 1e-5;
+constexpr int kSpEigFineT = 8;
+constexpr int kSpEigFine = 12;      // 9^12 > 2.8e11: from 2.1e-5 ||T|| to below 1e-16 ||T||
 
-__global__ void __launch_bounds__(2 * kSpEigT) sp_eig(SpState* st, double rtol) {
+__device__ __forceinline__ void sp_eig_body(SpState* st, double rtol) {
   __shared__ double s_lo[2], s_hi[2];
   __shared__ int s_cnt[2][kSpEigT];
+  __shared__ int s_ok[2];
   __shared__ double s_a[kSpMax], s_b[kSpMax], s_b2[kSpMax], s_y[kSpMax], s_cp[kSpMax];
-  __shared__ double s_tn;
+  __shared__ float s_af[kSpMax], s_b2f[kSpMax];
+  __shared__ double s_tn, s_glo, s_ghi;
   const int m = st->m_eff;
   if (m <= 0 || m > kSpMax) return;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -301,6 +390,8 @@ __global__ void __launch_bounds__(2 * kSpEigT) sp_eig(SpState* st, double rtol) 
     s_a[i] = a;
     s_b[i] = b;
     s_b2[i] = b * b;
+    s_af[i] = (float)a;
+    s_b2f[i] = (float)(b * b);
   }
   __syncthreads();
   const int grp = threadIdx.x / kSpEigT, t = threadIdx.x % kSpEigT;
@@ -313,14 +404,15 @@ __global__ void __launch_bounds__(2 * kSpEigT) sp_eig(SpState* st, double rtol) 
       hi = fmax(hi, s_a[i] + r);
       tn = fmax(tn, fabs(s_a[i]) + r);
     }
-    s_lo[0] = s_lo[1] = lo;
-    s_hi[0] = s_hi[1] = hi;
+    s_lo[0] = s_lo[1] = s_glo = lo;
+    s_hi[0] = s_hi[1] = s_ghi = hi;
     s_tn = tn;
   }
   __syncthreads();
-  for (int round = 0; round < kSpEigRounds; ++round) {
+  // (1) FP32 multisection
+  for (int round = 0; round < kSpEigCoarse; ++round) {
     const double lo = s_lo[grp], w = s_hi[grp] - lo;
-    s_cnt[grp][t] = sturm_count_poly(s_a, s_b2, m, lo + w * (double)(t + 1) / (double)(kSpEigT + 1));
+    s_cnt[grp][t] = sturm_count_f32(s_af, s_b2f, m, (float)(lo + w * (double)(t + 1) / (double)(kSpEigT + 1)));
     __syncthreads();
     if (t == 0) {
       int k = 0;
@@ -329,6 +421,52 @@ __global__ void __launch_bounds__(2 * kSpEigT) sp_eig(SpState* st, double rtol) 
       s_hi[grp] = lo + w * (double)(k + 1) / (double)(kSpEigT + 1);
     }
     __syncthreads();
+  }
+  // (2) widen and check in FP64: count(lo) <= idx < count(hi)
+  if (t == 0) {
+    const double mg = kSpEigMargin * s_tn;
+    const double lo = fmax(s_glo, s_lo[grp] - mg), hi = fmin(s_ghi, s_hi[grp] + mg);
+    const bool ok = hi > lo && sturm_count_poly(s_a, s_b2, m, lo) <= idx && sturm_count_poly(s_a, s_b2, m, hi) > idx;
+    s_ok[grp] = ok ? 1 : 0;
+    s_lo[grp] = ok ? lo : s_glo;
+    s_hi[grp] = ok ? hi : s_ghi;
+  }
+  __syncthreads();
+  // (3) FP64 multisection: narrow on few threads, or the full one from the
+  // Gershgorin interval where the check failed (both loops are uniform over
+  // the block: the barriers inside them are reached by every thread)
+  const bool fine = s_ok[0] && s_ok[1];
+  const int rounds = fine ? kSpEigFine : kSpEigRounds;
+  for (int round = 0; round < rounds; ++round) {
+    const bool nar = s_ok[grp] != 0;
+    const int pts = nar ? kSpEigFineT : kSpEigT;
+    const bool act = fine ? true : !nar;  // a group already checked waits while the other runs the full search
+    const double lo = s_lo[grp], w = s_hi[grp] - lo;
+    if (act && t < pts) s_cnt[grp][t] = sturm_count_poly(s_a, s_b2, m, lo + w * (double)(t + 1) / (double)(pts + 1));
+    __syncthreads();
+    if (act && t == 0) {
+      int k = 0;
+      while (k < pts && s_cnt[grp][k] <= idx) ++k;
+      s_lo[grp] = lo + w * (double)k / (double)(pts + 1);
+      s_hi[grp] = lo + w * (double)(k + 1) / (double)(pts + 1);
+    }
+    __syncthreads();
+  }
+  if (!fine) {  // the checked group (if any) finishes its narrow search now
+    for (int round = 0; round < kSpEigFine; ++round) {
+      const bool act = s_ok[grp] != 0;
+      const double lo = s_lo[grp], w = s_hi[grp] - lo;
+      if (act && t < kSpEigFineT)
+        s_cnt[grp][t] = sturm_count_poly(s_a, s_b2, m, lo + w * (double)(t + 1) / (double)(kSpEigFineT + 1));
+      __syncthreads();
+      if (act && t == 0) {
+        int k = 0;
+        while (k < kSpEigFineT && s_cnt[grp][k] <= idx) ++k;
+        s_lo[grp] = lo + w * (double)k / (double)(kSpEigFineT + 1);
+        s_hi[grp] = lo + w * (double)(k + 1) / (double)(kSpEigFineT + 1);
+      }
+      __syncthreads();
+    }
   }
   if (threadIdx.x == 0) {
     const double th1 = 0.5 * (s_lo[0] + s_hi[0]);
@@ -380,7 +518,7 @@ __global__ void __launch_bounds__(2 * kSpEigT) sp_eig(SpState* st, double rtol) 
 
 // Ritz vector u = V_m y into W[1] (the start of the next run), |u|^2 and
 // u^T D u into out[5], out[6], start_norm = |u|
-__global__ void __launch_bounds__(kPhaseBlock) sp_ritz(SpArgs a) {
+__device__ __forceinline__ void sp_ritz_body(const SpArgs& a, int b, int nb) {
   __shared__ double s_tmp[kPhaseBlock];
   __shared__ double s_out[2];
   __shared__ float s_y[2][kSpMax];
@@ -394,7 +532,7 @@ __global__ void __launch_bounds__(kPhaseBlock) sp_ritz(SpArgs a) {
   __syncthreads();
   float nS = 0.f, nC = 0.f, dS = 0.f, dC = 0.f;
   float2* U = a.W[1];
-  for (int64_t i = (int64_t)blockIdx.x * kPhaseBlock + threadIdx.x; i < a.g.n; i += (int64_t)gridDim.x * kPhaseBlock) {
+  for (int64_t i = (int64_t)b * kPhaseBlock + threadIdx.x; i < a.g.n; i += (int64_t)nb * kPhaseBlock) {
     float s = 0.f, c = 0.f;
     for (int j = 0; j < m; ++j) df_acc2(s, c, df_mul(df{s_y[0][j], s_y[1][j]}, ld_df2(a.V + (size_t)j * a.g.n + i)));
     const df u = two_sum(s, c);
@@ -405,14 +543,118 @@ __global__ void __launch_bounds__(kPhaseBlock) sp_ritz(SpArgs a) {
   }
   // two column sums through the K = 2 reduction (deterministic)
   double acc[2] = {(double)nS + (double)nC, (double)dS + (double)dC};
-  if (!block_partials_last<double, 2>(acc, a.part, &st->ticket)) return;
-  sum_partials<2>(a.part, gridDim.x, s_tmp, s_out);
+  if (!sp_partials_last<2>(acc, a.part, &st->ticket, b, nb)) return;
+  sum_partials<2>(a.part, nb, s_tmp, s_out);
   if (threadIdx.x == 0) {
     st->out[5] = s_out[0];
     st->out[6] = s_out[1];
     st->start_norm = sqrt(s_out[0]);
     st->ticket = 0;
   }
+}
+
+// ---------------------------------------------------------------- one problem
+__global__ void __launch_bounds__(kPhaseBlock) sp_init(SpArgs a) { sp_init_body(a, blockIdx.x, gridDim.x); }
+__global__ void sp_restart(SpState* st, int resume) { sp_restart_body(st, resume); }
+__global__ void __launch_bounds__(kPhaseBlock) sp_s(SpArgs a) { sp_s_body(a, a.j, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(kPhaseBlock) sp_u(SpArgs a, int last) {
+  sp_u_body(a, a.j, last, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(2 * kSpEigT) sp_eig(SpState* st, double rtol) { sp_eig_body(st, rtol); }
+__global__ void __launch_bounds__(kPhaseBlock) sp_ritz(SpArgs a) { sp_ritz_body(a, blockIdx.x, gridDim.x); }
+
+// ---------------------------------------------------------------- many problems
+// The grid of a batched row kernel is the concatenation of the problems'
+// shares: problem p owns CTAs off[p] .. off[p + 1] - 1 (off[np] = grid).
+// Each CTA copies its problem's arguments into registers first: read in
+// place, every field would be reloaded after each store (the stores could
+// alias the job array).
+__device__ __forceinline__ int sp_job_of(const int* __restrict__ off, int np, int b) {
+  int lo = 0, hi = np;  // the p with off[p] <= b < off[p + 1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= b) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Ritz vectors of the jobs that ask for one (CTAs by the gu offsets)
+__global__ void __launch_bounds__(kPhaseBlock) sp_ritz_multi(const SpJob* __restrict__ jobs,
+                                                             const int* __restrict__ off_u, int np) {
+  const int p = sp_job_of(off_u, np, blockIdx.x);
+  if (!jobs[p].ritz) return;
+  const SpArgs a = jobs[p].a;
+  sp_ritz_body(a, blockIdx.x - off_u[p], off_u[p + 1] - off_u[p]);
+}
+
+// Start of each job's run: one CTA per job. Mode 0 clears the whole state
+// (tickets and flags start at zero, as the fresh run's init kernel needs).
+__global__ void sp_prep_multi(const SpJob* __restrict__ jobs, int np) {
+  const int p = blockIdx.x;
+  if (p >= np) return;
+  const SpJob& jb = jobs[p];
+  if (jb.mode == 0) {
+    uint32_t* w = (uint32_t*)jb.a.st;
+    for (int i = threadIdx.x; i < (int)(sizeof(SpState) / 4); i += blockDim.x) w[i] = 0u;
+  } else if (jb.mode == 1 || jb.mode == 2) {
+    sp_restart_body(jb.a.st, jb.mode == 2 ? 1 : 0);
+  }
+}
+
+__global__ void __launch_bounds__(kPhaseBlock) sp_init_multi(const SpJob* __restrict__ jobs,
+                                                             const int* __restrict__ off_u, int np) {
+  const int p = sp_job_of(off_u, np, blockIdx.x);
+  if (jobs[p].mode != 0) return;
+  const SpArgs a = jobs[p].a;
+  sp_init_body(a, blockIdx.x - off_u[p], off_u[p + 1] - off_u[p]);
+}
+
+// step j0 + s of every job that has it
+__global__ void __launch_bounds__(kPhaseBlock) sp_s_multi(const SpJob* __restrict__ jobs,
+                                                          const int* __restrict__ off_s, int np, int s) {
+  const int p = sp_job_of(off_s, np, blockIdx.x);
+  const int j = jobs[p].j0 + s;
+  if (jobs[p].mode < 0 || j >= jobs[p].j1) return;
+  const SpArgs a = jobs[p].a;
+  sp_s_body(a, j, blockIdx.x - off_s[p], off_s[p + 1] - off_s[p]);
+}
+
+__global__ void __launch_bounds__(kPhaseBlock) sp_u_multi(const SpJob* __restrict__ jobs,
+                                                          const int* __restrict__ off_u, int np, int s) {
+  const int p = sp_job_of(off_u, np, blockIdx.x);
+  const int j = jobs[p].j0 + s;
+  if (jobs[p].mode < 0 || j >= jobs[p].j1) return;
+  const int last = (j == jobs[p].cap - 1) ? 1 : 0;
+  const SpArgs a = jobs[p].a;
+  sp_u_body(a, j, last, blockIdx.x - off_u[p], off_u[p + 1] - off_u[p]);
+}
+
+// the eigen step after step j0 + s of the jobs whose check falls there (every
+// `check` steps and at the round's last step), one CTA per job
+__global__ void __launch_bounds__(2 * kSpEigT) sp_eig_multi(const SpJob* __restrict__ jobs, int np, int s,
+                                                            int check) {
+  const int p = blockIdx.x;
+  if (p >= np) return;
+  const SpJob& jb = jobs[p];
+  const int j = jb.j0 + s;
+  if (jb.mode < 0 || j >= jb.j1) return;
+  if ((j + 1) % check != 0 && j + 1 != jb.j1) return;
+  sp_eig_body(jb.a.st, jb.rtol);
+}
+
+// the host's copy of every job's state
+__global__ void sp_pack_multi(const SpJob* __restrict__ jobs, int np, SpOut* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const SpState* st = jobs[p].a.st;
+  SpOut o;
+  o.start_norm = st->start_norm;
+  for (int i = 0; i < 8; ++i) o.out[i] = st->out[i];
+  o.m_eff = st->m_eff;
+  o.stop = st->stop;
+  o.brk = st->brk;
+  o.pad = 0;
+  out[p] = o;
 }
 #endif  // WL_SPEC_KERNELS
 
