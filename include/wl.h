@@ -378,10 +378,12 @@ typedef struct wl_batch wl_batch;
  * p->alpha is used for all; every problem must have alpha rho(Z_mu) < 1
  * (else WL_ERR_ALPHA_RANGE). p->prec is WL_FP64 or WL_REFINED; tol,
  * max_iter, max_outer and stream as in wl_build. Synchronous. The spectral
- * searches of all graphs run together: each round of Lanczos steps is one
- * launch per kernel and step over every graph in flight (the values equal
- * those of a search on each graph alone). st may be NULL: time_ms, status,
- * outer_iters = the rounds of those shared searches. */
+ * searches (lambda_max(A) and rho(Z_mu) to 1e-10 relative) of all graphs run
+ * together: each round of Lanczos steps is one launch per kernel and step
+ * over every search in flight, and the searches of a graph's mu values > 0
+ * run side by side, each from the Ritz vector of its lambda_max(A) run. st
+ * may be NULL: time_ms, status, outer_iters = the rounds of those shared
+ * searches. */
 int wl_batch_build(const wl_csr* graphs, int ngraph, const double* mus, int nmu, const wl_params* p,
                    wl_batch** out, wl_stats* st);
 

@@ -15,6 +15,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -286,6 +287,16 @@ SpBatch* sp_batch_new(int participants) {
 }
 
 void sp_batch_bind(SpBatch* b) { t_sp_batch = b; }
+
+// k more participants. A round waits for every participant, and none can run
+// while the caller (a participant not waiting) has not submitted, so the
+// count can grow at any time the caller chooses.
+void sp_batch_join(SpBatch* b, int k) {
+  std::unique_lock<std::mutex> lk(b->m);
+  b->live += k;
+}
+
+SpBatch* sp_batch_current() { return t_sp_batch; }
 
 void sp_batch_leave(SpBatch* b) {
   std::unique_lock<std::mutex> lk(b->m);
@@ -2576,9 +2587,65 @@ int report_cuda_error(cudaError_t e, const char* where) { return set_cuda_error(
 void report_error(const std::string& msg) { g_last_error = msg; }
 std::string last_error_copy() { return g_last_error; }
 
+namespace {
+// A second search context on the graph of h, for a search that runs beside
+// others: it borrows h's graph, row lists and stream and owns its Lanczos
+// basis and state, which start as copies of h's (so its first run starts
+// from h's last Ritz vector).
+int sp_clone(wl_handle* h, wl_handle** out) {
+  wl_handle* c = new wl_handle();
+  c->n = h->n;
+  c->nnz = h->nnz;
+  c->variant = h->variant;
+  c->prm = h->prm;
+  c->stream = h->stream;
+  c->g = h->g;
+  c->hubs = h->hubs;  // borrowed: cleared before the clone is freed
+  c->mid = h->mid;
+  c->nhub = h->nhub;
+  c->nmid = h->nmid;
+  c->nmid_blk = h->nmid_blk;
+  c->lmax = h->lmax;
+  c->sp_c0 = h->sp_c0;
+  c->sp_cD = h->sp_cD;
+  c->sp_theta = h->sp_theta;
+  c->sp_ritz_ready = h->sp_ritz_ready;
+  c->sp_ritz_uu = h->sp_ritz_uu;
+  c->sp_ritz_udu = h->sp_ritz_udu;
+  auto fail = [&](int rc) {
+    c->hubs = Buf{};
+    c->mid = Buf{};
+    free_handle(c);
+    return rc;
+  };
+  if (pool_malloc_host((void**)&c->h_pin, 4096 * sizeof(double)) != cudaSuccess)
+    return fail(set_cuda_error(cudaGetLastError(), "cudaMallocHost"));
+  int rc = sp_buffers(c, sp_grid(c) + c->nhub + c->nmid_blk);
+  if (rc != WL_OK) return fail(rc);
+  cudaError_t e = cudaMemcpyAsync(c->spW.p, h->spW.p, (size_t)2 * h->n * 8, cudaMemcpyDeviceToDevice, S(h));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->spstate.p, h->spstate.p, sizeof(SpState), cudaMemcpyDeviceToDevice, S(h));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S(h));
+  if (e != cudaSuccess) return fail(set_cuda_error(e, "search context copy"));
+  *out = c;
+  return WL_OK;
+}
+
+void sp_clone_free(wl_handle* c) {
+  if (!c) return;
+  c->hubs = Buf{};
+  c->mid = Buf{};
+  free_handle(c);
+}
+}  // namespace
+
 // Spectral scale of one graph for several mu values (Sec. 4.1): validates
 // the CSR as wl_build does, then lambda_max(A) and rho(Z_mu) for each mu
-// (rho(Z_0) = lambda_max(A)).
+// (rho(Z_0) = lambda_max(A)). Inside a batched build (the calling thread
+// bound to an SpBatch) the searches of the mu values > 0 run side by side,
+// each on its own thread and search context started from the Ritz vector of
+// the lambda_max(A) run, so that the batch's rounds advance them together;
+// elsewhere they run one after another, each from the previous one's Ritz
+// vector.
 int graph_spectral(const wl_csr* A, const double* mus, int nmu, void* stream, double* lmax, double* rho,
                    double rtol) {
   struct RtolScope {
@@ -2586,6 +2653,8 @@ int graph_spectral(const wl_csr* A, const double* mus, int nmu, void* stream, do
     explicit RtolScope(double r) : old(t_spec_rtol) { t_spec_rtol = r; }
     ~RtolScope() { t_spec_rtol = old; }
   } rs(rtol);
+  for (int i = 0; i < nmu; ++i)
+    if (!(mus[i] >= 0.0 && mus[i] <= 1.0)) return WL_ERR_INVALID_ARG;
   wl_params p;
   memset(&p, 0, sizeof(p));
   p.f = WL_F_IDENTITY;
@@ -2596,16 +2665,64 @@ int graph_spectral(const wl_csr* A, const double* mus, int nmu, void* stream, do
   int rc = wl_build(A, WL_ALLWALK, &p, &h, nullptr);
   if (rc != WL_OK) return rc;
   *lmax = h->lmax;
-  for (int i = 0; i < nmu && rc == WL_OK; ++i) {
-    if (!(mus[i] >= 0.0 && mus[i] <= 1.0)) {
-      rc = WL_ERR_INVALID_ARG;
-      break;
+  std::vector<int> todo;
+  for (int i = 0; i < nmu; ++i) {
+    if (h->n == 0 || h->nnz == 0 || mus[i] == 0.0)
+      rho[i] = (h->n == 0 || h->nnz == 0) ? 0.0 : h->lmax;
+    else
+      todo.push_back(i);
+  }
+  SpBatch* bt = sp_batch_current();
+  if (!bt || todo.size() <= 1) {
+    for (int i : todo) {
+      rc = rho_companion(h, mus[i], h->lmax, &rho[i]);
+      if (rc != WL_OK) break;
     }
-    if (h->n == 0 || h->nnz == 0) {
-      rho[i] = 0.0;
-      continue;
+    wl_destroy(h);
+    return rc;
+  }
+  // the Ritz vector of the lambda_max(A) run, then one context per search
+  // (the first search runs on h itself, the others on copies made first)
+  double q = 0.0, uAu = 0.0;
+  rc = sp_ritz_q(h, &q, &uAu);
+  std::vector<wl_handle*> ctx(todo.size(), nullptr);
+  ctx[0] = h;
+  for (size_t k = 1; k < todo.size() && rc == WL_OK; ++k) rc = sp_clone(h, &ctx[k]);
+  if (rc != WL_OK) {
+    for (size_t k = 1; k < ctx.size(); ++k) sp_clone_free(ctx[k]);
+    wl_destroy(h);
+    return rc;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<int> rcs(todo.size(), WL_OK);
+  std::vector<std::string> msgs(todo.size());
+  sp_batch_join(bt, (int)todo.size());  // the searches join before this thread leaves
+  std::vector<std::thread> th;
+  for (size_t k = 0; k < todo.size(); ++k)
+    th.emplace_back([&, k]() {
+      struct Leave {
+        SpBatch* b;
+        ~Leave() {
+          sp_batch_bind(nullptr);
+          sp_batch_leave(b);
+        }
+      } leave{bt};
+      cudaSetDevice(dev);
+      sp_batch_bind(bt);
+      RtolScope r2(rtol);
+      rcs[k] = rho_companion(ctx[k], mus[todo[k]], h->lmax, &rho[todo[k]]);
+      if (rcs[k] != WL_OK) msgs[k] = last_error_copy();
+    });
+  sp_batch_leave(bt);  // this thread submits nothing while it waits
+  for (auto& x : th) x.join();
+  sp_batch_join(bt, 1);
+  for (size_t k = 0; k < todo.size(); ++k) {
+    if (rc == WL_OK && rcs[k] != WL_OK) {
+      rc = rcs[k];
+      report_error(msgs[k]);
     }
-    rc = rho_companion(h, mus[i], h->lmax, &rho[i]);
+    if (k > 0) sp_clone_free(ctx[k]);
   }
   wl_destroy(h);
   return rc;

@@ -251,7 +251,9 @@ void report_error(const std::string& msg);
 struct SpBatch;
 SpBatch* sp_batch_new(int participants);
 void sp_batch_bind(SpBatch* b);  // the calling thread's searches go through b (nullptr: its own stream)
+void sp_batch_join(SpBatch* b, int k);  // k more participants (called by a participant that is not waiting)
 void sp_batch_leave(SpBatch* b);
+SpBatch* sp_batch_current();  // the calling thread's batch, or nullptr
 int sp_batch_rounds(const SpBatch* b);
 void sp_batch_free(SpBatch* b);
 std::string last_error_copy();

@@ -346,63 +346,132 @@ __device__ inline int sturm_count_f32(const float* a, const float* b2, int m, fl
   if (fabsf(d) < tiny) d = -tiny;
   int cnt = (d < 0.f) ? 1 : 0;
   for (int i = 1; i < m; ++i) {
-    d = (a[i] - x) - b2[i - 1] / d;
+    d = (a[i] - x) - __fdividef(b2[i - 1], d);  // |d| >= tiny keeps the fast division in range
     if (fabsf(d) < tiny) d = -tiny;
     cnt += (d < 0.f) ? 1 : 0;
   }
   return cnt;
 }
 
+// Sturm count (eigenvalues below x) in double-float arithmetic: the scaled
+// three-term determinant recurrence of sturm_count_poly on FP32 pairs. A
+// dependent FP64 operation costs about a hundred cycles on this GPU, the
+// FP32 operations of a double-float one a few each.
+__device__ inline int sturm_count_df(const float* ah, const float* al, const float* bh, const float* bl, int m,
+                                     df x) {
+  df pm{1.f, 0.f};
+  df p = df_sub(df{ah[0], al[0]}, x);
+  int cnt = (p.hi < 0.f) ? 1 : 0;
+  float sprev = (p.hi == 0.f) ? -1.f : p.hi;
+  for (int i = 1; i < m; ++i) {
+    const df pn = df_sub(df_mul(df_sub(df{ah[i], al[i]}, x), p), df_mul(df{bh[i - 1], bl[i - 1]}, pm));
+    pm = p;
+    p = pn;
+    const float ap = fabsf(p.hi);
+    if (ap > 0x1p64f) {
+      p = df{p.hi * 0x1p-64f, p.lo * 0x1p-64f};
+      pm = df{pm.hi * 0x1p-64f, pm.lo * 0x1p-64f};
+    } else if (ap < 0x1p-64f && fabsf(pm.hi) < 0x1p-64f) {
+      p = df{p.hi * 0x1p64f, p.lo * 0x1p64f};
+      pm = df{pm.hi * 0x1p64f, pm.lo * 0x1p64f};
+    }
+    const float sc = (p.hi == 0.f) ? -sprev : p.hi;
+    if ((sc < 0.f) != (sprev < 0.f)) ++cnt;
+    sprev = sc;
+  }
+  return cnt;
+}
+
+// 1/a in double-float: an approximate FP32 reciprocal of a.hi and one
+// correction step (|a.hi| between 2^-126 and 2^126)
+__device__ __forceinline__ df df_rcp(df a) {
+  const float r0 = __fdividef(1.f, a.hi);
+  const df e = df_sub(df{1.f, 0.f}, df_mul_f(a, r0));
+  return df_add(df{r0, 0.f}, df_mul_f(e, r0));
+}
+
 // Two largest eigenvalues of T_m (a group of kSpEigT threads per eigenvalue),
 // then the top eigenvector by inverse iteration and the error bound; stops
-// the run when the bound is below rtol |theta_1|. FP64 runs at 1/64 of the
-// FP32 rate on this GPU and the Sturm counts are its whole cost, so:
+// the run when the bound is below rtol |theta_1|. A dependent FP64 operation
+// costs about a hundred cycles on this GPU (measured: a Sturm count over 256
+// rows took 200k cycles in FP64), so the serial work runs in FP32 and
+// double-float:
 //   1. kSpEigCoarse rounds of FP32 multisection (kSpEigT points each) from
 //      the Gershgorin interval bracket each eigenvalue to about 1e-6 ||T||;
 //   2. the bracket, widened by kSpEigMargin ||T|| on both sides, is checked
-//      by two FP64 Sturm counts;
-//   3. kSpEigFine rounds of FP64 multisection on kSpEigFineT threads per
-//      eigenvalue narrow it below 1e-16 ||T||.
-// If a check fails (the FP32 counts were wrong, or T overflows FP32), the
-// eigenvalue is found as before: kSpEigRounds rounds of FP64 multisection on
-// kSpEigT threads from the Gershgorin interval (129^7 > 1e14).
-// T_m, its squared off-diagonal and the inverse-iteration vectors are staged
-// in shared memory (the serial sweeps of one thread would otherwise wait on
-// global memory at every row).
+//      by two double-float Sturm counts;
+//   3. kSpEigFine rounds of double-float multisection narrow it to about
+//      1e-14 ||T|| (the resolution of double-float counts; the searches
+//      stop at 1e-10 to 1e-12 of theta_1);
+//   4. inverse iteration in double-float gives the eigenvector.
+// If a check fails (the FP32 counts were wrong, or T overflows FP32), that
+// eigenvalue is found as before: kSpEigRounds rounds of FP64 multisection
+// from the Gershgorin interval (129^7 > 1e14).
 constexpr int kSpEigT = 128;
 constexpr int kSpEigRounds = 7;
 constexpr int kSpEigCoarse = 3;     // 129^3 > 2e6: the FP32 bracket is below 1e-6 of the interval
-constexpr double kSpEigMargin = 1e-5;
-constexpr int kSpEigFineT = 8;
-constexpr int kSpEigFine = 12;      // 9^12 > 2.8e11: from 2.1e-5 ||T|| to below 1e-16 ||T||
+constexpr double kSpEigMargin = 1e-6;
+constexpr int kSpEigFine = 4;       // 129^4 > 2.7e8: from 2.9e-6 ||T|| to 1.1e-14 ||T||
+static_assert(kSpEigFine <= kSpEigRounds, "the narrow search ends within the full one");
+static_assert(2 * kSpEigT == kSpMax, "one row per thread in the eigen step");
 
 __device__ __forceinline__ void sp_eig_body(SpState* st, double rtol) {
   __shared__ double s_lo[2], s_hi[2];
   __shared__ int s_cnt[2][kSpEigT];
   __shared__ int s_ok[2];
-  __shared__ double s_a[kSpMax], s_b[kSpMax], s_b2[kSpMax], s_y[kSpMax], s_cp[kSpMax];
+  __shared__ double s_a[kSpMax], s_b[kSpMax], s_b2[kSpMax];
   __shared__ float s_af[kSpMax], s_b2f[kSpMax];
-  __shared__ double s_tn, s_glo, s_ghi;
+  __shared__ float s_ah[kSpMax], s_al[kSpMax], s_qh[kSpMax], s_ql[kSpMax];  // a and b^2 as pairs
+  __shared__ float s_bh[kSpMax], s_bl[kSpMax];                              // b as pairs
+  __shared__ float s_yh[kSpMax], s_yl[kSpMax], s_ch[kSpMax], s_cl[kSpMax];  // inverse iteration
+  __shared__ double s_red[3][kSpEigT * 2 / 32];
+  __shared__ double s_tn, s_glo, s_ghi, s_nn;
   const int m = st->m_eff;
   if (m <= 0 || m > kSpMax) return;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const double a = st->alpha[i], b = (i + 1 < m) ? st->beta[i] : 0.0;
-    s_a[i] = a;
-    s_b[i] = b;
-    s_b2[i] = b * b;
-    s_af[i] = (float)a;
-    s_b2f[i] = (float)(b * b);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // one row per thread (m <= kSpMax = blockDim): staging and the Gershgorin
+  // interval by a block reduction
+  double glo = 1e300, ghi = -1e300, gtn = 0.0;
+  if (tid < m) {
+    const double a = st->alpha[tid], b = (tid + 1 < m) ? st->beta[tid] : 0.0;
+    const double bp = (tid > 0) ? st->beta[tid - 1] : 0.0;
+    s_a[tid] = a;
+    s_b[tid] = b;
+    s_b2[tid] = b * b;
+    s_af[tid] = (float)a;
+    s_b2f[tid] = (float)(b * b);
+    const df ad = df_from_double(a), qd = df_from_double(b * b), bd = df_from_double(b);
+    s_ah[tid] = ad.hi;
+    s_al[tid] = ad.lo;
+    s_qh[tid] = qd.hi;
+    s_ql[tid] = qd.lo;
+    s_bh[tid] = bd.hi;
+    s_bl[tid] = bd.lo;
+    const double r = fabs(bp) + fabs(b);
+    glo = a - r;
+    ghi = a + r;
+    gtn = fabs(a) + r;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, off));
+    ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, off));
+    gtn = fmax(gtn, __shfl_xor_sync(0xffffffffu, gtn, off));
+  }
+  if (lane == 0) {
+    s_red[0][warp] = glo;
+    s_red[1][warp] = ghi;
+    s_red[2][warp] = gtn;
   }
   __syncthreads();
-  const int grp = threadIdx.x / kSpEigT, t = threadIdx.x % kSpEigT;
+  const int grp = tid / kSpEigT, t = tid % kSpEigT;
   const int idx = grp == 0 ? m - 1 : (m >= 2 ? m - 2 : m - 1);
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double lo = 1e300, hi = -1e300, tn = 0.0;
-    for (int i = 0; i < m; ++i) {
-      const double r = (i > 0 ? fabs(s_b[i - 1]) : 0.0) + fabs(s_b[i]);
-      lo = fmin(lo, s_a[i] - r);
-      hi = fmax(hi, s_a[i] + r);
-      tn = fmax(tn, fabs(s_a[i]) + r);
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+      lo = fmin(lo, s_red[0][w]);
+      hi = fmax(hi, s_red[1][w]);
+      tn = fmax(tn, s_red[2][w]);
     }
     s_lo[0] = s_lo[1] = s_glo = lo;
     s_hi[0] = s_hi[1] = s_ghi = hi;
@@ -422,85 +491,106 @@ __device__ __forceinline__ void sp_eig_body(SpState* st, double rtol) {
     }
     __syncthreads();
   }
-  // (2) widen and check in FP64: count(lo) <= idx < count(hi)
+  // (2) widen by kSpEigMargin ||T|| and check with two double-float counts:
+  // count(lo) <= idx < count(hi)
+  const double mg = kSpEigMargin * s_tn;
+  const double wlo = fmax(s_glo, s_lo[grp] - mg), whi = fmin(s_ghi, s_hi[grp] + mg);
+  if (t < 2) s_cnt[grp][t] = sturm_count_df(s_ah, s_al, s_qh, s_ql, m, df_from_double(t == 0 ? wlo : whi));
+  __syncthreads();
   if (t == 0) {
-    const double mg = kSpEigMargin * s_tn;
-    const double lo = fmax(s_glo, s_lo[grp] - mg), hi = fmin(s_ghi, s_hi[grp] + mg);
-    const bool ok = hi > lo && sturm_count_poly(s_a, s_b2, m, lo) <= idx && sturm_count_poly(s_a, s_b2, m, hi) > idx;
+    const bool ok = whi > wlo && s_cnt[grp][0] <= idx && s_cnt[grp][1] > idx;
     s_ok[grp] = ok ? 1 : 0;
-    s_lo[grp] = ok ? lo : s_glo;
-    s_hi[grp] = ok ? hi : s_ghi;
+    s_lo[grp] = ok ? wlo : s_glo;
+    s_hi[grp] = ok ? whi : s_ghi;
   }
   __syncthreads();
-  // (3) FP64 multisection: narrow on few threads, or the full one from the
-  // Gershgorin interval where the check failed (both loops are uniform over
-  // the block: the barriers inside them are reached by every thread)
-  const bool fine = s_ok[0] && s_ok[1];
-  const int rounds = fine ? kSpEigFine : kSpEigRounds;
+  // (3) multisection to the end: double-float counts from the checked
+  // bracket, or FP64 counts from the Gershgorin interval where the check
+  // failed (the loop is uniform over the block: every thread reaches its
+  // barriers)
+  const int rounds = (s_ok[0] && s_ok[1]) ? kSpEigFine : kSpEigRounds;
   for (int round = 0; round < rounds; ++round) {
     const bool nar = s_ok[grp] != 0;
-    const int pts = nar ? kSpEigFineT : kSpEigT;
-    const bool act = fine ? true : !nar;  // a group already checked waits while the other runs the full search
+    const bool act = nar ? round < kSpEigFine : true;
     const double lo = s_lo[grp], w = s_hi[grp] - lo;
-    if (act && t < pts) s_cnt[grp][t] = sturm_count_poly(s_a, s_b2, m, lo + w * (double)(t + 1) / (double)(pts + 1));
+    const double x = lo + w * (double)(t + 1) / (double)(kSpEigT + 1);
+    if (act) s_cnt[grp][t] = nar ? sturm_count_df(s_ah, s_al, s_qh, s_ql, m, df_from_double(x))
+                                 : sturm_count_poly(s_a, s_b2, m, x);
     __syncthreads();
     if (act && t == 0) {
       int k = 0;
-      while (k < pts && s_cnt[grp][k] <= idx) ++k;
-      s_lo[grp] = lo + w * (double)k / (double)(pts + 1);
-      s_hi[grp] = lo + w * (double)(k + 1) / (double)(pts + 1);
+      while (k < kSpEigT && s_cnt[grp][k] <= idx) ++k;
+      s_lo[grp] = lo + w * (double)k / (double)(kSpEigT + 1);
+      s_hi[grp] = lo + w * (double)(k + 1) / (double)(kSpEigT + 1);
     }
     __syncthreads();
   }
-  if (!fine) {  // the checked group (if any) finishes its narrow search now
-    for (int round = 0; round < kSpEigFine; ++round) {
-      const bool act = s_ok[grp] != 0;
-      const double lo = s_lo[grp], w = s_hi[grp] - lo;
-      if (act && t < kSpEigFineT)
-        s_cnt[grp][t] = sturm_count_poly(s_a, s_b2, m, lo + w * (double)(t + 1) / (double)(kSpEigFineT + 1));
-      __syncthreads();
-      if (act && t == 0) {
-        int k = 0;
-        while (k < kSpEigFineT && s_cnt[grp][k] <= idx) ++k;
-        s_lo[grp] = lo + w * (double)k / (double)(kSpEigFineT + 1);
-        s_hi[grp] = lo + w * (double)(k + 1) / (double)(kSpEigFineT + 1);
+  const double th1 = 0.5 * (s_lo[0] + s_hi[0]);
+  const double th2 = 0.5 * (s_lo[1] + s_hi[1]);
+  // (4) top eigenvector: two steps of inverse iteration on T_m - sigma I,
+  // sigma just above theta_1 (Thomas algorithm in double-float, tiny pivots
+  // replaced, rescaled by a power of two after each step), then the FP64
+  // norm by a block reduction
+  if (tid == 0) {
+    const double tn = s_tn;
+    const df sig = df_from_double(th1 + 1e-13 * (tn + 1e-300));
+    const float tiny = fmaxf(1e-30f, (float)(1e-15 * tn));
+    for (int i = 0; i < m; ++i) {
+      s_yh[i] = 1.f + 0.01f * (float)(i % 7);
+      s_yl[i] = 0.f;
+    }
+    for (int it = 0; it < 2; ++it) {
+      df cprev{0.f, 0.f}, yprev{0.f, 0.f}, bprev{0.f, 0.f};
+      for (int i = 0; i < m; ++i) {
+        df piv = df_sub(df{s_ah[i], s_al[i]}, sig);
+        if (i > 0) piv = df_sub(piv, df_mul(bprev, cprev));
+        if (fabsf(piv.hi) < tiny) piv = df{tiny, 0.f};
+        const df rp = df_rcp(piv);
+        const df bi{s_bh[i], s_bl[i]};
+        cprev = df_mul(bi, rp);
+        df yi{s_yh[i], s_yl[i]};
+        if (i > 0) yi = df_sub(yi, df_mul(bprev, yprev));
+        yprev = df_mul(yi, rp);
+        s_ch[i] = cprev.hi;
+        s_cl[i] = cprev.lo;
+        s_yh[i] = yprev.hi;
+        s_yl[i] = yprev.lo;
+        bprev = bi;
       }
-      __syncthreads();
+      df ynext{s_yh[m - 1], s_yl[m - 1]};
+      float mx = fabsf(ynext.hi);
+      for (int i = m - 2; i >= 0; --i) {
+        ynext = df_sub(df{s_yh[i], s_yl[i]}, df_mul(df{s_ch[i], s_cl[i]}, ynext));
+        s_yh[i] = ynext.hi;
+        s_yl[i] = ynext.lo;
+        mx = fmaxf(mx, fabsf(ynext.hi));
+      }
+      int ex = 0;
+      frexpf(mx, &ex);
+      const float sc = ldexpf(1.f, -ex);  // exact: the largest entry into [0.5, 1)
+      for (int i = 0; i < m; ++i) {
+        s_yh[i] *= sc;
+        s_yl[i] *= sc;
+      }
     }
   }
-  if (threadIdx.x == 0) {
-    const double th1 = 0.5 * (s_lo[0] + s_hi[0]);
-    const double th2 = 0.5 * (s_lo[1] + s_hi[1]);
-    // inverse iteration on T_m - sigma I (Thomas algorithm, tiny pivots
-    // replaced), sigma just above theta_1
-    const double tn = s_tn;
-    const double sigma = th1 + 1e-13 * (tn + 1e-300);
-    const double tiny = 1e-300 + 1e-15 * tn;
-    double* y = s_y;
-    double* cp = s_cp;
-    for (int i = 0; i < m; ++i) y[i] = 1.0 + 0.01 * (double)(i % 7);
-    for (int it = 0; it < 2; ++it) {
-      // forward sweep: T - sigma I = L U, solve in place (one division a row)
-      double piv = s_a[0] - sigma;
-      if (fabs(piv) < tiny) piv = tiny;
-      double rp = 1.0 / piv;
-      cp[0] = s_b[0] * rp;
-      y[0] = y[0] * rp;
-      for (int i = 1; i < m; ++i) {
-        const double bl = s_b[i - 1];
-        piv = (s_a[i] - sigma) - bl * cp[i - 1];
-        if (fabs(piv) < tiny) piv = tiny;
-        rp = 1.0 / piv;
-        cp[i] = s_b[i] * rp;
-        y[i] = (y[i] - bl * y[i - 1]) * rp;
-      }
-      for (int i = m - 2; i >= 0; --i) y[i] -= cp[i] * y[i + 1];
-      double nn = 0.0;
-      for (int i = 0; i < m; ++i) nn += y[i] * y[i];
-      const double sc = 1.0 / sqrt(nn);
-      for (int i = 0; i < m; ++i) y[i] *= sc;
-    }
-    const double r = fabs(st->beta[m - 1] * y[m - 1]);
+  __syncthreads();
+  const double yv = (tid < m) ? (double)s_yh[tid] + (double)s_yl[tid] : 0.0;
+  double nn = yv * yv;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, off);
+  if (lane == 0) s_red[0][warp] = nn;
+  __syncthreads();
+  if (tid == 0) {
+    double t2 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t2 += s_red[0][w];
+    s_nn = t2;
+  }
+  __syncthreads();
+  const double inv = 1.0 / sqrt(s_nn);
+  if (tid < m) st->y[tid] = yv * inv;
+  if (tid == m - 1) {
+    const double r = fabs(st->beta[m - 1] * yv * inv);
     const double gap = th1 - th2;
     double bound = r;
     if (gap > 0.0) bound = fmin(r, r * r / gap);
@@ -512,8 +602,6 @@ __device__ __forceinline__ void sp_eig_body(SpState* st, double rtol) {
     st->out[4] = (double)m;
     if (bound <= rtol * fabs(th1)) st->stop = 1;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < m; i += blockDim.x) st->y[i] = s_y[i];
 }
 
 // Ritz vector u = V_m y into W[1] (the start of the next run), |u|^2 and
