@@ -174,3 +174,36 @@ def test_batch_workload_sampled_against_single_graph_path():
         assert relerr(Df[j, sl], Dref) <= 1e-8, (gi, j)
         assert relerr(W[j, sl], Wref) <= 1e-8, (gi, j)
     b.destroy()
+
+
+def test_batch_spectral_scales_with_more_graphs_than_search_threads():
+    """150 small graphs (more than the build runs searches for at a time, so
+    host threads take several graphs each and the mu searches join and leave
+    the shared rounds as they go): every lambda_max(A) and rho(Z_mu) against the
+    oracle's dense eigenvalues, and the build reports its shared rounds."""
+    from paper_2601_11338_gb300 import wl
+    rng = np.random.default_rng(17)
+    gs = []
+    for i in range(150):
+        kind = i % 3
+        if kind == 0:
+            gs.append(wlgen.erdos_renyi(int(rng.integers(20, 80)), 5.0, 100 + i))
+        elif kind == 1:
+            gs.append(wlgen.barabasi_albert(int(rng.integers(20, 80)), 2, 100 + i))
+        else:
+            gs.append(wlgen.grid2d(int(rng.integers(3, 9)), int(rng.integers(3, 9))))
+    mus = [1.0, 0.5, 0.0]
+    p = wl.make_params(f=wl.WL_F_RESOLVENT, alpha_rel=0.5, prec=wl.WL_FP64, tol=1e-12,
+                       stream=torch.cuda.current_stream().cuda_stream)
+    st = wl.wl_stats()
+    b = wl.wl_batch_build([(g.row_ptr.astype(np.int32), g.col_idx, g.n, g.nnz) for g in gs], mus, p, st)
+    assert st.status == wl.WL_OK and st.outer_iters > 0
+    for gi, g in enumerate(gs):
+        A = graph.dense_adjacency(g.row_ptr, g.col_idx, g.n)
+        lmax = spectral.lambda_max(A)
+        for j, mu in enumerate(mus):
+            info = wl.wl_batch_info(b, gi, j)
+            assert abs(info["lambda_max"] - lmax) <= 1e-9 * lmax, (gi, mu)
+            rho = spectral.rho_companion(A, mu) if mu > 0 else lmax
+            assert abs(info["rho"] - rho) <= 1e-8 * rho, (gi, mu)
+    b.destroy()
