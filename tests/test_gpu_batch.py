@@ -207,3 +207,28 @@ def test_batch_spectral_scales_with_more_graphs_than_search_threads():
             rho = spectral.rho_companion(A, mu) if mu > 0 else lmax
             assert abs(info["rho"] - rho) <= 1e-8 * rho, (gi, mu)
     b.destroy()
+
+
+def test_batch_invalid_graph_among_valid_ones_fails_without_hanging():
+    """One unsorted graph among 40 valid ones: its search thread fails at
+    validation and leaves while the others are in their shared rounds; the
+    build reports the error (in bounded time) and the next build works."""
+    import time
+    from paper_2601_11338_gb300 import wl
+    gs = [wlgen.erdos_renyi(200 + 7 * i, 6.0, 300 + i) for i in range(40)]
+    graphs = [(g.row_ptr.astype(np.int32), g.col_idx.copy(), g.n, g.nnz) for g in gs]
+    col = graphs[17][1]
+    col[0], col[1] = col[1], col[0]  # an unsorted row
+    p = wl.make_params(f=wl.WL_F_RESOLVENT, alpha_rel=0.5, prec=wl.WL_FP64, tol=1e-12,
+                       stream=torch.cuda.current_stream().cuda_stream)
+    t0 = time.perf_counter()
+    with pytest.raises(wl.WLError):
+        wl.wl_batch_build(graphs, [1.0, 0.5, 0.0], p)
+    assert time.perf_counter() - t0 < 60.0
+    good = [(g.row_ptr.astype(np.int32), g.col_idx, g.n, g.nnz) for g in gs[:5]]
+    b = wl.wl_batch_build(good, [1.0, 0.5, 0.0], p)
+    A = graph.dense_adjacency(gs[3].row_ptr, gs[3].col_idx, gs[3].n)
+    info = wl.wl_batch_info(b, 3, 0)
+    rho = spectral.rho_companion(A, 1.0)
+    assert abs(info["rho"] - rho) <= 1e-8 * rho
+    b.destroy()
