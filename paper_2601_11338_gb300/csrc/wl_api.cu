@@ -1619,7 +1619,11 @@ int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& inf
             ny += yt[i] * yt[i];
             dy += d * d;
           }
-          if (!(ny > 0.0) || yp.empty() || !(std::sqrt(dy) <= h->prm.outer_tol * std::sqrt(ny))) all = false;
+          // a column whose y vanishes (a zero start vector: the padding
+          // columns of a block) has converged once it stays zero, as in the
+          // polynomial run's rule
+          const bool ok = !yp.empty() && (ny > 0.0 ? std::sqrt(dy) <= h->prm.outer_tol * std::sqrt(ny) : dy == 0.0);
+          if (!ok) all = false;
           si_prev[(size_t)c * ntau + t].assign(yt, yt + m);
         }
       }

@@ -92,6 +92,26 @@ def test_si_return_probability_matches_alg1(prec, etol):
         assert abs(p[i] - exact[i]) <= 8 * e[i] + 1e-12, (ts[i], p[i], exact[i], e[i])
 
 
+def test_si_return_probability_with_a_padded_column_block():
+    """M = 7 test vectors run as a block of 8 columns, one of them zero: the
+    run stops by the rule (the zero column's y stays zero) instead of running
+    to its step cap, and the estimates match Alg. 1 with the oracle's Y."""
+    g = wlgen.erdos_renyi(500, 8, 51)
+    w = WL(g, variant="nbt", alpha_rel=0.5, prec="refined", tol=1e-12, outer_tol=1e-10, shift=0.5, max_outer=150)
+    L = oracle_L(g, 1.0, w.info["alpha"])
+    ts = [0.0, 0.3, 1.0, 2.5, 20.0]
+    M, seed = 7, 4243
+    p, e = w.return_prob(M, seed, ts)
+    steps, status = w.last.outer_iters, w.last.status
+    w.close()
+    assert status == 0 and steps < 150, (status, steps)
+    Om, _ = philox.gaussian_sketch(g.n, M, seed)
+    want = xnys.xnys_return_probability(L, Om, ts)
+    for i, (pe, ee) in enumerate(want):
+        assert abs(p[i] - pe) <= 1e-8 * abs(pe), (ts[i], p[i], pe)
+        assert abs(e[i] - ee) <= 1e-6 * ee + 1e-12, (ts[i], e[i], ee)
+
+
 def test_si_return_probability_on_a_cycle_closed_form():
     """C_n is 2-regular, so M = (a + alpha^2 mu 2) I - alpha A shares A's
     eigenvectors and L has eigenvalues g(2) - g(2 cos(2 pi j / n)) with
