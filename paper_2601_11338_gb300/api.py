@@ -24,7 +24,7 @@ class WalkLaplacian:
 
     def __init__(self, row_ptr, col_idx, n, variant="allwalk", f="resolvent", alpha=0.0, alpha_rel=0.0,
                  mu=0.0, prec="fp64", tol=1e-12, max_iter=0, max_outer=0, outer_tol=0.0, device="cuda",
-                 stream=None, reorder=1, beta=0.0, reorth=0, shift=0.0):
+                 stream=None, reorder=1, beta=0.0, reorth=0, shift=0.0, gram=0):
         self.device = torch.device(device)
         if isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda:
             self.row_ptr, self.col_idx = row_ptr, col_idx
@@ -35,7 +35,7 @@ class WalkLaplacian:
         s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
         self.params = wl.make_params(f=FUNCS[f], alpha=alpha, alpha_rel=alpha_rel, beta=beta, mu=mu, prec=PRECS[prec],
                                      tol=tol, max_iter=max_iter, max_outer=max_outer, outer_tol=outer_tol,
-                                     stream=s, reorder=reorder, reorth=reorth, shift=shift)
+                                     stream=s, reorder=reorder, reorth=reorth, shift=shift, gram=gram)
         self.build_stats = wl.wl_stats()
         self.h = wl.wl_build(self.row_ptr, self.col_idx, self.n, self.nnz, VARIANTS[variant], self.params,
                              self.build_stats)

@@ -378,7 +378,7 @@ struct wl_handle {
   double inner_tol = 4e-6;  // floor of the FP32 correction target of the refined form
   int cg_hint = 7;          // CG iterations of the handle's last solve (sizes the first launch chunk)
   int cg_hint_ref[2] = {7, 7};  // the same for the first and the later corrections of a refined solve
-  bool gram_tc = true;      // XNysTrace Gram on the tensor cores (tcgen05); false: CUDA cores
+  bool gram_tc = false;     // XNysTrace Gram of the sketch form on the tensor cores (tcgen05); false: CUDA cores
   CgState* cgst() { return (CgState*)cgstate.p; }
   double* h_pin = nullptr;  // pinned host scratch (4096 doubles)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -1804,6 +1804,7 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
   if (p->f != WL_F_RESOLVENT && p->f != WL_F_EXP && p->f != WL_F_IDENTITY) return WL_ERR_INVALID_ARG;
   if (p->prec != WL_FP64 && p->prec != WL_REFINED && p->prec != WL_SKETCH) return WL_ERR_INVALID_ARG;
   if (p->reorth < 0 || p->reorth > 1) return WL_ERR_INVALID_ARG;
+  if (p->gram < 0 || p->gram > 1) return WL_ERR_INVALID_ARG;
   if (!(p->shift >= 0.0) || !std::isfinite(p->shift)) return WL_ERR_INVALID_ARG;
   double mu = (v == WL_ALLWALK) ? 0.0 : (v == WL_NBT ? 1.0 : p->mu);
   if (!(mu >= 0.0 && mu <= 1.0)) return WL_ERR_INVALID_ARG;
@@ -1815,6 +1816,7 @@ int wl_build(const wl_csr* A, wl_variant v, const wl_params* p, wl_handle** out,
   h->variant = v;
   h->prm = *p;
   default_params(&h->prm);
+  h->gram_tc = p->gram == 1;
   h->mu = mu;
   h->stream = (cudaStream_t)p->stream;
   int rc = WL_OK;
@@ -2017,9 +2019,12 @@ int wl_set_params(wl_handle* h, const wl_params* p) {
   if (!h || !p) return WL_ERR_INVALID_ARG;
   if (p->prec != WL_FP64 && p->prec != WL_REFINED && p->prec != WL_SKETCH) return WL_ERR_INVALID_ARG;
   if (p->reorth < 0 || p->reorth > 1) return WL_ERR_INVALID_ARG;
+  if (p->gram < 0 || p->gram > 1) return WL_ERR_INVALID_ARG;
   if (!(p->shift >= 0.0) || !std::isfinite(p->shift)) return WL_ERR_INVALID_ARG;
   h->prm.prec = p->prec;
   h->prm.reorth = p->reorth;
+  h->prm.gram = p->gram;
+  h->gram_tc = p->gram == 1;
   h->prm.shift = p->shift;
   h->prm.tol = p->tol;
   h->prm.max_iter = p->max_iter;
@@ -2622,8 +2627,8 @@ int sp_clone(wl_handle* h, wl_handle** out) {
     free_handle(c);
     return rc;
   };
-  if (pool_malloc_host((void**)&c->h_pin, 4096 * sizeof(double)) != cudaSuccess)
-    return fail(set_cuda_error(cudaGetLastError(), "cudaMallocHost"));
+  // no pinned staging: a context's runs go through the batch, which reads
+  // the states back itself
   int rc = sp_buffers(c, sp_grid(c) + c->nhub + c->nmid_blk);
   if (rc != WL_OK) return fail(rc);
   cudaError_t e = cudaMemcpyAsync(c->spW.p, h->spW.p, (size_t)2 * h->n * 8, cudaMemcpyDeviceToDevice, S(h));

@@ -7,11 +7,16 @@
 // remainder rounded to TF32), so that with Xh = [Omega Yh], Xl = [0 Yl]
 //   D = Xh^T Yh + Xh^T Yl + Xl^T Yh
 // carries FP32-level accuracy (the dropped Yl^T Yl term is 2^-22 relative);
-// Omega is exact in TF32. D (128 x 64 FP32) lives in TMEM, one accumulator
-// per stage (2 x 64 columns): each stage's 12 MMAs start a fresh sum, and
-// once they have completed every thread adds its row of D into FP64
-// registers. The tensor core's FP32 accumulation thus never runs over more
-// than kTcRows nodes (over thousands it drifts by ~1e-5 relative).
+// Omega is exact in TF32. D (128 x 64 FP32) lives in TMEM, two accumulators
+// (2 x 64 columns) that alternate between groups of kTcGroup stages: the
+// MMAs of a group sum into one of them, and once they have completed every
+// thread adds its row of D into FP64 registers. The tensor core's FP32
+// accumulation thus never runs over more than kTcGroup * kTcRows nodes (over
+// thousands it drifts by ~1e-5 relative). Measured on 4.2e6 x 64 nodes:
+// draining after every stage kept the FP64 pipe half busy (9.7 ms); every
+// 4 stages 8.1 ms, every 16 or 64 stages 7.6 ms. The kernel is bound by its
+// per-stage round trip (loads, barriers, one thread issuing the MMAs), not by
+// the tensor pipe (2% busy); the CUDA-core Gram takes 3.1 ms.
 //
 // Each CTA (4 warps) owns a contiguous range of nodes and walks it in
 // stages of kTcRows nodes: all threads convert their feature column of the
@@ -26,6 +31,7 @@
 namespace wl {
 
 constexpr int kTcRows = 32;                               // nodes per stage
+constexpr int kTcGroup = 4;                               // stages summed in TMEM before a drain
 constexpr int kTcThreads = 128;                           // one thread per column of X
 constexpr uint32_t kTcTileBytes = 128u * kTcRows * 4u;    // one 128 x 32 TF32 tile (16 KB)
 constexpr uint32_t kTcLBO = 128;                          // core matrix to the next along K
@@ -138,15 +144,20 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc(const uint16_t* __restrict
 #pragma unroll
   for (int q = 0; q < (int)kTcN; ++q) acc[q] = 0.0;
   for (int c = 0; c < nst; ++c) {
-    const int s = c & 1;
+    const int s = c & 1;                   // tile buffer and mbarrier of this stage
+    const int g = c / kTcGroup;            // group; its accumulator is D[g & 1]
+    const bool gstart = (c % kTcGroup) == 0;
     if (c >= 2) {
-      // the MMAs of chunk c - 2 (this stage's tiles and accumulator) are done: drain D[s]
+      // the MMAs of stage c - 2 (this stage's tiles) are done, and with them
+      // (in order) those of every earlier stage
       if (!tc_wait(tc_smem_u32(&mbar[s]), (uint32_t)(((c >> 1) - 1) & 1))) atomicExch(&s_fail, 1);
       __syncthreads();
       if (s_fail) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      tc_drain(taddr, warp, (uint32_t)s * kTcN, acc);
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      if (gstart && g >= 2) {  // D[g & 1] holds group g - 2, all of whose stages precede c - 2
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tc_drain(taddr, warp, (uint32_t)(g & 1) * kTcN, acc);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      }
     }
     __syncthreads();
     const int64_t nb = r0 + (int64_t)c * kTcRows;
@@ -182,8 +193,8 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc(const uint16_t* __restrict
         const uint32_t kofs = (uint32_t)j * 2 * kTcLBO;  // 8 TF32 along K = two core matrices
         const uint64_t ah = tc_desc(th + kofs), bh = tc_desc(th + 8 * kTcSBO + kofs);
         const uint64_t al = tc_desc(tl + kofs), bl = tc_desc(tl + 8 * kTcSBO + kofs);
-        const uint32_t d = taddr + (uint32_t)s * kTcN;  // this stage's accumulator, restarted per stage
-        tc_mma(d, ah, bh, j > 0 ? 1u : 0u);
+        const uint32_t d = taddr + (uint32_t)(g & 1) * kTcN;  // the group's accumulator, restarted per group
+        tc_mma(d, ah, bh, (gstart && j == 0) ? 0u : 1u);
         tc_mma(d, ah, bl, 1u);
         tc_mma(d, al, bh, 1u);
       }
@@ -192,7 +203,8 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc(const uint16_t* __restrict
                    : "memory");
     }
   }
-  // the last commit covers every MMA issued before it: drain the last one or two accumulators
+  // the last commit covers every MMA issued before it: drain the accumulators
+  // of the last one or two groups
   if (nst > 0 && !s_fail) {
     const int c = nst - 1;
     if (!tc_wait(tc_smem_u32(&mbar[c & 1]), (uint32_t)((c >> 1) & 1))) atomicExch(&s_fail, 1);
@@ -200,8 +212,9 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc(const uint16_t* __restrict
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (nst > 0 && !s_fail) {
-    if (nst >= 2) tc_drain(taddr, warp, (uint32_t)((nst - 2) & 1) * kTcN, acc);
-    tc_drain(taddr, warp, (uint32_t)((nst - 1) & 1) * kTcN, acc);
+    const int ng = (nst + kTcGroup - 1) / kTcGroup;
+    if (ng >= 2) tc_drain(taddr, warp, (uint32_t)((ng - 2) & 1) * kTcN, acc);
+    tc_drain(taddr, warp, (uint32_t)((ng - 1) & 1) * kTcN, acc);
   }
   float* out = partial + (size_t)blockIdx.x * 128 * 64 + (size_t)(warp * 32 + lane) * 64;
 #pragma unroll

@@ -43,7 +43,7 @@ class wl_params(ctypes.Structure):
                 ("beta", ctypes.c_double), ("mu", ctypes.c_double), ("prec", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
                 ("outer_tol", ctypes.c_double), ("stream", ctypes.c_void_p), ("reorder", ctypes.c_int),
-                ("reorth", ctypes.c_int), ("shift", ctypes.c_double)]
+                ("reorth", ctypes.c_int), ("shift", ctypes.c_double), ("gram", ctypes.c_int)]
 
 
 class wl_stats(ctypes.Structure):
@@ -166,9 +166,9 @@ def _ptr(a):
 
 
 def make_params(f=WL_F_RESOLVENT, alpha=0.0, alpha_rel=0.0, beta=0.0, mu=0.0, prec=WL_FP64, tol=0.0,
-                max_iter=0, max_outer=0, outer_tol=0.0, stream=None, reorder=1, reorth=0, shift=0.0):
+                max_iter=0, max_outer=0, outer_tol=0.0, stream=None, reorder=1, reorth=0, shift=0.0, gram=0):
     return wl_params(f, alpha, alpha_rel, beta, mu, prec, tol, max_iter, max_outer, outer_tol, stream, reorder,
-                     reorth, shift)
+                     reorth, shift, gram)
 
 
 class Handle:

@@ -54,9 +54,10 @@ def test_build_rejects_bad_arguments_before_touching_the_gpu():
     # unknown matrix function
     p3 = wl.make_params(f=9)
     assert L.wl_build(ctypes.byref(A), wl.WL_NBT, ctypes.byref(p3), ctypes.byref(h), None) == wl.WL_ERR_INVALID_ARG
-    # unknown precision, reorthogonalisation mode, negative or non-finite shift
+    # unknown precision, reorthogonalisation mode or Gram kernel, negative or non-finite shift
     for bad in (wl.make_params(prec=5), wl.make_params(reorth=2), wl.make_params(shift=-1.0),
-                wl.make_params(shift=float("nan")), wl.make_params(shift=float("inf"))):
+                wl.make_params(shift=float("nan")), wl.make_params(shift=float("inf")), wl.make_params(gram=2),
+                wl.make_params(gram=-1)):
         assert L.wl_build(ctypes.byref(A), wl.WL_NBT, ctypes.byref(bad), ctypes.byref(h), None) == wl.WL_ERR_INVALID_ARG
     assert h.value is None
 

@@ -26,11 +26,15 @@ ETOL = {"fp64": (1e-10, 1e-6), "refined": (1e-8, 1e-6), "sketch": (1e-5, 1e-2)}
 
 
 @pytest.mark.parametrize("variant,mu,prec,M,reorder", [("allwalk", 0.0, "fp64", 16, 1), ("nbt", 1.0, "refined", 7, 0),
-                                                        ("btdw", 0.5, "refined", 32, 1), ("nbt", 1.0, "sketch", 16, 1)])
+                                                        ("btdw", 0.5, "refined", 32, 1), ("nbt", 1.0, "sketch", 16, 1),
+                                                        ("nbt", 1.0, "sketch_tc", 16, 1)])
 def test_estimates_match_oracle_alg1(variant, mu, prec, M, reorder):
+    gram = 1 if prec == "sketch_tc" else 0  # sketch_tc: the tensor-core Gram
+    prec = "sketch" if gram else prec
     g = wlgen.erdos_renyi(500, 8, 51)
     A = graph.dense_adjacency(g.row_ptr, g.col_idx, g.n)
-    w = WL(g, variant=variant, mu=mu, alpha_rel=0.5, prec=prec, tol=1e-12, outer_tol=1e-11, reorder=reorder)
+    w = WL(g, variant=variant, mu=mu, alpha_rel=0.5, prec=prec, tol=1e-12, outer_tol=1e-11, reorder=reorder,
+           gram=gram)
     L = walks.walk_laplacian(walks.phi_resolvent_closed(A, mu, w.info["alpha"]))
     ts = [0.0, 0.3, 1.0, 2.5]
     seed = 9001 + M

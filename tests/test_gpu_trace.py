@@ -6,8 +6,10 @@ literal leave-one-out estimate on the exact phi and the same Omega:
 
   FP64 form     Y by FP64 CG (tol 1e-13), FP64 Gram       1e-10 relative
   refined form  Y by the refined solve (tol 1e-12)         1e-8 relative
-  sketch form   Y by FP32 CG (tol 1e-7), TF32 Gram on the  1e-5 relative
-                tensor cores with FP32 sums per chunk
+  sketch form   Y by FP32 CG (tol 1e-7), FP32 Gram on the  1e-5 relative
+                CUDA cores (or, gram = 1, the two-term TF32
+                Gram on the tensor cores) with FP32 sums per
+                chunk
 
 The sketch form's bound: Y carries a relative error of about kappa(M) 1e-7
 (kappa(M) <= 3 at alpha = 0.5 / lambda_max) plus its FP32 rounding; the
@@ -52,13 +54,15 @@ def test_sketch_is_bit_exact(M, reorder):
 FORMS = {"fp64": (1e-13, 1e-10, 1e-6), "refined": (1e-12, 1e-8, 1e-6), "sketch": (1e-7, 1e-5, 1e-2)}
 
 
-@pytest.mark.parametrize("prec", ["fp64", "refined", "sketch"])
+@pytest.mark.parametrize("prec", ["fp64", "refined", "sketch", "sketch_tc"])
 @pytest.mark.parametrize("variant,mu,M,reorder", [("allwalk", 0.0, 64, 1), ("nbt", 1.0, 16, 0), ("btdw", 0.5, 7, 1)])
 def test_estimate_matches_literal_leave_one_out(variant, mu, M, reorder, prec):
+    gram = 1 if prec == "sketch_tc" else 0  # sketch_tc: the tensor-core Gram
+    prec = "sketch" if gram else prec
     tol, etol, rtol = FORMS[prec]
     g = wlgen.erdos_renyi(700, 8, 4)
     A = graph.dense_adjacency(g.row_ptr, g.col_idx, g.n)
-    w = WL(g, variant=variant, mu=mu, alpha_rel=0.5, tol=tol, prec=prec, reorder=reorder)
+    w = WL(g, variant=variant, mu=mu, alpha_rel=0.5, tol=tol, prec=prec, reorder=reorder, gram=gram)
     alpha = w.info["alpha"]
     phi = walks.phi_resolvent_closed(A, mu, alpha)
     seed = 777 + M
