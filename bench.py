@@ -811,7 +811,7 @@ def leg_trace(args, scale=22, steps=3, warmup=1):
     """XNysTrace of the all-walk resolvent (I - alpha A)^{-1}, alpha = 0.5 /
     lambda_max(A), on R-MAT scale 22 (a = .57, b = c = .19, edge factor 16):
     M = 64 Philox Gaussian BF16 test vectors. A step is one wl_trace in the
-    sketch form (FP32 block CG to 1e-7, TF32 Gram on the tensor cores, FP64
+    sketch form (FP32 block CG to 1e-7, FP32 Gram on the CUDA cores, FP64
     leave-one-out core). Time to 1e-8: the same estimate (same Omega) in the
     refined and the FP64 form (CG tol 3e-10), errors against the FP64 form
     at tol 1e-13. Error against the exact trace on the scale-14 instance
