@@ -71,7 +71,7 @@ cudaError_t launch_gram(const uint16_t* omega, const float* Y, int64_t n, int M,
     }
     gram_tc<<<G, kTcThreads, kTcSmem, s>>>(omega, Y, n, M, K, chunk, partial, err);
   } else {
-    gram_cc<<<G, 256, 0, s>>>(omega, Y, n, M, K, chunk, partial);
+    gram_cc<<<G, kGramThreads, 0, s>>>(omega, Y, n, M, K, chunk, partial);
   }
   gram_reduce<<<(2 * kMaxSketch * kMaxSketch + 255) / 256, 256, 0, s>>>(partial, G, out);
   return cudaGetLastError();

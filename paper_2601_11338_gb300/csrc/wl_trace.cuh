@@ -117,57 +117,79 @@ __global__ void to_f32(const double* X, int64_t total, float* Y) {
 }
 
 // ---------------------------------------------------------------- Gram on CUDA cores
-// Grid of G CTAs, CTA g sums rows [g * chunk, min(n, (g+1) * chunk)).
-// Thread t owns output pairs (r, c) for r in {rt, rt + 16, ...} x c in {ct, ct + 16, ...}
-// of the 2M x M block [Omega Y]^T Y, with M <= 64: 8 x 4 = 32 outputs per thread.
-constexpr int kGramRows = 32;  // rows staged per tile
+// Grid of G CTAs of kGramThreads, CTA g sums rows [g * chunk, min(n, (g+1) *
+// chunk)) of the 2M x M block [Omega Y]^T Y (M <= 64). Thread (tr, tc) =
+// (t / 8, t % 8) owns the 8 x 8 outputs of X columns 8 tr .. 8 tr + 7 (X =
+// [Omega Y], 128 columns) and Y columns 8 tc .. 8 tc + 7: per staged row it
+// reads two float4 of X and two of Y from shared memory for 64 FMAs. Tiles
+// of kGramRows rows alternate between two buffers; the next tile's loads are
+// issued into registers before the current tile's products.
+constexpr int kGramRows = 32;     // rows staged per tile
+constexpr int kGramThreads = 128;
+constexpr int kGramLoads = kGramRows * kMaxSketch / kGramThreads;  // elements of Omega (and of Y) per thread and tile
 
-__global__ void __launch_bounds__(256) gram_cc(const uint16_t* omega, const float* Y, int64_t n, int M, int K,
-                                               int64_t chunk, float* partial /* G x 2M x M */) {
-  __shared__ float sX[kGramRows][2 * kMaxSketch];  // [Omega_i, Y_i]
-  __shared__ float sY[kGramRows][kMaxSketch];
+__global__ void __launch_bounds__(kGramThreads) gram_cc(const uint16_t* omega, const float* Y, int64_t n, int M,
+                                                        int K, int64_t chunk, float* partial /* G x 2M x M */) {
+  __shared__ __align__(16) float sX[2][kGramRows][2 * kMaxSketch];  // [Omega_i, Y_i]
   const int tid = threadIdx.x;
-  const int rt = tid / 16, ct = tid % 16;  // 16 x 16 thread grid
+  const int tr = tid >> 3, tc = tid & 7;
   const int64_t r0 = (int64_t)blockIdx.x * chunk;
   const int64_t r1 = min(n, r0 + chunk);
-  float acc[8][4];
+  float acc[8][8];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  float po[kGramLoads], py[kGramLoads];  // the next tile, in flight
+  auto fetch = [&](int64_t base) {
+#pragma unroll
+    for (int u = 0; u < kGramLoads; ++u) {
+      const int e = tid + u * kGramThreads, i = e / kMaxSketch, j = e % kMaxSketch;
+      const int64_t r = base + i;
+      float om = 0.f, y = 0.f;
+      if (r < r1 && j < M) {
+        om = bf16_to_f32(omega[r * M + j]);
+        y = Y[r * K + j];
+      }
+      po[u] = om;
+      py[u] = y;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < kGramLoads; ++u) {
+      const int e = tid + u * kGramThreads, i = e / kMaxSketch, j = e % kMaxSketch;
+      sX[buf][i][j] = po[u];
+      sX[buf][i][kMaxSketch + j] = py[u];
+    }
+  };
+  if (r0 < r1) fetch(r0);
+  int buf = 0;
   for (int64_t base = r0; base < r1; base += kGramRows) {
     const int rows = (int)min((int64_t)kGramRows, r1 - base);
+    stash(buf);
     __syncthreads();
-    for (int e = tid; e < kGramRows * kMaxSketch; e += 256) {
-      const int i = e / kMaxSketch, j = e % kMaxSketch;
-      float om = 0.f, y = 0.f;
-      if (i < rows && j < M) {
-        om = bf16_to_f32(omega[(base + i) * M + j]);
-        y = Y[(base + i) * K + j];
-      }
-      sX[i][j] = om;
-      sX[i][kMaxSketch + j] = y;
-      sY[i][j] = y;
-    }
-    __syncthreads();
+    if (base + kGramRows < r1) fetch(base + kGramRows);
     for (int i = 0; i < rows; ++i) {
-      float xv[8], yv[4];
-#pragma unroll
-      for (int a = 0; a < 8; ++a) xv[a] = sX[i][rt + 16 * a];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) yv[b] = sY[i][ct + 16 * b];
+      const float4 x0 = *reinterpret_cast<const float4*>(&sX[buf][i][8 * tr]);
+      const float4 x1 = *reinterpret_cast<const float4*>(&sX[buf][i][8 * tr + 4]);
+      const float4 y0 = *reinterpret_cast<const float4*>(&sX[buf][i][kMaxSketch + 8 * tc]);
+      const float4 y1 = *reinterpret_cast<const float4*>(&sX[buf][i][kMaxSketch + 8 * tc + 4]);
+      const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
       for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xv[a], yv[b], acc[a][b]);
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(xv[a], yv[b], acc[a][b]);
     }
+    buf ^= 1;  // the other buffer is written next: no barrier needed before it
   }
   // rows of the 2M block: index rr in [0, 128): rr < 64 -> Omega column rr, else Y column rr - 64
   float* out = partial + (size_t)blockIdx.x * (2 * kMaxSketch) * kMaxSketch;
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) out[(rt + 16 * a) * kMaxSketch + (ct + 16 * b)] = acc[a][b];
+    for (int b = 0; b < 8; ++b) out[(8 * tr + a) * kMaxSketch + (8 * tc + b)] = acc[a][b];
 }
 
 // out[r * 64 + c] = sum_g partial[g][r][c] in FP64, fixed order
