@@ -16,7 +16,7 @@
 // draining after every stage kept the FP64 pipe half busy (9.7 ms); every
 // 4 stages 8.1 ms, every 16 or 64 stages 7.6 ms. The kernel is bound by its
 // per-stage round trip (loads, barriers, one thread issuing the MMAs), not by
-// the tensor pipe (2% busy); the CUDA-core Gram takes 3.1 ms.
+// the tensor pipe (2% busy); the CUDA-core Gram takes 1.9 ms.
 //
 // Each CTA (4 warps) owns a contiguous range of nodes and walks it in
 // stages of kTcRows nodes: all threads convert their feature column of the
