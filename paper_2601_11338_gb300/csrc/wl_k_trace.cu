@@ -61,8 +61,13 @@ int gram_grid(int64_t n) {
 
 cudaError_t launch_gram(const uint16_t* omega, const float* Y, int64_t n, int M, int K, float* partial, int G,
                         double* out, bool tensor_cores, int* err, cudaStream_t s) {
-  const int64_t chunk = (n + G - 1) / G;
+  int64_t chunk = (n + G - 1) / G;
+  // the tensor-core kernel's bulk copies need 16-byte aligned rows of Omega
+  // and Y (stage offsets are then multiples of 16 bytes)
+  if (tensor_cores && ((reinterpret_cast<uintptr_t>(omega) | reinterpret_cast<uintptr_t>(Y)) & 15u) != 0)
+    tensor_cores = false;
   if (tensor_cores) {
+    chunk = (chunk + kTcRows - 1) / kTcRows * kTcRows;  // each CTA's range starts at a stage boundary
     static bool attr = false;
     if (!attr) {
       cudaError_t e = cudaFuncSetAttribute(gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
