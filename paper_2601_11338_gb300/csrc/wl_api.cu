@@ -547,7 +547,11 @@ int run_cg(wl_handle* h, int K, const PhaseArgs<T>& a_in, int grid_s, int grid_u
   const int pc = prof_begin(h, kCatCG);
   counted(h, 1);
   WL_CU(launch(0, 0));
-  int* hp = (int*)h->h_pin;
+  // the whole CG state comes back after every chunk: the check of the last
+  // chunk also carries the per-column results (the deferred x update launched
+  // after it changes none of them), so the solve ends without another wait
+  CgState* hs = reinterpret_cast<CgState*>(h->h_pin);
+  static_assert(sizeof(CgState) <= 4096 * sizeof(double), "pinned staging holds the CG state");
   // first chunk: one more iteration than the handle's previous solve took (a
   // launch that finds the solve finished returns at once, but still costs a
   // grid); later chunks of kChunkMore iterations
@@ -555,29 +559,22 @@ int run_cg(wl_handle* h, int K, const PhaseArgs<T>& a_in, int grid_s, int grid_u
   for (;;) {
     counted(h, 2 * chunk);
     WL_CU(launch(1, chunk));
-    WL_CU(cudaMemcpyAsync(hp, &h->cgst()->active, 2 * sizeof(int), cudaMemcpyDeviceToHost, S(h)));
+    WL_CU(cudaMemcpyAsync(hs, h->cgst(), sizeof(CgState), cudaMemcpyDeviceToHost, S(h)));
     WL_CU(cudaStreamSynchronize(S(h)));
-    if (!hp[0]) break;
+    if (!hs->active) break;
     chunk = kChunkMore;
   }
   counted(h, 1);
   WL_CU(launch(2, 0));
   prof_end(h, pc);
   // per-column results
-  CgState* st = h->cgst();
-  double* hd = h->h_pin;
-  WL_CU(cudaMemcpyAsync(hd, st->gamma, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
-  WL_CU(cudaMemcpyAsync(hd + 64, st->b2, 64 * 8, cudaMemcpyDeviceToHost, S(h)));
-  WL_CU(cudaMemcpyAsync(hd + 128, st->status, 64 * 4, cudaMemcpyDeviceToHost, S(h)));
-  WL_CU(cudaMemcpyAsync(hd + 160, &st->iters, 4, cudaMemcpyDeviceToHost, S(h)));
-  WL_CU(cudaMemcpyAsync(hd + 192, st->done, 64 * 4, cudaMemcpyDeviceToHost, S(h)));
-  WL_CU(cudaStreamSynchronize(S(h)));
-  const int it = *(const int*)(hd + 160);
+  const int it = hs->iters;
   h->cg_hint = it;
-  int* cs = (int*)(hd + 128);
-  const int* dn = (const int*)(hd + 192);
-  for (int c = 0; c < K; ++c)  // iteration cap reached with this column still iterating
-    if (!dn[c] && cs[c] == 0) cs[c] = WL_ERR_NO_CONVERGENCE;
+  int cs[64];
+  for (int c = 0; c < K; ++c) {  // iteration cap reached with a column still iterating
+    cs[c] = hs->status[c];
+    if (!hs->done[c] && cs[c] == 0) cs[c] = WL_ERR_NO_CONVERGENCE;
+  }
   info.iters += it;
   info.cg_iters += it;
   info.nnz_rhs += (double)it * h->nnz * K;
@@ -585,7 +582,7 @@ int run_cg(wl_handle* h, int K, const PhaseArgs<T>& a_in, int grid_s, int grid_u
   info.last_rel = 0.0;
   for (int c = 0; c < K; ++c) {
     if (cs[c] != 0 && info.status == WL_OK) info.status = cs[c];
-    if (hd[64 + c] > 0) info.last_rel = std::max(info.last_rel, std::sqrt(hd[c] / hd[64 + c]));
+    if (hs->b2[c] > 0) info.last_rel = std::max(info.last_rel, std::sqrt(hs->gamma[c] / hs->b2[c]));
   }
   return WL_OK;
 }
@@ -688,31 +685,39 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
   const double inner0 = std::min(1e-3, std::max(h->inner_tol, kInner0C * std::sqrt(tol)));
   const int max_ref = 12;
   int ndf = 0;
+  int* dskip = (int*)((double*)h->small.p + 256);
   for (int ref = 0;; ++ref) {
-    WL_CU(cudaMemcpyAsync(hp, st->gamma, K * 8, cudaMemcpyDeviceToHost, S(h)));
-    WL_CU(cudaMemcpyAsync(hp + 64, bn2, K * 8, cudaMemcpyDeviceToHost, S(h)));
-    WL_CU(cudaStreamSynchronize(S(h)));
     info.refinements++;
-    bool all = true;
-    double mx = 0.0;
-    int skip[64];
-    for (int c = 0; c < K; ++c) {
-      const double rr = hp[c], bb = hp[64 + c];
-      if (!std::isfinite(rr)) info.status = WL_ERR_NONFINITE;
-      const double rel = bb > 0 ? std::sqrt(rr / bb) : 0.0;
-      mx = std::max(mx, rel);
-      skip[c] = (rel <= tol) ? 1 : 0;
-      if (!skip[c]) all = false;
-    }
-    info.max_rel = mx;
-    if (all || info.status == WL_ERR_NONFINITE) break;
-    if (ref >= max_ref) {
-      if (info.status == WL_OK) info.status = WL_ERR_NO_CONVERGENCE;
-      break;
+    double mx = 1.0;
+    if (ref == 0 && x_zero) {
+      // the residual is B itself: every column with B != 0 still needs its
+      // first correction (rel = 1), and the inner solve's start marks a zero
+      // column done by itself, so no host check (and no wait) is needed
+      WL_CU(cudaMemsetAsync(dskip, 0, K * sizeof(int), S(h)));
+    } else {
+      WL_CU(cudaMemcpyAsync(hp, st->gamma, K * 8, cudaMemcpyDeviceToHost, S(h)));
+      WL_CU(cudaMemcpyAsync(hp + 64, bn2, K * 8, cudaMemcpyDeviceToHost, S(h)));
+      WL_CU(cudaStreamSynchronize(S(h)));
+      bool all = true;
+      mx = 0.0;
+      int skip[64];
+      for (int c = 0; c < K; ++c) {
+        const double rr = hp[c], bb = hp[64 + c];
+        if (!std::isfinite(rr)) info.status = WL_ERR_NONFINITE;
+        const double rel = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+        mx = std::max(mx, rel);
+        skip[c] = (rel <= tol) ? 1 : 0;
+        if (!skip[c]) all = false;
+      }
+      info.max_rel = mx;
+      if (all || info.status == WL_ERR_NONFINITE) break;
+      if (ref >= max_ref) {
+        if (info.status == WL_OK) info.status = WL_ERR_NO_CONVERGENCE;
+        break;
+      }
+      WL_CU(cudaMemcpyAsync(dskip, skip, K * sizeof(int), cudaMemcpyHostToDevice, S(h)));
     }
     const double inner_tol = ref == 0 && x_zero ? inner0 : std::min(1e-3, std::max(h->inner_tol, 0.5 * tol / mx));
-    int* dskip = (int*)((double*)h->small.p + 256);
-    WL_CU(cudaMemcpyAsync(dskip, skip, K * sizeof(int), cudaMemcpyHostToDevice, S(h)));
     WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
     PhaseArgs<float> a{phase_graph_mid(h, grid_u), dcur, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
                        h->ca, h->cA, h->cD, nullptr, dskip, (double*)h->part.p, st, h->prm.max_iter,
