@@ -530,7 +530,8 @@ constexpr int kChunkMore = 4;  // iterations of every chunk after the first
 // Runs the CG iterations of an initialised solve state to completion (or the
 // iteration cap), reading back one flag per chunk, then the final x update.
 template <typename T>
-int run_cg(wl_handle* h, int K, const PhaseArgs<T>& a_in, int grid_s, int grid_u, SolveInfo& info, int cat_bytes) {
+int run_cg(wl_handle* h, int K, const PhaseArgs<T>& a_in, int grid_s, int grid_u, SolveInfo& info, int cat_bytes,
+           bool init = true) {
   PhaseArgs<T> a = a_in;
   const int fault = fault_mode();
   if (fault == kFaultNoconv) a.max_iter = 1;
@@ -545,8 +546,10 @@ int run_cg(wl_handle* h, int K, const PhaseArgs<T>& a_in, int grid_s, int grid_u
       return launch_cg_phases_f64(K, a, grid_s, grid_u, mode, chunk, S(h));
   };
   const int pc = prof_begin(h, kCatCG);
-  counted(h, 1);
-  WL_CU(launch(0, 0));
+  if (init) {  // else the caller has set the state from known residual norms
+    counted(h, 1);
+    WL_CU(launch(0, 0));
+  }
   // the whole CG state comes back after every chunk: the check of the last
   // chunk also carries the per-column results (the deferred x update launched
   // after it changes none of them), so the solve ends without another wait
@@ -718,7 +721,10 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
       WL_CU(cudaMemcpyAsync(dskip, skip, K * sizeof(int), cudaMemcpyHostToDevice, S(h)));
     }
     const double inner_tol = ref == 0 && x_zero ? inner0 : std::min(1e-3, std::max(h->inner_tol, 0.5 * tol / mx));
-    WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
+    // the inner solve starts from the residual norms in st->gamma (from the
+    // double-float residual, or B's norms): no pass over r32 to recompute them
+    counted(h);
+    WL_CU(launch_cg_state_restart(st, dskip, K, S(h)));
     PhaseArgs<float> a{phase_graph_mid(h, grid_u), dcur, (float*)h->r32.p, (float*)h->p.p, (float*)h->q.p,
                        h->ca, h->cA, h->cD, nullptr, dskip, (double*)h->part.p, st, h->prm.max_iter,
                        inner_tol * inner_tol};
@@ -728,7 +734,7 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
     // sizes its first launch chunk from the previous solve of its kind
     int& hint = h->cg_hint_ref[ref == 0 ? 0 : 1];
     h->cg_hint = hint;
-    WL_TRY(run_cg<float>(h, K, a, grid_s, grid_u, inner, 4));
+    WL_TRY(run_cg<float>(h, K, a, grid_s, grid_u, inner, 4, false));
     hint = h->cg_hint;
     if (inner.status == WL_ERR_NOT_SPD || inner.status == WL_ERR_NONFINITE) {
       info.status = inner.status;

@@ -91,6 +91,8 @@ cudaError_t launch_permute_vec(const double* in, int64_t n, const int32_t* perm,
 
 // ---- wl_k_cg64.cu / wl_k_cg32.cu: CG phase kernels
 // mode 0: init (gamma_0, flags); 1: `chunk` iterations (S, U pairs); 2: final x += alpha p
+// a solve's start from the residual norms already in st->gamma (no pass over r)
+cudaError_t launch_cg_state_restart(CgState* st, const int* skip, int K, cudaStream_t s);
 cudaError_t launch_cg_phases_f32(int K, const PhaseArgs<float>& a, int grid_s, int grid_u, int mode, int chunk,
                                  cudaStream_t s);
 cudaError_t launch_cg_phases_f64(int K, const PhaseArgs<double>& a, int grid_s, int grid_u, int mode, int chunk,

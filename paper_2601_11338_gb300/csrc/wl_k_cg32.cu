@@ -25,6 +25,39 @@ static cudaError_t run_cg32(const PhaseArgs<float>& a, int grid_s, int grid_u, i
   return cudaGetLastError();
 }
 
+// Start of a solve whose residual norms are already in st->gamma (written by
+// the double-float residual that produced r): the state the init phase would
+// set, without its pass over r. Column c is done when its norm is zero or not
+// finite, or skip[c] is set.
+__global__ void cg_state_restart(CgState* st, const int* skip, int K) {
+  const int c = threadIdx.x;
+  __shared__ int s_any;
+  if (c == 0) s_any = 0;
+  __syncthreads();
+  if (c < K) {
+    const double gn = st->gamma[c];
+    st->b2[c] = gn;
+    st->alpha[c] = 0.0;
+    st->beta[c] = 0.0;
+    int status = 0, done = !(gn > 0.0) || (skip && skip[c]);
+    if (!isfinite(gn)) { done = 1; status = WL_ERR_NONFINITE; }
+    st->status[c] = status;
+    st->done[c] = done;
+    if (!done) atomicOr(&s_any, 1);
+  }
+  __syncthreads();
+  if (c == 0) {
+    st->iters = 0;
+    st->ticket = 0;
+    st->active = s_any;
+  }
+}
+
+cudaError_t launch_cg_state_restart(CgState* st, const int* skip, int K, cudaStream_t s) {
+  cg_state_restart<<<1, 64, 0, s>>>(st, skip, K);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cg_phases_f32(int K, const PhaseArgs<float>& a, int grid_s, int grid_u, int mode, int chunk,
                                  cudaStream_t s) {
   switch (K) {
