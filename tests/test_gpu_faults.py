@@ -113,3 +113,27 @@ def test_injected_barrier_timeout(fault):
     fault("")
     w.close()
     assert _clean_solve_matches_oracle(g, A)
+
+
+def test_injected_allocation_failure_in_the_batched_build(fault):
+    """Every search thread of a batched build fails its first allocation: the
+    threads leave the shared rounds as they fail, the build reports
+    WL_ERR_OOM in bounded time, and a clean build afterwards is correct."""
+    from oracle import spectral
+    from paper_2601_11338_gb300 import wl
+    gs = [wlgen.erdos_renyi(200 + 11 * i, 6.0, 500 + i) for i in range(24)]
+    graphs = [(g.row_ptr.astype(np.int32), g.col_idx, g.n, g.nnz) for g in gs]
+    p = wl.make_params(f=wl.WL_F_RESOLVENT, alpha_rel=0.5, prec=wl.WL_FP64, tol=1e-12,
+                       stream=torch.cuda.current_stream().cuda_stream)
+    fault("alloc")
+    t0 = time.perf_counter()
+    with pytest.raises(wl.WLError) as e:
+        wl.wl_batch_build(graphs, [1.0, 0.5, 0.0], p)
+    assert e.value.status == wl.WL_ERR_OOM
+    assert time.perf_counter() - t0 < 30.0
+    fault("")
+    b = wl.wl_batch_build(graphs, [1.0, 0.5, 0.0], p)
+    A = graph.dense_adjacency(gs[5].row_ptr, gs[5].col_idx, gs[5].n)
+    rho = spectral.rho_companion(A, 1.0)
+    assert abs(wl.wl_batch_info(b, 5, 0)["rho"] - rho) <= 1e-8 * rho
+    b.destroy()
