@@ -1446,7 +1446,13 @@ int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& inf
   const int64_t n = h->n;
   const int ldT = kLdT;
   const int maxm = std::min(h->prm.max_outer, ldT - 1);
-  const int check = 4;
+  // steps between convergence checks: the shift-and-invert check is a host
+  // eigendecomposition of the small T_m (microseconds), so it runs every 2
+  // steps (every 4 overshot the headline diffusion by 2 steps; every step
+  // stops on a change between consecutive steps that underestimates the error
+  // and ended at 1e-8 instead of 1.3e-9); the polynomial check is a device
+  // series with a host read, every 4 steps
+  const int check = (h->prm.shift > 0.0) ? 2 : 4;
   // refined resolvent form: double-float outer recurrence (FP32 instructions only)
   const bool dfp = h->prm.prec != WL_FP64 && h->prm.f == WL_F_RESOLVENT;
   o = OuterRun{};
@@ -1631,10 +1637,11 @@ int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& inf
             ny += yt[i] * yt[i];
             dy += d * d;
           }
-          // a column whose y vanishes (a zero start vector: the padding
-          // columns of a block) has converged once it stays zero, as in the
-          // polynomial run's rule
-          const bool ok = !yp.empty() && (ny > 0.0 ? std::sqrt(dy) <= h->prm.outer_tol * std::sqrt(ny) : dy == 0.0);
+          // a zero start column (the padding of a block) has nothing to
+          // converge; in any other column a y that vanished is not converged
+          // (the space has not reached the slow modes yet)
+          const bool ok =
+              hdone[c] || (!yp.empty() && ny > 0.0 && std::sqrt(dy) <= h->prm.outer_tol * std::sqrt(ny));
           if (!ok) all = false;
           si_prev[(size_t)c * ntau + t].assign(yt, yt + m);
         }
