@@ -1500,8 +1500,9 @@ int outer_run(wl_handle* h, int K, const double* dtaus, int ntau, SolveInfo& inf
   int* mprev = done + 128;
   double* errd = (double*)h->errb.p;
   // V_0 = U0 block / |U0 block| (per column)
-  counted(h, 2);
-  cudaError_t e = launch_colnorms((const double*)h->packX.p, n, K, nrm, S(h));
+  counted(h, 3);
+  WL_TRY(ensure(h->part, (size_t)304 * 64 * 8 + 1024));
+  cudaError_t e = launch_colnorms((const double*)h->packX.p, n, K, nrm, (double*)h->part.p, S(h));
   if (e == cudaSuccess)
     e = dfp ? launch_df_scale_cols((const double*)h->packX.p, n, K, nrm, (float*)basis, (float*)basis + blk, S(h))
             : launch_scale_cols((const double*)h->packX.p, n, K, nrm, basis, S(h));

@@ -252,13 +252,17 @@ __global__ void __launch_bounds__(kBlock) df_combine(DfCombineArgs a) {
   }
 }
 
-// X (n x K FP64, contiguous) scaled per column by inv[c] -> (hi, lo)
+// X (n x K FP64, contiguous; K a power of two <= 64) scaled per column by
+// 1 / nrm[c] -> (hi, lo): one reciprocal per column and CTA, then a multiply
+// per element
 __global__ void __launch_bounds__(kBlock) df_scale_cols(const double* X, int64_t n, int K, const double* nrm,
                                                         float* hi, float* lo) {
+  __shared__ double inv[64];
+  if (threadIdx.x < K) inv[threadIdx.x] = nrm[threadIdx.x] > 0.0 ? 1.0 / nrm[threadIdx.x] : 0.0;
+  __syncthreads();
   const size_t total = (size_t)n * K;
   for (size_t e = (size_t)blockIdx.x * kBlock + threadIdx.x; e < total; e += (size_t)gridDim.x * kBlock) {
-    const double s = nrm[e % K];
-    const double x = s > 0.0 ? X[e] / s : 0.0;
+    const double x = X[e] * inv[e & (size_t)(K - 1)];
     const float h = (float)x;
     hi[e] = h;
     lo[e] = (float)(x - (double)h);

@@ -55,7 +55,8 @@ cudaError_t launch_apply_out(const double* V, int64_t ldv, const double* X, cons
 cudaError_t launch_fill(double* dst, double v, int64_t count, cudaStream_t s);
 cudaError_t launch_degree_vector(const Graph& g, double* out, cudaStream_t s);
 // out[c] = |X[:, c]|_2 (X contiguous n x K), deterministic
-cudaError_t launch_colnorms(const double* X, int64_t n, int K, double* out, cudaStream_t s);
+// column 2-norms of X (n x K, K a power of two <= 64); scratch: 304 x K doubles
+cudaError_t launch_colnorms(const double* X, int64_t n, int K, double* out, double* scratch, cudaStream_t s);
 // Y[:, c] = X[:, c] * inv[c]
 cudaError_t launch_scale_cols(const double* X, int64_t n, int K, const double* inv, double* Y, cudaStream_t s);
 cudaError_t launch_f2d_acc(const float* src, double* dst, int64_t count, cudaStream_t s);
