@@ -663,7 +663,6 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
   WL_CU(cudaMemsetAsync(dcur, 0, nk * 4, S(h)));
   WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
   if (x_zero) {
-    counted(h);
     WL_CU(cudaMemcpyAsync(h->r32.p, bh, nk * 4, cudaMemcpyDeviceToDevice, S(h)));
     WL_CU(cudaMemcpyAsync(st->gamma, bn2, K * 8, cudaMemcpyDeviceToDevice, S(h)));
   } else {
