@@ -688,6 +688,11 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
   const int max_ref = 12;
   int ndf = 0;
   int* dskip = (int*)((double*)h->small.p + 256);
+  // r32 (the next inner solve's right-hand side) and dcur (its zero start)
+  // are ready: the residual after the first correction writes them, later
+  // ones do not (the solve almost always ends there), and a further
+  // correction stages them itself
+  bool staged = true;
   for (int ref = 0;; ++ref) {
     info.refinements++;
     double mx = 1.0;
@@ -718,6 +723,11 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
         break;
       }
       WL_CU(cudaMemcpyAsync(dskip, skip, K * sizeof(int), cudaMemcpyHostToDevice, S(h)));
+      if (!staged) {
+        WL_CU(cudaMemcpyAsync(h->r32.p, rh, nk * 4, cudaMemcpyDeviceToDevice, S(h)));
+        WL_CU(cudaMemsetAsync(dcur, 0, nk * 4, S(h)));
+        staged = true;
+      }
     }
     const double inner_tol = ref == 0 && x_zero ? inner0 : std::min(1e-3, std::max(h->inner_tol, 0.5 * tol / mx));
     // the inner solve starts from the residual norms in st->gamma (from the
@@ -745,7 +755,9 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
     info.bytes += inner.bytes;
     // r <- r - M d, x <- x + d, next correction buffer zeroed
     WL_CU(cudaMemsetAsync(st, 0, sizeof(CgState), S(h)));
-    DfResArgs ra{phase_graph_mid(h, grid_r - h->nhub), dcur, nullptr, rch, rcl, rh, rl, (float*)h->r32.p, xh, xl, dnext,
+    const bool stage_next = (ref == 0);
+    DfResArgs ra{phase_graph_mid(h, grid_r - h->nhub), dcur, nullptr, rch, rcl, rh, rl,
+                 stage_next ? (float*)h->r32.p : nullptr, xh, xl, stage_next ? dnext : nullptr,
                  ca, cA, cD, (double*)h->part.p, st, x_zero ? 1 : 0};
     ra.dsh_h = h->si_dsh_h;
     ra.dsh_l = h->si_dsh_l;
@@ -756,6 +768,7 @@ int solve_refined_df(wl_handle* h, const float* bh, const float* bl, const doubl
     info.nnz_rhs += (double)h->nnz * K;
     ++ndf;
     x_zero = false;
+    staged = stage_next;
     rch = rh;
     rcl = rl;
     std::swap(dcur, dnext);
